@@ -1,0 +1,219 @@
+"""Oracle for the Toeplitz OLS (TOLS) problem of an AR(p) fit — TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference leg may import, call or run this
+module. The CUDA library never does, and this module imports nothing from it: the two share no code.
+
+Everything here is plain float64 NumPy/LAPACK on the CPU, written to be checked against the paper by eye.
+Notation (0-based, series y[0..n-1], order p, m = n - p rows):
+
+    X[i, j] = y[p + i - j - 1],   b[i] = y[p + i],   i in [0, m), j in [0, p)
+
+which is eq. (xphi) of Section 3 (1-based there: row 1 is (y_p ... y_1), response y_{p+1}).
+
+Functions and the passage each follows:
+  lag_matrix          eq. (xphi), Section 3 (the data matrix X_{n-p,p} and response y_{n-p,1}).
+  matvec / rmatvec    explicit products X v and X^T u with the matrix of eq. (xphi).
+  ols_qr              Def. "Ordinary Least Squares Problem" and Thm. "Solution to OLS problem" (Section 2):
+                      the minimiser of ||X phi - b||, unique when X^T X is nonsingular, else the minimum-norm
+                      one through the SVD. Computed by Householder QR (LAPACK dgeqrf through numpy) of the
+                      explicit [X | b]; for large m the rows are fed in blocks and each block is stacked under
+                      the previous triangle, because QR([R; X_2]) has the same R as QR([X_1; X_2]).
+  residual_check      the normal equation of Thm. "Solution to OLS problem": g = X^T (b - X phi) and the ratio
+                      ||g|| / (||X||_2 ||r||), with ||.|| the spectral norm as in the Notation paragraph
+                      (Section 1).
+  gram                X^T X and X^T b written out from eq. (xphi).
+  row_norms           ||X(i,:)||^2 and ||X||_F^2 (Section 1 notation: X(i,:) is the i-th row).
+  exact_leverage      Def. "Leverage Score" (Section 2.1.2): l(i) = e_i^T X (X^T X)^{-1} X^T e_i.
+  leverage_p1         the exact scores for p = 1 printed after eq. (FASD) (Section 3.1):
+                      l_{n,1}(i) = y_i^2 / sum_{t=1}^{n-1} y_t^2.
+  leverage_step       eqs. (FALS), (FAR), (FASD), Section 3.1: l_{n,p} = l_{n-1,p-1} + r^2/||r||^2 with
+                      r = X_{n-1,p-1} phi_hat - y_{n-1,p-1}, and pi = l / p.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+U64 = np.finfo(np.float64).eps / 2.0   # unit roundoff of float64
+
+
+def _series(y, p: int) -> np.ndarray:
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+    if y.ndim != 1:
+        raise ValueError("y must be one-dimensional")
+    if p < 1 or y.size <= p:
+        raise ValueError("need p >= 1 and n > p")
+    return y
+
+
+def lag_matrix(y, p: int, start: int = 0, stop: int | None = None):
+    """Rows [start, stop) of X and b, eq. (xphi): X[i, j] = y[p+i-j-1], b[i] = y[p+i]."""
+    y = _series(y, p)
+    m = y.size - p
+    stop = m if stop is None else min(stop, m)
+    rows = np.arange(start, stop)
+    cols = np.arange(p)
+    X = y[p + rows[:, None] - cols[None, :] - 1]
+    b = y[p + rows]
+    return X, b
+
+
+def matvec(y, p: int, v) -> np.ndarray:
+    """(X v)[i] = sum_j X[i, j] v[j] with the explicit X of eq. (xphi)."""
+    X, _ = lag_matrix(y, p)
+    return X @ np.asarray(v, dtype=np.float64)
+
+
+def rmatvec(y, p: int, u) -> np.ndarray:
+    """(X^T u)[j] = sum_i X[i, j] u[i] with the explicit X of eq. (xphi)."""
+    X, _ = lag_matrix(y, p)
+    return X.T @ np.asarray(u, dtype=np.float64)
+
+
+@dataclass
+class OracleSolution:
+    phi: np.ndarray          # the least-squares (or minimum-norm least-squares) coefficients
+    rnorm: float             # ||b - X phi||_2 recomputed explicitly from phi
+    R: np.ndarray            # p x p triangle of the QR of X
+    c: np.ndarray            # first p entries of Q^T b
+    sigma: np.ndarray        # singular values of R (= of X), descending
+    rank_deficient: bool
+    ne_ratio: float          # ||X^T r|| / (||X||_2 ||r||)
+    g: np.ndarray            # X^T r
+
+    @property
+    def norm2(self) -> float:
+        return float(self.sigma[0]) if self.sigma.size else 0.0
+
+    @property
+    def kappa(self) -> float:
+        return float(self.sigma[0] / self.sigma[-1]) if self.sigma[-1] > 0 else math.inf
+
+    @property
+    def eta(self) -> float:
+        nphi = float(np.linalg.norm(self.phi))
+        return self.rnorm / (self.norm2 * nphi) if nphi > 0 and self.norm2 > 0 else math.inf
+
+    def forward_error_bound(self) -> float:
+        """First-order relative forward-error bound 10 u (kappa + kappa^2 eta) of a backward-stable LS solve."""
+        k = self.kappa
+        return 10.0 * U64 * (k + k * k * self.eta)
+
+
+def _qr_triangle(y: np.ndarray, p: int, block_rows: int) -> np.ndarray:
+    """The (p+1) x (p+1) triangle of the Householder QR of [X | b], rows streamed in blocks."""
+    m = y.size - p
+    tri = np.zeros((0, p + 1))
+    for start in range(0, m, block_rows):
+        X, b = lag_matrix(y, p, start, start + block_rows)
+        stacked = np.vstack([tri, np.column_stack([X, b])])
+        tri = np.linalg.qr(stacked, mode="r")
+    if tri.shape[0] < p + 1:
+        tri = np.vstack([tri, np.zeros((p + 1 - tri.shape[0], p + 1))])
+    return tri
+
+
+def residual_check(y, p: int, phi, norm2: float | None = None, block_rows: int = 65536):
+    """r = b - X phi, g = X^T r, ||r|| and ||g|| / (||X||_2 ||r||), with explicit X in row blocks.
+
+    ||r||^2 is a compensated (math.fsum) total of per-block sums. norm2 = ||X||_2 when known; otherwise it is
+    taken from the singular values of the QR triangle.
+    """
+    y = _series(y, p)
+    phi = np.asarray(phi, dtype=np.float64)
+    m = y.size - p
+    g = np.zeros(p)
+    parts = []
+    for start in range(0, m, block_rows):
+        X, b = lag_matrix(y, p, start, start + block_rows)
+        r = b - X @ phi
+        parts.append(float(np.dot(r, r)))
+        g += X.T @ r
+    rnorm = math.sqrt(math.fsum(parts))
+    if norm2 is None:
+        tri = _qr_triangle(y, p, block_rows)
+        norm2 = float(np.linalg.svd(tri[:p, :p], compute_uv=False)[0])
+    ratio = float(np.linalg.norm(g)) / (norm2 * rnorm) if rnorm > 0 and norm2 > 0 else 0.0
+    return rnorm, g, ratio
+
+
+def ols_qr(y, p: int, block_rows: int = 65536, rank_tol: float | None = None) -> OracleSolution:
+    """argmin_phi ||X phi - b||_2 (minimum-norm when rank deficient), Thm. "Solution to OLS problem".
+
+    R phi = c by back substitution when R is numerically nonsingular
+    (sigma_min / sigma_max > rank_tol, default 1e-13 * p); otherwise phi = R^+ c from the SVD of R, which is
+    the minimum-norm solution because X^+ = R^+ Q^T when Q has orthonormal columns.
+    """
+    y = _series(y, p)
+    tri = _qr_triangle(y, p, block_rows)
+    R = tri[:p, :p]
+    c = tri[:p, p]
+    U, s, Vt = np.linalg.svd(R)
+    tol = (1e-13 * p) if rank_tol is None else rank_tol
+    deficient = not (s[0] > 0 and s[-1] > tol * s[0])
+    if not deficient:
+        phi = scipy.linalg.solve_triangular(R, c, lower=False)
+    else:
+        keep = s > (tol * s[0] if s[0] > 0 else 0.0)
+        phi = Vt[keep].T @ ((U[:, keep].T @ c) / s[keep])
+    rnorm, g, ratio = residual_check(y, p, phi, norm2=float(s[0]), block_rows=block_rows)
+    return OracleSolution(phi=phi, rnorm=rnorm, R=R, c=c, sigma=s, rank_deficient=deficient, ne_ratio=ratio, g=g)
+
+
+def gram(y, p: int, block_rows: int = 65536):
+    """G = X^T X (p x p) and h = X^T b (p), summed over row blocks of the explicit X."""
+    y = _series(y, p)
+    m = y.size - p
+    G = np.zeros((p, p))
+    h = np.zeros(p)
+    for start in range(0, m, block_rows):
+        X, b = lag_matrix(y, p, start, start + block_rows)
+        G += X.T @ X
+        h += X.T @ b
+    return G, h
+
+
+def row_norms(y, p: int):
+    """||X(i,:)||^2 for every row i, and ||X||_F^2 (compensated total)."""
+    X, _ = lag_matrix(y, p)
+    rn = np.sum(X * X, axis=1)
+    return rn, math.fsum(rn.tolist())
+
+
+def exact_leverage(y, p: int) -> np.ndarray:
+    """Def. "Leverage Score": l(i) = x_i^T (X^T X)^{-1} x_i, the diagonal of the hat matrix (small m only)."""
+    X, _ = lag_matrix(y, p)
+    Ginv = np.linalg.inv(X.T @ X)
+    return np.einsum("ij,jk,ik->i", X, Ginv, X)
+
+
+def leverage_p1(y) -> np.ndarray:
+    """l_{n,1}(i) = y_i^2 / sum_{t=1}^{n-1} y_t^2 for the n-1 rows of the AR(1) matrix (0-based: y[0..n-2])."""
+    y = np.asarray(y, dtype=np.float64)
+    head = y[:-1]
+    return head * head / math.fsum((head * head).tolist())
+
+
+def leverage_step(y, p: int, phi_hat, lev_prev):
+    """One step of eqs. (FALS)/(FAR)/(FASD) for order p >= 2.
+
+    The order-(p-1) problem lives on the first n-1 samples: X' = X_{n-1,p-1}, b' = y_{n-1,p-1}, both with
+    m = n - p rows. Its matrix satisfies X_{n,p} = [b' | X'] (the lag-1 column of the order-p matrix is the
+    order-(p-1) response), so with r = X' phi_hat - b':
+
+        l_new(i) = lev_prev(i) + r(i)^2 / ||r||^2,   pi(i) = l_new(i) / p.
+
+    Returns (l_new, pi, ||r||^2).
+    """
+    y = _series(y, p)
+    phi_hat = np.asarray(phi_hat, dtype=np.float64)
+    if phi_hat.size != p - 1:
+        raise ValueError("phi_hat must have p-1 entries")
+    Xp, bp = lag_matrix(y[:-1], p - 1)
+    r = Xp @ phi_hat - bp
+    s = math.fsum((r * r).tolist())
+    lev = np.asarray(lev_prev, dtype=np.float64) + r * r / s
+    return lev, lev / p, s

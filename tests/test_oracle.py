@@ -1,0 +1,270 @@
+"""Pins for the CPU oracle (no GPU): hand-written fixtures, exact rational solves, closed forms, invariants.
+
+Each test would fail under a plausible mistake in the oracle (a shifted lag, a transposed operand, a dropped
+term, a wrong sign); test_planted_mistakes_are_caught checks a few of those directly.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import tols
+from synthetic import ar_series, coefficients_from_inverse_roots, draw_inverse_roots, rng_for, simulate
+from tests.exact import normal_equations_exact, solve_spd_exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["xphi_n5_p2.json", "xphi_n7_p3.json"])
+def test_lag_matrix_matches_hand_written_xphi(name):
+    g = _golden(name)
+    X, b = oracle.lag_matrix(np.array(g["y"], float), g["p"])
+    assert X.tolist() == g["X"]
+    assert b.tolist() == g["b"]
+
+
+def _int_series(seed, n, lo=-9, hi=9):
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=n)
+
+
+def _rows_from_definition(y, p):
+    # independent index expression from the 1-based eq. (xphi): row i (1..n-p) = (y_{p+i-1}, ..., y_i)
+    n = len(y)
+    rows = [[int(y[(p + i - 1) - k - 1]) for k in range(p)] for i in range(1, n - p + 1)]
+    rhs = [int(y[p + i - 1]) for i in range(1, n - p + 1)]
+    return rows, rhs
+
+
+@pytest.mark.parametrize("seed,n,p", [(1, 30, 3), (2, 41, 5), (3, 25, 1), (4, 60, 7)])
+def test_oracle_equals_exact_rational_solution(seed, n, p):
+    y = _int_series(seed, n)
+    rows, rhs = _rows_from_definition(y, p)
+    G, h = normal_equations_exact(rows, rhs)
+    phi_exact = solve_spd_exact(G, h)
+    sol = oracle.ols_qr(y.astype(float), p)
+    ref = np.array([float(v) for v in phi_exact])
+    assert np.linalg.norm(sol.phi - ref) <= 1e-12 * np.linalg.norm(ref)
+    # residual norm against the exact rational residual
+    r2 = sum((Fraction(bb) - sum(Fraction(r[j]) * phi_exact[j] for j in range(p))) ** 2 for r, bb in zip(rows, rhs))
+    assert sol.rnorm == pytest.approx(math.sqrt(float(r2)), rel=1e-12)
+    assert not sol.rank_deficient
+
+
+def test_p1_closed_form():
+    # p = 1: phi = sum_i y_i y_{i+1} / sum_i y_i^2 over the n-1 rows (exact rationals)
+    y = _int_series(11, 200)
+    num = sum(Fraction(int(y[i])) * int(y[i + 1]) for i in range(len(y) - 1))
+    den = sum(Fraction(int(y[i])) ** 2 for i in range(len(y) - 1))
+    sol = oracle.ols_qr(y.astype(float), 1)
+    assert sol.phi[0] == pytest.approx(float(num / den), rel=1e-14)
+
+
+def test_noise_free_recursion_is_recovered_exactly():
+    # y_t = 1.5 y_{t-1} - 0.75 y_{t-2} + 0.125 y_{t-3}: dyadic coefficients and integer starts keep y exact
+    phi = np.array([1.5, -0.75, 0.125])
+    y = [3.0, -2.0, 5.0]
+    for _ in range(37):
+        y.append(phi[0] * y[-1] + phi[1] * y[-2] + phi[2] * y[-3])
+    sol = oracle.ols_qr(np.array(y), 3)
+    assert np.max(np.abs(sol.phi - phi)) < 1e-11
+    assert sol.rnorm < 1e-9 * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("p", [1, 3, 8])
+def test_constant_series_gives_min_norm(p):
+    # X = k * ones(m, p): every phi with sum(phi) = 1 fits exactly; the minimum-norm one is 1/p each
+    sol = oracle.ols_qr(np.full(50, 3.0), p)
+    assert sol.rank_deficient or p == 1
+    assert np.allclose(sol.phi, 1.0 / p, atol=1e-12)
+    assert sol.rnorm < 1e-12
+
+
+def test_periodic_series_min_norm_matches_svd_lstsq():
+    # period 3 with p = 6: rank 3; compare with LAPACK's SVD-based gelsd and check phi lies in the row space
+    y = np.tile([1.0, -2.0, 0.5], 30)
+    p = 6
+    sol = oracle.ols_qr(y, p)
+    X, b = oracle.lag_matrix(y, p)
+    ref = scipy.linalg.lstsq(X, b, lapack_driver="gelsd")[0]
+    assert sol.rank_deficient
+    assert np.allclose(sol.phi, ref, atol=1e-10)
+    _, s, Vt = np.linalg.svd(X)
+    null = Vt[s < 1e-10 * s[0]]
+    assert np.max(np.abs(null @ sol.phi)) < 1e-10
+
+
+def test_blocked_qr_equals_single_block():
+    s = ar_series(5000, 12, config_id=7)
+    a = oracle.ols_qr(s.y, 12)
+    b = oracle.ols_qr(s.y, 12, block_rows=333)
+    assert np.max(np.abs(a.phi - b.phi)) < 1e-13 * np.max(np.abs(a.phi)) * 100
+    assert a.rnorm == pytest.approx(b.rnorm, rel=1e-13)
+
+
+def test_products_reduce_to_convolution_and_correlation():
+    # (X v)[i] = sum_j y[p-1+i-j] v[j] is the 'valid' convolution of y[0..n-2] with v;
+    # (X^T u)[j] is the 'valid' correlation of y[0..n-2] with u, read backwards.
+    rng = np.random.default_rng(5)
+    for n, p in [(40, 1), (57, 6), (300, 31)]:
+        y = rng.standard_normal(n)
+        v = rng.standard_normal(p)
+        u = rng.standard_normal(n - p)
+        assert np.allclose(oracle.matvec(y, p, v), np.convolve(y[:-1], v, mode="valid"), rtol=1e-13, atol=1e-13)
+        assert np.allclose(oracle.rmatvec(y, p, u), np.correlate(y[:-1], u, mode="valid")[::-1], rtol=1e-12,
+                           atol=1e-12)
+        # adjoint identity <X v, u> = <v, X^T u>
+        assert np.dot(oracle.matvec(y, p, v), u) == pytest.approx(np.dot(v, oracle.rmatvec(y, p, u)), rel=1e-12)
+
+
+def test_normal_equation_invariant_and_loop_residual():
+    s = ar_series(3000, 5, config_id=8)
+    sol = oracle.ols_qr(s.y, 5)
+    assert sol.ne_ratio < 1e-12
+    # X^T r with plain loops, no matrix built
+    y, p = s.y, 5
+    g = [0.0] * p
+    for i in range(len(y) - p):
+        r = y[p + i] - sum(y[p + i - j - 1] * sol.phi[j] for j in range(p))
+        for j in range(p):
+            g[j] += y[p + i - j - 1] * r
+    assert np.allclose(g, sol.g, atol=1e-8)
+    assert np.linalg.norm(g) < 1e-9 * sol.norm2 * sol.rnorm
+
+
+def test_residual_check_detects_wrong_phi():
+    s = ar_series(2000, 4, config_id=9)
+    sol = oracle.ols_qr(s.y, 4)
+    bad = sol.phi.copy()
+    bad[2] += 1e-3
+    rn, _, ratio = oracle.residual_check(s.y, 4, bad, norm2=sol.norm2)
+    assert ratio > 1e-6 and rn > sol.rnorm
+
+
+def test_consistency_error_shrinks_like_inverse_sqrt_n():
+    errs = {}
+    for n in (2000, 20000, 200000):
+        e = []
+        for k in range(6):
+            s = ar_series(n, 4, config_id=10, series_index=k)
+            e.append(np.linalg.norm(oracle.ols_qr(s.y, 4).phi - s.phi_true))
+        errs[n] = float(np.mean(e))
+    slope = np.polyfit(np.log10(list(errs)), np.log10(list(errs.values())), 1)[0]
+    assert -0.8 < slope < -0.3, errs
+
+
+def test_gram_matches_exact_and_displacement_identity():
+    y = _int_series(21, 35)
+    p = 4
+    rows, rhs = _rows_from_definition(y, p)
+    Gx, hx = normal_equations_exact(rows, rhs)
+    G, h = oracle.gram(y.astype(float), p)
+    assert G.tolist() == [[float(v) for v in row] for row in Gx]
+    assert h.tolist() == [float(v) for v in hx]
+    # G[j+1,k+1] = G[j,k] + y[a-1] y[c-1] - y[a-1+m] y[c-1+m],  a = p-1-j, c = p-1-k, m = n-p
+    m = len(y) - p
+    for j in range(p - 1):
+        for k in range(p - 1):
+            a, c = p - 1 - j, p - 1 - k
+            assert G[j + 1, k + 1] == G[j, k] + y[a - 1] * y[c - 1] - y[a - 1 + m] * y[c - 1 + m]
+
+
+def test_row_norms_window_sum_and_trace():
+    y = _int_series(31, 80).astype(float)
+    p = 6
+    rn, fro2 = oracle.row_norms(y, p)
+    cs = np.concatenate([[0.0], np.cumsum(y * y)])
+    assert rn.tolist() == [cs[i + p] - cs[i] for i in range(len(y) - p)]
+    G, _ = oracle.gram(y, p)
+    assert fro2 == pytest.approx(np.trace(G), rel=1e-15)
+
+
+def test_leverage_p1_hand_written():
+    g = _golden("leverage_p1_n4.json")
+    lev = oracle.leverage_p1(np.array(g["y"], float))
+    assert np.allclose(lev, np.array(g["lev_num"], float) / g["lev_den"], rtol=1e-15)
+    # same thing from the general definition with p = 1
+    assert np.allclose(oracle.exact_leverage(np.array(g["y"], float), 1), lev, rtol=1e-14)
+
+
+def test_exact_leverage_properties():
+    s = ar_series(400, 5, config_id=12)
+    lev = oracle.exact_leverage(s.y, 5)
+    assert lev.min() >= 0 and lev.max() <= 1
+    assert lev.sum() == pytest.approx(5.0, rel=1e-12)
+    X, _ = oracle.lag_matrix(s.y, 5)
+    Q, _ = np.linalg.qr(X)
+    assert np.allclose(lev, np.sum(Q * Q, axis=1), atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 3, 6])
+def test_leverage_step_with_exact_phi_gives_exact_leverage(p):
+    # With phi_hat the exact OLS solution of the order-(p-1) problem, the update of eq. (FALS) is the exact
+    # rank-one update of the hat-matrix diagonal, so it reproduces Def. "Leverage Score" for order p.
+    s = ar_series(500, p, config_id=13)
+    y = s.y
+    prev = oracle.exact_leverage(y[:-1], p - 1)
+    phi_hat = oracle.ols_qr(y[:-1], p - 1).phi
+    lev, pi, _ = oracle.leverage_step(y, p, phi_hat, prev)
+    assert np.allclose(lev, oracle.exact_leverage(y, p), atol=1e-12)
+    assert pi.sum() == pytest.approx(1.0, rel=1e-12)
+
+
+def test_generator_roots_stationary_and_coefficients():
+    rng = rng_for(99, 0)
+    inv = draw_inverse_roots(rng, 9, 1.2, 3.0)
+    phi = coefficients_from_inverse_roots(inv)
+    roots = np.roots(np.r_[1.0, -phi][::-1])
+    assert np.min(np.abs(roots)) > 1.0
+    # product form equals expanded polynomial at a few points
+    for z in (0.3, -0.7 + 0.2j, 1.1j):
+        assert abs(np.prod(1 - inv * z) - (1 - np.sum(phi * z ** np.arange(1, 10)))) < 1e-12
+
+
+def test_generator_autocorrelation_matches_spectrum():
+    s = ar_series(200_000, 3, config_id=14)
+    y = s.y - 0.0
+    n = y.size
+    w = np.linspace(0, 2 * np.pi, 1 << 14, endpoint=False)
+    z = np.exp(1j * w)
+    S = 1.0 / np.abs(np.prod(1 - s.inv_roots[:, None] * z[None, :], axis=0)) ** 2
+    acov = np.real(np.fft.ifft(S))
+    rho_true = acov[:6] / acov[0]
+    rho_hat = np.array([np.dot(y[: n - h], y[h:]) / np.dot(y, y) for h in range(6)])
+    assert np.max(np.abs(rho_hat - rho_true)) < 3 / math.sqrt(n) * 3
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plant mistakes in the oracle (CPU only) and check the pins above notice them."""
+    g = _golden("xphi_n5_p2.json")
+    y = np.array(g["y"], float)
+    real_lag = tols.lag_matrix
+
+    def shifted(y_, p_, start=0, stop=None):          # off-by-one lag
+        X, b = real_lag(y_, p_, start, stop)
+        return np.roll(X, 1, axis=1), b
+
+    monkeypatch.setattr(tols, "lag_matrix", shifted)
+    X, _ = tols.lag_matrix(y, 2)
+    assert X.tolist() != g["X"]
+    yi = _int_series(1, 30)
+    rows, rhs = _rows_from_definition(yi, 3)
+    G, h = normal_equations_exact(rows, rhs)
+    ref = np.array([float(v) for v in solve_spd_exact(G, h)])
+    assert np.linalg.norm(tols.ols_qr(yi.astype(float), 3).phi - ref) > 1e-6
+    monkeypatch.setattr(tols, "lag_matrix", real_lag)
+
+    # transposed-product mistake: X^T u computed as a convolution instead of a correlation
+    rng = np.random.default_rng(0)
+    yy, v = rng.standard_normal(50), rng.standard_normal(45)
+    wrong = np.convolve(yy[:-1], v, mode="valid")
+    assert not np.allclose(wrong, oracle.rmatvec(yy, 5, v))

@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark: AR(p) Toeplitz-LSQR solves/s, FP64 and mixed precision, on one GB300 per rank.
+
+Workload (default): one stationary AR(100) series, n = 2^22, roots of modulus U[1.05, 2], Student-t(5)
+innovations scaled to unit variance, FP64 throughout, solved to a normal-equation ratio of 1e-10. A step is
+one complete solve (Gram pass, Cholesky preconditioner, LSQR passes, float64 check pass) of that series with
+the series already resident in HBM. The same series is also solved in mixed precision, and end to end from
+pinned host memory through the C ABI (toeplitz_ols_solve).
+
+Under torchrun every rank solves its own replica (weak scaling, no collective on the data path); value is the
+whole-job solves/s with the max time over ranks.
+
+--impl reference times the CPU oracle (float64 Householder QR, NumPy/LAPACK on the host cores) on a bounded
+sample of the same workload and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AR(p) Toeplitz-LSQR solves/s & matvec HBM GB/s, mixed vs FP64; p99 latency"
+WORKLOADS = {
+    "ar100_n4M": dict(n=1 << 22, p=100, root_lo=1.05, root_hi=2.0, noise="t5", tol=1e-10, config_id=2,
+                      desc="AR(100), n=2^22, roots |r| in U[1.05,2], Student-t(5) innovations, FP64, ne-ratio 1e-10"),
+    "ar100_n64M": dict(n=1 << 26, p=100, root_lo=1.05, root_hi=2.0, noise="normal", tol=1e-10, config_id=3,
+                       desc="AR(100), n=2^26, roots |r| in U[1.05,2], N(0,1) innovations (kernel profiling size)"),
+    "ar10_n10k": dict(n=10_000, p=10, root_lo=1.2, root_hi=3.0, noise="normal", tol=1e-12, config_id=1,
+                      desc="AR(10), n=10,000, roots |r| in U[1.2,3], N(0,1) innovations, FP64, ne-ratio 1e-12"),
+}
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA (4 flop)/clk/SM x 2.07 GHz max clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ar100_n4M")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the fused product pass (toeplitz_ols_gk_pass), float64 then float32")
+    ap.add_argument("--reps", type=int, default=5)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu_index)],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median([r[0] for r in rows]) if rows else None,
+                "sm_max_mhz": max(r[1] for r in rows) if rows else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(i.get("num_threads", 0) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def make_series(wl):
+    from synthetic import ar_series
+    return ar_series(wl["n"], wl["p"], config_id=wl["config_id"], root_lo=wl["root_lo"], root_hi=wl["root_hi"],
+                     noise=wl["noise"])
+
+
+# ---------------------------------------------------------------------------------------------------------
+def run_reference(args, wl):
+    """The oracle on the host cores, each step a bounded sample of the workload: the first rows of the series."""
+    world, rank, _ = dist()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    s = make_series(wl)
+    p = wl["p"]
+    m_full = wl["n"] - p
+    m_s = min(m_full, 1 << 19)
+    ys = s.y[: m_s + p]
+    for _ in range(args.warmup):
+        oracle.ols_qr(ys, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ols_qr(ys, p)
+    dt = (time.perf_counter() - t0) / args.steps
+    per_solve = dt * (m_full / m_s)      # dense QR cost is linear in the row count
+    value = 1.0 / per_solve
+    sample = f"oracle (blocked Householder QR, float64) on the first {m_s} of {m_full} rows per step; " \
+             f"solves/s scaled by {m_full / m_s:.3g}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": wl["n"], "p": p},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------------------
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    import paper_2112_12994_gb300 as tols
+
+    world, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as tdist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    s = make_series(wl)
+    n, p, tol = wl["n"], wl["p"], wl["tol"]
+    m = n - p
+    stream = torch.cuda.Stream(dev)
+    d_y = torch.tensor(s.y, dtype=torch.float64, device=dev)
+    d_phi = torch.empty(p, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed_solves(ctx, steps, host_y=None, phi_host=None):
+        times, infos = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)                       # evict y and the work vectors from L2 (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host_y is None:
+                _, info, rc = tols.toeplitz_ols_solve_device(ctx, d_y, n, p, d_phi, tol)
+            else:
+                phi, _, info, rc = tols.toeplitz_ols_solve(ctx, host_y, p, tol)
+                phi_host[:] = phi
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return times, infos
+
+    results = {}
+    for name, prec in (("fp64", tols.TOLS_FP64), ("mixed", tols.TOLS_MIXED)):
+        ctx = tols.Context(precision=prec, device=local, cuda_stream=stream.cuda_stream)
+        timed_solves(ctx, args.warmup)
+        tols.toeplitz_ols_profile(ctx, True)
+        clocks = ClockSampler(_smi_index(local)) if name == "fp64" else None
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        times, infos = timed_solves(ctx, args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        prof = {tols.PROFILE_CLASS_NAMES[k]: tols.toeplitz_ols_profile_read(ctx, k)
+                for k in range(tols.TOLS_PROFILE_CLASSES)}
+        launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
+        tols.toeplitz_ols_profile(ctx, False)
+        phi = d_phi.cpu().numpy().copy()
+        total_ms = max_over_ranks(sum(times))
+        results[name] = dict(times=times, infos=infos, prof=prof, launches=launches, phi=phi, total_ms=total_ms,
+                             clocks=clk, ctx=ctx)
+
+    # end to end: pinned host series in, phi out, through toeplitz_ols_solve (FP64, the headline precision)
+    pinned = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(s.y))
+    host_y = pinned.numpy()
+    phi_h = np.zeros(p)
+    ctx = results["fp64"]["ctx"]
+    timed_solves(ctx, 1, host_y, phi_h)
+    barrier()
+    torch.cuda.synchronize()
+    e2e_times, _ = timed_solves(ctx, args.steps, host_y, phi_h)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(sum(e2e_times))
+
+    hbm_peak, hbm_src = peaks()
+    r64, rmx = results["fp64"], results["mixed"]
+    K = args.steps
+    value = world * K / (r64["total_ms"] / 1e3)
+    mixed_value = world * K / (rmx["total_ms"] / 1e3)
+
+    def per_launch(prof, key):
+        cnt, ms = prof[key]
+        return (ms / cnt if cnt else float("nan")), cnt
+
+    # dominant kernel of the FP64 step and its roofline (float64 FMA units bound it; see the design notes)
+    dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0), key=lambda k: r64["prof"][k][1])
+    avg_ms, cnt = per_launch(r64["prof"], dom)
+    lags = p + 1 if dom.endswith("gram") else p
+    flops = (2.0 if dom.endswith("gram") else 4.0) * m * lags
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    byts_fp64 = 8.0 * n + 16.0 * m
+    roofline = {"bound": "alu", "kernel": f"pass_kernel<double> ({dom})", "achieved": achieved_tf,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt}
+    mx_dom = "pass_f32_lsqr" if rmx["prof"]["pass_f32_lsqr"][0] else "pass_f32_necorr"
+    mx_ms, mx_cnt = per_launch(rmx["prof"], mx_dom)
+    byts_mx = 4.0 * n + 8.0 * m
+    mx_gbs = byts_mx / (mx_ms * 1e-3) / 1e9 if mx_cnt else None
+    fp64_pass_ms, _ = per_launch(r64["prof"], "pass_f64_lsqr")
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": r64["total_ms"] / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic: seeded stationary AR series (see config)",
+           "config": {"workload": wl["desc"], "n": n, "p": p, "tol": tol, "series_per_rank": 1,
+                      "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, not timed)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "roofline": roofline,
+           "matvec": {"fp64_pass_ms": fp64_pass_ms,
+                      "fp64_pass_gbs": byts_fp64 / (fp64_pass_ms * 1e-3) / 1e9 if fp64_pass_ms == fp64_pass_ms else None,
+                      "mixed_pass_kernel": mx_dom, "mixed_pass_ms": mx_ms, "mixed_pass_gbs": mx_gbs,
+                      "mixed_pass_frac_hbm": (mx_gbs / hbm_peak) if mx_gbs else None,
+                      "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+                      "bytes_per_pass": {"fp64": byts_fp64, "mixed": byts_mx}},
+           "mixed": {"value": mixed_value, "unit": "solves/s", "ms_per_step": rmx["total_ms"] / K,
+                     "vs_fp64": mixed_value / value,
+                     "precision_used": rmx["infos"][-1]["precision_used"], "iters": rmx["infos"][-1]["iters"],
+                     "sweeps": rmx["infos"][-1]["sweeps"], "ne_ratio": rmx["infos"][-1]["ne_ratio"]},
+           "latency_ms": {"fp64_p50": float(np.percentile(r64["times"], 50)),
+                          "fp64_p99": float(np.percentile(r64["times"], 99)),
+                          "mixed_p50": float(np.percentile(rmx["times"], 50)),
+                          "mixed_p99": float(np.percentile(rmx["times"], 99))},
+           "solve": {"iters": r64["infos"][-1]["iters"], "sweeps": r64["infos"][-1]["sweeps"],
+                     "ne_ratio": r64["infos"][-1]["ne_ratio"], "cond_est": r64["infos"][-1]["cond_est"],
+                     "status": r64["infos"][-1]["status"]},
+           "e2e": {"value": world * K / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * p},
+           "gpu_launches": int(r64["launches"] + rmx["launches"]),
+           "clocks": r64["clocks"],
+           "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r64["prof"].items() if v[0]}}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.ols_qr(s.y, p)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": "one full solve of the same series (blocked Householder QR, float64)"}
+        out["accuracy"] = {"fp64_coef_rel_err": float(np.linalg.norm(r64["phi"] - ref.phi) / np.linalg.norm(ref.phi)),
+                           "mixed_coef_rel_err": float(np.linalg.norm(rmx["phi"] - ref.phi) / np.linalg.norm(ref.phi)),
+                           "oracle_kappa": ref.kappa, "oracle_forward_bound": ref.forward_error_bound(),
+                           "oracle_ne_ratio": ref.ne_ratio}
+    for r in results.values():
+        r["ctx"].close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def run_kernel_only(args, wl):
+    """The fused pass u_new = X v - c u_old, ||u_new||^2, X^T u_new alone, in both precisions."""
+    import numpy as np
+    import torch
+
+    import paper_2112_12994_gb300 as tols
+    s = make_series(wl)
+    n, p = wl["n"], wl["p"]
+    m = n - p
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    rng = np.random.default_rng(1)
+    v = torch.tensor(rng.standard_normal(p), dtype=torch.float64, device=dev)
+    t = torch.empty(p, dtype=torch.float64, device=dev)
+    out = {"kernel_only": True, "workload": wl["desc"], "n": n, "p": p}
+    hbm, src = peaks()
+    with tols.Context(precision=tols.TOLS_FP64, cuda_stream=stream.cuda_stream) as ctx:
+        for name, dt, prec, nbytes, flops in (("fp64", torch.float64, tols.TOLS_FP64, 8.0 * n + 16.0 * m, 4.0 * m * p),
+                                              ("fp32", torch.float32, tols.TOLS_MIXED, 4.0 * n + 8.0 * m, 4.0 * m * p)):
+            d_y = torch.tensor(s.y, dtype=dt, device=dev)
+            u0 = torch.tensor(rng.standard_normal(m), dtype=dt, device=dev)
+            u1 = torch.empty(m, dtype=dt, device=dev)
+            times = []
+            for _ in range(args.reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tols.toeplitz_ols_gk_pass(ctx, prec, d_y, n, p, v, u0, 0.5, u1, t)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = min(times)
+            out[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                         "tflops": flops / (ms * 1e-3) / 1e12, "bytes": nbytes}
+            del d_y, u0, u1
+    out["hbm_peak_gbs"] = hbm
+    out["hbm_peak_source"] = src
+    print(json.dumps(out), flush=True)
+
+
+def _smi_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and local < len(ids) and ids[local].strip().isdigit():
+        return int(ids[local])
+    return local
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    elif args.kernel_only:
+        run_kernel_only(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * toeplitz_ols.h — C ABI of the GB300 (sm_103a) Toeplitz least-squares / AR(p) solver.
+ *
+ * Problem (eq. (xphi), Section 3; Def. "Ordinary Least Squares Problem", Section 2). For a series
+ * y[0..n-1], an order p >= 1 and m = n - p rows,
+ *
+ *     X[i][j] = y[p + i - j - 1],   b[i] = y[p + i],   i in [0, m), j in [0, p),
+ *
+ *     phi* = argmin_phi || X phi - b ||_2     (minimum-norm when X is rank deficient, Thm. "Solution to OLS
+ *                                              problem").
+ *
+ * X is never formed: the Toeplitz structure means only the n numbers of y are needed (Section 3, "there are
+ * only n+p-1 distinct numbers").
+ *
+ * Conventions for every function below:
+ *   - Return 0 (TOLS_OK) on success, TOLS_NOT_CONVERGED (> 0, a warning) or a negative TOLS_ERR_* code.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; the library copies what it needs and keeps
+ *     no caller pointer after the call returns.
+ *   - "device" pointers are global memory on the context's GPU (e.g. a torch tensor's data_ptr()); they are
+ *     read/written on the context's stream, and the call returns after that stream work has completed.
+ *   - All arrays are dense and contiguous; vectors of length p are indexed by j = 0..p-1 as in phi_{j+1}.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef TOEPLITZ_OLS_H
+#define TOEPLITZ_OLS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------------------- */
+#define TOLS_OK 0
+#define TOLS_NOT_CONVERGED 1        /* warning: phi holds the last iterate, info holds the achieved ratio   */
+#define TOLS_ERR_ARG (-1)           /* null pointer, n <= p, p < 1, p > TOLS_MAX_P, bad enum                 */
+#define TOLS_ERR_NONFINITE (-2)     /* y holds NaN or Inf                                                    */
+#define TOLS_ERR_OOM (-3)           /* device or pinned-host allocation failed, or mem_cap_bytes exceeded   */
+#define TOLS_ERR_CUDA (-4)          /* a CUDA runtime call failed; the message is in toeplitz_ols_last_error */
+#define TOLS_ERR_DEVICE_TIMEOUT (-5)/* a bounded device-side wait gave up                                   */
+#define TOLS_ERR_NO_DEVICE (-6)     /* no CUDA device, or the device is not sm_103                          */
+#define TOLS_ERR_BUSY (-7)          /* serving: no slot or memory free for this request right now           */
+
+#define TOLS_MAX_P 1024             /* largest order handled                                                */
+
+/* ---- configuration ------------------------------------------------------------------------------- */
+typedef enum {
+  TOLS_FP64 = 0,   /* every product of X in float64 on the GPU                                               */
+  TOLS_MIXED = 1   /* float32 products, float64 recurrence scalars, float64 residual-correction passes       */
+} tols_precision;
+
+typedef enum {
+  TOLS_PRECOND_NONE = 0,      /* plain LSQR on X                                                           */
+  TOLS_PRECOND_GRAM_CHOL = 1  /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X          */
+} tols_precond;
+
+typedef enum {
+  TOLS_PRODUCT_AUTO = 0,      /* pick per (n, p, precision)                                               */
+  TOLS_PRODUCT_DIRECT = 1,    /* sliding-window dot products                                              */
+  TOLS_PRODUCT_FFT = 2        /* overlap-save FFT blocks                                                  */
+} tols_product;
+
+typedef struct {
+  int precision;          /* tols_precision                                                                 */
+  int device;             /* CUDA device ordinal                                                            */
+  size_t mem_cap_bytes;   /* cap on the context's device arena; 0 = no cap                                  */
+  int max_iter;           /* cap on LSQR iterations per solve (FP64) / per inner solve (mixed); 0 = 4p+200 */
+  int max_sweeps;         /* mixed: cap on float64 residual-correction passes; 0 = 6                        */
+  int precond;            /* tols_precond                                                                   */
+  int product;            /* tols_product                                                                   */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = a stream owned by the context                   */
+} tols_config;
+
+/* Per-solve report. ne_ratio and rnorm always come from an explicit float64 pass over the data. */
+typedef struct {
+  int status;             /* same code the call returned (per series in batched calls)                      */
+  int iters;              /* LSQR iterations (FP64) or inner iterations over all sweeps (mixed)             */
+  int sweeps;             /* float64 residual passes made                                                   */
+  int precision_used;     /* tols_precision actually used (mixed falls back to FP64 when kappa is too big)  */
+  int precond_used;       /* tols_precond actually used (falls back to NONE if the Gram matrix is singular) */
+  int product_used;       /* tols_product actually used                                                     */
+  double ne_ratio;        /* ||X^T r|| / (||X||_2est ||r||), r = b - X phi, from a float64 pass             */
+  double rnorm;           /* ||b - X phi||_2 from the same pass                                             */
+  double bnorm;           /* ||b||_2                                                                        */
+  double anorm_2;         /* estimate of ||X||_2 (power iteration on X^T X, a lower bound)                 */
+  double anorm_f;         /* ||X||_F                                                                        */
+  double cond_est;        /* max R_jj / min R_jj of the Cholesky factor (a rough lower bound of kappa(X))   */
+} tols_info;
+
+typedef struct tols_ctx tols_ctx;
+
+/* Fill *cfg with defaults: FP64, device 0, no cap, Gram-Cholesky preconditioner, AUTO product. */
+void toeplitz_ols_config_default(tols_config* cfg);
+
+/* Create a context on cfg->device (host pointer cfg, copied). *out receives an opaque handle owned by the
+ * caller until toeplitz_ols_destroy. Errors: TOLS_ERR_ARG, TOLS_ERR_NO_DEVICE, TOLS_ERR_CUDA. */
+int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg);
+
+/* Free every device and host resource of ctx. NULL is accepted. */
+int toeplitz_ols_destroy(tols_ctx* ctx);
+
+/* Text for a status code (static storage). */
+const char* toeplitz_ols_strerror(int code);
+
+/* Last detailed error message of ctx (static per context, overwritten by the next failing call). */
+const char* toeplitz_ols_last_error(const tols_ctx* ctx);
+
+/* ---- solves ----------------------------------------------------------------------------------------- */
+
+/* Solve the AR(p) least-squares problem of eq. (xphi) for host series y[0..n-1].
+ *   tol   : stop when ||X^T r|| <= tol ||X||_2 ||r|| (Thm. "Solution to OLS problem": the normal equation),
+ *           checked by a float64 pass; 0 means 1e-12.
+ *   phi   : host, p doubles, written on success and on TOLS_NOT_CONVERGED.
+ *   rnorm : host, nullable; ||b - X phi||_2.
+ *   info  : host, nullable.
+ * Errors: TOLS_ERR_ARG, TOLS_ERR_NONFINITE, TOLS_ERR_OOM, TOLS_ERR_CUDA. */
+int toeplitz_ols_solve(tols_ctx* ctx, const double* y, long long n, int p, double tol, double* phi,
+                       double* rnorm, tols_info* info);
+
+/* Same as toeplitz_ols_solve with y already on the device (d_y, n doubles) and phi written to device memory
+ * d_phi (p doubles). Nothing crosses PCIe/C2C except p-sized results copied into *rnorm and *info. */
+int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, double* d_phi,
+                              double* rnorm, tols_info* info);
+
+/* Solve count independent problems (host series y[k][0..n[k]-1], orders p[k]) in one batched launch
+ * sequence. phi[k] (host, p[k] doubles), rnorm (host, count, nullable), info (host, count, nullable).
+ * Returns the worst status over the batch; info[k].status holds each series' own code. */
+int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
+                               const int* p, double tol, double* const* phi, double* rnorm, tols_info* info);
+
+/* ---- streaming series: append samples and re-solve, warm-started from the previous phi ---------------- */
+int toeplitz_ols_stream_open(tols_ctx* ctx, int p, double tol, int* handle);
+int toeplitz_ols_stream_push(tols_ctx* ctx, int handle, const double* y_chunk, long long len);
+int toeplitz_ols_stream_solve(tols_ctx* ctx, int handle, double* phi, double* rnorm, tols_info* info);
+int toeplitz_ols_stream_close(tols_ctx* ctx, int handle);
+
+/* ---- hot-path steps, exposed one by one -------------------------------------------------------------
+ * Each runs the same kernels the solver runs. All pointers are device pointers unless marked host.
+ * precision selects the element type of d_y / d_u_old / d_u_new: TOLS_FP64 -> double, TOLS_MIXED -> float.
+ */
+
+/* One fused Golub-Kahan product pass (the products of X used by every LSQR iteration):
+ *     u_new = X v - c u_old           (m entries; u_old may be NULL, then the term is dropped)
+ *     *unorm2 = ||u_new||^2           (host, accumulated in float64)
+ *     xtu = X^T u_new                 (p doubles, device)
+ * v: p doubles (device). d_u_new may be NULL (then u_new is only used for the norm and X^T u_new).
+ * d_u_old and d_u_new may not alias. */
+int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long long n, int p, const double* d_v,
+                         const void* d_u_old, double c, void* d_u_new, double* d_xtu, double* unorm2);
+
+/* The Gram matrix G = X^T X (p*p doubles, row-major, device) and h = X^T b (p doubles, device) from one
+ * correlation pass over y plus O(p^2) edge corrections; TOLS_MIXED forms the lag sums from float32 products. */
+int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, double* d_G,
+                      double* d_h, double* bnorm2);
+
+/* Row norms of X: d_rn2[i] = ||X(i,:)||^2 = sum_{t=i}^{i+p-1} y[t]^2 (m doubles, device, nullable) and
+ * *fro2 = ||X||_F^2 (host), from a float64 prefix scan of y^2. */
+int toeplitz_ols_row_norms(tols_ctx* ctx, const double* d_y, long long n, int p, double* d_rn2, double* fro2);
+
+/* The float64 residual pass used for correction and for the final check:
+ *     r = b - X phi (not stored),  d_g = X^T r (p doubles, device),  *rnorm = ||r||_2 (host). */
+int toeplitz_ols_residual(tols_ctx* ctx, const double* d_y, long long n, int p, const double* d_phi, double* d_g,
+                          double* rnorm);
+
+/* Exact leverage scores for p = 1 (after eq. (FASD), Section 3.1): d_lev[i] = y[i]^2 / sum_{t<n-1} y[t]^2,
+ * i in [0, n-1) (device, n-1 doubles). */
+int toeplitz_ols_leverage_p1(tols_ctx* ctx, const double* d_y, long long n, double* d_lev);
+
+/* One step of the approximate-leverage recursion, eqs. (FALS)-(FASD), Section 3.1, for order p >= 2:
+ * with X', b' the order-(p-1) problem on y[0..n-2] (m = n-p rows) and phi_hat (p-1 doubles, device),
+ *     r = X' phi_hat - b',   d_lev[i] = d_lev_prev[i] + r[i]^2 / ||r||^2,   d_pi[i] = d_lev[i] / p,
+ * all m doubles on the device (d_lev may equal d_lev_prev; d_pi nullable); *rnorm2 = ||r||^2 (host). */
+int toeplitz_ols_leverage_step(tols_ctx* ctx, const double* d_y, long long n, int p, const double* d_phi_hat,
+                               const double* d_lev_prev, double* d_lev, double* d_pi, double* rnorm2);
+
+/* ---- instrumentation (no counterpart in the paper: measurement of this library's own kernels) ----------
+ * toeplitz_ols_profile(ctx, 1) clears the counters and starts timing every kernel the context launches with
+ * a pair of CUDA events on the context's stream; 0 stops timing (counters are kept).
+ * toeplitz_ols_profile_read returns, for one kernel class, the number of launches that did work and their
+ * summed device time in milliseconds. Classes:
+ *   0..4  float32 pass kernel with tail STORE, LSQR, NECORR, CHECK, GRAM
+ *   5..9  float64 pass kernel with tail STORE, LSQR, NECORR, CHECK, GRAM
+ *   10    preconditioner (Cholesky + inverse), 11 float32 conversion, 12 other small kernels
+ *   -1    every kernel launch the context made since profiling was enabled (launches only; ms = 0),
+ *         counted whether or not timing is on, including launches that found no work. */
+#define TOLS_PROFILE_CLASSES 13
+int toeplitz_ols_profile(tols_ctx* ctx, int enable);
+int toeplitz_ols_profile_read(tols_ctx* ctx, int kind, long long* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOEPLITZ_OLS_H */

@@ -1,0 +1,297 @@
+"""Python binding of libtoeplitz_ols.so (the C ABI in include/toeplitz_ols.h): argument marshalling only.
+
+Every step of a solve runs in the library's CUDA kernels. Importing this module loads the shared library and
+raises if it is missing (run ``python -m paper_2112_12994_gb300.build`` or ``__graft_entry__.build()``); there
+is no CPU fallback.
+
+Host arrays are numpy float64 arrays. Device arrays are anything with a ``data_ptr()`` method (a CUDA torch
+tensor) or a plain integer address; their element type must match the call (float64, or float32 for the mixed
+step entry points).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtoeplitz_ols.so")
+
+TOLS_OK = 0
+TOLS_NOT_CONVERGED = 1
+TOLS_ERR_ARG = -1
+TOLS_ERR_NONFINITE = -2
+TOLS_ERR_OOM = -3
+TOLS_ERR_CUDA = -4
+TOLS_ERR_DEVICE_TIMEOUT = -5
+TOLS_ERR_NO_DEVICE = -6
+TOLS_ERR_BUSY = -7
+TOLS_MAX_P = 1024
+
+TOLS_FP64 = 0
+TOLS_MIXED = 1
+TOLS_PRECOND_NONE = 0
+TOLS_PRECOND_GRAM_CHOL = 1
+TOLS_PRODUCT_AUTO = 0
+TOLS_PRODUCT_DIRECT = 1
+TOLS_PRODUCT_FFT = 2
+TOLS_PROFILE_CLASSES = 13
+PROFILE_CLASS_NAMES = ["pass_f32_store", "pass_f32_lsqr", "pass_f32_necorr", "pass_f32_check", "pass_f32_gram",
+                       "pass_f64_store", "pass_f64_lsqr", "pass_f64_necorr", "pass_f64_check", "pass_f64_gram",
+                       "precond", "convert_f32", "small"]
+
+
+class tols_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t),
+                ("max_iter", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("precond", ctypes.c_int),
+                ("product", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class tols_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("precision_used", ctypes.c_int), ("precond_used", ctypes.c_int), ("product_used", ctypes.c_int),
+                ("ne_ratio", ctypes.c_double), ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("anorm_2", ctypes.c_double), ("anorm_f", ctypes.c_double), ("cond_est", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TolsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2112_12994_gb300.build.build()")
+    return ctypes.CDLL(LIB_PATH)
+
+
+lib = _load()
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+
+# symbol table: name -> (restype, argtypes); every entry point of include/toeplitz_ols.h
+SIGNATURES = {
+    "toeplitz_ols_config_default": (None, [ctypes.POINTER(tols_config)]),
+    "toeplitz_ols_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tols_config)]),
+    "toeplitz_ols_destroy": (_I, [_P]),
+    "toeplitz_ols_strerror": (ctypes.c_char_p, [_I]),
+    "toeplitz_ols_last_error": (ctypes.c_char_p, [_P]),
+    "toeplitz_ols_solve": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, _D, ctypes.POINTER(tols_info)]),
+    "toeplitz_ols_solve_device": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, _D, ctypes.POINTER(tols_info)]),
+    "toeplitz_ols_solve_batched": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P]),
+    "toeplitz_ols_stream_open": (_I, [_P, _I, ctypes.c_double, ctypes.POINTER(_I)]),
+    "toeplitz_ols_stream_push": (_I, [_P, _I, _P, _LL]),
+    "toeplitz_ols_stream_solve": (_I, [_P, _I, _P, _D, ctypes.POINTER(tols_info)]),
+    "toeplitz_ols_stream_close": (_I, [_P, _I]),
+    "toeplitz_ols_gk_pass": (_I, [_P, _I, _P, _LL, _I, _P, _P, ctypes.c_double, _P, _P, _D]),
+    "toeplitz_ols_gram": (_I, [_P, _I, _P, _LL, _I, _P, _P, _D]),
+    "toeplitz_ols_row_norms": (_I, [_P, _P, _LL, _I, _P, _D]),
+    "toeplitz_ols_residual": (_I, [_P, _P, _LL, _I, _P, _P, _D]),
+    "toeplitz_ols_leverage_p1": (_I, [_P, _P, _LL, _P]),
+    "toeplitz_ols_leverage_step": (_I, [_P, _P, _LL, _I, _P, _P, _P, _P, _D]),
+    "toeplitz_ols_profile": (_I, [_P, _I]),
+    "toeplitz_ols_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), _D]),
+}
+
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _ptr(x):
+    """Device address of a torch tensor / integer, or host address of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def strerror(code: int) -> str:
+    return lib.toeplitz_ols_strerror(code).decode()
+
+
+class Context:
+    """Owns a tols_ctx handle (toeplitz_ols_create / toeplitz_ols_destroy)."""
+
+    def __init__(self, precision=TOLS_FP64, device=0, mem_cap_bytes=0, max_iter=0, max_sweeps=0,
+                 precond=TOLS_PRECOND_GRAM_CHOL, product=TOLS_PRODUCT_AUTO, cuda_stream=None):
+        cfg = tols_config()
+        lib.toeplitz_ols_config_default(ctypes.byref(cfg))
+        cfg.precision, cfg.device, cfg.mem_cap_bytes = precision, device, mem_cap_bytes
+        cfg.max_iter, cfg.max_sweeps, cfg.precond, cfg.product = max_iter, max_sweeps, precond, product
+        cfg.cuda_stream = cuda_stream
+        h = ctypes.c_void_p()
+        rc = lib.toeplitz_ols_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != TOLS_OK:
+            raise TolsError(rc, "toeplitz_ols_create: " + strerror(rc))
+        self.handle = h
+        self.config = cfg
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.toeplitz_ols_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return lib.toeplitz_ols_last_error(self.handle).decode()
+
+    def check(self, rc, what, allow=(TOLS_OK, TOLS_NOT_CONVERGED)):
+        if rc not in allow:
+            raise TolsError(rc, f"{what}: {strerror(rc)}: {self.last_error()}")
+        return rc
+
+
+def toeplitz_ols_create(**kw) -> Context:
+    return Context(**kw)
+
+
+def toeplitz_ols_destroy(ctx: Context):
+    ctx.close()
+
+
+def toeplitz_ols_solve(ctx: Context, y, p: int, tol: float = 0.0):
+    """Host series y -> (phi (p,), rnorm, info dict, status)."""
+    y = _host_f64(y)
+    phi = np.zeros(p, dtype=np.float64)
+    rn = ctypes.c_double()
+    info = tols_info()
+    rc = lib.toeplitz_ols_solve(ctx.handle, y.ctypes.data, y.size, p, tol, phi.ctypes.data, ctypes.byref(rn),
+                                ctypes.byref(info))
+    ctx.check(rc, "toeplitz_ols_solve")
+    return phi, rn.value, info.as_dict(), rc
+
+
+def toeplitz_ols_solve_device(ctx: Context, d_y, n: int, p: int, d_phi, tol: float = 0.0):
+    """Device series d_y (n float64) -> d_phi (p float64, device); returns (rnorm, info dict, status)."""
+    rn = ctypes.c_double()
+    info = tols_info()
+    rc = lib.toeplitz_ols_solve_device(ctx.handle, _ptr(d_y), n, p, tol, _ptr(d_phi), ctypes.byref(rn),
+                                       ctypes.byref(info))
+    ctx.check(rc, "toeplitz_ols_solve_device")
+    return rn.value, info.as_dict(), rc
+
+
+def toeplitz_ols_solve_batched(ctx: Context, ys, ps, tol: float = 0.0):
+    """List of host series and orders -> (list of phi, rnorm array, list of info dicts, worst status)."""
+    count = len(ys)
+    ys = [_host_f64(y) for y in ys]
+    phis = [np.zeros(int(p), dtype=np.float64) for p in ps]
+    yp = (ctypes.c_void_p * count)(*[y.ctypes.data for y in ys])
+    pp = (ctypes.c_void_p * count)(*[f.ctypes.data for f in phis])
+    ns = np.array([y.size for y in ys], dtype=np.int64)
+    pv = np.array(ps, dtype=np.int32)
+    rn = np.zeros(count, dtype=np.float64)
+    infos = (tols_info * count)()
+    rc = lib.toeplitz_ols_solve_batched(ctx.handle, count, ctypes.cast(yp, _P), ns.ctypes.data, pv.ctypes.data, tol,
+                                        ctypes.cast(pp, _P), rn.ctypes.data, ctypes.cast(infos, _P))
+    ctx.check(rc, "toeplitz_ols_solve_batched")
+    return phis, rn, [i.as_dict() for i in infos], rc
+
+
+def toeplitz_ols_stream_open(ctx: Context, p: int, tol: float = 0.0) -> int:
+    h = ctypes.c_int()
+    ctx.check(lib.toeplitz_ols_stream_open(ctx.handle, p, tol, ctypes.byref(h)), "toeplitz_ols_stream_open")
+    return h.value
+
+
+def toeplitz_ols_stream_push(ctx: Context, handle: int, chunk):
+    chunk = _host_f64(chunk)
+    ctx.check(lib.toeplitz_ols_stream_push(ctx.handle, handle, chunk.ctypes.data, chunk.size),
+              "toeplitz_ols_stream_push")
+
+
+def toeplitz_ols_stream_solve(ctx: Context, handle: int, p: int):
+    phi = np.zeros(p, dtype=np.float64)
+    rn = ctypes.c_double()
+    info = tols_info()
+    rc = lib.toeplitz_ols_stream_solve(ctx.handle, handle, phi.ctypes.data, ctypes.byref(rn), ctypes.byref(info))
+    ctx.check(rc, "toeplitz_ols_stream_solve")
+    return phi, rn.value, info.as_dict(), rc
+
+
+def toeplitz_ols_stream_close(ctx: Context, handle: int):
+    ctx.check(lib.toeplitz_ols_stream_close(ctx.handle, handle), "toeplitz_ols_stream_close")
+
+
+def toeplitz_ols_gk_pass(ctx: Context, precision: int, d_y, n: int, p: int, d_v, d_u_old, c: float, d_u_new, d_xtu):
+    """u_new = X v - c u_old, X^T u_new -> d_xtu; returns ||u_new||^2 (device buffers)."""
+    n2 = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_gk_pass(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_v), _ptr(d_u_old), c,
+                                       _ptr(d_u_new), _ptr(d_xtu), ctypes.byref(n2)), "toeplitz_ols_gk_pass")
+    return n2.value
+
+
+def toeplitz_ols_gram(ctx: Context, precision: int, d_y, n: int, p: int, d_G, d_h):
+    b2 = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_gram(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_G), _ptr(d_h), ctypes.byref(b2)),
+              "toeplitz_ols_gram")
+    return b2.value
+
+
+def toeplitz_ols_row_norms(ctx: Context, d_y, n: int, p: int, d_rn2=None):
+    f = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_row_norms(ctx.handle, _ptr(d_y), n, p, _ptr(d_rn2), ctypes.byref(f)),
+              "toeplitz_ols_row_norms")
+    return f.value
+
+
+def toeplitz_ols_residual(ctx: Context, d_y, n: int, p: int, d_phi, d_g):
+    rn = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_residual(ctx.handle, _ptr(d_y), n, p, _ptr(d_phi), _ptr(d_g), ctypes.byref(rn)),
+              "toeplitz_ols_residual")
+    return rn.value
+
+
+def toeplitz_ols_leverage_p1(ctx: Context, d_y, n: int, d_lev):
+    ctx.check(lib.toeplitz_ols_leverage_p1(ctx.handle, _ptr(d_y), n, _ptr(d_lev)), "toeplitz_ols_leverage_p1")
+
+
+def toeplitz_ols_leverage_step(ctx: Context, d_y, n: int, p: int, d_phi_hat, d_lev_prev, d_lev, d_pi=None):
+    rr = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_leverage_step(ctx.handle, _ptr(d_y), n, p, _ptr(d_phi_hat), _ptr(d_lev_prev),
+                                             _ptr(d_lev), _ptr(d_pi), ctypes.byref(rr)), "toeplitz_ols_leverage_step")
+    return rr.value
+
+
+def toeplitz_ols_profile(ctx: Context, enable: bool):
+    ctx.check(lib.toeplitz_ols_profile(ctx.handle, int(bool(enable))), "toeplitz_ols_profile")
+
+
+def toeplitz_ols_profile_read(ctx: Context, kind: int):
+    """(launches, total_ms) of one kernel class; kind = -1 gives (all launches, 0.0)."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    ctx.check(lib.toeplitz_ols_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(ms)),
+              "toeplitz_ols_profile_read")
+    return n.value, ms.value

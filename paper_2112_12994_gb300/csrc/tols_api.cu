@@ -1,0 +1,843 @@
+// C ABI of the Toeplitz-OLS solver: context, device arena, the solve drivers and the step entry points.
+//
+// A solve (eq. (xphi), Section 3; Thm. "Solution to OLS problem", Section 2) runs as a device-resident state
+// machine. The host launches pass kernels; the last CTA of each pass performs the scalar step and writes
+// the next phase into DevState, so the host only polls a status word every few launches:
+//
+//   FP64  : Gram pass -> Cholesky preconditioner -> LSQR passes (float64) -> float64 check pass
+//           [-> LSQR on the residual -> check ...]
+//   MIXED : Gram pass (float products) -> Cholesky -> LSQR passes (float products, float64 scalars)
+//           -> float64 check pass -> correction solve (float products) -> float64 check pass -> ...
+//           Falls back to FP64 when the refinement stops contracting (kappa(X)^2 too large for float).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "tols_internal.cuh"
+
+using namespace tols;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct StreamSeries {
+  int p;
+  double tol;
+  std::vector<double> y;
+  std::vector<double> phi;  // last solution (warm start)
+};
+
+}  // namespace
+
+struct tols_ctx {
+  tols_config cfg{};
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t used = 0;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf;
+  DevState* h_state = nullptr;  // pinned copy of the device state
+  std::string err;
+  std::map<int, StreamSeries> streams;
+  int next_handle = 1;
+  int grid[2] = {0, 0};         // pass grid (float, double)
+  size_t grid_pad[2] = {0, 0};  // p_pad the grid was computed for
+  // instrumentation (toeplitz_ols_profile)
+  bool prof = false;
+  long long launch_total = 0;
+  long long prof_launches[TOLS_PROFILE_CLASSES] = {};
+  double prof_ms[TOLS_PROFILE_CLASSES] = {};
+  struct Pending { cudaEvent_t e0, e1; int slot, kind; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_free;
+  int* d_worklog = nullptr;
+  int* h_worklog = nullptr;
+};
+
+namespace {
+
+int fail(tols_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
+  if (c) {
+    char buf[512];
+    if (e != cudaSuccess)
+      snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    else
+      snprintf(buf, sizeof buf, "%s", what);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CK(expr)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (expr);                                              \
+    if (e_ != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, #expr, e_);    \
+  } while (0)
+
+// Grow a device buffer to at least bytes (contents are not preserved), honouring the memory cap.
+int ensure(tols_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (b.cap >= bytes) return TOLS_OK;
+  if (b.p) {
+    cudaFree(b.p);
+    ctx->used -= b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->cfg.mem_cap_bytes && ctx->used + bytes > ctx->cfg.mem_cap_bytes)
+    return fail(ctx, TOLS_ERR_OOM, "device arena would exceed mem_cap_bytes");
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TOLS_ERR_OOM, "cudaMalloc", e);
+  }
+  b.cap = bytes;
+  ctx->used += bytes;
+  return TOLS_OK;
+}
+
+void release(tols_ctx* ctx, DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  ctx->used -= b.cap;
+  b = DevBuf{};
+}
+
+constexpr int kMaxPending = 512;
+
+// Accumulate the timed launches recorded since the last call (the stream is synchronised here).
+int flush_profile(tols_ctx* ctx) {
+  if (ctx->pending.empty()) return TOLS_OK;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(ctx->h_worklog, ctx->d_worklog, sizeof(int) * kMaxPending, cudaMemcpyDeviceToHost));
+  for (const auto& q : ctx->pending) {
+    const int kind = q.kind >= 0 ? q.kind : ctx->h_worklog[q.slot] - 1;
+    if (kind >= 0 && kind < TOLS_PROFILE_CLASSES) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, q.e0, q.e1));
+      ctx->prof_launches[kind] += 1;
+      ctx->prof_ms[kind] += ms;
+    }
+    ctx->ev_free.push_back(q.e0);
+    ctx->ev_free.push_back(q.e1);
+  }
+  ctx->pending.clear();
+  CK(cudaMemsetAsync(ctx->d_worklog, 0, sizeof(int) * kMaxPending, ctx->stream));
+  return TOLS_OK;
+}
+
+int take_event(tols_ctx* ctx, cudaEvent_t* e) {
+  if (!ctx->ev_free.empty()) {
+    *e = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    return TOLS_OK;
+  }
+  CK(cudaEventCreate(e));
+  return TOLS_OK;
+}
+
+// Launch a pass kernel (timed when profiling).
+template <typename T>
+int run_pass(tols_ctx* ctx, PassArgs<T> a, int grid) {
+  ctx->launch_total++;
+  if (!ctx->prof) {
+    CK(launch_pass<T>(a, grid, ctx->stream));
+    return TOLS_OK;
+  }
+  int rc;
+  if ((int)ctx->pending.size() >= kMaxPending && (rc = flush_profile(ctx))) return rc;
+  tols_ctx::Pending q;
+  if ((rc = take_event(ctx, &q.e0)) || (rc = take_event(ctx, &q.e1))) return rc;
+  q.slot = (int)ctx->pending.size();
+  q.kind = -1;
+  a.worklog = ctx->d_worklog;
+  a.work_slot = q.slot;
+  CK(cudaEventRecord(q.e0, ctx->stream));
+  CK(launch_pass<T>(a, grid, ctx->stream));
+  CK(cudaEventRecord(q.e1, ctx->stream));
+  ctx->pending.push_back(q);
+  return TOLS_OK;
+}
+
+// Launch one of the small kernels of class kind (timed when profiling).
+template <typename F>
+int run_small(tols_ctx* ctx, int kind, F launch) {
+  ctx->launch_total++;
+  if (!ctx->prof) {
+    CK(launch());
+    return TOLS_OK;
+  }
+  int rc;
+  if ((int)ctx->pending.size() >= kMaxPending && (rc = flush_profile(ctx))) return rc;
+  tols_ctx::Pending q;
+  if ((rc = take_event(ctx, &q.e0)) || (rc = take_event(ctx, &q.e1))) return rc;
+  q.slot = -1;
+  q.kind = kind;
+  CK(cudaEventRecord(q.e0, ctx->stream));
+  CK(launch());
+  CK(cudaEventRecord(q.e1, ctx->stream));
+  ctx->pending.push_back(q);
+  return TOLS_OK;
+}
+
+#define RUN(expr)                       \
+  do {                                  \
+    int rc_ = (expr);                   \
+    if (rc_) return rc_;                \
+  } while (0)
+
+int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad) {
+  if (ctx->grid[is_double] == 0 || ctx->grid_pad[is_double] != (size_t)p_pad) {
+    int nb = 0;
+    const size_t smem = pass_smem_bytes(is_double, p_pad);
+    cudaFuncSetAttribute(pass_kernel_ptr(is_double), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel_ptr(is_double), kThreads, smem) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    ctx->grid[is_double] = std::min(kMaxGrid, ctx->sms * std::min(nb, 4));
+    ctx->grid_pad[is_double] = p_pad;
+  }
+  return ctx->grid[is_double];
+}
+
+// Lay out one solve's workspace in the context buffers. y64 is the caller's (or staged) device series.
+int prepare_work(tols_ctx* ctx, const double* y64, long long n, int p, bool mixed, bool need_u, Work& w) {
+  memset(&w, 0, sizeof w);
+  w.n = n;
+  w.m = n - p;
+  w.p = p;
+  w.p_pad = pad_p(p + 1);
+  w.y64 = y64;
+  const size_t m = (size_t)w.m;
+  int rc;
+  if (mixed) {
+    if ((rc = ensure(ctx, ctx->y32, sizeof(float) * (size_t)n))) return rc;
+    w.y32 = (float*)ctx->y32.p;
+  }
+  if (need_u) {
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    if ((rc = ensure(ctx, ctx->u0, es * m))) return rc;
+    if ((rc = ensure(ctx, ctx->u1, es * m))) return rc;
+    w.U[0] = ctx->u0.p;
+    w.U[1] = ctx->u1.p;
+  }
+  const size_t pp = (size_t)w.p_pad;
+  // The arrival counters sit at a fixed offset at the head of the buffer, whatever p is: every pass leaves
+  // them at zero, and they are zeroed whenever the buffer is (re)allocated.
+  const size_t cnt_bytes = 256 * ((sizeof(unsigned int) * (kMaxGroups + 1) + 255) / 256);
+  const size_t part_bytes = cnt_bytes + sizeof(double) * (kMaxGrid * pp + kMaxGrid + kMaxGroups * pp + kMaxGroups);
+  const bool fresh_part = ctx->part.cap < part_bytes;
+  if ((rc = ensure(ctx, ctx->part, part_bytes))) return rc;
+  w.counters = (unsigned int*)ctx->part.p;
+  double* q = (double*)((char*)ctx->part.p + cnt_bytes);
+  w.part_n2 = q; q += kMaxGrid;
+  w.grp_n2 = q; q += kMaxGroups;
+  w.part_t = q; q += kMaxGrid * pp;
+  w.grp_t = q; q += kMaxGroups * pp;
+  if (fresh_part) CK(cudaMemsetAsync(ctx->part.p, 0, cnt_bytes, ctx->stream));
+  if ((rc = ensure(ctx, ctx->vecs, sizeof(double) * (10 * pp + 8)))) return rc;
+  q = (double*)ctx->vecs.p;
+  w.v = q; q += pp;
+  w.w = q; q += pp;
+  w.z = q; q += pp;
+  w.d = q; q += pp;
+  w.phi = q; q += pp;
+  w.g = q; q += pp;
+  w.h = q; q += pp;
+  w.t = q; q += pp;
+  w.best = q; q += pp;
+  w.bnorm2 = q; q += pp;
+  const size_t pq = (size_t)p * p;
+  if ((rc = ensure(ctx, ctx->mats, sizeof(double) * 3 * pq + sizeof(float) * 2 * pq + 1024))) return rc;
+  q = (double*)ctx->mats.p;
+  w.G = q; q += pq;
+  w.M = q; q += pq;
+  w.Mt = q; q += pq;
+  float* f = (float*)q;
+  w.M32 = f; f += pq;
+  w.Mt32 = f;
+  if ((rc = ensure(ctx, ctx->state, sizeof(DevState)))) return rc;
+  w.st = (DevState*)ctx->state.p;
+  return TOLS_OK;
+}
+
+template <typename T>
+PassArgs<T> base_args(const Work& w, const T* y, long long n, int p, int p_pad) {
+  PassArgs<T> a;
+  memset(&a, 0, sizeof a);
+  a.y = y;
+  a.n = n;
+  a.m = n - p;
+  a.p = p;
+  a.p_pad = p_pad;
+  a.nlag = p;
+  a.d_scale = 1.0;
+  a.w = w;
+  return a;
+}
+
+int validate(tols_ctx* ctx, long long n, int p) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (p < 1 || p > TOLS_MAX_P) return fail(ctx, TOLS_ERR_ARG, "p out of range [1, TOLS_MAX_P]");
+  if (n <= p) return fail(ctx, TOLS_ERR_ARG, "need n > p");
+  return TOLS_OK;
+}
+
+// Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path).
+int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond) {
+  const int pg = pad_p(w.p + 1);
+  if (mixed) {
+    RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
+    PassArgs<float> a = base_args<float>(w, w.y32, w.n, w.p, pg);
+    a.gram = 1;
+    a.nlag = w.p + 1;
+    a.tail = TAIL_GRAM;
+    a.out_n2 = w.bnorm2;
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg)));
+  } else {
+    PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
+    a.gram = 1;
+    a.nlag = w.p + 1;
+    a.tail = TAIL_GRAM;
+    a.out_n2 = w.bnorm2;
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg)));
+  }
+  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
+  RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
+  return TOLS_OK;
+}
+
+void fill_info(tols_info* info, const DevState& s, int prec) {
+  if (!info) return;
+  info->status = s.status;
+  info->iters = s.total_iter;
+  info->sweeps = s.sweeps;
+  info->precision_used = prec;
+  info->precond_used = s.precond;
+  info->product_used = TOLS_PRODUCT_DIRECT;
+  info->ne_ratio = s.ne_ratio;
+  info->rnorm = s.rnorm;
+  info->bnorm = s.bnorm;
+  info->anorm_2 = s.anorm_2;
+  info->anorm_f = s.anorm_f;
+  info->cond_est = s.cond_est;
+}
+
+// One complete solve of the series at d_y (device). phi0 (device, nullable) warm-starts. Leaves phi in w.phi
+// and the final state in *ctx->h_state.
+int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, bool mixed, const double* phi0,
+               Work& w, bool no_precond = false) {
+  int rc = prepare_work(ctx, d_y, n, p, mixed, true, w);
+  if (rc) return rc;
+  const int max_iter = ctx->cfg.max_iter > 0 ? ctx->cfg.max_iter : 4 * p + 200;
+  const int max_sweeps = ctx->cfg.max_sweeps > 0 ? ctx->cfg.max_sweeps : 6;
+  DevState hs;
+  memset(&hs, 0, sizeof hs);
+  hs.tol = tol;
+  hs.tol_inner = 1e-5;
+  hs.est_ratio = tol;
+  hs.max_iter = max_iter;
+  // float inner solves that need more than ~100 preconditioned iterations mean kappa(X) is too large for
+  // float products; they stop early and the stall test hands the problem to the float64 path
+  hs.iter_cap = mixed ? std::min(max_iter, 100) : max_iter;
+  hs.max_sweeps = max_sweeps;
+  hs.mixed = mixed ? 1 : 0;
+  hs.mixed_ok = 1;
+  hs.ne_ratio = 1e300;
+  hs.ne_best = 1e300;
+  hs.rnorm_best = 0.0;
+  hs.status = TOLS_NOT_CONVERGED;
+  hs.phase = PH_LSQR;
+  *ctx->h_state = hs;
+  CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = run_setup(ctx, w, mixed, no_precond))) return rc;
+  if (phi0) {
+    CK(cudaMemcpyAsync(w.phi, phi0, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    RUN(run_small(ctx, 12, [&] { return launch_init_lsqr(w, 1, ctx->stream); }));
+  } else {
+    RUN(run_small(ctx, 12, [&] { return launch_init_lsqr(w, 0, ctx->stream); }));
+  }
+  const int pp = pad_p(p);
+  PassArgs<double> ad = base_args<double>(w, w.y64, n, p, pp);
+  ad.check_done = 1;
+  ad.d = w.d;
+  PassArgs<float> af = base_args<float>(w, w.y32, n, p, pp);
+  af.check_done = 1;
+  af.d = w.d;
+  const int gd = pass_grid_for(ctx, 1, pp);
+  const int gf = mixed ? pass_grid_for(ctx, 0, pp) : 0;
+  const long long max_launch = (long long)(max_iter + 4) * (max_sweeps + 2) * 2 + 16;
+  long long launched = 0;
+  int burst = 4;
+  while (true) {
+    if (mixed) {
+      for (int k = 0; k < burst; ++k) RUN(run_pass<float>(ctx, af, gf));
+      RUN(run_pass<double>(ctx, ad, gd));
+      launched += burst + 1;
+    } else {
+      for (int k = 0; k < burst; ++k) RUN(run_pass<double>(ctx, ad, gd));
+      launched += burst;
+    }
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    RUN(flush_profile(ctx));
+    if (ctx->h_state->done || ctx->h_state->phase == PH_DONE) break;
+    if (launched > max_launch) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "solver did not reach a final state");
+    burst = std::min(burst * 2, 16);
+  }
+  RUN(run_small(ctx, 12, [&] { return launch_finish(w, ctx->stream); }));
+  CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  RUN(flush_profile(ctx));
+  return TOLS_OK;
+}
+
+// Solve with precision fallback; phi (device) receives the result.
+int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, double* d_phi,
+                      double* rnorm, tols_info* info, const double* phi0) {
+  if (tol <= 0) tol = 1e-12;
+  bool mixed = ctx->cfg.precision == TOLS_MIXED;
+  Work w;
+  int rc = solve_core(ctx, d_y, n, p, tol, mixed, phi0, w);
+  if (rc) return rc;
+  if (mixed && (ctx->h_state->mixed_ok == 0 || ctx->h_state->precond == 0) &&
+      ctx->h_state->status != TOLS_ERR_NONFINITE && ctx->h_state->status != TOLS_OK) {
+    // float products cannot refine this problem (kappa(X)^2 * u32 too large): redo it in float64,
+    // warm-started from the best mixed iterate when that one is usable, else from zero
+    const bool warm = ctx->h_state->ne_best < 1e-3;
+    if (warm) CK(cudaMemcpyAsync(d_phi, w.best, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    mixed = false;
+    const int saved_iter = ctx->h_state->total_iter;
+    rc = solve_core(ctx, d_y, n, p, tol, false, warm ? d_phi : nullptr, w);
+    if (rc) return rc;
+    ctx->h_state->total_iter += saved_iter;
+  }
+  if (ctx->h_state->singular && ctx->h_state->compatible && ctx->h_state->status >= 0) {
+    // X is exactly rank deficient (singular Gram matrix, zero residual): the shifted preconditioner does not
+    // give the minimum-norm solution, plain LSQR from zero does. Keep the first result if the repeat fails.
+    CK(cudaMemcpyAsync(d_phi, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    const DevState first = *ctx->h_state;
+    rc = solve_core(ctx, d_y, n, p, tol, false, nullptr, w, true);
+    if (rc) return rc;
+    if (!(ctx->h_state->status == TOLS_OK && ctx->h_state->compatible)) {
+      *ctx->h_state = first;
+      CK(cudaMemcpyAsync(w.phi, d_phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      ctx->h_state->total_iter += first.total_iter;
+      ctx->h_state->sweeps += first.sweeps;
+      mixed = false;
+    }
+  }
+  const DevState& s = *ctx->h_state;
+  if (s.status == TOLS_ERR_NONFINITE) return fail(ctx, TOLS_ERR_NONFINITE, "y holds NaN or Inf");
+  CK(cudaMemcpyAsync(d_phi, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rnorm) *rnorm = s.rnorm;
+  fill_info(info, s, mixed ? TOLS_MIXED : TOLS_FP64);
+  return s.status;
+}
+
+int stage_y(tols_ctx* ctx, const double* y, long long n) {
+  int rc = ensure(ctx, ctx->y64, sizeof(double) * (size_t)n);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(ctx->y64.p, y, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+  return TOLS_OK;
+}
+
+int host_solve(tols_ctx* ctx, const double* y, long long n, int p, double tol, double* phi, double* rnorm,
+               tols_info* info, const double* phi0_host) {
+  int rc = stage_y(ctx, y, n);
+  if (rc) return rc;
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)p + 64)))) return rc;
+  double* d_phi = (double*)ctx->scratch.p;
+  double* d_phi0 = nullptr;
+  if (phi0_host) {
+    d_phi0 = d_phi + p;
+    CK(cudaMemcpyAsync(d_phi0, phi0_host, sizeof(double) * p, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  rc = solve_device_impl(ctx, (const double*)ctx->y64.p, n, p, tol, d_phi, rnorm, info, d_phi0);
+  if (rc < 0) return rc;
+  cudaError_t e = cudaMemcpyAsync(phi, d_phi, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "copy phi to host", e);
+  return rc;
+}
+
+}  // namespace
+
+// ======================================================================================================
+extern "C" {
+
+void toeplitz_ols_config_default(tols_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->precision = TOLS_FP64;
+  cfg->device = 0;
+  cfg->precond = TOLS_PRECOND_GRAM_CHOL;
+  cfg->product = TOLS_PRODUCT_AUTO;
+}
+
+const char* toeplitz_ols_strerror(int code) {
+  switch (code) {
+    case TOLS_OK: return "ok";
+    case TOLS_NOT_CONVERGED: return "not converged (phi holds the best iterate)";
+    case TOLS_ERR_ARG: return "invalid argument";
+    case TOLS_ERR_NONFINITE: return "series holds NaN or Inf";
+    case TOLS_ERR_OOM: return "out of device memory (or memory cap reached)";
+    case TOLS_ERR_CUDA: return "CUDA runtime error";
+    case TOLS_ERR_DEVICE_TIMEOUT: return "device-side wait gave up";
+    case TOLS_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    case TOLS_ERR_BUSY: return "no slot or memory free";
+    default: return "unknown status";
+  }
+}
+
+const char* toeplitz_ols_last_error(const tols_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
+  if (!out) return TOLS_ERR_ARG;
+  *out = nullptr;
+  tols_config c;
+  if (cfg) c = *cfg;
+  else toeplitz_ols_config_default(&c);
+  if (c.precision != TOLS_FP64 && c.precision != TOLS_MIXED) return TOLS_ERR_ARG;
+  if (c.precond != TOLS_PRECOND_NONE && c.precond != TOLS_PRECOND_GRAM_CHOL) return TOLS_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= c.device || c.device < 0) {
+    cudaGetLastError();
+    return TOLS_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) return TOLS_ERR_NO_DEVICE;
+  if (!(prop.major == 10 && prop.minor == 3)) return TOLS_ERR_NO_DEVICE;
+  if (cudaSetDevice(c.device) != cudaSuccess) return TOLS_ERR_NO_DEVICE;
+  tols_ctx* ctx = new tols_ctx;
+  ctx->cfg = c;
+  ctx->device = c.device;
+  ctx->sms = prop.multiProcessorCount;
+  if (c.cuda_stream) {
+    ctx->stream = (cudaStream_t)c.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return TOLS_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->d_worklog, sizeof(int) * kMaxPending) != cudaSuccess ||
+      cudaMemset(ctx->d_worklog, 0, sizeof(int) * kMaxPending) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_worklog, sizeof(int) * kMaxPending) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TOLS_ERR_OOM;
+  }
+  if (cudaMallocHost(&ctx->h_state, sizeof(DevState)) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TOLS_ERR_OOM;
+  }
+  *out = ctx;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_destroy(tols_ctx* ctx) {
+  if (!ctx) return TOLS_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  DevBuf* bufs[] = {&ctx->y64, &ctx->y32, &ctx->u0, &ctx->u1, &ctx->part, &ctx->vecs,
+                    &ctx->mats, &ctx->state, &ctx->scratch, &ctx->rbuf};
+  for (DevBuf* b : bufs) release(ctx, *b);
+  if (ctx->h_state) cudaFreeHost(ctx->h_state);
+  if (ctx->h_worklog) cudaFreeHost(ctx->h_worklog);
+  if (ctx->d_worklog) cudaFree(ctx->d_worklog);
+  for (auto& q : ctx->pending) { cudaEventDestroy(q.e0); cudaEventDestroy(q.e1); }
+  for (auto e : ctx->ev_free) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_solve(tols_ctx* ctx, const double* y, long long n, int p, double tol, double* phi, double* rnorm,
+                       tols_info* info) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!y || !phi) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  cudaSetDevice(ctx->device);
+  rc = host_solve(ctx, y, n, p, tol, phi, rnorm, info, nullptr);
+  if (info && rc < 0) info->status = rc;
+  return rc;
+}
+
+int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, double* d_phi,
+                              double* rnorm, tols_info* info) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y || !d_phi) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  cudaSetDevice(ctx->device);
+  rc = solve_device_impl(ctx, d_y, n, p, tol <= 0 ? 1e-12 : tol, d_phi, rnorm, info, nullptr);
+  if (info && rc < 0) info->status = rc;
+  return rc;
+}
+
+int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n, const int* p,
+                               double tol, double* const* phi, double* rnorm, tols_info* info) {
+  if (!ctx || count < 0 || (count > 0 && (!y || !n || !p || !phi))) return TOLS_ERR_ARG;
+  int worst = TOLS_OK;
+  for (int k = 0; k < count; ++k) {
+    tols_info one;
+    double rn = 0.0;
+    int rc = validate(ctx, n[k], p[k]);
+    if (!rc) rc = (!y[k] || !phi[k]) ? TOLS_ERR_ARG : host_solve(ctx, y[k], n[k], p[k], tol, phi[k], &rn, &one, nullptr);
+    if (rc < 0) memset(&one, 0, sizeof one);
+    one.status = rc;
+    if (info) info[k] = one;
+    if (rnorm) rnorm[k] = rn;
+    if (rc < 0) worst = worst < 0 ? std::min(worst, rc) : rc;
+    else if (worst >= 0) worst = std::max(worst, rc);
+  }
+  return worst;
+}
+
+int toeplitz_ols_stream_open(tols_ctx* ctx, int p, double tol, int* handle) {
+  if (!ctx || !handle || p < 1 || p > TOLS_MAX_P) return TOLS_ERR_ARG;
+  StreamSeries s;
+  s.p = p;
+  s.tol = tol;
+  *handle = ctx->next_handle++;
+  ctx->streams[*handle] = s;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_stream_push(tols_ctx* ctx, int handle, const double* y_chunk, long long len) {
+  if (!ctx || len < 0 || (len > 0 && !y_chunk)) return TOLS_ERR_ARG;
+  auto it = ctx->streams.find(handle);
+  if (it == ctx->streams.end()) return TOLS_ERR_ARG;
+  it->second.y.insert(it->second.y.end(), y_chunk, y_chunk + len);
+  return TOLS_OK;
+}
+
+int toeplitz_ols_stream_solve(tols_ctx* ctx, int handle, double* phi, double* rnorm, tols_info* info) {
+  if (!ctx || !phi) return TOLS_ERR_ARG;
+  auto it = ctx->streams.find(handle);
+  if (it == ctx->streams.end()) return TOLS_ERR_ARG;
+  StreamSeries& s = it->second;
+  int rc = validate(ctx, (long long)s.y.size(), s.p);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  rc = host_solve(ctx, s.y.data(), (long long)s.y.size(), s.p, s.tol, phi, rnorm, info,
+                  s.phi.empty() ? nullptr : s.phi.data());
+  if (rc >= 0) s.phi.assign(phi, phi + s.p);
+  if (info && rc < 0) info->status = rc;
+  return rc;
+}
+
+int toeplitz_ols_stream_close(tols_ctx* ctx, int handle) {
+  if (!ctx) return TOLS_ERR_ARG;
+  return ctx->streams.erase(handle) ? TOLS_OK : TOLS_ERR_ARG;
+}
+
+// ---- step entry points ----------------------------------------------------------------------------
+int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long long n, int p, const double* d_v,
+                         const void* d_u_old, double c, void* d_u_new, double* d_xtu, double* unorm2) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y || !d_v || !d_xtu || (precision != TOLS_FP64 && precision != TOLS_MIXED))
+    return fail(ctx, TOLS_ERR_ARG, "bad argument");
+  cudaSetDevice(ctx->device);
+  Work w;
+  if ((rc = prepare_work(ctx, nullptr, n, p, false, false, w))) return rc;
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)p + 64)))) return rc;
+  double* d_n2 = (double*)ctx->scratch.p;
+  const int pp = pad_p(p);
+  if (precision == TOLS_FP64) {
+    PassArgs<double> a = base_args<double>(w, (const double*)d_y, n, p, pp);
+    a.d = d_v;
+    a.u_old = (const double*)d_u_old;
+    a.coef_host = c;
+    a.u_new = (double*)d_u_new;
+    a.tail = TAIL_STORE;
+    a.out_t = d_xtu;
+    a.out_n2 = d_n2;
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp)));
+  } else {
+    PassArgs<float> a = base_args<float>(w, (const float*)d_y, n, p, pp);
+    a.d = d_v;
+    a.u_old = (const float*)d_u_old;
+    a.coef_host = c;
+    a.u_new = (float*)d_u_new;
+    a.tail = TAIL_STORE;
+    a.out_t = d_xtu;
+    a.out_n2 = d_n2;
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pp)));
+  }
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (unorm2) *unorm2 = h;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, double* d_G, double* d_h,
+                      double* bnorm2) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y || !d_G || !d_h || (precision != TOLS_FP64 && precision != TOLS_MIXED))
+    return fail(ctx, TOLS_ERR_ARG, "bad argument");
+  cudaSetDevice(ctx->device);
+  const bool mixed = precision == TOLS_MIXED;
+  Work w;
+  if ((rc = prepare_work(ctx, d_y, n, p, mixed, false, w))) return rc;
+  w.G = d_G;
+  w.h = d_h;
+  const int pg = pad_p(p + 1);
+  if (mixed) {
+    RUN(run_small(ctx, 11, [&] { return launch_convert_f32(d_y, w.y32, n, ctx->stream); }));
+    PassArgs<float> a = base_args<float>(w, w.y32, n, p, pg);
+    a.gram = 1;
+    a.nlag = p + 1;
+    a.tail = TAIL_GRAM;
+    a.out_n2 = w.bnorm2;
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg)));
+  } else {
+    PassArgs<double> a = base_args<double>(w, d_y, n, p, pg);
+    a.gram = 1;
+    a.nlag = p + 1;
+    a.tail = TAIL_GRAM;
+    a.out_n2 = w.bnorm2;
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg)));
+  }
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, w.bnorm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (bnorm2) *bnorm2 = h;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_row_norms(tols_ctx* ctx, const double* d_y, long long n, int p, double* d_rn2, double* fro2) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  cudaSetDevice(ctx->device);
+  const long long m = n - p;
+  const size_t blocks = (size_t)((m + 2047) / 2048);
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (blocks + 64)))) return rc;
+  double* s = (double*)ctx->scratch.p;
+  RUN(run_small(ctx, 12, [&] { return launch_row_norms(d_y, n, p, d_rn2, s, s + 8, ctx->stream); }));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, s, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (fro2) *fro2 = h;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_residual(tols_ctx* ctx, const double* d_y, long long n, int p, const double* d_phi, double* d_g,
+                          double* rnorm) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y || !d_phi || !d_g) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  cudaSetDevice(ctx->device);
+  Work w;
+  if ((rc = prepare_work(ctx, d_y, n, p, false, false, w))) return rc;
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * 64))) return rc;
+  double* d_n2 = (double*)ctx->scratch.p;
+  const int pp = pad_p(p);
+  PassArgs<double> a = base_args<double>(w, d_y, n, p, pp);
+  a.d = d_phi;
+  a.d_scale = -1.0;     // u = -X phi - (-1) b = b - X phi
+  a.u_old = d_y + p;
+  a.coef_host = -1.0;
+  a.tail = TAIL_STORE;
+  a.out_t = d_g;
+  a.out_n2 = d_n2;
+  RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp)));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rnorm) *rnorm = sqrt(h);
+  return TOLS_OK;
+}
+
+int toeplitz_ols_leverage_p1(tols_ctx* ctx, const double* d_y, long long n, double* d_lev) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (!d_y || !d_lev || n < 2) return fail(ctx, TOLS_ERR_ARG, "bad argument");
+  cudaSetDevice(ctx->device);
+  const size_t blocks = (size_t)((n - 1 + 4095) / 4096);
+  int rc = ensure(ctx, ctx->scratch, sizeof(double) * (blocks + 64));
+  if (rc) return rc;
+  RUN(run_small(ctx, 12, [&] { return launch_leverage_p1(d_y, n, d_lev, (double*)ctx->scratch.p, ctx->stream); }));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TOLS_OK;
+}
+
+int toeplitz_ols_leverage_step(tols_ctx* ctx, const double* d_y, long long n, int p, const double* d_phi_hat,
+                               const double* d_lev_prev, double* d_lev, double* d_pi, double* rnorm2) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (p < 2 || !d_y || !d_phi_hat || !d_lev_prev || !d_lev) return fail(ctx, TOLS_ERR_ARG, "bad argument");
+  cudaSetDevice(ctx->device);
+  const long long m = n - p;
+  // the order-(p-1) problem on y[0..n-2]: X' phi_hat - b' with b' = y + (p-1)
+  Work w;
+  if ((rc = prepare_work(ctx, d_y, n - 1, p - 1, false, false, w))) return rc;
+  if ((rc = ensure(ctx, ctx->rbuf, sizeof(double) * (size_t)m))) return rc;
+  if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * 64))) return rc;
+  double* d_rr = (double*)ctx->scratch.p;
+  const int pp = pad_p(p - 1);
+  PassArgs<double> a = base_args<double>(w, d_y, n - 1, p - 1, pp);
+  a.d = d_phi_hat;
+  a.u_old = d_y + (p - 1);
+  a.coef_host = 1.0;
+  a.u_new = (double*)ctx->rbuf.p;
+  a.nlag = 0;
+  a.tail = TAIL_STORE;
+  a.out_t = nullptr;
+  a.out_n2 = d_rr;
+  RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp)));
+  RUN(run_small(ctx, 12, [&] {
+    return launch_leverage_step((const double*)ctx->rbuf.p, m, p, d_rr, d_lev_prev, d_lev, d_pi, nullptr, ctx->stream);
+  }));
+  double h = 0.0;
+  CK(cudaMemcpyAsync(&h, d_rr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rnorm2) *rnorm2 = h;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_profile(tols_ctx* ctx, int enable) {
+  if (!ctx) return TOLS_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  int rc = flush_profile(ctx);
+  if (rc) return rc;
+  if (enable) {
+    ctx->launch_total = 0;
+    for (int k = 0; k < TOLS_PROFILE_CLASSES; ++k) { ctx->prof_launches[k] = 0; ctx->prof_ms[k] = 0.0; }
+  }
+  ctx->prof = enable != 0;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_profile_read(tols_ctx* ctx, int kind, long long* launches, double* total_ms) {
+  if (!ctx || kind < -1 || kind >= TOLS_PROFILE_CLASSES) return TOLS_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  int rc = flush_profile(ctx);
+  if (rc) return rc;
+  if (kind == -1) {
+    if (launches) *launches = ctx->launch_total;
+    if (total_ms) *total_ms = 0.0;
+  } else {
+    if (launches) *launches = ctx->prof_launches[kind];
+    if (total_ms) *total_ms = ctx->prof_ms[kind];
+  }
+  return TOLS_OK;
+}
+
+}  // extern "C"

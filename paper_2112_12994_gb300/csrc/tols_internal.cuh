@@ -1,0 +1,125 @@
+// Internal declarations of the Toeplitz-OLS CUDA library (sm_103a).
+//
+// Notation (0-based): series y[0..n-1], order p, m = n - p rows,
+//   X[i][j] = y[p + i - j - 1],  b[i] = y[p + i]                       (eq. (xphi), Section 3).
+// The kernels index the lags by k = p - 1 - j, so that
+//   (X d)[i]     = sum_k y[i + k] * d[p - 1 - k]
+//   (X^T u)[j]   = sum_i u[i] * y[i + p - 1 - j] = tk[p - 1 - j],  tk[k] = sum_i u[i] * y[i + k].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/toeplitz_ols.h"
+
+namespace tols {
+
+constexpr int kThreads = 256;            // threads per CTA of every pass kernel
+constexpr int kGroup = 16;               // CTAs per first-level reduction group
+constexpr int kMaxGrid = 152 * 4;        // upper bound on pass grid size (partials buffer rows)
+constexpr int kMaxGroups = (kMaxGrid + kGroup - 1) / kGroup;
+
+// Round p up to the lag-chunk granularity used by the direct kernels.
+__host__ __device__ inline int pad_p(int p) { return (p + 15) & ~15; }
+
+// What the last CTA of a pass does after the grid-wide reduction (see tails in tols_kernels.cu).
+enum TailMode : int {
+  TAIL_STORE = 0,    // write the reduced X^T u and ||u||^2 to out_t / out_n2
+  TAIL_LSQR = 1,     // LSQR (Golub-Kahan Bidiag 1 + Givens) scalar step
+  TAIL_NECORR = 2,   // Golub-Kahan Bidiag 2 step for the normal-equation correction (X^T X) delta = g
+  TAIL_CHECK = 3,    // float64 residual check: g = X^T r, ||r||, ne ratio; mixed: start the next correction
+  TAIL_GRAM = 4,     // Gram matrix from lag sums plus edge corrections
+};
+
+// Phases of the device-driven solver state machine.
+enum Phase : int {
+  PH_LSQR = 0,       // iterating LSQR
+  PH_CHECK = 1,      // a float64 residual check pass is due
+  PH_NECORR = 2,     // iterating the correction solve
+  PH_DONE = 3,
+};
+
+// Scalars of one solve, resident in device memory. Vectors live in the Work buffers.
+struct DevState {
+  // LSQR (Paige & Saunders 1982) scalars
+  double alpha, beta, rhobar, phibar, anorm2, bnorm, beta1;
+  // Bidiag 2 (correction solve) scalars
+  double theta, rho, f, theta1;
+  // coefficient for the next pass: u_new = X d - coef * u_old
+  double coef;
+  // norms
+  double anorm_f, anorm_2, ne_ratio, rnorm, ne_best, rnorm_best;
+  double tol, tol_inner, est_ratio, cond_est;
+  int iter, max_iter, iter_cap, inner_iter, total_iter, sweeps, max_sweeps;
+  int phase, status, precond, mixed, mixed_ok;
+  int done;          // 1 => every pass kernel returns at once
+  int singular;      // the Gram matrix was singular at working precision
+  int compatible;    // a check found ||r|| <= tol ||b||
+};
+
+// Device pointers of one solve's workspace.
+struct Work {
+  long long n, m;
+  int p, p_pad;
+  const double* y64;      // n doubles
+  float* y32;             // n floats (mixed)
+  void* U[2];             // ping-pong m-vectors (double in FP64 mode, float in mixed)
+  double* part_t;         // [kMaxGrid][p_pad] per-CTA partial X^T u (lag order k)
+  double* part_n2;        // [kMaxGrid]
+  double* grp_t;          // [kMaxGroups][p_pad]
+  double* grp_n2;         // [kMaxGroups]
+  unsigned int* counters; // [kMaxGroups + 1]
+  // p-vectors (each p_pad doubles)
+  double *v, *w, *z, *d, *phi, *g, *h, *t, *best;
+  double* G;              // p*p Gram matrix (row-major), later overwritten by R
+  double* M;              // p*p upper-triangular R^{-1} (row-major)
+  double* Mt;             // p*p its transpose (row-major)
+  float* M32;             // float copies for the mixed path
+  float* Mt32;
+  double* bnorm2;         // device scalar ||b||^2 written by the Gram pass
+  DevState* st;
+};
+
+// Arguments of a pass kernel (passed by value).
+template <typename T>
+struct PassArgs {
+  const T* y;             // series, n elements (the window of row i is y[i .. i+p-1])
+  long long n, m;
+  int p, p_pad;
+  int nlag;               // number of lags in the correlation (p for X^T u, p+1 for the Gram lag sums)
+  int gram;               // 1: correlation of y with itself (u := y[i]), no X d product
+  const double* d;        // p-vector (device) for X d; lag-reversed internally
+  double d_scale;         // the pass multiplies by d_scale * d
+  const T* u_old;         // nullable
+  T* u_new;               // nullable
+  const double* coef_dev; // device scalar c (nullable => coef_host)
+  double coef_host;
+  int tail;               // TailMode
+  Work w;                 // workspace (for the reduction buffers and the tails)
+  double* out_t;          // TAIL_STORE: reduced X^T u (p, j order)
+  double* out_n2;         // TAIL_STORE: reduced ||u||^2 (1)
+  int check_done;         // 1: return at once when w.st->done is set
+  int* worklog;           // nullable: the tail writes 1 + tail + 5 * (T == double) into worklog[work_slot]
+  int work_slot;
+};
+
+// Launch helpers (tols_kernels.cu).
+size_t pass_smem_bytes(int is_double, int p_pad);
+int pass_tile_rows(int is_double);
+const void* pass_kernel_ptr(int is_double);
+template <typename T>
+cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s);
+
+cudaError_t launch_convert_f32(const double* y, float* y32, long long n, cudaStream_t s);
+cudaError_t launch_precond(Work w, int mixed, cudaStream_t s);
+cudaError_t launch_init_lsqr(Work w, int mixed, cudaStream_t s);
+cudaError_t launch_finish(Work w, cudaStream_t s);
+cudaError_t launch_prepare_check(Work w, cudaStream_t s);
+cudaError_t launch_row_norms(const double* y, long long n, int p, double* rn2, double* fro2_dev, double* scratch,
+                             cudaStream_t s);
+cudaError_t launch_leverage_p1(const double* y, long long n, double* lev, double* scratch, cudaStream_t s);
+cudaError_t launch_leverage_step(const double* r, long long m, int p, const double* rr, const double* lev_prev,
+                                 double* lev, double* pi, double* unused, cudaStream_t s);
+cudaError_t launch_check_finite(const double* y, long long n, int* flag, cudaStream_t s);
+
+}  // namespace tols

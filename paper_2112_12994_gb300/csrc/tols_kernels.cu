@@ -1,0 +1,1071 @@
+// Kernels of the Toeplitz-OLS solver for sm_103a.
+//
+// One "pass" kernel carries the whole per-iteration hot path of LSQR on the structured matrix of
+// eq. (xphi), Section 3 (X[i][j] = y[p+i-j-1], b[i] = y[p+i]):
+//
+//   u_new = X d - c * u_old        sliding-window dot products over a shared-memory tile of y
+//   ||u_new||^2                    float64 accumulation
+//   X^T u_new                      lag correlations of the fresh u tile against the same y tile
+//
+// so one iteration reads y once, reads u_old once and writes u_new once. The last CTA to finish (found with
+// an atomic counter, no spinning) reduces the per-CTA partials in a fixed order and runs the scalar step of
+// the solver (LSQR recurrence, correction solve or residual check) on the device, so the host never waits
+// per iteration. FP64 products run in double; the mixed path runs the products in float with float64
+// accumulation of every norm and every cross-tile sum.
+#include <math.h>
+#include <stdio.h>
+
+#include "tols_internal.cuh"
+
+namespace tols {
+
+__host__ __device__ inline long long lmin(long long a, long long b) { return a < b ? a : b; }
+
+// ------------------------------------------------------------------------------------------------------
+// shared-memory layout of the y window: 4 pad elements after every 16, so that 16-B vector loads by lanes
+// 16 elements apart hit distinct banks.
+__device__ __forceinline__ int phys(int i) { return i + ((i >> 4) << 2); }
+__host__ __device__ inline int phys_size(int n) { return n + ((n + 15) >> 4) * 4 + 4; }
+
+template <typename T>
+struct TileCfg;
+template <>
+struct TileCfg<float> {
+  static constexpr int RB = 16;    // consecutive rows per thread
+  static constexpr int KC = 8;     // lags per inner step
+  static constexpr int TILE = kThreads * RB;
+  static constexpr int MINB = 3;   // resident CTAs per SM the register budget aims at
+};
+template <>
+struct TileCfg<double> {
+  static constexpr int RB = 8;
+  static constexpr int KC = 8;
+  static constexpr int TILE = kThreads * RB;
+  static constexpr int MINB = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* s, int i, T* out);
+template <>
+__device__ __forceinline__ void lds4<float>(const float* s, int i, float* out) {
+  float4 v = *reinterpret_cast<const float4*>(s + phys(i));
+  out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(const double* s, int i, double* out) {
+  const double2* q = reinterpret_cast<const double2*>(s + phys(i));
+  double2 a = q[0], b = q[1];
+  out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* g, const T* v);
+template <>
+__device__ __forceinline__ void st4<float>(float* g, const float* v) {
+  *reinterpret_cast<float4*>(g) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double* g, const double* v) {
+  reinterpret_cast<double2*>(g)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(g)[1] = make_double2(v[2], v[3]);
+}
+
+// Sum 8 values over the 32 lanes of a warp, scattered: afterwards every lane holds the full sum of value
+// j = 4 [lane & 16] + 2 [lane & 8] + [lane & 4]. Fixed butterfly order, so the result is deterministic.
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter8(const T* t, int lane) {
+  const unsigned full = 0xffffffffu;
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  T a4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T keep = h16 ? t[4 + i] : t[i];
+    const T send = h16 ? t[i] : t[4 + i];
+    a4[i] = keep + __shfl_xor_sync(full, send, 16);
+  }
+  T a2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const T keep = h8 ? a4[2 + i] : a4[i];
+    const T send = h8 ? a4[i] : a4[2 + i];
+    a2[i] = keep + __shfl_xor_sync(full, send, 8);
+  }
+  T a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(full, h4 ? a2[0] : a2[1], 4);
+  a1 += __shfl_xor_sync(full, a1, 2);
+  a1 += __shfl_xor_sync(full, a1, 1);
+  return a1;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the 256 threads of a CTA; every thread gets the result. scratch: >= 8 doubles of shared memory.
+__device__ double block_sum(double v, double* scratch) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int k = 0; k < kThreads / 32; ++k) r += scratch[k];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Preconditioner applications on p-vectors (M = R^{-1} upper triangular, Mt = M^T, both row-major).
+// out = M^T in : out[j] = sum_{i<=j} M[i][j] in[i]
+__device__ void apply_Mt(const Work& w, int precond, int mixed, const double* in, double* out) {
+  const int p = w.p;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    if (!precond) { out[j] = in[j]; continue; }
+    if (mixed) {
+      float acc = 0.f;
+      for (int i = 0; i <= j; ++i) acc = fmaf(w.M32[(size_t)i * p + j], (float)in[i], acc);
+      out[j] = acc;
+    } else {
+      double acc = 0.0;
+      for (int i = 0; i <= j; ++i) acc = fma(w.M[(size_t)i * p + j], in[i], acc);
+      out[j] = acc;
+    }
+  }
+}
+// out = M in : out[i] = sum_{j>=i} M[i][j] in[j] = sum_{j>=i} Mt[j][i] in[j]
+__device__ void apply_M(const Work& w, int precond, int mixed, const double* in, double* out) {
+  const int p = w.p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    if (!precond) { out[i] = in[i]; continue; }
+    if (mixed) {
+      float acc = 0.f;
+      for (int j = i; j < p; ++j) acc = fmaf(w.Mt32[(size_t)j * p + i], (float)in[j], acc);
+      out[i] = acc;
+    } else {
+      double acc = 0.0;
+      for (int j = i; j < p; ++j) acc = fma(w.Mt[(size_t)j * p + i], in[j], acc);
+      out[i] = acc;
+    }
+  }
+}
+// out = M in with float64 arithmetic on whatever M the solve uses (float-rounded M in the mixed path).
+__device__ void apply_M_exact(const Work& w, int precond, int mixed, const double* in, double* out) {
+  const int p = w.p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    if (!precond) { out[i] = in[i]; continue; }
+    double acc = 0.0;
+    for (int j = i; j < p; ++j)
+      acc = fma(mixed ? (double)w.Mt32[(size_t)j * p + i] : w.Mt[(size_t)j * p + i], in[j], acc);
+    out[i] = acc;
+  }
+}
+
+__device__ double vec_norm2(const double* a, int p, double* scratch) {
+  double s = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) s += a[j] * a[j];
+  return block_sum(s, scratch);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Solver tails. Run by the last CTA of a pass with tk[k] = sum_i u_new[i] y[i+k] (k in [0, nlag)) in shared
+// memory and n2 = ||u_new||^2. They update DevState and the p-vectors for the next launch.
+
+// After LSQR or the correction solve has finished: the next pass is a float64 residual check with
+// d = -phi and u_old = b, c = -1, so that u_new = b - X phi.
+__device__ void schedule_check(const Work& w, DevState* st, double* scratch) {
+  for (int j = threadIdx.x; j < w.p; j += blockDim.x) w.d[j] = -w.phi[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->phase = PH_CHECK;
+    st->coef = -1.0;
+  }
+}
+
+// Start (or restart) LSQR on  min || A z - rhs ||,  A = X M, with beta1 = ||rhs|| and g = X^T rhs given.
+// The correction M z is added to phi when LSQR stops.
+__device__ void start_lsqr(const Work& w, DevState* st, const double* g, double beta1, double* scratch) {
+  const int p = w.p;
+  const int mixed = st->mixed;
+  double* tmp = w.t;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) tmp[j] = beta1 > 0 ? g[j] / beta1 : 0.0;
+  __syncthreads();
+  apply_Mt(w, st->precond, mixed, tmp, w.v);
+  __syncthreads();
+  double alpha = sqrt(vec_norm2(w.v, p, scratch));
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    double vj = alpha > 0 ? w.v[j] / alpha : 0.0;
+    w.v[j] = vj;
+    w.w[j] = vj;
+    w.z[j] = 0.0;
+  }
+  __syncthreads();
+  apply_M(w, st->precond, mixed, w.v, w.d);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->alpha = alpha;
+    st->beta = beta1;
+    st->beta1 = beta1;
+    st->phibar = beta1;
+    st->rhobar = alpha;
+    st->anorm2 = 0.0;
+    st->iter = 0;
+    st->coef = beta1 > 0 ? alpha / beta1 : 0.0;
+    st->phase = PH_LSQR;
+  }
+  __syncthreads();
+  if (beta1 == 0.0 || alpha == 0.0) {
+    // X^T rhs = 0: the correction is zero; go straight to the check.
+    schedule_check(w, st, scratch);
+  }
+}
+
+// Start the normal-equation correction solve (A^T A) zeta = M^T g, A = X M, by Golub-Kahan Bidiag 2.
+__device__ void start_necorr(const Work& w, DevState* st, double* scratch) {
+  const int p = w.p;
+  apply_Mt(w, st->precond, 1, w.g, w.v);
+  __syncthreads();
+  double theta1 = sqrt(vec_norm2(w.v, p, scratch));
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    w.v[j] = theta1 > 0 ? w.v[j] / theta1 : 0.0;
+    w.w[j] = 0.0;
+    w.z[j] = 0.0;
+  }
+  __syncthreads();
+  apply_M(w, st->precond, 1, w.v, w.d);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->theta = theta1;
+    st->theta1 = theta1;
+    st->f = -1.0;
+    st->coef = 0.0;
+    st->anorm2 = 0.0;
+    st->inner_iter = 0;
+    st->phase = PH_NECORR;
+  }
+  __syncthreads();
+}
+
+// LSQR step (Paige & Saunders 1982, Bidiag 1 with Givens rotations), after the pass produced
+// U_new = A v_i - alpha_i u_i (unnormalised, ||U_new|| = beta_{i+1}) and tk = X^T U_new in lag order.
+__device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double n2, double* scratch) {
+  const int p = w.p;
+  const int mixed = st->mixed;
+  double beta = sqrt(n2);
+  // a beta at rounding level relative to ||B_k||_F means the Krylov space is exhausted: treat it as zero
+  if (beta <= 1e-14 * sqrt(st->anorm2 + st->alpha * st->alpha)) beta = 0.0;
+  double* tmp = w.t;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) tmp[j] = beta > 0 ? tk[p - 1 - j] / beta : 0.0;
+  __syncthreads();
+  double* s = w.g;  // scratch p-vector: A^T u_{i+1}
+  apply_Mt(w, st->precond, mixed, tmp, s);
+  __syncthreads();
+  for (int j = threadIdx.x; j < p; j += blockDim.x) s[j] = s[j] - beta * w.v[j];
+  __syncthreads();
+  double alpha = sqrt(vec_norm2(s, p, scratch));
+  if (beta == 0.0 || alpha <= 1e-14 * sqrt(st->anorm2 + alpha * alpha + beta * beta)) alpha = 0.0;
+  const double rhobar = st->rhobar, phibar = st->phibar;
+  const double rho = hypot(rhobar, beta);
+  const double c = rho > 0 ? rhobar / rho : 1.0, sn = rho > 0 ? beta / rho : 0.0;
+  const double theta = sn * alpha;
+  const double phi_i = c * phibar;
+  const double new_phibar = sn * phibar;
+  const double new_rhobar = -c * alpha;
+  const double step = rho > 0 ? phi_i / rho : 0.0, wscale = rho > 0 ? theta / rho : 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double wj = w.w[j];
+    w.z[j] += step * wj;
+    const double vj = alpha > 0 ? s[j] / alpha : 0.0;
+    w.v[j] = vj;
+    w.w[j] = vj - wscale * wj;
+  }
+  __syncthreads();
+  const double anorm2 = st->anorm2 + alpha * alpha + beta * beta;
+  const double arnorm = new_phibar * alpha * fabs(c);
+  const double ratio = (new_phibar > 0 && anorm2 > 0) ? arnorm / (sqrt(anorm2) * new_phibar) : 0.0;
+  const int iter = st->iter + 1;
+  const double tolA = st->mixed ? st->tol_inner : st->est_ratio;
+  // Paige-Saunders stopping tests: ||A^T r|| <= tol ||A|| ||r||, or a compatible system ||r|| <= tol ||rhs||
+  const bool stop = (ratio <= tolA) || (new_phibar <= tolA * st->beta1) || (beta == 0.0) || (alpha == 0.0) ||
+                    (iter >= st->iter_cap) ||
+                    (st->total_iter + 1 >= 64 * st->max_iter);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->alpha = alpha;
+    st->beta = beta;
+    st->rhobar = new_rhobar;
+    st->phibar = new_phibar;
+    st->anorm2 = anorm2;
+    st->iter = iter;
+    st->total_iter += 1;
+    st->coef = beta > 0 ? alpha / beta : 0.0;
+  }
+  if (stop) {
+    // phi += M z
+    apply_M_exact(w, st->precond, mixed, w.z, tmp);
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) w.phi[j] += tmp[j];
+    __syncthreads();
+    schedule_check(w, st, scratch);
+  } else {
+    apply_M(w, st->precond, mixed, w.v, w.d);
+  }
+}
+
+// Bidiag 2 step (Paige & Saunders 1982) for (A^T A) zeta = s: after the pass produced
+// P_i = A v_i - theta_i p_{i-1} (unnormalised, ||P_i|| = rho_i) and tk = X^T P_i.
+__device__ void tail_necorr(const Work& w, DevState* st, const double* tk, double n2, double* scratch) {
+  const int p = w.p;
+  double rho = sqrt(n2);
+  const double theta = st->theta;
+  // rho at rounding level relative to ||R_k||_F: the Krylov space is exhausted, keep zeta as it is
+  const bool rho_breakdown = rho <= 1e-14 * sqrt(st->anorm2 + theta * theta);
+  if (rho_breakdown) rho = 0.0;
+  const double f = rho > 0 ? -theta * st->f / rho : 0.0;
+  double* tmp = w.t;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double wj = rho > 0 ? (w.v[j] - theta * w.w[j]) / rho : 0.0;
+    w.w[j] = wj;
+    w.z[j] += f * wj;
+    tmp[j] = rho > 0 ? tk[p - 1 - j] / rho : 0.0;
+  }
+  __syncthreads();
+  double* s = w.g;
+  apply_Mt(w, st->precond, 1, tmp, s);
+  __syncthreads();
+  for (int j = threadIdx.x; j < p; j += blockDim.x) s[j] -= rho * w.v[j];
+  __syncthreads();
+  double theta_next = sqrt(vec_norm2(s, p, scratch));
+  if (rho == 0.0 || theta_next <= 1e-14 * sqrt(st->anorm2 + theta * theta + rho * rho)) theta_next = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) w.v[j] = theta_next > 0 ? s[j] / theta_next : 0.0;
+  __syncthreads();
+  const double resid = fabs(theta_next * f);
+  const int it = st->inner_iter + 1;
+  const bool stop = rho == 0.0 || theta_next == 0.0 || resid <= st->tol_inner * st->theta1 ||
+                    it >= st->iter_cap || (st->total_iter + 1 >= 64 * st->max_iter);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->anorm2 += theta * theta + rho * rho;
+    st->f = f;
+    st->rho = rho;
+    st->theta = theta_next;
+    st->inner_iter = it;
+    st->total_iter += 1;
+    st->coef = rho > 0 ? theta_next / rho : 0.0;
+  }
+  __syncthreads();
+  if (stop) {
+    apply_M_exact(w, st->precond, 1, w.z, tmp);
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) w.phi[j] += tmp[j];
+    __syncthreads();
+    schedule_check(w, st, scratch);
+  } else {
+    apply_M(w, st->precond, 1, w.v, w.d);
+  }
+}
+
+// float64 residual check: u_new = b - X phi was formed by the pass; tk = X^T r.
+__device__ void tail_check(const Work& w, DevState* st, const double* tk, double n2, double* scratch) {
+  const int p = w.p;
+  const double rnorm = sqrt(n2);
+  for (int j = threadIdx.x; j < p; j += blockDim.x) w.g[j] = tk[p - 1 - j];
+  __syncthreads();
+  const double gn = sqrt(vec_norm2(w.g, p, scratch));
+  const double ne = (rnorm > 0 && st->anorm_2 > 0) ? gn / (st->anorm_2 * rnorm) : 0.0;
+  const double prev = st->ne_ratio;
+  const int sweeps = st->sweeps + 1;
+  const bool better = ne < st->ne_best;
+  if (better)
+    for (int j = threadIdx.x; j < p; j += blockDim.x) w.best[j] = w.phi[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->ne_ratio = ne;
+    st->rnorm = rnorm;
+    st->sweeps = sweeps;
+    if (better) {
+      st->ne_best = ne;
+      st->rnorm_best = rnorm;
+    }
+  }
+  __syncthreads();
+  // Attainable ratio in float64: r = b - X phi carries an absolute error of order u ||b||, so the ratio cannot
+  // go much below u sqrt(p) ||b|| / ||r||.
+  const double floor64 = 1e-15 * sqrt((double)p) * fmax(1.0, rnorm > 0 ? st->bnorm / rnorm : 1.0);
+  int next;
+  if (threadIdx.x == 0 && rnorm <= st->tol * st->bnorm) st->compatible = 1;
+  if (ne <= st->tol || rnorm <= st->tol * st->bnorm) next = 0;           // converged (or compatible)
+  else if (sweeps >= st->max_sweeps || st->total_iter >= 64 * st->max_iter) next = 1;  // give up
+  else if (sweeps >= 2 && ne > 0.5 * prev) {                              // no progress since the last check
+    next = (st->mixed && ne > 10.0 * floor64) ? 2 : 1;                   // mixed: float cannot refine it
+  } else if (st->mixed && sweeps == 1 && ne > 1e-2) {
+    next = 2;                                                             // float LSQR gained < 2 digits
+  } else next = 3;                                                        // refine again
+  if (next == 0 || next == 1 || next == 2) {
+    if (threadIdx.x == 0) {
+      st->status = next == 0 ? TOLS_OK : TOLS_NOT_CONVERGED;
+      if (next == 2) st->mixed_ok = 0;
+      st->phase = PH_DONE;
+      st->done = 1;
+    }
+    return;
+  }
+  if (st->mixed) {
+    start_necorr(w, st, scratch);
+  } else {
+    // LSQR on the residual: rhs = r, stored by this pass in U[0]; tighten the internal tolerance and cap the
+    // restart at a few times the iterations the first run needed.
+    if (threadIdx.x == 0) {
+      st->est_ratio = fmax(st->est_ratio * 0.01, 1e-16);
+      st->iter_cap = min(st->max_iter, max(2 * st->iter + 10, 20));
+    }
+    __syncthreads();
+    start_lsqr(w, st, w.g, rnorm, scratch);
+  }
+}
+
+// Gram matrix from c[h] = sum_{i<m} y[i] y[i+h], h in [0, p], plus the edge corrections
+//   E_h(lo) = sum_{t<lo} (y[t+m] y[t+m+h] - y[t] y[t+h]):
+//   G[j][k] = c[|j-k|] + E_|j-k|(p-1-max(j,k)),  h_j = (X^T b)_j = c[j+1] + E_{j+1}(p-1-j),
+//   ||b||^2 = c[0] + E_0(p).
+__device__ void tail_gram(const Work& w, const double* ck, double* bnorm2_out) {
+  const int p = w.p;
+  const long long m = w.m;
+  const double* y = w.y64;
+  for (int hh = threadIdx.x; hh <= p; hh += blockDim.x) {
+    double E = 0.0;
+    for (int lo = 0; lo <= p - hh; ++lo) {
+      if (lo <= p - 1 - hh) {
+        const int j = p - 1 - lo, k = j - hh;
+        const double gv = ck[hh] + E;
+        w.G[(size_t)j * p + k] = gv;
+        w.G[(size_t)k * p + j] = gv;
+      }
+      if (lo == p - hh) {
+        if (hh >= 1) w.h[hh - 1] = ck[hh] + E;
+        else *bnorm2_out = ck[0] + E;
+      } else {
+        // term t = lo of the prefix; largest index read is y[p - 1 + m] = y[n - 1]
+        E += y[lo + m] * y[lo + m + hh] - y[lo] * y[lo + hh];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// The pass kernel.
+//
+// Shared memory (dynamic): ys[phys(TILE + p_pad + 16)] (T), us[phys(TILE)] (T), dr[p_pad] (T),
+// wpart[kThreads/32][p_pad] (T), tacc[p_pad + 16] (double), scratch[16] (double).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) pass_kernel(PassArgs<T> a) {
+  constexpr int RB = TileCfg<T>::RB;
+  constexpr int KC = TileCfg<T>::KC;
+  constexpr int TILE = TileCfg<T>::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+
+  DevState* st = a.w.st;
+  // Which solver phase this launch serves; all CTAs read the same state written by the previous launch.
+  int tail = a.tail;
+  const T* u_old = a.u_old;
+  T* u_new = a.u_new;
+  double coef = a.coef_host;
+  if (a.check_done) {
+    const int ph = st->phase;
+    if (st->done || ph == PH_DONE) return;
+    const bool is_double = sizeof(T) == 8;
+    if (is_double) {
+      if (ph == PH_CHECK) tail = TAIL_CHECK;
+      else if (ph == PH_LSQR && !st->mixed) tail = TAIL_LSQR;
+      else return;
+    } else {
+      if (ph == PH_LSQR && st->mixed) tail = TAIL_LSQR;
+      else if (ph == PH_NECORR) tail = TAIL_NECORR;
+      else return;
+    }
+    coef = st->coef;
+    // buffer selection (see tols_api.cu: U[0]/U[1] ping-pong; b is y + p)
+    const int it = (tail == TAIL_NECORR) ? st->inner_iter : st->iter;
+    if (tail == TAIL_CHECK) {
+      u_old = a.y + a.p;                     // b
+      u_new = st->mixed ? nullptr : (T*)a.w.U[0];  // FP64: keep r for a restart
+    } else if (tail == TAIL_NECORR) {
+      u_old = it == 0 ? nullptr : (const T*)a.w.U[(it + 1) & 1];
+      u_new = (T*)a.w.U[it & 1];
+    } else {  // LSQR: first pass reads rhs (b on the first sweep, r stored in U[0] after a check)
+      const int from_b = (st->sweeps == 0);
+      if (it == 0) {
+        u_old = from_b ? a.y + a.p : (const T*)a.w.U[0];
+        u_new = (T*)a.w.U[1];
+      } else {
+        u_old = (const T*)a.w.U[(it & 1)];
+        u_new = (T*)a.w.U[(it + 1) & 1];
+      }
+    }
+  } else if (a.coef_dev) {
+    coef = *a.coef_dev;
+  }
+
+  const int p = a.p, p_pad = a.p_pad, nlag = a.nlag;
+  const long long m = a.m, n = a.n;
+  T* ys = reinterpret_cast<T*>(smem_raw);
+  const int ys_len = phys_size(TILE + p_pad + 16);
+  T* us = ys + ys_len;                         // u_old tile, padded layout
+  const int us_len = phys_size(TILE);
+  T* dr = us + us_len;                         // lag-reversed d
+  T* wpart = dr + p_pad;                       // per-warp partial X^T u of the tile: [kThreads/32][p_pad]
+  double* tacc = reinterpret_cast<double*>(wpart + (kThreads / 32) * p_pad);
+  double* scratch = tacc + p_pad + 16;
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // lag-reversed d: dr[k] = d[p-1-k]
+  if (!a.gram)
+    for (int k = tid; k < p_pad; k += kThreads) dr[k] = k < p ? (T)(a.d_scale * a.d[p - 1 - k]) : (T)0;
+  for (int k = tid; k < p_pad + 16; k += kThreads) tacc[k] = 0.0;
+  double n2 = 0.0;
+  // lag owned by this lane after the warp reduce-scatter of 8 lags
+  const int jl = ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
+  const bool vec_out = u_new && ((reinterpret_cast<uintptr_t>(u_new) & 15) == 0);
+  const int r0 = tid * RB;                     // this thread's rows within the tile
+
+  const long long ntiles = (m + TILE - 1) / TILE;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long i0 = tile * TILE;
+    const int rows = (int)min((long long)TILE, m - i0);
+    const int wlen = TILE + p_pad + 16;
+    __syncthreads();
+    for (int q = tid; q < wlen; q += kThreads) {
+      const long long gi = i0 + q;
+      ys[phys(q)] = gi < n ? a.y[gi] : (T)0;
+    }
+    if (!a.gram && u_old) {
+      for (int q = tid; q < TILE; q += kThreads) us[phys(q)] = q < rows ? u_old[i0 + q] : (T)0;
+    }
+    __syncthreads();
+
+    // ---- this thread's RB entries of the fresh u (or of y itself for the Gram lag sums)
+    T uv[RB];
+    if (a.gram) {
+#pragma unroll
+      for (int q = 0; q < RB / 4; ++q) lds4<T>(ys, r0 + 4 * q, uv + 4 * q);
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r0 + r >= rows) uv[r] = (T)0;
+    } else {
+      // u_new = X d - c u_old : sliding window of y held in registers, KC lags per step
+      T acc[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) acc[r] = (T)0;
+      if (r0 < rows) {
+        for (int k0 = 0; k0 < p_pad; k0 += KC) {
+          T yv[RB + KC];
+#pragma unroll
+          for (int q = 0; q < (RB + KC) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
+          T dv[KC];
+#pragma unroll
+          for (int q = 0; q < KC; ++q) dv[q] = dr[k0 + q];
+#pragma unroll
+          for (int q = 0; q < KC; ++q)
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[r] = fma(yv[r + q], dv[q], acc[r]);
+        }
+      }
+      T uo[RB];
+      if (u_old) {
+#pragma unroll
+        for (int q = 0; q < RB / 4; ++q) lds4<T>(us, r0 + 4 * q, uo + 4 * q);
+      }
+      T nn = (T)0;
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        T u = (T)0;
+        if (r0 + r < rows) {
+          u = acc[r];
+          if (u_old) u = fma((T)(-coef), uo[r], u);
+        }
+        nn = fma(u, u, nn);
+        uv[r] = u;
+      }
+      n2 += (double)nn;
+      if (u_new && r0 < rows) {
+        T* dst = u_new + i0 + r0;
+        if (vec_out && r0 + RB <= rows) {
+#pragma unroll
+          for (int q = 0; q < RB / 4; ++q) st4<T>(dst + 4 * q, uv + 4 * q);
+        } else {
+#pragma unroll
+          for (int r = 0; r < RB; ++r)
+            if (r0 + r < rows) dst[r] = uv[r];
+        }
+      }
+    }
+
+    // ---- tk[k] += sum_r u[r] y[r + k]: 8 lags at a time from the same conflict-free window loads, then a
+    // warp reduce-scatter (9 shuffles) leaves lag k0 + jl on lanes with (lane & 3) == 0.
+    for (int k0 = 0; k0 < nlag; k0 += 8) {
+      T t8[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t8[q] = (T)0;
+      if (r0 < rows) {
+        T yv[RB + 8];
+#pragma unroll
+        for (int q = 0; q < (RB + 8) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int r = 0; r < RB; ++r) t8[q] = fma(uv[r], yv[r + q], t8[q]);
+      }
+      const T v = warp_reduce_scatter8<T>(t8, lane);
+      if ((lane & 3) == 0) wpart[warp * p_pad + k0 + jl] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < nlag; k += kThreads) {
+      T sum = (T)0;
+#pragma unroll
+      for (int q = 0; q < kThreads / 32; ++q) sum += wpart[q * p_pad + k];
+      tacc[k] += (double)sum;
+    }
+  }
+  __syncthreads();
+
+  // ---- per-CTA partials, then the two-level reduction by the last CTAs
+  const double n2_cta = block_sum(n2, scratch);
+  const int bid = blockIdx.x;
+  for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)bid * p_pad + k] = tacc[k];
+  if (tid == 0) a.w.part_n2[bid] = n2_cta;
+  __threadfence();
+  __syncthreads();
+  const int grp = bid / kGroup;
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int gsize = min(kGroup, (int)gridDim.x - grp * kGroup);
+  if (tid == 0) s_last = (atomicAdd(&a.w.counters[grp], 1u) == (unsigned)(gsize - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int k = tid; k < nlag; k += kThreads) {
+    double sum = 0.0;
+    for (int q = 0; q < gsize; ++q) sum += __ldcg(&a.w.part_t[(size_t)(grp * kGroup + q) * p_pad + k]);
+    a.w.grp_t[(size_t)grp * p_pad + k] = sum;
+  }
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < gsize; ++q) sum += __ldcg(&a.w.part_n2[grp * kGroup + q]);
+    a.w.grp_n2[grp] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&a.w.counters[kMaxGroups], 1u) == (unsigned)(ngroups - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // final reduction into tacc (lag order) and n2
+  for (int k = tid; k < nlag; k += kThreads) {
+    double sum = 0.0;
+    for (int q = 0; q < ngroups; ++q) sum += __ldcg(&a.w.grp_t[(size_t)q * p_pad + k]);
+    tacc[k] = sum;
+  }
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < ngroups; ++q) sum += __ldcg(&a.w.grp_n2[q]);
+    scratch[8] = sum;
+    for (int q = 0; q < ngroups; ++q) a.w.counters[q] = 0u;
+    a.w.counters[kMaxGroups] = 0u;
+  }
+  __syncthreads();
+  const double n2_all = scratch[8];
+  __syncthreads();
+
+  if (tid == 0 && a.worklog) a.worklog[a.work_slot] = 1 + tail + 5 * (int)(sizeof(T) == 8);
+  switch (tail) {
+    case TAIL_STORE:
+      for (int j = tid; j < nlag; j += kThreads) a.out_t[j] = a.gram ? tacc[j] : tacc[nlag - 1 - j];
+      if (tid == 0 && a.out_n2) *a.out_n2 = n2_all;
+      break;
+    case TAIL_LSQR: tail_lsqr(a.w, st, tacc, n2_all, scratch); break;
+    case TAIL_NECORR: tail_necorr(a.w, st, tacc, n2_all, scratch); break;
+    case TAIL_CHECK: tail_check(a.w, st, tacc, n2_all, scratch); break;
+    case TAIL_GRAM: tail_gram(a.w, tacc, a.out_n2); break;
+    default: break;
+  }
+}
+
+template <typename T>
+static size_t pass_smem(int p_pad) {
+  constexpr int TILE = TileCfg<T>::TILE;
+  size_t b = sizeof(T) * ((size_t)phys_size(TILE + p_pad + 16) + phys_size(TILE) + p_pad +
+                          (size_t)(kThreads / 32) * p_pad);
+  b += sizeof(double) * ((size_t)p_pad + 16 + 16);
+  return b;
+}
+
+template <typename T>
+cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
+  const size_t smem = pass_smem<T>(a.p_pad);
+  static int configured[2] = {0, 0};
+  const int which = sizeof(T) == 8;
+  if (!configured[which]) {
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured[which] = 1;
+  }
+  const long long ntiles = (a.m + TileCfg<T>::TILE - 1) / TileCfg<T>::TILE;
+  int g = (int)lmin((long long)grid, ntiles);
+  if (g < 1) g = 1;
+  pass_kernel<T><<<g, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pass<float>(const PassArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_pass<double>(const PassArgs<double>&, int, cudaStream_t);
+
+size_t pass_smem_bytes(int is_double, int p_pad) {
+  return is_double ? pass_smem<double>(p_pad) : pass_smem<float>(p_pad);
+}
+int pass_tile_rows(int is_double) { return is_double ? TileCfg<double>::TILE : TileCfg<float>::TILE; }
+const void* pass_kernel_ptr(int is_double) {
+  return is_double ? (const void*)pass_kernel<double> : (const void*)pass_kernel<float>;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Preconditioner: ||X||_F, a power-iteration estimate of ||X||_2, Cholesky G = R^T R (upper R, in place),
+// M = R^{-1} and M^T (float64 and float copies). One CTA; G is symmetric on entry.
+__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond) {
+  const int p = w.p;
+  DevState* st = w.st;
+  __shared__ double scratch[16];
+  __shared__ int s_fail;
+  __shared__ double s_val[2];
+  double* G = w.G;
+  // ||X||_F^2 = trace(G)
+  double tr = 0.0, dmax = 0.0;
+  for (int j = threadIdx.x; j < p; j += kThreads) {
+    tr += G[(size_t)j * p + j];
+    dmax = fmax(dmax, G[(size_t)j * p + j]);
+  }
+  tr = block_sum(tr, scratch);
+  // block max of the diagonal
+  {
+    double v = dmax;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = 0.0;
+      for (int k = 0; k < kThreads / 32; ++k) r = fmax(r, scratch[k]);
+      s_val[0] = r;
+    }
+    __syncthreads();
+    dmax = s_val[0];
+    __syncthreads();
+  }
+  // power iteration on G for lambda_max = ||X||_2^2 (w.t, w.g as work vectors)
+  double* x = w.t;
+  double* yv = w.g;
+  for (int j = threadIdx.x; j < p; j += kThreads) x[j] = 1.0 / sqrt((double)p);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < 24; ++it) {
+    for (int i = threadIdx.x; i < p; i += kThreads) {
+      double acc = 0.0;
+      for (int j = 0; j < p; ++j) acc = fma(G[(size_t)j * p + i], x[j], acc);
+      yv[i] = acc;
+    }
+    __syncthreads();
+    double nrm = sqrt(vec_norm2(yv, p, scratch));
+    double dot = 0.0;
+    for (int j = threadIdx.x; j < p; j += kThreads) dot += x[j] * yv[j];
+    lam = block_sum(dot, scratch);
+    for (int j = threadIdx.x; j < p; j += kThreads) x[j] = nrm > 0 ? yv[j] / nrm : 0.0;
+    __syncthreads();
+  }
+  if (!isfinite(tr) || !isfinite(*w.bnorm2)) {
+    if (threadIdx.x == 0) {
+      st->status = TOLS_ERR_NONFINITE;
+      st->phase = PH_DONE;
+      st->done = 1;
+      st->precond = 0;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    st->bnorm = sqrt(fmax(*w.bnorm2, 0.0));
+    st->anorm_f = sqrt(fmax(tr, 0.0));
+    st->anorm_2 = sqrt(fmax(lam, 0.0));
+    if (!(st->anorm_2 > 0.0)) st->anorm_2 = st->anorm_f;
+    s_fail = 0;
+  }
+  __syncthreads();
+
+  // Cholesky G = R^T R on the upper triangle (right-looking), first without a shift. If a pivot falls to
+  // rounding level (<= p u max_j G_jj, u of the precision G was formed in: G singular at working precision) or
+  // the factor has kappa(R)^2 u > 1e-3 (not trustworthy), G is refactored with the shift
+  // lambda = 10 p u max_j G_jj, which bounds kappa(X R^{-1}) by about sqrt(lambda) kappa(X). A singular G is
+  // flagged: if the solve then turns out compatible (an exactly rank-deficient X), the host repeats it with plain
+  // LSQR from zero, which returns the minimum-norm solution (Thm. "Solution to OLS problem").
+  const double ueps = st->mixed ? 5.96e-8 : 1.11e-16;
+  if (want_precond) {
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) w.M[q] = G[q];  // keep G for a refactor
+    __syncthreads();
+  }
+  for (int attempt = 0; attempt < 2 && want_precond; ++attempt) {
+    double lambda = 0.0;
+    if (attempt == 1) {
+      lambda = 10.0 * (double)p * ueps * dmax;
+      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.M[q];
+      __syncthreads();
+      for (int j = threadIdx.x; j < p; j += kThreads) G[(size_t)j * p + j] += lambda;
+      if (threadIdx.x == 0) s_fail = 0;
+      __syncthreads();
+    }
+    const double tiny = attempt == 0 ? (double)p * ueps * dmax : 1e-3 * lambda;
+    for (int k = 0; k < p; ++k) {
+      if (threadIdx.x == 0) {
+        const double piv = G[(size_t)k * p + k];
+        if (!(piv > tiny)) s_fail = 1;
+        else G[(size_t)k * p + k] = sqrt(piv);
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const double rkk = G[(size_t)k * p + k];
+      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) G[(size_t)k * p + j] /= rkk;
+      __syncthreads();
+      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) {
+        const double rkj = G[(size_t)k * p + j];
+        for (int i = k + 1; i <= j; ++i) G[(size_t)i * p + j] -= G[(size_t)k * p + i] * rkj;
+      }
+      __syncthreads();
+    }
+    if (s_fail) {
+      if (attempt == 1) break;                     // even the shifted matrix failed: no preconditioner
+      if (threadIdx.x == 0) st->singular = 1;      // singular at working precision: refactor with the shift
+      __syncthreads();
+      continue;
+    }
+    // kappa(R) >= max R_jj / min R_jj
+    double rmax = 0.0, rmin = 1e300;
+    for (int j = threadIdx.x; j < p; j += kThreads) {
+      rmax = fmax(rmax, G[(size_t)j * p + j]);
+      rmin = fmin(rmin, G[(size_t)j * p + j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { scratch[threadIdx.x >> 5] = rmax; scratch[8 + (threadIdx.x >> 5)] = rmin; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 1e300;
+      for (int q = 0; q < kThreads / 32; ++q) { a = fmax(a, scratch[q]); b = fmin(b, scratch[8 + q]); }
+      s_val[1] = b > 0 ? a / b : 1e300;
+    }
+    __syncthreads();
+    const double cond = s_val[1];
+    if (attempt == 0 && cond * cond * ueps <= 1e-3) break;  // unshifted factor is trustworthy
+  }
+  const int ok = want_precond && !s_fail;
+  if (ok) {
+    // M = R^{-1}: column c by back substitution (each thread its own columns)
+    for (int c = threadIdx.x; c < p; c += kThreads) {
+      for (int i = c + 1; i < p; ++i) w.M[(size_t)i * p + c] = 0.0;
+      w.M[(size_t)c * p + c] = 1.0 / G[(size_t)c * p + c];
+      for (int i = c - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int l = i + 1; l <= c; ++l) acc = fma(G[(size_t)i * p + l], w.M[(size_t)l * p + c], acc);
+        w.M[(size_t)i * p + c] = -acc / G[(size_t)i * p + i];
+      }
+    }
+    __syncthreads();
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) {
+      const int i = (int)(q / p), j = (int)(q % p);
+      const double mv = w.M[q];
+      w.Mt[(size_t)j * p + i] = mv;
+      w.M32[q] = (float)mv;
+      w.Mt32[(size_t)j * p + i] = (float)mv;
+    }
+    if (threadIdx.x == 0) {
+      st->precond = 1;
+      st->cond_est = s_val[1];
+    }
+  } else {
+    if (threadIdx.x == 0) { st->precond = 0; st->cond_est = 0.0; }
+  }
+}
+
+cudaError_t launch_precond(Work w, int want_precond, cudaStream_t s) {
+  precond_kernel<<<1, kThreads, 0, s>>>(w, want_precond);
+  return cudaGetLastError();
+}
+
+// LSQR start on rhs = b with X^T b = h and ||b|| = bnorm (already in state).
+__global__ void __launch_bounds__(kThreads) init_lsqr_kernel(Work w) {
+  __shared__ double scratch[16];
+  DevState* st = w.st;
+  for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
+  __syncthreads();
+  start_lsqr(w, st, w.h, st->bnorm, scratch);
+}
+
+// Warm start: phi already holds a guess; the first pass is a residual check.
+__global__ void __launch_bounds__(kThreads) init_check_kernel(Work w) {
+  __shared__ double scratch[16];
+  schedule_check(w, w.st, scratch);
+}
+
+cudaError_t launch_init_lsqr(Work w, int warm, cudaStream_t s) {
+  if (warm) init_check_kernel<<<1, kThreads, 0, s>>>(w);
+  else init_lsqr_kernel<<<1, kThreads, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+// Copy the best iterate into phi when the solve did not converge.
+__global__ void finish_kernel(Work w) {
+  DevState* st = w.st;
+  if (st->status != TOLS_OK && st->ne_best < st->ne_ratio) {
+    for (int j = threadIdx.x; j < w.p; j += blockDim.x) w.phi[j] = w.best[j];
+    __syncthreads();
+    if (threadIdx.x == 0) { st->ne_ratio = st->ne_best; st->rnorm = st->rnorm_best; }
+  }
+}
+cudaError_t launch_finish(Work w, cudaStream_t s) {
+  finish_kernel<<<1, kThreads, 0, s>>>(w);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+__global__ void convert_f32_kernel(const double* __restrict__ y, float* __restrict__ y32, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y32[i] = (float)y[i];
+}
+cudaError_t launch_convert_f32(const double* y, float* y32, long long n, cudaStream_t s) {
+  const int grid = (int)lmin((n + 255) / 256, 152 * 16);
+  convert_f32_kernel<<<grid, 256, 0, s>>>(y, y32, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Row norms of X (a float64 scan of y^2 local to each tile, so that cancellation is bounded by the tile):
+//   rn2[i] = sum_{t=i}^{i+p-1} y[t]^2,  ||X||_F^2 = sum_i rn2[i].
+constexpr int kScanTile = 2048;
+__global__ void __launch_bounds__(kThreads) row_norms_kernel(const double* __restrict__ y, long long n, int p,
+                                                             double* __restrict__ rn2, double* part) {
+  extern __shared__ double sq[];  // kScanTile + p + 1
+  __shared__ double scratch[16];
+  const long long m = n - p;
+  const long long i0 = (long long)blockIdx.x * kScanTile;
+  const int rows = (int)min((long long)kScanTile, m - i0);
+  const int len = rows + p;  // y[i0 .. i0+rows+p-1]
+  // inclusive prefix of y^2 over the window, in shared memory: sq[q+1] = sum_{s<=q} y[i0+s]^2
+  const int per = (len + kThreads - 1) / kThreads;
+  const int beg = threadIdx.x * per, end = min(len, beg + per);
+  double run = 0.0;
+  for (int q = beg; q < end; ++q) {
+    const double v = y[i0 + q];
+    run += v * v;
+    sq[q + 1] = run;
+  }
+  // exclusive scan of per-thread totals
+  __shared__ double tot[kThreads];
+  tot[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < kThreads; ++k) { const double t = tot[k]; tot[k] = acc; acc += t; }
+    sq[0] = 0.0;
+  }
+  __syncthreads();
+  const double off = tot[threadIdx.x];
+  for (int q = beg; q < end; ++q) sq[q + 1] += off;
+  __syncthreads();
+  double loc = 0.0;
+  for (int r = threadIdx.x; r < rows; r += kThreads) {
+    const double v = sq[r + p] - sq[r];
+    if (rn2) rn2[i0 + r] = v;
+    loc += v;
+  }
+  loc = block_sum(loc, scratch);
+  if (threadIdx.x == 0) part[blockIdx.x] = loc;
+}
+
+__global__ void sum_parts_kernel(const double* part, int count, double* out) {
+  __shared__ double scratch[16];
+  double s = 0.0;
+  // fixed order: each thread a contiguous chunk, then the block sum
+  const int per = (count + kThreads - 1) / kThreads;
+  for (int q = threadIdx.x * per; q < min(count, (int)(threadIdx.x + 1) * per); ++q) s += part[q];
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) *out = s;
+}
+
+cudaError_t launch_row_norms(const double* y, long long n, int p, double* rn2, double* fro2_dev, double* scratch,
+                             cudaStream_t s) {
+  const long long m = n - p;
+  const int blocks = (int)((m + kScanTile - 1) / kScanTile);
+  const size_t smem = sizeof(double) * (kScanTile + p + 2);
+  cudaError_t e = cudaFuncSetAttribute(row_norms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  if (e != cudaSuccess) return e;
+  row_norms_kernel<<<blocks, kThreads, smem, s>>>(y, n, p, rn2, scratch);
+  sum_parts_kernel<<<1, kThreads, 0, s>>>(scratch, blocks, fro2_dev);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Leverage scores (Section 3.1).
+constexpr int kLevTile = 4096;
+__global__ void __launch_bounds__(kThreads) sumsq_kernel(const double* __restrict__ y, long long cnt, double* part) {
+  __shared__ double scratch[16];
+  const long long i0 = (long long)blockIdx.x * kLevTile;
+  double s = 0.0;
+  for (long long i = i0 + threadIdx.x; i < min(cnt, i0 + kLevTile); i += kThreads) s = fma(y[i], y[i], s);
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void lev_p1_kernel(const double* __restrict__ y, long long cnt, const double* total, double* lev) {
+  const double inv = 1.0 / *total;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+    lev[i] = y[i] * y[i] * inv;
+}
+cudaError_t launch_leverage_p1(const double* y, long long n, double* lev, double* scratch, cudaStream_t s) {
+  const long long cnt = n - 1;
+  const int blocks = (int)((cnt + kLevTile - 1) / kLevTile);
+  sumsq_kernel<<<blocks, kThreads, 0, s>>>(y, cnt, scratch + 1);
+  sum_parts_kernel<<<1, kThreads, 0, s>>>(scratch + 1, blocks, scratch);
+  const int grid = (int)lmin((cnt + 255) / 256, 152 * 16);
+  lev_p1_kernel<<<grid, 256, 0, s>>>(y, cnt, scratch, lev);
+  return cudaGetLastError();
+}
+
+// lev[i] = lev_prev[i] + r[i]^2 / ||r||^2, pi[i] = lev[i] / p; r stored by a pass, ||r||^2 in *rr.
+__global__ void lev_update_kernel(const double* __restrict__ r, long long m, const double* rr,
+                                  const double* __restrict__ lev_prev, double* lev, double* pi, int p) {
+  const double inv = 1.0 / *rr;
+  const double invp = 1.0 / (double)p;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x) {
+    const double v = fma(r[i] * r[i], inv, lev_prev[i]);
+    lev[i] = v;
+    if (pi) pi[i] = v * invp;
+  }
+}
+cudaError_t launch_leverage_step(const double* r, long long m, int p, const double* rr, const double* lev_prev,
+                                 double* lev, double* pi, double* /*unused*/, cudaStream_t s) {
+  const int grid = (int)lmin((m + 255) / 256, 152 * 16);
+  lev_update_kernel<<<grid, 256, 0, s>>>(r, m, rr, lev_prev, lev, pi, p);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+__global__ void check_finite_kernel(const double* __restrict__ y, long long n, int* flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(y[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+cudaError_t launch_check_finite(const double* y, long long n, int* flag, cudaStream_t s) {
+  const int grid = (int)lmin((n + 255) / 256, 152 * 8);
+  check_finite_kernel<<<grid, 256, 0, s>>>(y, n, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace tols

@@ -148,6 +148,28 @@ int toeplitz_ols_stream_close(tols_ctx* ctx, int handle);
 int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long long n, int p, const double* d_v,
                          const void* d_u_old, double c, void* d_u_new, double* d_xtu, double* unorm2);
 
+/* Allocation-free variant of toeplitz_ols_gk_pass. The paper has no counterpart: this exists for callers that
+ * cannot let the library allocate device memory — applications whose device memory is owned by another
+ * allocator (a framework's caching allocator, or a pool reserved up front to a fixed budget), where an extra
+ * cudaMalloc could fail or break the budget, and latency-critical loops that cannot afford cudaMalloc/cudaFree,
+ * which can synchronise the device. It needs no context and calls no allocating routine.
+ *   - Same operation and arguments as toeplitz_ols_gk_pass, except: ||u_new||^2 is written to d_unorm2 (one
+ *     double, device), and the call only enqueues work on cuda_stream (a cudaStream_t; NULL = the legacy default
+ *     stream) of the current device and returns without waiting: synchronise the stream before reading outputs.
+ *   - The cross-CTA partial sums live in one fixed array of about 660 KB inside the library image, present on
+ *     every GPU that loads the library until the process exits. Its size limits p to TOLS_NOALLOC_MAX_P; larger
+ *     p returns TOLS_ERR_ARG, as do n <= p, a bad precision and null d_y, d_v, d_xtu or d_unorm2.
+ *   - The first call on a device looks up that array's device address (cudaGetSymbolAddress) with that device
+ *     current; make this first call before any stream capture on that device.
+ *   - Every call on a device shares the one array: calls whose work overlaps on the GPU (different streams, or
+ *     different host threads) race and give wrong results. Serialise them (one stream, or events). Each call
+ *     clears the arrival counters it relies on before its kernel runs.
+ * Errors: TOLS_ERR_ARG, TOLS_ERR_NO_DEVICE (no current device), TOLS_ERR_CUDA (lookup or launch failed). */
+#define TOLS_NOALLOC_MAX_P 256
+int toeplitz_ols_gk_pass_noalloc(int precision, const void* d_y, long long n, int p, const double* d_v,
+                                 const void* d_u_old, double c, void* d_u_new, double* d_xtu, double* d_unorm2,
+                                 void* cuda_stream);
+
 /* The Gram matrix G = X^T X (p*p doubles, row-major, device) and h = X^T b (p doubles, device) from one
  * correlation pass over y plus O(p^2) edge corrections; TOLS_MIXED forms the lag sums from float32 products. */
 int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, double* d_G,

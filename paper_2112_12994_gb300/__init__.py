@@ -28,6 +28,7 @@ TOLS_ERR_DEVICE_TIMEOUT = -5
 TOLS_ERR_NO_DEVICE = -6
 TOLS_ERR_BUSY = -7
 TOLS_MAX_P = 1024
+TOLS_NOALLOC_MAX_P = 256
 
 TOLS_FP64 = 0
 TOLS_MIXED = 1
@@ -92,6 +93,7 @@ SIGNATURES = {
     "toeplitz_ols_stream_solve": (_I, [_P, _I, _P, _D, ctypes.POINTER(tols_info)]),
     "toeplitz_ols_stream_close": (_I, [_P, _I]),
     "toeplitz_ols_gk_pass": (_I, [_P, _I, _P, _LL, _I, _P, _P, ctypes.c_double, _P, _P, _D]),
+    "toeplitz_ols_gk_pass_noalloc": (_I, [_I, _P, _LL, _I, _P, _P, ctypes.c_double, _P, _P, _P, _P]),
     "toeplitz_ols_gram": (_I, [_P, _I, _P, _LL, _I, _P, _P, _D]),
     "toeplitz_ols_row_norms": (_I, [_P, _P, _LL, _I, _P, _D]),
     "toeplitz_ols_residual": (_I, [_P, _P, _LL, _I, _P, _P, _D]),
@@ -250,6 +252,14 @@ def toeplitz_ols_gk_pass(ctx: Context, precision: int, d_y, n: int, p: int, d_v,
     ctx.check(lib.toeplitz_ols_gk_pass(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_v), _ptr(d_u_old), c,
                                        _ptr(d_u_new), _ptr(d_xtu), ctypes.byref(n2)), "toeplitz_ols_gk_pass")
     return n2.value
+
+
+def toeplitz_ols_gk_pass_noalloc(precision: int, d_y, n: int, p: int, d_v, d_u_old, c: float, d_u_new, d_xtu,
+                                 d_unorm2, stream=None) -> int:
+    """The allocation-free fused pass (no context): enqueues on `stream` (a cudaStream_t handle or None) and
+    returns the status code without waiting; ||u_new||^2 goes to the device scalar d_unorm2."""
+    return lib.toeplitz_ols_gk_pass_noalloc(precision, _ptr(d_y), n, p, _ptr(d_v), _ptr(d_u_old), c, _ptr(d_u_new),
+                                            _ptr(d_xtu), _ptr(d_unorm2), stream)
 
 
 def toeplitz_ols_gram(ctx: Context, precision: int, d_y, n: int, p: int, d_G, d_h):

@@ -20,7 +20,7 @@ constexpr int kMaxGrid = 152 * 4;        // upper bound on pass grid size (parti
 constexpr int kMaxGroups = (kMaxGrid + kGroup - 1) / kGroup;
 
 // Round p up to the lag-chunk granularity used by the direct kernels.
-__host__ __device__ inline int pad_p(int p) { return (p + 15) & ~15; }
+__host__ __device__ constexpr int pad_p(int p) { return (p + 15) & ~15; }
 
 // What the last CTA of a pass does after the grid-wide reduction (see tails in tols_kernels.cu).
 enum TailMode : int {

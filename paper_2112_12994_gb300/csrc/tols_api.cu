@@ -46,6 +46,10 @@ struct tols_ctx {
   bool own_stream = false;
   size_t used = 0;
   DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf;
+  // batched solves: pooled per-series buffers
+  DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
+  double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
+  size_t h_stage_cap = 0;
   DevState* h_state = nullptr;  // pinned copy of the device state
   std::string err;
   std::map<int, StreamSeries> streams;
@@ -472,6 +476,272 @@ int host_solve(tols_ctx* ctx, const double* y, long long n, int p, double tol, d
   return rc;
 }
 
+
+// ------------------------------------------------------------------------------------------------------
+// Batched solves: every series gets its own slices of pooled buffers; one tile list per precision covers all
+// series; burst launches of the batched pass kernel (captured once into a CUDA graph) run until every series has
+// reached its final state.
+constexpr int kTileF = 4096, kTileD = 2048;   // rows per tile of the float / double pass kernels
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct BatchPlan {
+  std::vector<int> idx;                      // caller index of every valid series
+  std::vector<long long> n, m, off_y, off_u, off_part, off_cnt, ntd, ntf;
+  std::vector<int> p;
+  std::vector<size_t> off_vec, off_phi, off_mat;
+  size_t y_elems = 0, u_elems = 0, part_doubles = 0, cnt_uints = 0, vec_doubles = 0, phi_doubles = 0,
+         mat_bytes = 0;
+  long long tiles_f = 0, tiles_d = 0;
+  int p_pad_max = 16;
+};
+
+void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status) {
+  for (int k = 0; k < count; ++k) {
+    if (p[k] < 1 || p[k] > TOLS_MAX_P || n[k] <= p[k]) { status[k] = TOLS_ERR_ARG; continue; }
+    const long long nn = n[k], mm = nn - p[k];
+    const int pp1 = pad_p(p[k] + 1);
+    B.idx.push_back(k);
+    B.n.push_back(nn);
+    B.m.push_back(mm);
+    B.p.push_back(p[k]);
+    B.off_y.push_back((long long)B.y_elems);
+    B.y_elems += align_up((size_t)nn, 64);
+    B.off_u.push_back((long long)B.u_elems);
+    B.u_elems += align_up((size_t)mm, 64);
+    const long long ntd = (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
+    const long long ngr = (ntd + kGroup - 1) / kGroup;
+    B.ntd.push_back(ntd);
+    B.ntf.push_back(ntf);
+    B.off_part.push_back((long long)B.part_doubles);
+    B.part_doubles += (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr);
+    B.off_cnt.push_back((long long)B.cnt_uints);
+    B.cnt_uints += (size_t)align_up((size_t)ngr + 1, 4);
+    B.off_vec.push_back(B.vec_doubles);
+    B.vec_doubles += 10 * (size_t)pp1;
+    B.off_phi.push_back(B.phi_doubles);
+    B.phi_doubles += (size_t)p[k];
+    B.off_mat.push_back(B.mat_bytes);
+    B.mat_bytes += align_up(sizeof(double) * 3 * (size_t)p[k] * p[k] + sizeof(float) * 2 * (size_t)p[k] * p[k], 256);
+    B.tiles_f += ntf;
+    B.tiles_d += ntd;
+    B.p_pad_max = std::max(B.p_pad_max, pp1);
+  }
+}
+
+int batch_grid(tols_ctx* ctx, int is_double, int p_pad) {
+  int nb = 0;
+  cudaFuncSetAttribute(batch_kernel_ptr(is_double), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(is_double), kThreads,
+                                                    pass_smem_bytes(is_double, p_pad)) != cudaSuccess || nb < 1)
+    nb = 1;
+  return ctx->sms * std::min(nb, 4);
+}
+
+// d_y_packed: device series packed at B.off_y. Results: phi (device, packed at B.off_phi), states (host).
+int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states) {
+  const int cnt = (int)B.idx.size();
+  if (cnt == 0) return TOLS_OK;
+  int rc;
+  if (mixed && (rc = ensure(ctx, ctx->b_y32, sizeof(float) * B.y_elems))) return rc;
+  const size_t ues = mixed ? sizeof(float) : sizeof(double);
+  if ((rc = ensure(ctx, ctx->b_u0, ues * B.u_elems)) || (rc = ensure(ctx, ctx->b_u1, ues * B.u_elems))) return rc;
+  if ((rc = ensure(ctx, ctx->b_part, sizeof(double) * B.part_doubles))) return rc;
+  const bool fresh_cnt = ctx->b_cnt.cap < sizeof(unsigned) * (B.cnt_uints + 4);
+  if ((rc = ensure(ctx, ctx->b_cnt, sizeof(unsigned) * (B.cnt_uints + 4)))) return rc;
+  if ((rc = ensure(ctx, ctx->b_vecs, sizeof(double) * B.vec_doubles))) return rc;
+  if ((rc = ensure(ctx, ctx->b_phi, sizeof(double) * B.phi_doubles))) return rc;
+  if ((rc = ensure(ctx, ctx->b_mats, B.mat_bytes))) return rc;
+  if ((rc = ensure(ctx, ctx->b_state, sizeof(DevState) * cnt))) return rc;
+  if ((rc = ensure(ctx, ctx->b_series, sizeof(BatchSeries) * cnt))) return rc;
+  if ((rc = ensure(ctx, ctx->b_tiles, sizeof(int) * (size_t)(B.tiles_f + B.tiles_d)))) return rc;
+  (void)fresh_cnt;
+  // counters (and the done counter after them) start at zero; every pass leaves the counters at zero
+  unsigned int* d_done = (unsigned int*)ctx->b_cnt.p + B.cnt_uints;
+  CK(cudaMemsetAsync(ctx->b_cnt.p, 0, sizeof(unsigned) * (B.cnt_uints + 4), ctx->stream));
+
+  const int max_iter_cfg = ctx->cfg.max_iter;
+  const int max_sweeps = ctx->cfg.max_sweeps > 0 ? ctx->cfg.max_sweeps : 6;
+  std::vector<BatchSeries> hs(cnt);
+  std::vector<int> tiles((size_t)(B.tiles_f + B.tiles_d));
+  states.assign(cnt, DevState{});
+  long long tf = 0, td = 0;
+  for (int k = 0; k < cnt; ++k) {
+    BatchSeries& S = hs[k];
+    memset(&S, 0, sizeof S);
+    Work& w = S.w;
+    const int p = B.p[k];
+    const size_t pp1 = (size_t)pad_p(p + 1);
+    w.n = B.n[k];
+    w.m = B.m[k];
+    w.p = p;
+    w.p_pad = (int)pp1;
+    w.y64 = (const double*)ctx->b_y64.p + B.off_y[k];
+    w.y32 = mixed ? (float*)ctx->b_y32.p + B.off_y[k] : nullptr;
+    w.U[0] = (char*)ctx->b_u0.p + ues * B.off_u[k];
+    w.U[1] = (char*)ctx->b_u1.p + ues * B.off_u[k];
+    double* q = (double*)ctx->b_part.p + B.off_part[k];
+    const long long ntd = B.ntd[k], ngr = (ntd + kGroup - 1) / kGroup;
+    w.part_t = q; q += ntd * pp1;
+    w.part_n2 = q; q += ntd;
+    w.grp_t = q; q += ngr * pp1;
+    w.grp_n2 = q;
+    w.counters = (unsigned int*)ctx->b_cnt.p + B.off_cnt[k];
+    q = (double*)ctx->b_vecs.p + B.off_vec[k];
+    w.v = q; q += pp1;
+    w.w = q; q += pp1;
+    w.z = q; q += pp1;
+    w.d = q; q += pp1;
+    w.g = q; q += pp1;
+    w.h = q; q += pp1;
+    w.t = q; q += pp1;
+    w.best = q; q += pp1;
+    w.bnorm2 = q; q += pp1;
+    w.phi = (double*)ctx->b_phi.p + B.off_phi[k];
+    char* mb = (char*)ctx->b_mats.p + B.off_mat[k];
+    const size_t pq = (size_t)p * p;
+    w.G = (double*)mb;
+    w.M = w.G + pq;
+    w.Mt = w.M + pq;
+    w.M32 = (float*)(w.Mt + pq);
+    w.Mt32 = w.M32 + pq;
+    w.st = (DevState*)ctx->b_state.p + k;
+    S.tile0_f = tf;               // index in the float tile list
+    for (long long t = 0; t < B.ntf[k]; ++t) tiles[(size_t)(tf + t)] = k;
+    for (long long t = 0; t < B.ntd[k]; ++t) tiles[(size_t)(B.tiles_f + td + t)] = k;
+    tf += B.ntf[k];
+    td += B.ntd[k];
+    S.tile0_d = td - B.ntd[k];   // index in the double tile list (stored after the float list)
+    DevState& st = states[k];
+    memset(&st, 0, sizeof st);
+    const int max_iter = max_iter_cfg > 0 ? max_iter_cfg : 4 * p + 200;
+    st.tol = tol;
+    st.tol_inner = 1e-5;
+    st.est_ratio = tol;
+    st.max_iter = max_iter;
+    st.iter_cap = mixed ? std::min(max_iter, 100) : max_iter;
+    st.max_sweeps = max_sweeps;
+    st.mixed = mixed ? 1 : 0;
+    st.mixed_ok = 1;
+    st.ne_ratio = 1e300;
+    st.ne_best = 1e300;
+    st.status = TOLS_NOT_CONVERGED;
+    st.phase = PH_LSQR;
+  }
+  const BatchSeries* d_series = (const BatchSeries*)ctx->b_series.p;
+  CK(cudaMemcpyAsync(ctx->b_series.p, hs.data(), sizeof(BatchSeries) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_state.p, states.data(), sizeof(DevState) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
+  BatchArgs a;
+  memset(&a, 0, sizeof a);
+  a.series = d_series;
+  a.tile_series_f = (const int*)ctx->b_tiles.p;
+  a.tile_series_d = (const int*)ctx->b_tiles.p + B.tiles_f;
+  a.tiles_f = B.tiles_f;
+  a.tiles_d = B.tiles_d;
+  a.done_count = d_done;
+  const int gf = batch_grid(ctx, 0, B.p_pad_max), gd = batch_grid(ctx, 1, B.p_pad_max);
+
+  // setup: float copy, Gram lag sums, preconditioner, LSQR start
+  if (mixed)
+    RUN(run_small(ctx, 11, [&] { return launch_convert_f32((const double*)ctx->b_y64.p, (float*)ctx->b_y32.p,
+                                                           (long long)B.y_elems, ctx->stream); }));
+  BatchArgs ag = a;
+  ag.gram = 1;
+  ag.gram_double = mixed ? 0 : 1;
+  ctx->launch_total++;
+  if (mixed) CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
+  else CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
+  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
+  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream); }));
+  RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
+
+  // iterations: a burst of batched passes captured once into a CUDA graph, replayed until all series are done
+  const int burst = mixed ? 6 : 4;
+  cudaGraphExec_t exec = nullptr;
+  auto enqueue_burst = [&]() -> int {
+    for (int k = 0; k < burst; ++k) {
+      ctx->launch_total++;
+      CK(mixed ? launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream)
+               : launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+    }
+    if (mixed) {
+      ctx->launch_total++;
+      CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+    }
+    return TOLS_OK;
+  };
+  if (!ctx->prof) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = ctx->launch_total;
+    rc = enqueue_burst();
+    ctx->launch_total = before;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "capture of the batched burst", e);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "instantiate the batched burst", e);
+  }
+  unsigned int* h_done = (unsigned int*)ctx->h_worklog;  // pinned, reused as a 4-byte landing slot
+  int max_iter_all = 0;
+  for (int k = 0; k < cnt; ++k) max_iter_all = std::max(max_iter_all, states[k].max_iter);
+  const long long max_rounds = ((long long)(max_iter_all + 4) * (max_sweeps + 2) * 2) / burst + 16;
+  int out = TOLS_OK;
+  for (long long round = 0;; ++round) {
+    if (exec) {
+      ctx->launch_total += burst + (mixed ? 1 : 0);
+      cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+      if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "cudaGraphLaunch", e); break; }
+    } else if ((out = enqueue_burst())) {
+      break;
+    }
+    cudaError_t e = cudaMemcpyAsync(h_done, d_done, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "batched poll", e); break; }
+    if ((out = flush_profile(ctx))) break;
+    if (*h_done >= (unsigned)cnt) break;
+    if (round > max_rounds) { out = fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "batched solve did not finish"); break; }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (out) return out;
+  RUN(run_small(ctx, 12, [&] { return launch_finish_batch(d_series, cnt, ctx->stream); }));
+  CK(cudaMemcpyAsync(states.data(), ctx->b_state.p, sizeof(DevState) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  RUN(flush_profile(ctx));
+  return TOLS_OK;
+}
+
+// After a batched pass: series that need the single-series path (mixed refinement that stalled, or an exactly
+// rank-deficient X) are solved again one by one. phi_out: device, packed like b_phi.
+int batch_fixups(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states,
+                 std::vector<int>& prec_used) {
+  const int cnt = (int)B.idx.size();
+  prec_used.assign(cnt, mixed ? TOLS_MIXED : TOLS_FP64);
+  for (int k = 0; k < cnt; ++k) {
+    const DevState& s = states[k];
+    const bool stalled = mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
+                         (s.mixed_ok == 0 || s.precond == 0);
+    const bool rankdef = s.singular && s.compatible && s.status >= 0;
+    if (!stalled && !rankdef) continue;
+    double* d_phi = (double*)ctx->b_phi.p + B.off_phi[k];
+    const double* d_y = (const double*)ctx->b_y64.p + B.off_y[k];
+    double rn = 0.0;
+    tols_info inf;
+    int rc = solve_device_impl(ctx, d_y, B.n[k], B.p[k], tol, d_phi, &rn, &inf, nullptr);
+    if (rc < 0) return rc;
+    DevState& t = states[k];
+    t.status = rc;
+    t.ne_ratio = inf.ne_ratio;
+    t.rnorm = inf.rnorm;
+    t.total_iter += inf.iters;
+    t.sweeps += inf.sweeps;
+    t.precond = inf.precond_used;
+    prec_used[k] = inf.precision_used;
+  }
+  return TOLS_OK;
+}
 }  // namespace
 
 // ======================================================================================================
@@ -553,9 +823,12 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
   if (!ctx) return TOLS_OK;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->y64, &ctx->y32, &ctx->u0, &ctx->u1, &ctx->part, &ctx->vecs,
-                    &ctx->mats, &ctx->state, &ctx->scratch, &ctx->rbuf};
+  DevBuf* bufs[] = {&ctx->y64,    &ctx->y32,   &ctx->u0,    &ctx->u1,     &ctx->part,    &ctx->vecs,
+                    &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
+                    &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
+                    &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles};
   for (DevBuf* b : bufs) release(ctx, *b);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
   if (ctx->h_worklog) cudaFreeHost(ctx->h_worklog);
   if (ctx->d_worklog) cudaFree(ctx->d_worklog);
@@ -591,18 +864,59 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n, const int* p,
                                double tol, double* const* phi, double* rnorm, tols_info* info) {
   if (!ctx || count < 0 || (count > 0 && (!y || !n || !p || !phi))) return TOLS_ERR_ARG;
+  if (count == 0) return TOLS_OK;
+  cudaSetDevice(ctx->device);
+  if (tol <= 0) tol = 1e-12;
+  std::vector<int> status(count, TOLS_OK);
+  BatchPlan B;
+  plan_batch(B, count, n, p, status);
+  for (int k : B.idx)
+    if (!y[k] || !phi[k]) return fail(ctx, TOLS_ERR_ARG, "null series or phi pointer");
+  int rc;
+  // stage the host series in pinned memory, then one copy to the device
+  if (ctx->h_stage_cap < B.y_elems) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_cap = 0;
+    if (cudaMallocHost(&ctx->h_stage, sizeof(double) * std::max<size_t>(B.y_elems, 1)) != cudaSuccess)
+      return fail(ctx, TOLS_ERR_OOM, "pinned staging buffer");
+    ctx->h_stage_cap = B.y_elems;
+  }
+  if ((rc = ensure(ctx, ctx->b_y64, sizeof(double) * std::max<size_t>(B.y_elems, 1)))) return rc;
+  for (size_t k = 0; k < B.idx.size(); ++k)
+    memcpy(ctx->h_stage + B.off_y[k], y[B.idx[k]], sizeof(double) * (size_t)B.n[k]);
+  CK(cudaMemcpyAsync(ctx->b_y64.p, ctx->h_stage, sizeof(double) * B.y_elems, cudaMemcpyHostToDevice, ctx->stream));
+  const bool mixed = ctx->cfg.precision == TOLS_MIXED;
+  std::vector<DevState> states;
+  if ((rc = batch_core(ctx, B, tol, mixed, states))) return rc;
+  std::vector<int> prec_used;
+  if ((rc = batch_fixups(ctx, B, tol, mixed, states, prec_used))) return rc;
+  std::vector<double> phis(B.phi_doubles);
+  if (!phis.empty()) {
+    CK(cudaMemcpyAsync(phis.data(), ctx->b_phi.p, sizeof(double) * B.phi_doubles, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
   int worst = TOLS_OK;
   for (int k = 0; k < count; ++k) {
-    tols_info one;
-    double rn = 0.0;
-    int rc = validate(ctx, n[k], p[k]);
-    if (!rc) rc = (!y[k] || !phi[k]) ? TOLS_ERR_ARG : host_solve(ctx, y[k], n[k], p[k], tol, phi[k], &rn, &one, nullptr);
-    if (rc < 0) memset(&one, 0, sizeof one);
-    one.status = rc;
-    if (info) info[k] = one;
-    if (rnorm) rnorm[k] = rn;
-    if (rc < 0) worst = worst < 0 ? std::min(worst, rc) : rc;
-    else if (worst >= 0) worst = std::max(worst, rc);
+    if (info) memset(&info[k], 0, sizeof(tols_info));
+    if (rnorm) rnorm[k] = 0.0;
+  }
+  for (size_t j = 0; j < B.idx.size(); ++j) {
+    const int k = B.idx[j];
+    const DevState& s = states[j];
+    status[k] = s.status;
+    memcpy(phi[k], phis.data() + B.off_phi[j], sizeof(double) * B.p[j]);
+    if (rnorm) rnorm[k] = s.rnorm;
+    if (info) {
+      fill_info(&info[k], s, prec_used[j]);
+    }
+  }
+  for (int k = 0; k < count; ++k) {
+    if (info) info[k].status = status[k];
+    const int rc2 = status[k];
+    if (rc2 < 0) worst = worst < 0 ? std::min(worst, rc2) : rc2;
+    else if (worst >= 0) worst = std::max(worst, rc2);
   }
   return worst;
 }

@@ -103,6 +103,24 @@ struct PassArgs {
   int work_slot;
 };
 
+// One series of a batch (device array). Its Work points at the series' own slices of the batch buffers; its
+// partial buffers hold one row per tile (of the float64 tile size, the larger count).
+struct BatchSeries {
+  Work w;
+  long long tile0_f, tile0_d;   // first index of this series in the float / double tile lists
+};
+
+// Arguments of a batched pass launch.
+struct BatchArgs {
+  const BatchSeries* series;
+  const int* tile_series_f;     // float tile list: tile -> series
+  const int* tile_series_d;     // double tile list: tile -> series
+  long long tiles_f, tiles_d;
+  int gram;                     // 1: Gram lag-sum pass (TAIL_GRAM) instead of a solver pass
+  int gram_double;              // for gram passes: which precision runs it
+  unsigned int* done_count;     // incremented once per series that reaches PH_DONE
+};
+
 // Launch helpers (tols_kernels.cu).
 size_t pass_smem_bytes(int is_double, int p_pad);
 int pass_tile_rows(int is_double);
@@ -110,6 +128,12 @@ const void* pass_kernel_ptr(int is_double);
 template <typename T>
 cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s);
+const void* batch_kernel_ptr(int is_double);
+cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s);
+cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s);
+cudaError_t launch_finish_batch(const BatchSeries* series, int count, cudaStream_t s);
 cudaError_t launch_convert_f32(const double* y, float* y32, long long n, cudaStream_t s);
 cudaError_t launch_precond(Work w, int mixed, cudaStream_t s);
 cudaError_t launch_init_lsqr(Work w, int mixed, cudaStream_t s);

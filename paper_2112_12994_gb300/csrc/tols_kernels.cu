@@ -454,240 +454,340 @@ __device__ void tail_gram(const Work& w, const double* ck, double* bnorm2_out) {
 }
 
 // ------------------------------------------------------------------------------------------------------
-// The pass kernel.
+// Pieces of the pass kernels (single series and batched).
 //
 // Shared memory (dynamic): ys[phys(TILE + p_pad + 16)] (T), us[phys(TILE)] (T), dr[p_pad] (T),
 // wpart[kThreads/32][p_pad] (T), tacc[p_pad + 16] (double), scratch[16] (double).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) pass_kernel(PassArgs<T> a) {
+struct Smem {
+  T *ys, *us, *dr, *wpart;
+  double *tacc, *scratch;
+  __device__ Smem(unsigned char* raw, int p_pad) {
+    constexpr int TILE = TileCfg<T>::TILE;
+    ys = reinterpret_cast<T*>(raw);
+    us = ys + phys_size(TILE + p_pad + 16);      // u_old tile, padded layout
+    dr = us + phys_size(TILE);                   // lag-reversed d
+    wpart = dr + p_pad;                          // per-warp partial X^T u of a tile: [kThreads/32][p_pad]
+    tacc = reinterpret_cast<double*>(wpart + (kThreads / 32) * p_pad);
+    scratch = tacc + p_pad + 16;
+  }
+};
+
+// For a solver-driven pass: which tail this kernel type runs for the series in state st, and its buffers
+// (U[0]/U[1] ping-pong; b is y + p). Returns false when the phase belongs to the other precision or is done.
+template <typename T>
+__device__ bool select_phase(const DevState* st, const T* y, int p, const Work& w, int& tail, const T*& u_old,
+                             T*& u_new, double& coef) {
+  const int ph = st->phase;
+  if (st->done || ph == PH_DONE) return false;
+  if (sizeof(T) == 8) {
+    if (ph == PH_CHECK) tail = TAIL_CHECK;
+    else if (ph == PH_LSQR && !st->mixed) tail = TAIL_LSQR;
+    else return false;
+  } else {
+    if (ph == PH_LSQR && st->mixed) tail = TAIL_LSQR;
+    else if (ph == PH_NECORR) tail = TAIL_NECORR;
+    else return false;
+  }
+  coef = st->coef;
+  const int it = (tail == TAIL_NECORR) ? st->inner_iter : st->iter;
+  if (tail == TAIL_CHECK) {
+    u_old = y + p;                                   // b
+    u_new = st->mixed ? nullptr : (T*)w.U[0];        // FP64: keep r for a restart
+  } else if (tail == TAIL_NECORR) {
+    u_old = it == 0 ? nullptr : (const T*)w.U[(it + 1) & 1];
+    u_new = (T*)w.U[it & 1];
+  } else {  // LSQR: the first pass reads the rhs (b on the first sweep, r stored in U[0] after a check)
+    const int from_b = (st->sweeps == 0);
+    if (it == 0) {
+      u_old = from_b ? y + p : (const T*)w.U[0];
+      u_new = (T*)w.U[1];
+    } else {
+      u_old = (const T*)w.U[(it & 1)];
+      u_new = (T*)w.U[(it + 1) & 1];
+    }
+  }
+  return true;
+}
+
+// Lag-reversed, scaled d into shared memory: dr[k] = d_scale * d[p-1-k], zero for k >= p.
+template <typename T>
+__device__ void load_dr(T* dr, const double* d, double d_scale, int p, int p_pad) {
+  for (int k = threadIdx.x; k < p_pad; k += kThreads) dr[k] = k < p ? (T)(d_scale * d[p - 1 - k]) : (T)0;
+}
+
+// One tile of rows [i0, i0 + TILE): u_new = X d - c u_old (or u = y itself for the Gram lag sums), its squared
+// norm (returned per thread) and the tile's X^T u contribution left in sm.wpart (per warp, lag order). The
+// caller synchronises before reading wpart.
+template <typename T>
+__device__ double process_tile(const Smem<T>& sm, const T* __restrict__ y, long long n, long long m, int p_pad,
+                               int nlag, int gram, const T* u_old, T* u_new, double coef, long long i0) {
   constexpr int RB = TileCfg<T>::RB;
   constexpr int KC = TileCfg<T>::KC;
   constexpr int TILE = TileCfg<T>::TILE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jl = ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
+  const int r0 = tid * RB;                       // this thread's rows within the tile
+  const int rows = (int)min((long long)TILE, m - i0);
+  const int wlen = TILE + p_pad + 16;
+  T* ys = sm.ys;
+  T* us = sm.us;
+  __syncthreads();                               // previous readers of ys / us / wpart are done
+  for (int q = tid; q < wlen; q += kThreads) {
+    const long long gi = i0 + q;
+    ys[phys(q)] = gi < n ? y[gi] : (T)0;
+  }
+  if (!gram && u_old) {
+    for (int q = tid; q < TILE; q += kThreads) us[phys(q)] = q < rows ? u_old[i0 + q] : (T)0;
+  }
+  __syncthreads();
 
-  DevState* st = a.w.st;
-  // Which solver phase this launch serves; all CTAs read the same state written by the previous launch.
+  double n2 = 0.0;
+  T uv[RB];
+  if (gram) {
+#pragma unroll
+    for (int q = 0; q < RB / 4; ++q) lds4<T>(ys, r0 + 4 * q, uv + 4 * q);
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      if (r0 + r >= rows) uv[r] = (T)0;
+  } else {
+    // u_new = X d - c u_old : sliding window of y held in registers, KC lags per step
+    T acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = (T)0;
+    if (r0 < rows) {
+      for (int k0 = 0; k0 < p_pad; k0 += KC) {
+        T yv[RB + KC];
+#pragma unroll
+        for (int q = 0; q < (RB + KC) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
+        T dv[KC];
+#pragma unroll
+        for (int q = 0; q < KC; ++q) dv[q] = sm.dr[k0 + q];
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+#pragma unroll
+          for (int r = 0; r < RB; ++r) acc[r] = fma(yv[r + q], dv[q], acc[r]);
+      }
+    }
+    T uo[RB];
+    if (u_old) {
+#pragma unroll
+      for (int q = 0; q < RB / 4; ++q) lds4<T>(us, r0 + 4 * q, uo + 4 * q);
+    }
+    T nn = (T)0;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      T u = (T)0;
+      if (r0 + r < rows) {
+        u = acc[r];
+        if (u_old) u = fma((T)(-coef), uo[r], u);
+      }
+      nn = fma(u, u, nn);
+      uv[r] = u;
+    }
+    n2 = (double)nn;
+    if (u_new && r0 < rows) {
+      T* dst = u_new + i0 + r0;
+      if (((reinterpret_cast<uintptr_t>(dst) & 15) == 0) && r0 + RB <= rows) {
+#pragma unroll
+        for (int q = 0; q < RB / 4; ++q) st4<T>(dst + 4 * q, uv + 4 * q);
+      } else {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r0 + r < rows) dst[r] = uv[r];
+      }
+    }
+  }
+
+  // tk[k] += sum_r u[r] y[r + k]: 8 lags at a time from the same conflict-free window loads, then a warp
+  // reduce-scatter (9 shuffles) leaves lag k0 + jl on lanes with (lane & 3) == 0.
+  for (int k0 = 0; k0 < nlag; k0 += 8) {
+    T t8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t8[q] = (T)0;
+    if (r0 < rows) {
+      T yv[RB + 8];
+#pragma unroll
+      for (int q = 0; q < (RB + 8) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int r = 0; r < RB; ++r) t8[q] = fma(uv[r], yv[r + q], t8[q]);
+    }
+    const T v = warp_reduce_scatter8<T>(t8, lane);
+    if ((lane & 3) == 0) sm.wpart[warp * p_pad + k0 + jl] = v;
+  }
+  return n2;
+}
+
+// Sum of the per-warp partials of lag k (fixed order).
+template <typename T>
+__device__ __forceinline__ double warp_parts_sum(const T* wpart, int p_pad, int k) {
+  T sum = (T)0;
+#pragma unroll
+  for (int q = 0; q < kThreads / 32; ++q) sum += wpart[q * p_pad + k];
+  return (double)sum;
+}
+
+// Two-level arrival of `nunits` partial results (unit u wrote part_t[u][.] and part_n2[u]): groups of kGroup
+// units, then the groups. Returns true in the CTA that arrived last overall, which then holds the totals in
+// tacc[0 .. nlag) and scratch[8], and has reset the counters it used. No waiting anywhere.
+__device__ bool arrive(const Work& w, long long unit, long long nunits, int nlag, int p_pad, double* tacc,
+                       double* scratch, int* s_last) {
+  const int tid = threadIdx.x;
+  const long long grp = unit / kGroup;
+  const long long ngroups = (nunits + kGroup - 1) / kGroup;
+  const int gsize = (int)min((long long)kGroup, nunits - grp * kGroup);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_last = (atomicAdd(&w.counters[grp], 1u) == (unsigned)(gsize - 1));
+  __syncthreads();
+  if (!*s_last) return false;
+  __threadfence();
+  for (int k = tid; k < nlag; k += kThreads) {
+    double sum = 0.0;
+    for (int q = 0; q < gsize; ++q) sum += __ldcg(&w.part_t[(size_t)(grp * kGroup + q) * p_pad + k]);
+    w.grp_t[(size_t)grp * p_pad + k] = sum;
+  }
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < gsize; ++q) sum += __ldcg(&w.part_n2[grp * kGroup + q]);
+    w.grp_n2[grp] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_last = (atomicAdd(&w.counters[ngroups], 1u) == (unsigned)(ngroups - 1));
+  __syncthreads();
+  if (!*s_last) return false;
+  __threadfence();
+  for (int k = tid; k < nlag; k += kThreads) {
+    double sum = 0.0;
+    for (long long q = 0; q < ngroups; ++q) sum += __ldcg(&w.grp_t[(size_t)q * p_pad + k]);
+    tacc[k] = sum;
+  }
+  if (tid == 0) {
+    double sum = 0.0;
+    for (long long q = 0; q < ngroups; ++q) sum += __ldcg(&w.grp_n2[q]);
+    scratch[8] = sum;
+    for (long long q = 0; q <= ngroups; ++q) w.counters[q] = 0u;
+  }
+  __syncthreads();
+  return true;
+}
+
+// The scalar step after a pass (run by the last CTA with the totals in tacc / n2_all).
+template <typename T>
+__device__ void run_tail(int tail, const Work& w, int gram, int nlag, const double* tacc, double n2_all,
+                         double* scratch, double* out_t, double* out_n2) {
+  DevState* st = w.st;
+  switch (tail) {
+    case TAIL_STORE:
+      if (out_t)
+        for (int j = threadIdx.x; j < nlag; j += kThreads) out_t[j] = gram ? tacc[j] : tacc[nlag - 1 - j];
+      if (threadIdx.x == 0 && out_n2) *out_n2 = n2_all;
+      break;
+    case TAIL_LSQR: tail_lsqr(w, st, tacc, n2_all, scratch); break;
+    case TAIL_NECORR: tail_necorr(w, st, tacc, n2_all, scratch); break;
+    case TAIL_CHECK: tail_check(w, st, tacc, n2_all, scratch); break;
+    case TAIL_GRAM: tail_gram(w, tacc, out_n2); break;
+    default: break;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Single-series pass kernel: each CTA accumulates its tiles, the CTAs then arrive.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) pass_kernel(PassArgs<T> a) {
+  constexpr int TILE = TileCfg<T>::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
   int tail = a.tail;
   const T* u_old = a.u_old;
   T* u_new = a.u_new;
   double coef = a.coef_host;
   if (a.check_done) {
-    const int ph = st->phase;
-    if (st->done || ph == PH_DONE) return;
-    const bool is_double = sizeof(T) == 8;
-    if (is_double) {
-      if (ph == PH_CHECK) tail = TAIL_CHECK;
-      else if (ph == PH_LSQR && !st->mixed) tail = TAIL_LSQR;
-      else return;
-    } else {
-      if (ph == PH_LSQR && st->mixed) tail = TAIL_LSQR;
-      else if (ph == PH_NECORR) tail = TAIL_NECORR;
-      else return;
-    }
-    coef = st->coef;
-    // buffer selection (see tols_api.cu: U[0]/U[1] ping-pong; b is y + p)
-    const int it = (tail == TAIL_NECORR) ? st->inner_iter : st->iter;
-    if (tail == TAIL_CHECK) {
-      u_old = a.y + a.p;                     // b
-      u_new = st->mixed ? nullptr : (T*)a.w.U[0];  // FP64: keep r for a restart
-    } else if (tail == TAIL_NECORR) {
-      u_old = it == 0 ? nullptr : (const T*)a.w.U[(it + 1) & 1];
-      u_new = (T*)a.w.U[it & 1];
-    } else {  // LSQR: first pass reads rhs (b on the first sweep, r stored in U[0] after a check)
-      const int from_b = (st->sweeps == 0);
-      if (it == 0) {
-        u_old = from_b ? a.y + a.p : (const T*)a.w.U[0];
-        u_new = (T*)a.w.U[1];
-      } else {
-        u_old = (const T*)a.w.U[(it & 1)];
-        u_new = (T*)a.w.U[(it + 1) & 1];
-      }
-    }
+    if (!select_phase<T>(a.w.st, a.y, a.p, a.w, tail, u_old, u_new, coef)) return;
   } else if (a.coef_dev) {
     coef = *a.coef_dev;
   }
-
-  const int p = a.p, p_pad = a.p_pad, nlag = a.nlag;
-  const long long m = a.m, n = a.n;
-  T* ys = reinterpret_cast<T*>(smem_raw);
-  const int ys_len = phys_size(TILE + p_pad + 16);
-  T* us = ys + ys_len;                         // u_old tile, padded layout
-  const int us_len = phys_size(TILE);
-  T* dr = us + us_len;                         // lag-reversed d
-  T* wpart = dr + p_pad;                       // per-warp partial X^T u of the tile: [kThreads/32][p_pad]
-  double* tacc = reinterpret_cast<double*>(wpart + (kThreads / 32) * p_pad);
-  double* scratch = tacc + p_pad + 16;
-  __shared__ int s_last;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // lag-reversed d: dr[k] = d[p-1-k]
-  if (!a.gram)
-    for (int k = tid; k < p_pad; k += kThreads) dr[k] = k < p ? (T)(a.d_scale * a.d[p - 1 - k]) : (T)0;
-  for (int k = tid; k < p_pad + 16; k += kThreads) tacc[k] = 0.0;
+  const int p_pad = a.p_pad, nlag = a.nlag;
+  Smem<T> sm(smem_raw, p_pad);
+  const int tid = threadIdx.x;
+  if (!a.gram) load_dr<T>(sm.dr, a.d, a.d_scale, a.p, p_pad);
+  for (int k = tid; k < p_pad + 16; k += kThreads) sm.tacc[k] = 0.0;
   double n2 = 0.0;
-  // lag owned by this lane after the warp reduce-scatter of 8 lags
-  const int jl = ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
-  const bool vec_out = u_new && ((reinterpret_cast<uintptr_t>(u_new) & 15) == 0);
-  const int r0 = tid * RB;                     // this thread's rows within the tile
-
-  const long long ntiles = (m + TILE - 1) / TILE;
+  const long long ntiles = (a.m + TILE - 1) / TILE;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i0 = tile * TILE;
-    const int rows = (int)min((long long)TILE, m - i0);
-    const int wlen = TILE + p_pad + 16;
+    n2 += process_tile<T>(sm, a.y, a.n, a.m, p_pad, nlag, a.gram, u_old, u_new, coef, tile * TILE);
     __syncthreads();
-    for (int q = tid; q < wlen; q += kThreads) {
-      const long long gi = i0 + q;
-      ys[phys(q)] = gi < n ? a.y[gi] : (T)0;
-    }
-    if (!a.gram && u_old) {
-      for (int q = tid; q < TILE; q += kThreads) us[phys(q)] = q < rows ? u_old[i0 + q] : (T)0;
-    }
-    __syncthreads();
-
-    // ---- this thread's RB entries of the fresh u (or of y itself for the Gram lag sums)
-    T uv[RB];
-    if (a.gram) {
-#pragma unroll
-      for (int q = 0; q < RB / 4; ++q) lds4<T>(ys, r0 + 4 * q, uv + 4 * q);
-#pragma unroll
-      for (int r = 0; r < RB; ++r)
-        if (r0 + r >= rows) uv[r] = (T)0;
-    } else {
-      // u_new = X d - c u_old : sliding window of y held in registers, KC lags per step
-      T acc[RB];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) acc[r] = (T)0;
-      if (r0 < rows) {
-        for (int k0 = 0; k0 < p_pad; k0 += KC) {
-          T yv[RB + KC];
-#pragma unroll
-          for (int q = 0; q < (RB + KC) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
-          T dv[KC];
-#pragma unroll
-          for (int q = 0; q < KC; ++q) dv[q] = dr[k0 + q];
-#pragma unroll
-          for (int q = 0; q < KC; ++q)
-#pragma unroll
-            for (int r = 0; r < RB; ++r) acc[r] = fma(yv[r + q], dv[q], acc[r]);
-        }
-      }
-      T uo[RB];
-      if (u_old) {
-#pragma unroll
-        for (int q = 0; q < RB / 4; ++q) lds4<T>(us, r0 + 4 * q, uo + 4 * q);
-      }
-      T nn = (T)0;
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        T u = (T)0;
-        if (r0 + r < rows) {
-          u = acc[r];
-          if (u_old) u = fma((T)(-coef), uo[r], u);
-        }
-        nn = fma(u, u, nn);
-        uv[r] = u;
-      }
-      n2 += (double)nn;
-      if (u_new && r0 < rows) {
-        T* dst = u_new + i0 + r0;
-        if (vec_out && r0 + RB <= rows) {
-#pragma unroll
-          for (int q = 0; q < RB / 4; ++q) st4<T>(dst + 4 * q, uv + 4 * q);
-        } else {
-#pragma unroll
-          for (int r = 0; r < RB; ++r)
-            if (r0 + r < rows) dst[r] = uv[r];
-        }
-      }
-    }
-
-    // ---- tk[k] += sum_r u[r] y[r + k]: 8 lags at a time from the same conflict-free window loads, then a
-    // warp reduce-scatter (9 shuffles) leaves lag k0 + jl on lanes with (lane & 3) == 0.
-    for (int k0 = 0; k0 < nlag; k0 += 8) {
-      T t8[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) t8[q] = (T)0;
-      if (r0 < rows) {
-        T yv[RB + 8];
-#pragma unroll
-        for (int q = 0; q < (RB + 8) / 4; ++q) lds4<T>(ys, r0 + k0 + 4 * q, yv + 4 * q);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-#pragma unroll
-          for (int r = 0; r < RB; ++r) t8[q] = fma(uv[r], yv[r + q], t8[q]);
-      }
-      const T v = warp_reduce_scatter8<T>(t8, lane);
-      if ((lane & 3) == 0) wpart[warp * p_pad + k0 + jl] = v;
-    }
-    __syncthreads();
-    for (int k = tid; k < nlag; k += kThreads) {
-      T sum = (T)0;
-#pragma unroll
-      for (int q = 0; q < kThreads / 32; ++q) sum += wpart[q * p_pad + k];
-      tacc[k] += (double)sum;
-    }
+    for (int k = tid; k < nlag; k += kThreads) sm.tacc[k] += warp_parts_sum<T>(sm.wpart, p_pad, k);
   }
   __syncthreads();
-
-  // ---- per-CTA partials, then the two-level reduction by the last CTAs
-  const double n2_cta = block_sum(n2, scratch);
-  const int bid = blockIdx.x;
-  for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)bid * p_pad + k] = tacc[k];
-  if (tid == 0) a.w.part_n2[bid] = n2_cta;
-  __threadfence();
+  const double n2_cta = block_sum(n2, sm.scratch);
+  for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
+  if (tid == 0) a.w.part_n2[blockIdx.x] = n2_cta;
+  if (!arrive(a.w, blockIdx.x, gridDim.x, nlag, p_pad, sm.tacc, sm.scratch, &s_last)) return;
+  const double n2_all = sm.scratch[8];
   __syncthreads();
-  const int grp = bid / kGroup;
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-  const int gsize = min(kGroup, (int)gridDim.x - grp * kGroup);
-  if (tid == 0) s_last = (atomicAdd(&a.w.counters[grp], 1u) == (unsigned)(gsize - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int k = tid; k < nlag; k += kThreads) {
-    double sum = 0.0;
-    for (int q = 0; q < gsize; ++q) sum += __ldcg(&a.w.part_t[(size_t)(grp * kGroup + q) * p_pad + k]);
-    a.w.grp_t[(size_t)grp * p_pad + k] = sum;
-  }
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int q = 0; q < gsize; ++q) sum += __ldcg(&a.w.part_n2[grp * kGroup + q]);
-    a.w.grp_n2[grp] = sum;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&a.w.counters[kMaxGroups], 1u) == (unsigned)(ngroups - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // final reduction into tacc (lag order) and n2
-  for (int k = tid; k < nlag; k += kThreads) {
-    double sum = 0.0;
-    for (int q = 0; q < ngroups; ++q) sum += __ldcg(&a.w.grp_t[(size_t)q * p_pad + k]);
-    tacc[k] = sum;
-  }
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int q = 0; q < ngroups; ++q) sum += __ldcg(&a.w.grp_n2[q]);
-    scratch[8] = sum;
-    for (int q = 0; q < ngroups; ++q) a.w.counters[q] = 0u;
-    a.w.counters[kMaxGroups] = 0u;
-  }
-  __syncthreads();
-  const double n2_all = scratch[8];
-  __syncthreads();
-
   if (tid == 0 && a.worklog) a.worklog[a.work_slot] = 1 + tail + 5 * (int)(sizeof(T) == 8);
-  switch (tail) {
-    case TAIL_STORE:
-      for (int j = tid; j < nlag; j += kThreads) a.out_t[j] = a.gram ? tacc[j] : tacc[nlag - 1 - j];
-      if (tid == 0 && a.out_n2) *a.out_n2 = n2_all;
-      break;
-    case TAIL_LSQR: tail_lsqr(a.w, st, tacc, n2_all, scratch); break;
-    case TAIL_NECORR: tail_necorr(a.w, st, tacc, n2_all, scratch); break;
-    case TAIL_CHECK: tail_check(a.w, st, tacc, n2_all, scratch); break;
-    case TAIL_GRAM: tail_gram(a.w, tacc, a.out_n2); break;
-    default: break;
+  run_tail<T>(tail, a.w, a.gram, nlag, sm.tacc, n2_all, sm.scratch, a.out_t, a.out_n2);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Batched pass kernel: the CTAs stride over one tile list that concatenates the tiles of every series. Each
+// tile leaves its own partials, the tiles of a series arrive in groups of kGroup, and the CTA that completes a
+// series runs that series' scalar step. A series' reduction order depends only on its own tiles, so its result
+// is the same whatever else is in the batch.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) batch_pass_kernel(BatchArgs a) {
+  constexpr int TILE = TileCfg<T>::TILE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  __shared__ int s_skip;
+  const int is_double = sizeof(T) == 8;
+  const long long total = is_double ? a.tiles_d : a.tiles_f;
+  const int* tile_series = is_double ? a.tile_series_d : a.tile_series_f;
+  const int tid = threadIdx.x;
+  for (long long g = blockIdx.x; g < total; g += gridDim.x) {
+    const int sidx = tile_series[g];
+    const BatchSeries& S = a.series[sidx];
+    const Work& w = S.w;
+    const T* y = is_double ? (const T*)S.w.y64 : (const T*)S.w.y32;
+    const long long local = g - (is_double ? S.tile0_d : S.tile0_f);
+    const long long ntiles = (S.w.m + TILE - 1) / TILE;
+    int tail = TAIL_GRAM;
+    const T* u_old = nullptr;
+    T* u_new = nullptr;
+    double coef = 0.0;
+    const int gram = a.gram;
+    const int p = S.w.p;
+    const int p_pad = gram ? pad_p(p + 1) : pad_p(p);
+    const int nlag = gram ? p + 1 : p;
+    if (tid == 0) {
+      int skip = 0;
+      if (gram) skip = (a.gram_double != is_double);
+      else skip = !select_phase<T>(w.st, y, p, w, tail, u_old, u_new, coef);
+      s_skip = skip;
+    }
+    __syncthreads();
+    const int skip = s_skip;
+    __syncthreads();
+    if (skip) continue;
+    if (!gram) select_phase<T>(w.st, y, p, w, tail, u_old, u_new, coef);
+    Smem<T> sm(smem_raw, p_pad);
+    if (!gram) load_dr<T>(sm.dr, w.d, 1.0, p, p_pad);
+    const double n2t = process_tile<T>(sm, y, S.w.n, S.w.m, p_pad, nlag, gram, u_old, u_new, coef, local * TILE);
+    __syncthreads();
+    for (int k = tid; k < nlag; k += kThreads)
+      w.part_t[(size_t)local * p_pad + k] = warp_parts_sum<T>(sm.wpart, p_pad, k);
+    const double n2_tile = block_sum(n2t, sm.scratch);
+    if (tid == 0) w.part_n2[local] = n2_tile;
+    if (!arrive(w, local, ntiles, nlag, p_pad, sm.tacc, sm.scratch, &s_last)) continue;
+    const double n2_all = sm.scratch[8];
+    __syncthreads();
+    run_tail<T>(tail, w, gram, nlag, sm.tacc, n2_all, sm.scratch, nullptr, w.bnorm2);
+    __syncthreads();
+    if (tid == 0 && !gram && w.st->done && a.done_count) atomicAdd(a.done_count, 1u);
   }
 }
 
@@ -728,10 +828,33 @@ const void* pass_kernel_ptr(int is_double) {
   return is_double ? (const void*)pass_kernel<double> : (const void*)pass_kernel<float>;
 }
 
+template <typename T>
+cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s) {
+  const size_t smem = pass_smem<T>(p_pad_max);
+  static int configured[2] = {0, 0};
+  const int which = sizeof(T) == 8;
+  if (!configured[which]) {
+    cudaError_t e =
+        cudaFuncSetAttribute(batch_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured[which] = 1;
+  }
+  const long long total = sizeof(T) == 8 ? a.tiles_d : a.tiles_f;
+  int g = (int)lmin((long long)grid, total);
+  if (g < 1) g = 1;
+  batch_pass_kernel<T><<<g, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_batch_pass<float>(const BatchArgs&, int, int, cudaStream_t);
+template cudaError_t launch_batch_pass<double>(const BatchArgs&, int, int, cudaStream_t);
+const void* batch_kernel_ptr(int is_double) {
+  return is_double ? (const void*)batch_pass_kernel<double> : (const void*)batch_pass_kernel<float>;
+}
+
 // ------------------------------------------------------------------------------------------------------
 // Preconditioner: ||X||_F, a power-iteration estimate of ||X||_2, Cholesky G = R^T R (upper R, in place),
 // M = R^{-1} and M^T (float64 and float copies). One CTA; G is symmetric on entry.
-__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond) {
+__device__ void precond_body(const Work& w, int want_precond) {
   const int p = w.p;
   DevState* st = w.st;
   __shared__ double scratch[16];
@@ -894,8 +1017,17 @@ __global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_prec
   }
 }
 
+__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond) { precond_body(w, want_precond); }
+__global__ void __launch_bounds__(kThreads) precond_batch_kernel(const BatchSeries* series, int want_precond) {
+  precond_body(series[blockIdx.x].w, want_precond);
+}
+
 cudaError_t launch_precond(Work w, int want_precond, cudaStream_t s) {
   precond_kernel<<<1, kThreads, 0, s>>>(w, want_precond);
+  return cudaGetLastError();
+}
+cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s) {
+  precond_batch_kernel<<<count, kThreads, 0, s>>>(series, want_precond);
   return cudaGetLastError();
 }
 
@@ -914,6 +1046,23 @@ __global__ void __launch_bounds__(kThreads) init_check_kernel(Work w) {
   schedule_check(w, w.st, scratch);
 }
 
+__global__ void __launch_bounds__(kThreads) init_lsqr_batch_kernel(const BatchSeries* series, unsigned int* done) {
+  __shared__ double scratch[16];
+  const Work& w = series[blockIdx.x].w;
+  DevState* st = w.st;
+  if (st->done) {  // e.g. non-finite input found by the preconditioner kernel
+    if (threadIdx.x == 0 && done) atomicAdd(done, 1u);
+    return;
+  }
+  for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
+  __syncthreads();
+  start_lsqr(w, st, w.h, st->bnorm, scratch);
+}
+cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s) {
+  init_lsqr_batch_kernel<<<count, kThreads, 0, s>>>(series, done);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_lsqr(Work w, int warm, cudaStream_t s) {
   if (warm) init_check_kernel<<<1, kThreads, 0, s>>>(w);
   else init_lsqr_kernel<<<1, kThreads, 0, s>>>(w);
@@ -929,6 +1078,20 @@ __global__ void finish_kernel(Work w) {
     if (threadIdx.x == 0) { st->ne_ratio = st->ne_best; st->rnorm = st->rnorm_best; }
   }
 }
+__global__ void finish_batch_kernel(const BatchSeries* series) {
+  const Work& w = series[blockIdx.x].w;
+  DevState* st = w.st;
+  if (st->status != TOLS_OK && st->ne_best < st->ne_ratio) {
+    for (int j = threadIdx.x; j < w.p; j += blockDim.x) w.phi[j] = w.best[j];
+    __syncthreads();
+    if (threadIdx.x == 0) { st->ne_ratio = st->ne_best; st->rnorm = st->rnorm_best; }
+  }
+}
+cudaError_t launch_finish_batch(const BatchSeries* series, int count, cudaStream_t s) {
+  finish_batch_kernel<<<count, kThreads, 0, s>>>(series);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish(Work w, cudaStream_t s) {
   finish_kernel<<<1, kThreads, 0, s>>>(w);
   return cudaGetLastError();

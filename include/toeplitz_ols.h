@@ -128,6 +128,53 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
                                const int* p, double tol, double* const* phi, double* rnorm, tols_info* info);
 
+/* ---- serving: continuous batching of fit requests ----------------------------------------------------
+ * A server owns a context and one device arena. Submitted requests (series copied in at submit) wait in FIFO
+ * order; each toeplitz_ols_server_step admits waiting requests while fewer than max_active are active and the
+ * request's device footprint (about 24 n bytes in mixed precision, 40 n in float64, plus O(p^2)) fits in the
+ * arena, sets the newcomers up, runs one burst of batched iterations over every active request, and retires the
+ * finished ones (their memory is free for the next admission at once). A request's arithmetic depends only on
+ * its own data, so its result is the same alone or among any other requests. */
+typedef struct tols_server tols_server;
+
+typedef struct {
+  int precision;          /* tols_precision (default TOLS_MIXED)                                           */
+  int device;             /* CUDA device ordinal                                                           */
+  size_t arena_bytes;     /* device arena for active requests; 0 = half of the free device memory          */
+  int max_active;         /* admission cap on concurrently active requests (default 1024)                  */
+  int burst;              /* batched passes per step (default 4)                                           */
+  int max_iter, max_sweeps;  /* as in tols_config                                                          */
+  void* cuda_stream;      /* cudaStream_t, or NULL for a stream owned by the server                       */
+} tols_server_config;
+
+typedef struct {
+  long long id;           /* the id given at submit                                                       */
+  int status;             /* per-request status code                                                      */
+  int p;
+  double latency_s;       /* seconds from toeplitz_ols_server_submit to the step that retired it           */
+  tols_info info;
+} tols_result;
+
+typedef struct {
+  long long submitted, completed;
+  int active, queued;
+  size_t arena_bytes, arena_used;
+} tols_server_stats;
+
+void toeplitz_ols_server_config_default(tols_server_config* cfg);
+/* Errors: TOLS_ERR_ARG, TOLS_ERR_NO_DEVICE, TOLS_ERR_OOM (the arena could not be allocated). */
+int toeplitz_ols_server_create(tols_server** out, const tols_server_config* cfg);
+int toeplitz_ols_server_destroy(tols_server* srv);
+/* Queue a fit of host series y[0..n-1] at order p (copied; the caller keeps y). TOLS_ERR_OOM if the request
+ * could never fit in the arena, TOLS_ERR_ARG for bad sizes. */
+int toeplitz_ols_server_submit(tols_server* srv, long long id, const double* y, long long n, int p, double tol);
+/* Admit, iterate once, retire (blocks for one burst). *active / *queued (nullable) report the counts after. */
+int toeplitz_ols_server_step(tols_server* srv, int* active, int* queued);
+/* Move up to max finished results into out[] (host) and their coefficients into phi_out (host, nullable,
+ * max * TOLS_MAX_P doubles: result i at phi_out + i * TOLS_MAX_P). *got = number moved. */
+int toeplitz_ols_server_poll(tols_server* srv, tols_result* out, double* phi_out, int max, int* got);
+int toeplitz_ols_server_stats(tols_server* srv, tols_server_stats* st);
+
 /* ---- streaming series: append samples and re-solve, warm-started from the previous phi ---------------- */
 int toeplitz_ols_stream_open(tols_ctx* ctx, int p, double tol, int* handle);
 int toeplitz_ols_stream_push(tols_ctx* ctx, int handle, const double* y_chunk, long long len);

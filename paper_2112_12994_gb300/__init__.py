@@ -59,6 +59,22 @@ class tols_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class tols_server_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("arena_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_int), ("burst", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class tols_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("p", ctypes.c_int),
+                ("latency_s", ctypes.c_double), ("info", tols_info)]
+
+
+class tols_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("active", ctypes.c_int),
+                ("queued", ctypes.c_int), ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t)]
+
+
 class TolsError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{msg} (code {code})")
@@ -99,6 +115,13 @@ SIGNATURES = {
     "toeplitz_ols_residual": (_I, [_P, _P, _LL, _I, _P, _P, _D]),
     "toeplitz_ols_leverage_p1": (_I, [_P, _P, _LL, _P]),
     "toeplitz_ols_leverage_step": (_I, [_P, _P, _LL, _I, _P, _P, _P, _P, _D]),
+    "toeplitz_ols_server_config_default": (None, [ctypes.POINTER(tols_server_config)]),
+    "toeplitz_ols_server_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tols_server_config)]),
+    "toeplitz_ols_server_destroy": (_I, [_P]),
+    "toeplitz_ols_server_submit": (_I, [_P, _LL, _P, _LL, _I, ctypes.c_double]),
+    "toeplitz_ols_server_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "toeplitz_ols_server_poll": (_I, [_P, _P, _P, _I, ctypes.POINTER(_I)]),
+    "toeplitz_ols_server_stats": (_I, [_P, ctypes.POINTER(tols_server_stats)]),
     "toeplitz_ols_profile": (_I, [_P, _I]),
     "toeplitz_ols_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_longlong), _D]),
 }
@@ -305,3 +328,77 @@ def toeplitz_ols_profile_read(ctx: Context, kind: int):
     ctx.check(lib.toeplitz_ols_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(ms)),
               "toeplitz_ols_profile_read")
     return n.value, ms.value
+
+
+class Server:
+    """A continuous-batching server (toeplitz_ols_server_*): submit fit requests, step, poll results."""
+
+    def __init__(self, precision=TOLS_MIXED, device=0, arena_bytes=0, max_active=1024, burst=4, max_iter=0,
+                 max_sweeps=0, cuda_stream=None):
+        cfg = tols_server_config()
+        lib.toeplitz_ols_server_config_default(ctypes.byref(cfg))
+        cfg.precision, cfg.device, cfg.arena_bytes = precision, device, arena_bytes
+        cfg.max_active, cfg.burst, cfg.max_iter, cfg.max_sweeps = max_active, burst, max_iter, max_sweeps
+        cfg.cuda_stream = cuda_stream
+        h = ctypes.c_void_p()
+        rc = lib.toeplitz_ols_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if rc != TOLS_OK:
+            raise TolsError(rc, "toeplitz_ols_server_create: " + strerror(rc))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.toeplitz_ols_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, rid: int, y, p: int, tol: float = 0.0) -> int:
+        y = _host_f64(y)
+        return lib.toeplitz_ols_server_submit(self.handle, rid, y.ctypes.data, y.size, p, tol)
+
+    def step(self):
+        a, q = ctypes.c_int(), ctypes.c_int()
+        rc = lib.toeplitz_ols_server_step(self.handle, ctypes.byref(a), ctypes.byref(q))
+        if rc != TOLS_OK:
+            raise TolsError(rc, "toeplitz_ols_server_step: " + strerror(rc))
+        return a.value, q.value
+
+    def poll(self, max_results: int = 1024):
+        out = (tols_result * max_results)()
+        phi = np.zeros(max_results * TOLS_MAX_P)
+        got = ctypes.c_int()
+        rc = lib.toeplitz_ols_server_poll(self.handle, ctypes.cast(out, ctypes.c_void_p), phi.ctypes.data,
+                                          max_results, ctypes.byref(got))
+        if rc != TOLS_OK:
+            raise TolsError(rc, "toeplitz_ols_server_poll: " + strerror(rc))
+        res = []
+        for i in range(got.value):
+            r = out[i]
+            res.append({"id": r.id, "status": r.status, "p": r.p, "latency_s": r.latency_s,
+                        "info": r.info.as_dict(), "phi": phi[i * TOLS_MAX_P: i * TOLS_MAX_P + r.p].copy()})
+        return res
+
+    def stats(self):
+        st = tols_server_stats()
+        lib.toeplitz_ols_server_stats(self.handle, ctypes.byref(st))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def run_until_idle(self, max_steps: int = 100000):
+        results = []
+        for _ in range(max_steps):
+            active, queued = self.step()
+            results += self.poll()
+            if active == 0 and queued == 0:
+                break
+        return results

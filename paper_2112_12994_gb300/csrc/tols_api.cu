@@ -14,6 +14,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <deque>
 #include <map>
 #include <string>
 #include <vector>
@@ -742,6 +744,353 @@ int batch_fixups(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vecto
   }
   return TOLS_OK;
 }
+
+// ------------------------------------------------------------------------------------------------------
+// Serving: continuous batching over one device arena. Requests wait in FIFO order and are admitted while a slot
+// is free and their footprint fits in the arena; every step admits, sets up the newcomers (Gram pass,
+// preconditioner, LSQR start — batched over the newcomers), runs one burst of batched passes over all active
+// requests, and retires the finished ones, freeing their memory at once.
+class ArenaAlloc {
+ public:
+  void reset(size_t cap) {
+    free_.clear();
+    free_[0] = cap;
+    used_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = align_up(bytes, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes, noff = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[noff] = rest;
+      used_ += bytes;
+      return true;
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align_up(bytes, 256);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+// Bytes of one series' arena slice; with base != nullptr also lays the slice out into w.
+size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
+  const long long m = n - p;
+  const size_t pp1 = (size_t)pad_p(p + 1);
+  const long long ntd = (m + kTileD - 1) / kTileD, ngr = (ntd + kGroup - 1) / kGroup;
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align_up(bytes, 256);
+    return base ? base + o : nullptr;
+  };
+  char* st = take(sizeof(DevState));
+  char* cnt = take(sizeof(unsigned) * (size_t)(ngr + 1));
+  char* y64 = take(sizeof(double) * (size_t)n);
+  char* y32 = mixed ? take(sizeof(float) * (size_t)n) : nullptr;
+  char* u0 = take(es * (size_t)m);
+  char* u1 = take(es * (size_t)m);
+  char* part = take(sizeof(double) * (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr));
+  char* vec = take(sizeof(double) * (9 * pp1 + (size_t)p));
+  char* mat = take(sizeof(double) * 3 * (size_t)p * p + sizeof(float) * 2 * (size_t)p * p);
+  if (base && w) {
+    memset(w, 0, sizeof *w);
+    w->n = n;
+    w->m = m;
+    w->p = p;
+    w->p_pad = (int)pp1;
+    w->st = (DevState*)st;
+    w->counters = (unsigned*)cnt;
+    w->y64 = (const double*)y64;
+    w->y32 = (float*)y32;
+    w->U[0] = u0;
+    w->U[1] = u1;
+    double* q = (double*)part;
+    w->part_t = q; q += ntd * pp1;
+    w->part_n2 = q; q += ntd;
+    w->grp_t = q; q += ngr * pp1;
+    w->grp_n2 = q;
+    q = (double*)vec;
+    w->v = q; q += pp1;
+    w->w = q; q += pp1;
+    w->z = q; q += pp1;
+    w->d = q; q += pp1;
+    w->g = q; q += pp1;
+    w->h = q; q += pp1;
+    w->t = q; q += pp1;
+    w->best = q; q += pp1;
+    w->bnorm2 = q; q += pp1;
+    w->phi = q;
+    const size_t pq = (size_t)p * p;
+    w->G = (double*)mat;
+    w->M = w->G + pq;
+    w->Mt = w->M + pq;
+    w->M32 = (float*)(w->Mt + pq);
+    w->Mt32 = w->M32 + pq;
+  }
+  return off;
+}
+
+DevState initial_state(const tols_config& cfg, int p, double tol, bool mixed) {
+  DevState st;
+  memset(&st, 0, sizeof st);
+  const int max_iter = cfg.max_iter > 0 ? cfg.max_iter : 4 * p + 200;
+  st.tol = tol;
+  st.tol_inner = 1e-5;
+  st.est_ratio = tol;
+  st.max_iter = max_iter;
+  st.iter_cap = mixed ? std::min(max_iter, 100) : max_iter;
+  st.max_sweeps = cfg.max_sweeps > 0 ? cfg.max_sweeps : 6;
+  st.mixed = mixed ? 1 : 0;
+  st.mixed_ok = 1;
+  st.ne_ratio = 1e300;
+  st.ne_best = 1e300;
+  st.status = TOLS_NOT_CONVERGED;
+  st.phase = PH_LSQR;
+  return st;
+}
+
+struct SrvRequest {
+  long long id;
+  long long n;
+  int p;
+  double tol;
+  std::vector<double> y;
+  double t_submit;
+};
+
+struct SrvActive {
+  SrvRequest req;
+  size_t off = 0, bytes = 0;
+  Work w;
+};
+
+double now_s(const std::chrono::steady_clock::time_point& t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct tols_server {
+  tols_ctx* ctx = nullptr;
+  bool mixed = false;
+  int max_active = 0;
+  int burst = 4;
+  char* arena = nullptr;
+  size_t arena_cap = 0;
+  ArenaAlloc alloc;
+  std::deque<SrvRequest> queue;
+  std::vector<SrvActive> active;
+  std::vector<tols_result> results;
+  std::vector<double> result_phi;   // TOLS_MAX_P doubles per result
+  DevBuf table, tiles, gather;
+  std::vector<DevState> h_states;
+  std::vector<double> h_phi;
+  std::chrono::steady_clock::time_point t0;
+  long long submitted = 0, completed = 0;
+};
+
+namespace {
+
+// Upload a series table (and its tile lists) for the series in `list` (indices into srv->active).
+int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, int& p_pad_max) {
+  tols_ctx* ctx = srv->ctx;
+  const int cnt = (int)list.size();
+  std::vector<BatchSeries> hs(cnt);
+  long long tf = 0, td = 0;
+  p_pad_max = 16;
+  for (int k = 0; k < cnt; ++k) {
+    const Work& w = srv->active[list[k]].w;
+    memset(&hs[k], 0, sizeof(BatchSeries));
+    hs[k].w = w;
+    hs[k].tile0_f = tf;
+    hs[k].tile0_d = td;
+    tf += (w.m + kTileF - 1) / kTileF;
+    td += (w.m + kTileD - 1) / kTileD;
+    p_pad_max = std::max(p_pad_max, pad_p(w.p + 1));
+  }
+  std::vector<int> tiles((size_t)(tf + td));
+  for (int k = 0; k < cnt; ++k) {
+    const Work& w = hs[k].w;
+    const long long ntf = (w.m + kTileF - 1) / kTileF, ntd = (w.m + kTileD - 1) / kTileD;
+    for (long long t = 0; t < ntf; ++t) tiles[(size_t)(hs[k].tile0_f + t)] = k;
+    for (long long t = 0; t < ntd; ++t) tiles[(size_t)(tf + hs[k].tile0_d + t)] = k;
+  }
+  int rc;
+  if ((rc = ensure(ctx, srv->table, sizeof(BatchSeries) * std::max(cnt, 1)))) return rc;
+  if ((rc = ensure(ctx, srv->tiles, sizeof(int) * std::max<size_t>(tiles.size(), 1)))) return rc;
+  CK(cudaMemcpyAsync(srv->table.p, hs.data(), sizeof(BatchSeries) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(srv->tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
+  memset(&a, 0, sizeof a);
+  a.series = (const BatchSeries*)srv->table.p;
+  a.tile_series_f = (const int*)srv->tiles.p;
+  a.tile_series_d = (const int*)srv->tiles.p + tf;
+  a.tiles_f = tf;
+  a.tiles_d = td;
+  // the host vectors must outlive the copies: pageable-memory copies are staged before they return
+  return TOLS_OK;
+}
+
+int server_admit(tols_server* srv, std::vector<int>& fresh) {
+  tols_ctx* ctx = srv->ctx;
+  while (!srv->queue.empty() && (int)srv->active.size() < srv->max_active) {
+    SrvRequest& r = srv->queue.front();
+    const size_t bytes = series_slice(nullptr, r.n, r.p, srv->mixed, nullptr);
+    size_t off = 0;
+    if (!srv->alloc.alloc(bytes, &off)) break;  // FIFO: the head waits until memory frees up
+    SrvActive a;
+    a.off = off;
+    a.bytes = bytes;
+    series_slice(srv->arena + off, r.n, r.p, srv->mixed, &a.w);
+    const DevState st = initial_state(ctx->cfg, r.p, r.tol, srv->mixed);
+    CK(cudaMemcpyAsync((void*)a.w.y64, r.y.data(), sizeof(double) * (size_t)r.n, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemsetAsync(a.w.counters, 0, sizeof(unsigned) * (size_t)((((r.n - r.p) + kTileD - 1) / kTileD + kGroup - 1) / kGroup + 1),
+                       ctx->stream));
+    CK(cudaMemcpyAsync(a.w.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
+    a.req = std::move(r);
+    srv->queue.pop_front();
+    fresh.push_back((int)srv->active.size());
+    srv->active.push_back(std::move(a));
+  }
+  if (fresh.empty()) return TOLS_OK;
+  // setup of the newcomers, batched over them
+  BatchArgs a;
+  int pmax = 16;
+  RUN(upload_table(srv, fresh, a, pmax));
+  if (srv->mixed)
+    for (int k : fresh) {
+      const Work& w = srv->active[k].w;
+      RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
+    }
+  BatchArgs ag = a;
+  ag.gram = 1;
+  ag.gram_double = srv->mixed ? 0 : 1;
+  ctx->launch_total++;
+  CK(srv->mixed ? launch_batch_pass<float>(ag, batch_grid(ctx, 0, pmax), pmax, ctx->stream)
+                : launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
+  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
+  const int cnt = (int)fresh.size();
+  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(a.series, cnt, want, ctx->stream); }));
+  RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(a.series, cnt, nullptr, ctx->stream); }));
+  return TOLS_OK;
+}
+
+}  // namespace
+
+namespace tols {
+cudaError_t launch_gather_batch(const BatchSeries* series, int count, DevState* states, double* phis, int stride,
+                                cudaStream_t s);
+}
+
+namespace {
+
+int server_round(tols_server* srv) {
+  tols_ctx* ctx = srv->ctx;
+  const int cnt = (int)srv->active.size();
+  if (cnt == 0) return TOLS_OK;
+  std::vector<int> all(cnt);
+  for (int k = 0; k < cnt; ++k) all[k] = k;
+  BatchArgs a;
+  int pmax = 16;
+  RUN(upload_table(srv, all, a, pmax));
+  const int gf = batch_grid(ctx, 0, pmax), gd = batch_grid(ctx, 1, pmax);
+  for (int k = 0; k < srv->burst; ++k) {
+    ctx->launch_total++;
+    CK(srv->mixed ? launch_batch_pass<float>(a, gf, pmax, ctx->stream)
+                  : launch_batch_pass<double>(a, gd, pmax, ctx->stream));
+  }
+  if (srv->mixed) {
+    ctx->launch_total++;
+    CK(launch_batch_pass<double>(a, gd, pmax, ctx->stream));
+  }
+  RUN(run_small(ctx, 12, [&] { return launch_finish_batch(a.series, cnt, ctx->stream); }));
+  int rc;
+  if ((rc = ensure(ctx, srv->gather, (sizeof(DevState) + sizeof(double) * TOLS_MAX_P) * (size_t)cnt))) return rc;
+  DevState* d_st = (DevState*)srv->gather.p;
+  double* d_phi = (double*)(d_st + cnt);
+  RUN(run_small(ctx, 12, [&] { return launch_gather_batch(a.series, cnt, d_st, d_phi, TOLS_MAX_P, ctx->stream); }));
+  srv->h_states.resize(cnt);
+  srv->h_phi.resize((size_t)cnt * TOLS_MAX_P);
+  CK(cudaMemcpyAsync(srv->h_states.data(), d_st, sizeof(DevState) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(srv->h_phi.data(), d_phi, sizeof(double) * TOLS_MAX_P * cnt, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  RUN(flush_profile(ctx));
+  // retire the finished requests
+  std::vector<SrvActive> keep;
+  keep.reserve(cnt);
+  for (int k = 0; k < cnt; ++k) {
+    SrvActive& A = srv->active[k];
+    DevState s = srv->h_states[k];
+    if (!(s.done || s.phase == PH_DONE)) {
+      keep.push_back(std::move(A));
+      continue;
+    }
+    const double* phi = srv->h_phi.data() + (size_t)k * TOLS_MAX_P;
+    std::vector<double> fix;
+    int prec = srv->mixed ? TOLS_MIXED : TOLS_FP64;
+    const bool stalled = srv->mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
+                         (s.mixed_ok == 0 || s.precond == 0);
+    const bool rankdef = s.singular && s.compatible && s.status >= 0;
+    if (stalled || rankdef) {
+      // the single-series path handles these (float64 refinement, or plain LSQR for the minimum norm)
+      if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)A.req.p + 64)))) return rc;
+      double rn = 0.0;
+      tols_info inf;
+      rc = solve_device_impl(ctx, A.w.y64, A.req.n, A.req.p, A.req.tol, (double*)ctx->scratch.p, &rn, &inf, nullptr);
+      if (rc < 0) return rc;
+      fix.resize(A.req.p);
+      CK(cudaMemcpy(fix.data(), ctx->scratch.p, sizeof(double) * A.req.p, cudaMemcpyDeviceToHost));
+      phi = fix.data();
+      s.status = rc;
+      s.ne_ratio = inf.ne_ratio;
+      s.rnorm = inf.rnorm;
+      s.total_iter += inf.iters;
+      s.sweeps += inf.sweeps;
+      s.precond = inf.precond_used;
+      prec = inf.precision_used;
+    }
+    tols_result res;
+    memset(&res, 0, sizeof res);
+    res.id = A.req.id;
+    res.status = s.status;
+    res.p = A.req.p;
+    res.latency_s = now_s(srv->t0) - A.req.t_submit;
+    fill_info(&res.info, s, prec);
+    res.info.status = s.status;
+    srv->results.push_back(res);
+    const size_t base = srv->result_phi.size();
+    srv->result_phi.resize(base + TOLS_MAX_P, 0.0);
+    memcpy(srv->result_phi.data() + base, phi, sizeof(double) * A.req.p);
+    srv->alloc.release(A.off, A.bytes);
+    srv->completed++;
+  }
+  srv->active.swap(keep);
+  return TOLS_OK;
+}
 }  // namespace
 
 // ======================================================================================================
@@ -1123,6 +1472,124 @@ int toeplitz_ols_leverage_step(tols_ctx* ctx, const double* d_y, long long n, in
   CK(cudaMemcpyAsync(&h, d_rr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (rnorm2) *rnorm2 = h;
+  return TOLS_OK;
+}
+
+
+void toeplitz_ols_server_config_default(tols_server_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->precision = TOLS_MIXED;
+  cfg->device = 0;
+  cfg->max_active = 1024;
+  cfg->burst = 4;
+}
+
+int toeplitz_ols_server_create(tols_server** out, const tols_server_config* cfg) {
+  if (!out) return TOLS_ERR_ARG;
+  *out = nullptr;
+  tols_server_config c;
+  if (cfg) c = *cfg;
+  else toeplitz_ols_server_config_default(&c);
+  if (c.precision != TOLS_FP64 && c.precision != TOLS_MIXED) return TOLS_ERR_ARG;
+  tols_config cc;
+  toeplitz_ols_config_default(&cc);
+  cc.precision = c.precision;
+  cc.device = c.device;
+  cc.max_iter = c.max_iter;
+  cc.max_sweeps = c.max_sweeps;
+  cc.cuda_stream = c.cuda_stream;
+  tols_ctx* ctx = nullptr;
+  int rc = toeplitz_ols_create(&ctx, &cc);
+  if (rc) return rc;
+  tols_server* srv = new tols_server;
+  srv->ctx = ctx;
+  srv->mixed = c.precision == TOLS_MIXED;
+  srv->max_active = c.max_active > 0 ? c.max_active : 1024;
+  srv->burst = c.burst > 0 ? c.burst : 4;
+  size_t cap = c.arena_bytes;
+  if (cap == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    cap = fr / 2;
+  }
+  if (cudaMalloc(&srv->arena, cap) != cudaSuccess) {
+    cudaGetLastError();
+    toeplitz_ols_destroy(ctx);
+    delete srv;
+    return TOLS_ERR_OOM;
+  }
+  srv->arena_cap = cap;
+  srv->alloc.reset(cap);
+  srv->t0 = std::chrono::steady_clock::now();
+  *out = srv;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_server_destroy(tols_server* srv) {
+  if (!srv) return TOLS_OK;
+  tols_ctx* ctx = srv->ctx;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx, srv->table);
+  release(ctx, srv->tiles);
+  release(ctx, srv->gather);
+  if (srv->arena) cudaFree(srv->arena);
+  toeplitz_ols_destroy(ctx);
+  delete srv;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_server_submit(tols_server* srv, long long id, const double* y, long long n, int p, double tol) {
+  if (!srv || !y || p < 1 || p > TOLS_MAX_P || n <= p) return TOLS_ERR_ARG;
+  if (align_up(series_slice(nullptr, n, p, srv->mixed, nullptr), 256) > srv->arena_cap) return TOLS_ERR_OOM;
+  SrvRequest r;
+  r.id = id;
+  r.n = n;
+  r.p = p;
+  r.tol = tol > 0 ? tol : 1e-12;
+  r.y.assign(y, y + n);
+  r.t_submit = now_s(srv->t0);
+  srv->queue.push_back(std::move(r));
+  srv->submitted++;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_server_step(tols_server* srv, int* active, int* queued) {
+  if (!srv) return TOLS_ERR_ARG;
+  tols_ctx* ctx = srv->ctx;
+  cudaSetDevice(ctx->device);
+  std::vector<int> fresh;
+  int rc = server_admit(srv, fresh);
+  if (rc) return rc;
+  if ((rc = server_round(srv))) return rc;
+  if (active) *active = (int)srv->active.size();
+  if (queued) *queued = (int)srv->queue.size();
+  return TOLS_OK;
+}
+
+int toeplitz_ols_server_poll(tols_server* srv, tols_result* out, double* phi_out, int max, int* got) {
+  if (!srv || !got || max < 0 || (max > 0 && !out)) return TOLS_ERR_ARG;
+  const int k = std::min<int>(max, (int)srv->results.size());
+  for (int i = 0; i < k; ++i) {
+    out[i] = srv->results[i];
+    if (phi_out) memcpy(phi_out + (size_t)i * TOLS_MAX_P, srv->result_phi.data() + (size_t)i * TOLS_MAX_P,
+                        sizeof(double) * TOLS_MAX_P);
+  }
+  srv->results.erase(srv->results.begin(), srv->results.begin() + k);
+  srv->result_phi.erase(srv->result_phi.begin(), srv->result_phi.begin() + (size_t)k * TOLS_MAX_P);
+  *got = k;
+  return TOLS_OK;
+}
+
+int toeplitz_ols_server_stats(tols_server* srv, tols_server_stats* st) {
+  if (!srv || !st) return TOLS_ERR_ARG;
+  st->submitted = srv->submitted;
+  st->completed = srv->completed;
+  st->active = (int)srv->active.size();
+  st->queued = (int)srv->queue.size();
+  st->arena_bytes = srv->arena_cap;
+  st->arena_used = srv->alloc.used();
   return TOLS_OK;
 }
 

@@ -1087,6 +1087,18 @@ __global__ void finish_batch_kernel(const BatchSeries* series) {
     if (threadIdx.x == 0) { st->ne_ratio = st->ne_best; st->rnorm = st->rnorm_best; }
   }
 }
+// Copy each series' state and phi into contiguous arrays (phi at stride `stride`).
+__global__ void gather_batch_kernel(const BatchSeries* series, DevState* states, double* phis, int stride) {
+  const Work& w = series[blockIdx.x].w;
+  for (int j = threadIdx.x; j < w.p; j += blockDim.x) phis[(size_t)blockIdx.x * stride + j] = w.phi[j];
+  if (threadIdx.x == 0) states[blockIdx.x] = *w.st;
+}
+cudaError_t launch_gather_batch(const BatchSeries* series, int count, DevState* states, double* phis, int stride,
+                                cudaStream_t s) {
+  gather_batch_kernel<<<count, 128, 0, s>>>(series, states, phis, stride);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finish_batch(const BatchSeries* series, int count, cudaStream_t s) {
   finish_batch_kernel<<<count, kThreads, 0, s>>>(series);
   return cudaGetLastError();

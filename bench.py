@@ -36,6 +36,7 @@ WORKLOADS = {
                       desc="AR(10), n=10,000, roots |r| in U[1.2,3], N(0,1) innovations, FP64, ne-ratio 1e-12"),
 }
 L2_FLUSH_BYTES = 512 << 20
+BATCH_TOL = 1e-10   # normal-equation ratio for the batched and served fits (as for the AR(100) fit)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA (4 flop)/clk/SM x 2.07 GHz max clock
 
 
@@ -50,6 +51,10 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused product pass (toeplitz_ols_gk_pass), float64 then float32")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--batch-series", type=int, default=1024,
+                    help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
     return ap.parse_args()
 
 
@@ -125,6 +130,22 @@ def cpu_cores():
     return os.cpu_count()
 
 
+def _gen_one(args):
+    from synthetic import ar_series
+    n, p, cfg, idx, lo, hi = args
+    return ar_series(int(n), int(p), config_id=cfg, series_index=idx, root_lo=lo, root_hi=hi).y
+
+
+def gen_many(shapes, cfg, lo=1.2, hi=3.0):
+    """Seeded series for (n, p) shapes, generated in a spawn process pool (before any CUDA call)."""
+    import multiprocessing as mp
+    jobs = [(n, p, cfg, k, lo, hi) for k, (n, p) in enumerate(shapes)]
+    if len(jobs) < 8:
+        return [_gen_one(j) for j in jobs]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_gen_one, jobs, chunksize=4)
+
+
 def make_series(wl):
     from synthetic import ar_series
     return ar_series(wl["n"], wl["p"], config_id=wl["config_id"], root_lo=wl["root_lo"], root_hi=wl["root_hi"],
@@ -172,6 +193,15 @@ def run_ours(args, wl):
     import paper_2112_12994_gb300 as tols
 
     world, rank, local = dist()
+    from synthetic import batch_shapes
+    batch_in = serve_in = None
+    if args.batch_series > 0:
+        bn, bp = batch_shapes(args.batch_series, config_id=4, n_lo=1e4, n_hi=1e6, p_lo=5, p_hi=200)
+        batch_in = (gen_many(list(zip(bn, bp)), 4), [int(x) for x in bp])
+    if args.serve_requests > 0:
+        sn, sp = batch_shapes(args.serve_requests, config_id=5, n_lo=1e3, n_hi=1e7, p_lo=1, p_hi=300,
+                              p_log_uniform=True)
+        serve_in = (gen_many(list(zip(sn, sp)), 5), [int(x) for x in sp])
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -255,6 +285,9 @@ def run_ours(args, wl):
     barrier()
     e2e_ms = max_over_ranks(sum(e2e_times))
 
+    batched = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world) if batch_in else None
+    serving = run_serving(tols, serve_in, args) if serve_in else None
+
     hbm_peak, hbm_src = peaks()
     r64, rmx = results["fp64"], results["mixed"]
     K = args.steps
@@ -309,6 +342,8 @@ def run_ours(args, wl):
                      "status": r64["infos"][-1]["status"]},
            "e2e": {"value": world * K / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * p},
+           "batched": batched,
+           "serving": serving,
            "gpu_launches": int(r64["launches"] + rmx["launches"]),
            "clocks": r64["clocks"],
            "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r64["prof"].items() if v[0]}}
@@ -331,6 +366,94 @@ def run_ours(args, wl):
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
+
+
+def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world):
+    """Many series of uneven length in one batched solve (mixed precision), series resident in HBM."""
+    import numpy as np
+    ys, ps = batch_in
+    d_ys = [torch.tensor(y, dtype=torch.float64, device=dev) for y in ys]
+    d_phi = torch.empty(sum(ps), dtype=torch.float64, device=dev)
+    steps = max(2, min(args.steps, 5))
+    out = {"series": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "mixed",
+           "workload": "n log-uniform in [1e4, 1e6], p uniform in [5, 200], roots |r| in U[1.2, 3], N(0,1)"}
+    with tols.Context(precision=tols.TOLS_MIXED, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
+        tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)       # warm-up
+        tols.toeplitz_ols_profile(ctx, True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            rn, infos, rc = tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)
+        torch.cuda.synchronize()
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
+        f32 = tols.toeplitz_ols_profile_read(ctx, 1)
+        tols.toeplitz_ols_profile(ctx, False)
+        # end to end from host memory through toeplitz_ols_solve_batched
+        t1 = time.perf_counter()
+        phis_h, _, _, _ = tols.toeplitz_ols_solve_batched(ctx, ys, ps, BATCH_TOL)
+        e2e_dt = time.perf_counter() - t1
+    status = [i["status"] for i in infos]
+    out.update({"value": world * len(ys) * steps / dt, "unit": "solves/s", "ms_per_batch": 1e3 * dt / steps,
+                "steps": steps, "tol": BATCH_TOL, "statuses_ok": int(sum(1 for x in status if x == 0)),
+                "statuses_not_converged": int(sum(1 for x in status if x == 1)),
+                "fp64_fallbacks": int(sum(1 for i in infos if i["precision_used"] == 0)),
+                "mean_iters": float(np.mean([i["iters"] for i in infos])),
+                "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches),
+                "f32_lsqr_pass_launches": f32[0], "f32_lsqr_pass_ms": f32[1]})
+    # accuracy on a few series against the oracle (timed as the CPU baseline of this workload)
+    import oracle
+    phi_all = d_phi.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(ps)])
+    errs, t_or, rows = [], 0.0, 0
+    for k in range(0, len(ys), max(1, len(ys) // 4))[:4]:
+        t2 = time.perf_counter()
+        ref = oracle.ols_qr(ys[k], ps[k])
+        t_or += time.perf_counter() - t2
+        rows += 1
+        errs.append(float(np.linalg.norm(phi_all[offs[k]:offs[k + 1]] - ref.phi) / np.linalg.norm(ref.phi)))
+    out["max_coef_rel_err_sampled"] = max(errs)
+    out["cpu_baseline"] = {"value": rows / t_or, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                           "sample": f"{rows} series of the batch"}
+    return out
+
+
+def run_serving(tols, serve_in, args):
+    """Continuous batching: saturation throughput, then Poisson arrivals at half of it; p50/p99 latency."""
+    import numpy as np
+    ys, ps = serve_in
+    res = {"requests": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "mixed",
+           "workload": "n log-uniform in [1e3, 1e7], p log-uniform in [1, 300], roots |r| in U[1.2, 3], N(0,1)"}
+
+    def run(rate):
+        rng = np.random.default_rng(5)
+        arrivals = np.zeros(len(ys)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, size=len(ys)))
+        with tols.Server(precision=tols.TOLS_MIXED, burst=4) as srv:
+            t0 = time.perf_counter()
+            nxt, done, lat = 0, [], []
+            while len(done) < len(ys):
+                now = time.perf_counter() - t0
+                while nxt < len(ys) and arrivals[nxt] <= now:
+                    rc = srv.submit(nxt, ys[nxt], ps[nxt], BATCH_TOL)
+                    assert rc == 0, rc
+                    nxt += 1
+                active, queued = srv.step()
+                for r in srv.poll():
+                    done.append(r)
+                if active == 0 and queued == 0 and nxt < len(ys):
+                    time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+            makespan = time.perf_counter() - t0
+        lat = np.array([r["latency_s"] for r in done])
+        ok = sum(1 for r in done if r["status"] == 0)
+        return {"solves_per_s": len(done) / makespan, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "ok": ok}
+
+    sat = run(None)
+    res["saturation"] = sat
+    res["poisson_half_rate"] = dict(run(0.5 * sat["solves_per_s"]), rate_per_s=0.5 * sat["solves_per_s"])
+    return res
 
 
 def run_kernel_only(args, wl):

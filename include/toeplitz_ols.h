@@ -128,6 +128,12 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
                                const int* p, double tol, double* const* phi, double* rnorm, tols_info* info);
 
+/* Same as toeplitz_ols_solve_batched with every series already on the device: d_y is a host array of count
+ * device pointers (series k: n[k] doubles), and the coefficients are written to the device array d_phi, series
+ * k at d_phi + sum_{j<k} p[j] (zeros for a series rejected with TOLS_ERR_ARG). rnorm / info: host, nullable. */
+int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
+                                      const int* p, double tol, double* d_phi, double* rnorm, tols_info* info);
+
 /* ---- serving: continuous batching of fit requests ----------------------------------------------------
  * A server owns a context and one device arena. Submitted requests (series copied in at submit) wait in FIFO
  * order; each toeplitz_ols_server_step admits waiting requests while fewer than max_active are active and the

@@ -104,6 +104,7 @@ SIGNATURES = {
     "toeplitz_ols_solve": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, _D, ctypes.POINTER(tols_info)]),
     "toeplitz_ols_solve_device": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, _D, ctypes.POINTER(tols_info)]),
     "toeplitz_ols_solve_batched": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P]),
+    "toeplitz_ols_solve_batched_device": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P]),
     "toeplitz_ols_stream_open": (_I, [_P, _I, ctypes.c_double, ctypes.POINTER(_I)]),
     "toeplitz_ols_stream_push": (_I, [_P, _I, _P, _LL]),
     "toeplitz_ols_stream_solve": (_I, [_P, _I, _P, _D, ctypes.POINTER(tols_info)]),
@@ -242,6 +243,22 @@ def toeplitz_ols_solve_batched(ctx: Context, ys, ps, tol: float = 0.0):
                                         ctypes.cast(pp, _P), rn.ctypes.data, ctypes.cast(infos, _P))
     ctx.check(rc, "toeplitz_ols_solve_batched")
     return phis, rn, [i.as_dict() for i in infos], rc
+
+
+def toeplitz_ols_solve_batched_device(ctx: Context, d_ys, ps, d_phi, tol: float = 0.0):
+    """Device series (list of CUDA tensors / addresses) -> coefficients packed in d_phi (device, sum(ps));
+    returns (rnorm array, list of info dicts, worst status)."""
+    count = len(d_ys)
+    yp = (ctypes.c_void_p * count)(*[_ptr(y) for y in d_ys])
+    ns = np.array([int(y.numel()) if hasattr(y, "numel") else 0 for y in d_ys], dtype=np.int64)
+    pv = np.array(ps, dtype=np.int32)
+    rn = np.zeros(count, dtype=np.float64)
+    infos = (tols_info * count)()
+    rc = lib.toeplitz_ols_solve_batched_device(ctx.handle, count, ctypes.cast(yp, _P), ns.ctypes.data,
+                                               pv.ctypes.data, tol, _ptr(d_phi), rn.ctypes.data,
+                                               ctypes.cast(infos, _P))
+    ctx.check(rc, "toeplitz_ols_solve_batched_device")
+    return rn, [i.as_dict() for i in infos], rc
 
 
 def toeplitz_ols_stream_open(ctx: Context, p: int, tol: float = 0.0) -> int:

@@ -409,9 +409,9 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
 
 // Solve with precision fallback; phi (device) receives the result.
 int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, double* d_phi,
-                      double* rnorm, tols_info* info, const double* phi0) {
+                      double* rnorm, tols_info* info, const double* phi0, int force_prec = -1) {
   if (tol <= 0) tol = 1e-12;
-  bool mixed = ctx->cfg.precision == TOLS_MIXED;
+  bool mixed = force_prec >= 0 ? force_prec == TOLS_MIXED : ctx->cfg.precision == TOLS_MIXED;
   Work w;
   int rc = solve_core(ctx, d_y, n, p, tol, mixed, phi0, w);
   if (rc) return rc;
@@ -489,6 +489,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct BatchPlan {
   std::vector<int> idx;                      // caller index of every valid series
+  std::vector<const double*> y_dev;          // device series given by the caller (else packed in b_y64)
   std::vector<long long> n, m, off_y, off_u, off_part, off_cnt, ntd, ntf;
   std::vector<int> p;
   std::vector<size_t> off_vec, off_phi, off_mat;
@@ -541,7 +542,8 @@ int batch_grid(tols_ctx* ctx, int is_double, int p_pad) {
 }
 
 // d_y_packed: device series packed at B.off_y. Results: phi (device, packed at B.off_phi), states (host).
-int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states) {
+int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states,
+               bool no_precond = false) {
   const int cnt = (int)B.idx.size();
   if (cnt == 0) return TOLS_OK;
   int rc;
@@ -578,7 +580,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.m = B.m[k];
     w.p = p;
     w.p_pad = (int)pp1;
-    w.y64 = (const double*)ctx->b_y64.p + B.off_y[k];
+    w.y64 = B.y_dev.empty() ? (const double*)ctx->b_y64.p + B.off_y[k] : B.y_dev[k];
     w.y32 = mixed ? (float*)ctx->b_y32.p + B.off_y[k] : nullptr;
     w.U[0] = (char*)ctx->b_u0.p + ues * B.off_u[k];
     w.U[1] = (char*)ctx->b_u1.p + ues * B.off_u[k];
@@ -645,16 +647,17 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   const int gf = batch_grid(ctx, 0, B.p_pad_max), gd = batch_grid(ctx, 1, B.p_pad_max);
 
   // setup: float copy, Gram lag sums, preconditioner, LSQR start
-  if (mixed)
+  if (mixed && B.y_dev.empty())
     RUN(run_small(ctx, 11, [&] { return launch_convert_f32((const double*)ctx->b_y64.p, (float*)ctx->b_y32.p,
                                                            (long long)B.y_elems, ctx->stream); }));
+  else if (mixed)
+    RUN(run_small(ctx, 11, [&] { return launch_convert_batch(d_series, cnt, ctx->stream); }));
   BatchArgs ag = a;
   ag.gram = 1;
-  ag.gram_double = mixed ? 0 : 1;
   ctx->launch_total++;
   if (mixed) CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
   else CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
-  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
+  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
 
@@ -715,32 +718,58 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   return TOLS_OK;
 }
 
-// After a batched pass: series that need the single-series path (mixed refinement that stalled, or an exactly
-// rank-deficient X) are solved again one by one. phi_out: device, packed like b_phi.
-int batch_fixups(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states,
-                 std::vector<int>& prec_used) {
+// A plan over a subset of B's series (their float64 series stay where they are).
+BatchPlan sub_plan(tols_ctx* ctx, const BatchPlan& B, const std::vector<int>& which) {
+  BatchPlan S;
+  std::vector<long long> n;
+  std::vector<int> p;
+  for (int k : which) {
+    n.push_back(B.n[k]);
+    p.push_back(B.p[k]);
+  }
+  std::vector<int> st(which.size(), TOLS_OK);
+  plan_batch(S, (int)which.size(), n.data(), p.data(), st);
+  for (int k : which)
+    S.y_dev.push_back(B.y_dev.empty() ? (const double*)ctx->b_y64.p + B.off_y[k] : B.y_dev[k]);
+  return S;
+}
+
+// Run the batch, then, together as float64 sub-batches: the series the mixed path handed back (float products
+// cannot refine them: kappa(X)^2 u32 too large), and the exactly rank-deficient ones (plain LSQR from zero gives
+// the minimum norm). phi_host: coefficients packed at B.off_phi.
+int batch_solve_all(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states,
+                    std::vector<double>& phi_host, std::vector<int>& prec_used) {
   const int cnt = (int)B.idx.size();
   prec_used.assign(cnt, mixed ? TOLS_MIXED : TOLS_FP64);
-  for (int k = 0; k < cnt; ++k) {
-    const DevState& s = states[k];
-    const bool stalled = mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
-                         (s.mixed_ok == 0 || s.precond == 0);
-    const bool rankdef = s.singular && s.compatible && s.status >= 0;
-    if (!stalled && !rankdef) continue;
-    double* d_phi = (double*)ctx->b_phi.p + B.off_phi[k];
-    const double* d_y = (const double*)ctx->b_y64.p + B.off_y[k];
-    double rn = 0.0;
-    tols_info inf;
-    int rc = solve_device_impl(ctx, d_y, B.n[k], B.p[k], tol, d_phi, &rn, &inf, nullptr);
-    if (rc < 0) return rc;
-    DevState& t = states[k];
-    t.status = rc;
-    t.ne_ratio = inf.ne_ratio;
-    t.rnorm = inf.rnorm;
-    t.total_iter += inf.iters;
-    t.sweeps += inf.sweeps;
-    t.precond = inf.precond_used;
-    prec_used[k] = inf.precision_used;
+  phi_host.assign(B.phi_doubles, 0.0);
+  if (cnt == 0) return TOLS_OK;
+  int rc;
+  if ((rc = batch_core(ctx, B, tol, mixed, states))) return rc;
+  CK(cudaMemcpy(phi_host.data(), ctx->b_phi.p, sizeof(double) * B.phi_doubles, cudaMemcpyDeviceToHost));
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> which;
+    for (int k = 0; k < cnt; ++k) {
+      const DevState& s = states[k];
+      if (pass == 0 && mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
+          (s.mixed_ok == 0 || s.precond == 0))
+        which.push_back(k);
+      if (pass == 1 && s.singular && s.compatible && s.status >= 0) which.push_back(k);
+    }
+    if (which.empty()) continue;
+    BatchPlan S = sub_plan(ctx, B, which);
+    std::vector<DevState> sst;
+    if ((rc = batch_core(ctx, S, tol, false, sst, pass == 1))) return rc;
+    std::vector<double> sphi(S.phi_doubles);
+    CK(cudaMemcpy(sphi.data(), ctx->b_phi.p, sizeof(double) * S.phi_doubles, cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < which.size(); ++j) {
+      const int k = which[j];
+      if (pass == 1 && !(sst[j].status == TOLS_OK && sst[j].compatible)) continue;  // keep the first result
+      sst[j].total_iter += states[k].total_iter;
+      sst[j].sweeps += states[k].sweeps;
+      states[k] = sst[j];
+      memcpy(phi_host.data() + B.off_phi[k], sphi.data() + S.off_phi[j], sizeof(double) * B.p[k]);
+      prec_used[k] = TOLS_FP64;
+    }
   }
   return TOLS_OK;
 }
@@ -879,6 +908,9 @@ struct SrvRequest {
   double tol;
   std::vector<double> y;
   double t_submit;
+  bool mixed = false;       // precision of this attempt
+  bool no_precond = false;  // plain LSQR (minimum-norm repeat of an exactly rank-deficient problem)
+  int prior_iters = 0, prior_sweeps = 0;
 };
 
 struct SrvActive {
@@ -902,6 +934,7 @@ struct tols_server {
   size_t arena_cap = 0;
   ArenaAlloc alloc;
   std::deque<SrvRequest> queue;
+  std::vector<SrvRequest> requeue;
   std::vector<SrvActive> active;
   std::vector<tols_result> results;
   std::vector<double> result_phi;   // TOLS_MAX_P doubles per result
@@ -957,14 +990,15 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
   tols_ctx* ctx = srv->ctx;
   while (!srv->queue.empty() && (int)srv->active.size() < srv->max_active) {
     SrvRequest& r = srv->queue.front();
-    const size_t bytes = series_slice(nullptr, r.n, r.p, srv->mixed, nullptr);
+    const size_t bytes = series_slice(nullptr, r.n, r.p, r.mixed, nullptr);
     size_t off = 0;
     if (!srv->alloc.alloc(bytes, &off)) break;  // FIFO: the head waits until memory frees up
     SrvActive a;
     a.off = off;
     a.bytes = bytes;
-    series_slice(srv->arena + off, r.n, r.p, srv->mixed, &a.w);
-    const DevState st = initial_state(ctx->cfg, r.p, r.tol, srv->mixed);
+    series_slice(srv->arena + off, r.n, r.p, r.mixed, &a.w);
+    DevState st = initial_state(ctx->cfg, r.p, r.tol, r.mixed);
+    st.no_precond = r.no_precond ? 1 : 0;
     CK(cudaMemcpyAsync((void*)a.w.y64, r.y.data(), sizeof(double) * (size_t)r.n, cudaMemcpyHostToDevice,
                        ctx->stream));
     CK(cudaMemsetAsync(a.w.counters, 0, sizeof(unsigned) * (size_t)((((r.n - r.p) + kTileD - 1) / kTileD + kGroup - 1) / kGroup + 1),
@@ -980,17 +1014,27 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
   BatchArgs a;
   int pmax = 16;
   RUN(upload_table(srv, fresh, a, pmax));
-  if (srv->mixed)
-    for (int k : fresh) {
-      const Work& w = srv->active[k].w;
+  bool any_mixed = false, any_fp64 = false;
+  for (int k : fresh) {
+    const SrvActive& A = srv->active[k];
+    if (A.req.mixed) {
+      any_mixed = true;
+      const Work& w = A.w;
       RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
+    } else {
+      any_fp64 = true;
     }
+  }
   BatchArgs ag = a;
   ag.gram = 1;
-  ag.gram_double = srv->mixed ? 0 : 1;
-  ctx->launch_total++;
-  CK(srv->mixed ? launch_batch_pass<float>(ag, batch_grid(ctx, 0, pmax), pmax, ctx->stream)
-                : launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
+  if (any_mixed) {
+    ctx->launch_total++;
+    CK(launch_batch_pass<float>(ag, batch_grid(ctx, 0, pmax), pmax, ctx->stream));
+  }
+  if (any_fp64) {
+    ctx->launch_total++;
+    CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
+  }
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
   const int cnt = (int)fresh.size();
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(a.series, cnt, want, ctx->stream); }));
@@ -1017,12 +1061,15 @@ int server_round(tols_server* srv) {
   int pmax = 16;
   RUN(upload_table(srv, all, a, pmax));
   const int gf = batch_grid(ctx, 0, pmax), gd = batch_grid(ctx, 1, pmax);
+  bool any_mixed = false;
+  for (const SrvActive& A : srv->active) any_mixed |= A.req.mixed;
+  // float passes serve the mixed requests' iterations, double passes the float64 requests' iterations and every
+  // float64 check: interleaving them lets both kinds progress in every burst
   for (int k = 0; k < srv->burst; ++k) {
-    ctx->launch_total++;
-    CK(srv->mixed ? launch_batch_pass<float>(a, gf, pmax, ctx->stream)
-                  : launch_batch_pass<double>(a, gd, pmax, ctx->stream));
-  }
-  if (srv->mixed) {
+    if (any_mixed) {
+      ctx->launch_total++;
+      CK(launch_batch_pass<float>(a, gf, pmax, ctx->stream));
+    }
     ctx->launch_total++;
     CK(launch_batch_pass<double>(a, gd, pmax, ctx->stream));
   }
@@ -1050,29 +1097,24 @@ int server_round(tols_server* srv) {
       continue;
     }
     const double* phi = srv->h_phi.data() + (size_t)k * TOLS_MAX_P;
-    std::vector<double> fix;
-    int prec = srv->mixed ? TOLS_MIXED : TOLS_FP64;
-    const bool stalled = srv->mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
-                         (s.mixed_ok == 0 || s.precond == 0);
-    const bool rankdef = s.singular && s.compatible && s.status >= 0;
-    if (stalled || rankdef) {
-      // the single-series path handles these (float64 refinement, or plain LSQR for the minimum norm)
-      if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)A.req.p + 64)))) return rc;
-      double rn = 0.0;
-      tols_info inf;
-      rc = solve_device_impl(ctx, A.w.y64, A.req.n, A.req.p, A.req.tol, (double*)ctx->scratch.p, &rn, &inf, nullptr);
-      if (rc < 0) return rc;
-      fix.resize(A.req.p);
-      CK(cudaMemcpy(fix.data(), ctx->scratch.p, sizeof(double) * A.req.p, cudaMemcpyDeviceToHost));
-      phi = fix.data();
-      s.status = rc;
-      s.ne_ratio = inf.ne_ratio;
-      s.rnorm = inf.rnorm;
-      s.total_iter += inf.iters;
-      s.sweeps += inf.sweeps;
-      s.precond = inf.precond_used;
-      prec = inf.precision_used;
+    const bool hopeless = A.req.mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
+                          (s.mixed_ok == 0 || s.precond == 0);
+    const bool rankdef = s.singular && s.compatible && s.status >= 0 && !A.req.no_precond;
+    if (hopeless || rankdef) {
+      // back to the head of the queue as a float64 request (plain LSQR for the minimum norm when X is exactly
+      // rank deficient); it is batched with everything else from the next step on
+      SrvRequest r = std::move(A.req);
+      r.prior_iters += s.total_iter;
+      r.prior_sweeps += s.sweeps;
+      r.mixed = false;
+      if (rankdef) r.no_precond = true;
+      srv->alloc.release(A.off, A.bytes);
+      srv->requeue.push_back(std::move(r));
+      continue;
     }
+    s.total_iter += A.req.prior_iters;
+    s.sweeps += A.req.prior_sweeps;
+    const int prec = A.req.mixed ? TOLS_MIXED : TOLS_FP64;
     tols_result res;
     memset(&res, 0, sizeof res);
     res.id = A.req.id;
@@ -1089,6 +1131,8 @@ int server_round(tols_server* srv) {
     srv->completed++;
   }
   srv->active.swap(keep);
+  for (auto it = srv->requeue.rbegin(); it != srv->requeue.rend(); ++it) srv->queue.push_front(std::move(*it));
+  srv->requeue.clear();
   return TOLS_OK;
 }
 }  // namespace
@@ -1237,15 +1281,9 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
   CK(cudaMemcpyAsync(ctx->b_y64.p, ctx->h_stage, sizeof(double) * B.y_elems, cudaMemcpyHostToDevice, ctx->stream));
   const bool mixed = ctx->cfg.precision == TOLS_MIXED;
   std::vector<DevState> states;
-  if ((rc = batch_core(ctx, B, tol, mixed, states))) return rc;
   std::vector<int> prec_used;
-  if ((rc = batch_fixups(ctx, B, tol, mixed, states, prec_used))) return rc;
-  std::vector<double> phis(B.phi_doubles);
-  if (!phis.empty()) {
-    CK(cudaMemcpyAsync(phis.data(), ctx->b_phi.p, sizeof(double) * B.phi_doubles, cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
+  std::vector<double> phis;
+  if ((rc = batch_solve_all(ctx, B, tol, mixed, states, phis, prec_used))) return rc;
   int worst = TOLS_OK;
   for (int k = 0; k < count; ++k) {
     if (info) memset(&info[k], 0, sizeof(tols_info));
@@ -1266,6 +1304,52 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
     const int rc2 = status[k];
     if (rc2 < 0) worst = worst < 0 ? std::min(worst, rc2) : rc2;
     else if (worst >= 0) worst = std::max(worst, rc2);
+  }
+  return worst;
+}
+
+int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
+                                      const int* p, double tol, double* d_phi, double* rnorm, tols_info* info) {
+  if (!ctx || count < 0 || (count > 0 && (!d_y || !n || !p || !d_phi))) return TOLS_ERR_ARG;
+  if (count == 0) return TOLS_OK;
+  cudaSetDevice(ctx->device);
+  if (tol <= 0) tol = 1e-12;
+  std::vector<int> status(count, TOLS_OK);
+  BatchPlan B;
+  plan_batch(B, count, n, p, status);
+  for (int k : B.idx) {
+    if (!d_y[k]) return fail(ctx, TOLS_ERR_ARG, "null device series pointer");
+    B.y_dev.push_back(d_y[k]);
+  }
+  const bool mixed = ctx->cfg.precision == TOLS_MIXED;
+  std::vector<DevState> states;
+  std::vector<int> prec_used;
+  std::vector<double> phis;
+  int rc;
+  if ((rc = batch_solve_all(ctx, B, tol, mixed, states, phis, prec_used))) return rc;
+  // output: phi of series k at d_phi + sum_{j<k} p[j]
+  std::vector<size_t> out_off(count + 1, 0);
+  for (int k = 0; k < count; ++k) out_off[k + 1] = out_off[k] + (size_t)std::max(p[k], 0);
+  std::vector<double> outv(out_off[count], 0.0);
+  for (size_t j = 0; j < B.idx.size(); ++j)
+    memcpy(outv.data() + out_off[B.idx[j]], phis.data() + B.off_phi[j], sizeof(double) * B.p[j]);
+  CK(cudaMemcpyAsync(d_phi, outv.data(), sizeof(double) * outv.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int worst = TOLS_OK;
+  for (int k = 0; k < count; ++k) {
+    if (info) memset(&info[k], 0, sizeof(tols_info));
+    if (rnorm) rnorm[k] = 0.0;
+  }
+  for (size_t j = 0; j < B.idx.size(); ++j) {
+    const int k = B.idx[j];
+    status[k] = states[j].status;
+    if (rnorm) rnorm[k] = states[j].rnorm;
+    if (info) fill_info(&info[k], states[j], prec_used[j]);
+  }
+  for (int k = 0; k < count; ++k) {
+    if (info) info[k].status = status[k];
+    if (status[k] < 0) worst = worst < 0 ? std::min(worst, status[k]) : status[k];
+    else if (worst >= 0) worst = std::max(worst, status[k]);
   }
   return worst;
 }
@@ -1542,7 +1626,8 @@ int toeplitz_ols_server_destroy(tols_server* srv) {
 
 int toeplitz_ols_server_submit(tols_server* srv, long long id, const double* y, long long n, int p, double tol) {
   if (!srv || !y || p < 1 || p > TOLS_MAX_P || n <= p) return TOLS_ERR_ARG;
-  if (align_up(series_slice(nullptr, n, p, srv->mixed, nullptr), 256) > srv->arena_cap) return TOLS_ERR_OOM;
+  // a mixed request may be re-run in float64, which needs the larger footprint
+  if (align_up(series_slice(nullptr, n, p, false, nullptr), 256) > srv->arena_cap) return TOLS_ERR_OOM;
   SrvRequest r;
   r.id = id;
   r.n = n;
@@ -1550,6 +1635,7 @@ int toeplitz_ols_server_submit(tols_server* srv, long long id, const double* y, 
   r.tol = tol > 0 ? tol : 1e-12;
   r.y.assign(y, y + n);
   r.t_submit = now_s(srv->t0);
+  r.mixed = srv->mixed;
   srv->queue.push_back(std::move(r));
   srv->submitted++;
   return TOLS_OK;

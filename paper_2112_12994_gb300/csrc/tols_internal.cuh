@@ -55,6 +55,8 @@ struct DevState {
   int done;          // 1 => every pass kernel returns at once
   int singular;      // the Gram matrix was singular at working precision
   int compatible;    // a check found ||r|| <= tol ||b||
+  int shifted;       // the Cholesky factor needed the diagonal shift
+  int no_precond;    // set by the host: plain LSQR (minimum-norm repeat of a rank-deficient problem)
 };
 
 // Device pointers of one solve's workspace.
@@ -117,7 +119,6 @@ struct BatchArgs {
   const int* tile_series_d;     // double tile list: tile -> series
   long long tiles_f, tiles_d;
   int gram;                     // 1: Gram lag-sum pass (TAIL_GRAM) instead of a solver pass
-  int gram_double;              // for gram passes: which precision runs it
   unsigned int* done_count;     // incremented once per series that reaches PH_DONE
 };
 
@@ -134,6 +135,7 @@ const void* batch_kernel_ptr(int is_double);
 cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s);
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s);
 cudaError_t launch_finish_batch(const BatchSeries* series, int count, cudaStream_t s);
+cudaError_t launch_convert_batch(const BatchSeries* series, int count, cudaStream_t s);
 cudaError_t launch_convert_f32(const double* y, float* y32, long long n, cudaStream_t s);
 cudaError_t launch_precond(Work w, int mixed, cudaStream_t s);
 cudaError_t launch_init_lsqr(Work w, int mixed, cudaStream_t s);

@@ -285,7 +285,10 @@ __device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double 
   const double arnorm = new_phibar * alpha * fabs(c);
   const double ratio = (new_phibar > 0 && anorm2 > 0) ? arnorm / (sqrt(anorm2) * new_phibar) : 0.0;
   const int iter = st->iter + 1;
-  const double tolA = st->mixed ? st->tol_inner : st->est_ratio;
+  // the float64 floor of the ratio is about u sqrt(p) ||b|| / ||r|| (r = b - X phi carries an absolute error of
+  // order u ||b||); LSQR's estimate of ||r|| is phibar
+  const double floor64 = new_phibar > 0 ? 1e-15 * sqrt((double)p) * st->bnorm / new_phibar : 0.0;
+  const double tolA = st->mixed ? st->tol_inner : fmax(st->est_ratio, floor64);
   // Paige-Saunders stopping tests: ||A^T r|| <= tol ||A|| ||r||, or a compatible system ||r|| <= tol ||rhs||
   const bool stop = (ratio <= tolA) || (new_phibar <= tolA * st->beta1) || (beta == 0.0) || (alpha == 0.0) ||
                     (iter >= st->iter_cap) ||
@@ -765,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) batch_pass_kernel(
     const int nlag = gram ? p + 1 : p;
     if (tid == 0) {
       int skip = 0;
-      if (gram) skip = (a.gram_double != is_double);
+      if (gram) skip = (w.st->mixed ? 0 : 1) != is_double;   // Gram lag sums in the series' own precision
       else skip = !select_phase<T>(w.st, y, p, w, tail, u_old, u_new, coef);
       s_skip = skip;
     }
@@ -859,6 +862,7 @@ __device__ void precond_body(const Work& w, int want_precond) {
   DevState* st = w.st;
   __shared__ double scratch[16];
   __shared__ int s_fail;
+  __shared__ int s_shift;
   __shared__ double s_val[2];
   double* G = w.G;
   // ||X||_F^2 = trace(G)
@@ -923,7 +927,7 @@ __device__ void precond_body(const Work& w, int want_precond) {
 
   // Cholesky G = R^T R on the upper triangle (right-looking), first without a shift. If a pivot falls to
   // rounding level (<= p u max_j G_jj, u of the precision G was formed in: G singular at working precision) or
-  // the factor has kappa(R)^2 u > 1e-3 (not trustworthy), G is refactored with the shift
+  // the factor is not trustworthy (kappa(R)^2 u > 1, or > 1e-3 for the float Gram), G is refactored with the shift
   // lambda = 10 p u max_j G_jj, which bounds kappa(X R^{-1}) by about sqrt(lambda) kappa(X). A singular G is
   // flagged: if the solve then turns out compatible (an exactly rank-deficient X), the host repeats it with plain
   // LSQR from zero, which returns the minimum-norm solution (Thm. "Solution to OLS problem").
@@ -932,9 +936,12 @@ __device__ void precond_body(const Work& w, int want_precond) {
     for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) w.M[q] = G[q];  // keep G for a refactor
     __syncthreads();
   }
-  for (int attempt = 0; attempt < 2 && want_precond; ++attempt) {
+  if (threadIdx.x == 0) s_shift = 0;
+  __syncthreads();
+  for (int attempt = 0; attempt < 2 && want_precond && !st->no_precond; ++attempt) {
     double lambda = 0.0;
     if (attempt == 1) {
+      if (threadIdx.x == 0) s_shift = 1;
       lambda = 10.0 * (double)p * ueps * dmax;
       for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.M[q];
       __syncthreads();
@@ -986,9 +993,11 @@ __device__ void precond_body(const Work& w, int want_precond) {
     }
     __syncthreads();
     const double cond = s_val[1];
-    if (attempt == 0 && cond * cond * ueps <= 1e-3) break;  // unshifted factor is trustworthy
+    // unshifted factor trustworthy: a float64 factor still preconditions well while kappa(R)^2 u <= 1; the float
+    // Gram of the mixed path must also let float refinement contract, which needs kappa^2 u32 well below 1
+    if (attempt == 0 && cond * cond * ueps <= (st->mixed ? 1e-3 : 1.0)) break;
   }
-  const int ok = want_precond && !s_fail;
+  const int ok = want_precond && !st->no_precond && !s_fail;
   if (ok) {
     // M = R^{-1}: column c by back substitution (each thread its own columns)
     for (int c = threadIdx.x; c < p; c += kThreads) {
@@ -1011,6 +1020,7 @@ __device__ void precond_body(const Work& w, int want_precond) {
     if (threadIdx.x == 0) {
       st->precond = 1;
       st->cond_est = s_val[1];
+      st->shifted = s_shift;
     }
   } else {
     if (threadIdx.x == 0) { st->precond = 0; st->cond_est = 0.0; }
@@ -1032,11 +1042,26 @@ cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_
 }
 
 // LSQR start on rhs = b with X^T b = h and ||b|| = bnorm (already in state).
+// A mixed solve whose float Gram matrix needed the shifted factorisation (kappa(R)^2 u32 > 1e-3, or singular)
+// cannot be refined with float products: it is handed back to the float64 path at once.
+__device__ bool mixed_hopeless(DevState* st) {
+  if (!(st->mixed && (st->shifted || st->singular))) return false;
+  if (threadIdx.x == 0) {
+    st->mixed_ok = 0;
+    st->status = TOLS_NOT_CONVERGED;
+    st->phase = PH_DONE;
+    st->done = 1;
+  }
+  __syncthreads();
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads) init_lsqr_kernel(Work w) {
   __shared__ double scratch[16];
   DevState* st = w.st;
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
+  if (mixed_hopeless(st)) return;
   start_lsqr(w, st, w.h, st->bnorm, scratch);
 }
 
@@ -1056,6 +1081,10 @@ __global__ void __launch_bounds__(kThreads) init_lsqr_batch_kernel(const BatchSe
   }
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
+  if (mixed_hopeless(st)) {
+    if (threadIdx.x == 0 && done) atomicAdd(done, 1u);
+    return;
+  }
   start_lsqr(w, st, w.h, st->bnorm, scratch);
 }
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s) {
@@ -1096,6 +1125,16 @@ __global__ void gather_batch_kernel(const BatchSeries* series, DevState* states,
 cudaError_t launch_gather_batch(const BatchSeries* series, int count, DevState* states, double* phis, int stride,
                                 cudaStream_t s) {
   gather_batch_kernel<<<count, 128, 0, s>>>(series, states, phis, stride);
+  return cudaGetLastError();
+}
+
+// float copies of every series of a batch (one CTA per series)
+__global__ void convert_batch_kernel(const BatchSeries* series) {
+  const Work& w = series[blockIdx.x].w;
+  for (long long i = threadIdx.x; i < w.n; i += blockDim.x) w.y32[i] = (float)w.y64[i];
+}
+cudaError_t launch_convert_batch(const BatchSeries* series, int count, cudaStream_t s) {
+  convert_batch_kernel<<<count, 512, 0, s>>>(series);
   return cudaGetLastError();
 }
 

@@ -102,3 +102,18 @@ def test_batch_rank_deficient_member_gets_min_norm(tols, ctx):
     phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(ctx, ys, [5, 4], 1e-12)
     assert np.allclose(phis[0], 0.2, atol=1e-10)
     assert coef_rel_err(phis[1], oracle.ols_qr(ys[1], 4).phi) <= 1e-6
+
+
+def test_batched_device_equals_host_batched(tols, ctx):
+    import torch
+    ys, ps = _batch(10, 44, 2_000, 90_000, 1, 90)
+    phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(ctx, ys, ps, 1e-12)
+    d_ys = [torch.tensor(y, dtype=torch.float64, device="cuda") for y in ys]
+    d_phi = torch.empty(sum(ps), dtype=torch.float64, device="cuda")
+    rn_d, infos_d, rc_d = tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, 1e-12)
+    assert rc == rc_d == tols.TOLS_OK
+    out = d_phi.cpu().numpy()
+    off = 0
+    for phi, p in zip(phis, ps):
+        assert np.array_equal(out[off:off + p], phi)
+        off += p

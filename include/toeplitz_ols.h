@@ -206,7 +206,8 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
  * allocator (a framework's caching allocator, or a pool reserved up front to a fixed budget), where an extra
  * cudaMalloc could fail or break the budget, and latency-critical loops that cannot afford cudaMalloc/cudaFree,
  * which can synchronise the device. It needs no context and calls no allocating routine.
- *   - Same operation and arguments as toeplitz_ols_gk_pass, except: ||u_new||^2 is written to d_unorm2 (one
+ *   - Same operation and arguments as toeplitz_ols_gk_pass, always with the direct (sliding-window) products, as
+ *     toeplitz_ols_gk_pass computes them under TOLS_PRODUCT_DIRECT, except: ||u_new||^2 is written to d_unorm2 (one
  *     double, device), and the call only enqueues work on cuda_stream (a cudaStream_t; NULL = the legacy default
  *     stream) of the current device and returns without waiting: synchronise the stream before reading outputs.
  *   - The cross-CTA partial sums live in one fixed array of about 660 KB inside the library image, present on

@@ -13,6 +13,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <math.h>
+
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -47,7 +49,7 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -56,8 +58,12 @@ struct tols_ctx {
   std::string err;
   std::map<int, StreamSeries> streams;
   int next_handle = 1;
-  int grid[2] = {0, 0};         // pass grid (float, double)
-  size_t grid_pad[2] = {0, 0};  // p_pad the grid was computed for
+  int grid[4] = {0, 0, 0, 0};         // pass grid (float, double; direct, FFT)
+  size_t grid_pad[4] = {0, 0, 0, 0};  // p_pad the grid was computed for
+  void* tw32 = nullptr;               // FFT twiddle tables (float2[4096], double2[2048])
+  void* tw64 = nullptr;
+  std::map<int, int> fft_choice;      // autotuner: key (is_double, p_pad) -> 1 FFT, 0 direct
+  int last_fft = 0;                   // product of the last solve's iteration passes
   // instrumentation (toeplitz_ols_profile)
   bool prof = false;
   long long launch_total = 0;
@@ -201,18 +207,72 @@ int run_small(tols_ctx* ctx, int kind, F launch) {
     if (rc_) return rc_;                \
   } while (0)
 
-int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad) {
-  if (ctx->grid[is_double] == 0 || ctx->grid_pad[is_double] != (size_t)p_pad) {
+int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
+  const int slot = is_double + 2 * fft;
+  if (ctx->grid[slot] == 0 || ctx->grid_pad[slot] != (size_t)p_pad) {
     int nb = 0;
-    const size_t smem = pass_smem_bytes(is_double, p_pad);
-    cudaFuncSetAttribute(pass_kernel_ptr(is_double), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel_ptr(is_double), kThreads, smem) != cudaSuccess ||
-        nb < 1)
-      nb = 1;
-    ctx->grid[is_double] = std::min(kMaxGrid, ctx->sms * std::min(nb, 4));
-    ctx->grid_pad[is_double] = p_pad;
+    const void* fn = fft ? fft_kernel_ptr(is_double) : pass_kernel_ptr(is_double);
+    const size_t smem = pass_smem_bytes(is_double, p_pad, fft);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
+    ctx->grid[slot] = std::min(kMaxGrid, ctx->sms * std::min(nb, 4));
+    ctx->grid_pad[slot] = p_pad;
   }
-  return ctx->grid[is_double];
+  return ctx->grid[slot];
+}
+
+// Product kernel for a pass over series y (T = float or double): the sliding-window direct products or the
+// overlap-save FFT. DIRECT / FFT force one; AUTO times both once per (precision, p_pad) on the series at hand
+// when it is long enough for the choice to matter (cached in the context), else picks by p.
+template <typename T>
+int choose_fft(tols_ctx* ctx, const Work& w, const T* y, long long n, int p, int p_pad, int nlag, int gram) {
+  const int is_double = sizeof(T) == 8;
+  if (p_pad >= fft_size(is_double) / 2) return 0;       // too few rows per FFT tile
+  if (ctx->cfg.product == TOLS_PRODUCT_DIRECT) return 0;
+  if (ctx->cfg.product == TOLS_PRODUCT_FFT) return 1;
+  const long long m = n - p;
+  const int key = is_double * 100000 + p_pad * 2 + gram;
+  auto it = ctx->fft_choice.find(key);
+  if (it != ctx->fft_choice.end()) return it->second;
+  const int guess = p_pad >= (is_double ? 32 : 64);
+  if (m < (1 << 20) || ensure(ctx, ctx->tune, sizeof(double) * (4 * (size_t)p_pad + 64)) != TOLS_OK) return guess;
+  double* sc = (double*)ctx->tune.p;
+  PassArgs<T> a;
+  memset(&a, 0, sizeof a);
+  a.y = y;
+  a.n = n;
+  a.m = m;
+  a.p = p;
+  a.p_pad = p_pad;
+  a.nlag = nlag;
+  a.gram = gram;
+  a.d = sc + 2 * p_pad;           // contents do not matter for timing
+  a.d_scale = 1.0;
+  a.tail = TAIL_STORE;
+  a.w = w;
+  a.out_t = sc;
+  a.out_n2 = sc + p_pad + 8;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best[2] = {0.f, 0.f};
+  for (int f = 0; f < 2; ++f) {
+    a.fft = f;
+    const int grid = pass_grid_for(ctx, is_double, p_pad, f);
+    launch_pass<T>(a, grid, ctx->stream);                 // warm-up
+    cudaEventRecord(e0, ctx->stream);
+    launch_pass<T>(a, grid, ctx->stream);
+    launch_pass<T>(a, grid, ctx->stream);
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&best[f], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return guess;
+  const int choice = best[1] < best[0] ? 1 : 0;
+  ctx->fft_choice[key] = choice;
+  return choice;
 }
 
 // Lay out one solve's workspace in the context buffers. y64 is the caller's (or staged) device series.
@@ -273,6 +333,8 @@ int prepare_work(tols_ctx* ctx, const double* y64, long long n, int p, bool mixe
   w.Mt32 = f;
   if ((rc = ensure(ctx, ctx->state, sizeof(DevState)))) return rc;
   w.st = (DevState*)ctx->state.p;
+  w.tw32 = ctx->tw32;
+  w.tw64 = ctx->tw64;
   return TOLS_OK;
 }
 
@@ -308,14 +370,16 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond) {
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg)));
+    a.fft = choose_fft<float>(ctx, w, w.y32, w.n, w.p, pg, w.p + 1, 1);
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
   } else {
     PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
     a.gram = 1;
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg)));
+    a.fft = choose_fft<double>(ctx, w, w.y64, w.n, w.p, pg, w.p + 1, 1);
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
@@ -329,7 +393,7 @@ void fill_info(tols_info* info, const DevState& s, int prec) {
   info->sweeps = s.sweeps;
   info->precision_used = prec;
   info->precond_used = s.precond;
-  info->product_used = TOLS_PRODUCT_DIRECT;
+  info->product_used = TOLS_PRODUCT_DIRECT;  // overwritten by the single-series path when it used the FFT
   info->ne_ratio = s.ne_ratio;
   info->rnorm = s.rnorm;
   info->bnorm = s.bnorm;
@@ -376,11 +440,14 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   PassArgs<double> ad = base_args<double>(w, w.y64, n, p, pp);
   ad.check_done = 1;
   ad.d = w.d;
+  ad.fft = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
   PassArgs<float> af = base_args<float>(w, w.y32, n, p, pp);
   af.check_done = 1;
   af.d = w.d;
-  const int gd = pass_grid_for(ctx, 1, pp);
-  const int gf = mixed ? pass_grid_for(ctx, 0, pp) : 0;
+  af.fft = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0) : 0;
+  ctx->last_fft = mixed ? af.fft : ad.fft;
+  const int gd = pass_grid_for(ctx, 1, pp, ad.fft);
+  const int gf = mixed ? pass_grid_for(ctx, 0, pp, af.fft) : 0;
   const long long max_launch = (long long)(max_iter + 4) * (max_sweeps + 2) * 2 + 16;
   long long launched = 0;
   int burst = 4;
@@ -449,6 +516,7 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
   CK(cudaStreamSynchronize(ctx->stream));
   if (rnorm) *rnorm = s.rnorm;
   fill_info(info, s, mixed ? TOLS_MIXED : TOLS_FP64);
+  if (info && ctx->last_fft) info->product_used = TOLS_PRODUCT_FFT;
   return s.status;
 }
 
@@ -1203,6 +1271,27 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
     delete ctx;
     return TOLS_ERR_OOM;
   }
+  {
+    // FFT twiddles exp(-2 pi i t / N) in float64 on the host (libm), rounded to float for the float table
+    std::vector<double2> t64(2048);
+    std::vector<float2> t32(4096);
+    for (int t = 0; t < 2048; ++t) {
+      const double a = -2.0 * M_PI * (double)t / 2048.0;
+      t64[t] = make_double2(cos(a), sin(a));
+    }
+    for (int t = 0; t < 4096; ++t) {
+      const double a = -2.0 * M_PI * (double)t / 4096.0;
+      t32[t] = make_float2((float)cos(a), (float)sin(a));
+    }
+    if (cudaMalloc(&ctx->tw64, sizeof(double2) * 2048) != cudaSuccess ||
+        cudaMalloc(&ctx->tw32, sizeof(float2) * 4096) != cudaSuccess ||
+        cudaMemcpy(ctx->tw64, t64.data(), sizeof(double2) * 2048, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->tw32, t32.data(), sizeof(float2) * 4096, cudaMemcpyHostToDevice) != cudaSuccess) {
+      if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+      delete ctx;
+      return TOLS_ERR_OOM;
+    }
+  }
   if (cudaMallocHost(&ctx->h_state, sizeof(DevState)) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1219,11 +1308,13 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->y64,    &ctx->y32,   &ctx->u0,    &ctx->u1,     &ctx->part,    &ctx->vecs,
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
-                    &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles};
+                    &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
   if (ctx->h_worklog) cudaFreeHost(ctx->h_worklog);
+  if (ctx->tw32) cudaFree(ctx->tw32);
+  if (ctx->tw64) cudaFree(ctx->tw64);
   if (ctx->d_worklog) cudaFree(ctx->d_worklog);
   for (auto& q : ctx->pending) { cudaEventDestroy(q.e0); cudaEventDestroy(q.e1); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
@@ -1414,7 +1505,8 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     a.tail = TAIL_STORE;
     a.out_t = d_xtu;
     a.out_n2 = d_n2;
-    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp)));
+    a.fft = choose_fft<double>(ctx, w, (const double*)d_y, n, p, pp, p, 0);
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
   } else {
     PassArgs<float> a = base_args<float>(w, (const float*)d_y, n, p, pp);
     a.d = d_v;
@@ -1424,7 +1516,8 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     a.tail = TAIL_STORE;
     a.out_t = d_xtu;
     a.out_n2 = d_n2;
-    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pp)));
+    a.fft = choose_fft<float>(ctx, w, (const float*)d_y, n, p, pp, p, 0);
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pp, a.fft)));
   }
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1453,14 +1546,16 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
     a.nlag = p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg)));
+    a.fft = choose_fft<float>(ctx, w, w.y32, n, p, pg, p + 1, 1);
+    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
   } else {
     PassArgs<double> a = base_args<double>(w, d_y, n, p, pg);
     a.gram = 1;
     a.nlag = p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg)));
+    a.fft = choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
+    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, w.bnorm2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1505,7 +1600,8 @@ int toeplitz_ols_residual(tols_ctx* ctx, const double* d_y, long long n, int p, 
   a.tail = TAIL_STORE;
   a.out_t = d_g;
   a.out_n2 = d_n2;
-  RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp)));
+  a.fft = choose_fft<double>(ctx, w, d_y, n, p, pp, p, 0);
+  RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

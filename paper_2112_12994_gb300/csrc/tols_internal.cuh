@@ -80,6 +80,8 @@ struct Work {
   float* Mt32;
   double* bnorm2;         // device scalar ||b||^2 written by the Gram pass
   DevState* st;
+  const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
+  const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
 };
 
 // Arguments of a pass kernel (passed by value).
@@ -103,6 +105,7 @@ struct PassArgs {
   int check_done;         // 1: return at once when w.st->done is set
   int* worklog;           // nullable: the tail writes 1 + tail + 5 * (T == double) into worklog[work_slot]
   int work_slot;
+  int fft;                // 1: overlap-save FFT products (fft_pass_kernel) instead of the direct ones
 };
 
 // One series of a batch (device array). Its Work points at the series' own slices of the batch buffers; its
@@ -123,7 +126,9 @@ struct BatchArgs {
 };
 
 // Launch helpers (tols_kernels.cu).
-size_t pass_smem_bytes(int is_double, int p_pad);
+size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
+const void* fft_kernel_ptr(int is_double);
+int fft_size(int is_double);              // N of the real FFT per tile (float 4096, double 2048)
 int pass_tile_rows(int is_double);
 const void* pass_kernel_ptr(int is_double);
 template <typename T>

@@ -697,6 +697,8 @@ __device__ void run_tail(int tail, const Work& w, int gram, int nlag, const doub
   }
 }
 
+#include "tols_fft.cuh"
+
 // ------------------------------------------------------------------------------------------------------
 // Single-series pass kernel: each CTA accumulates its tiles, the CTAs then arrive.
 template <typename T>
@@ -805,27 +807,34 @@ static size_t pass_smem(int p_pad) {
 
 template <typename T>
 cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
-  const size_t smem = pass_smem<T>(a.p_pad);
-  static int configured[2] = {0, 0};
-  const int which = sizeof(T) == 8;
+  static int configured[4] = {0, 0, 0, 0};
+  const int which = (sizeof(T) == 8) + 2 * (a.fft != 0);
   if (!configured[which]) {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(a.fft ? (const void*)fft_pass_kernel<T> : (const void*)pass_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     configured[which] = 1;
   }
-  const long long ntiles = (a.m + TileCfg<T>::TILE - 1) / TileCfg<T>::TILE;
+  const long long rows_per_tile = a.fft ? (long long)(FftCfg<T>::N - a.p_pad) : (long long)TileCfg<T>::TILE;
+  const long long ntiles = (a.m + rows_per_tile - 1) / rows_per_tile;
   int g = (int)lmin((long long)grid, ntiles);
   if (g < 1) g = 1;
-  pass_kernel<T><<<g, kThreads, smem, s>>>(a);
+  if (a.fft) fft_pass_kernel<T><<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
+  else pass_kernel<T><<<g, kThreads, pass_smem<T>(a.p_pad), s>>>(a);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_pass<float>(const PassArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_pass<double>(const PassArgs<double>&, int, cudaStream_t);
 
-size_t pass_smem_bytes(int is_double, int p_pad) {
+size_t pass_smem_bytes(int is_double, int p_pad, int fft) {
+  if (fft) return is_double ? fft_pass_smem<double>(p_pad) : fft_pass_smem<float>(p_pad);
   return is_double ? pass_smem<double>(p_pad) : pass_smem<float>(p_pad);
 }
+const void* fft_kernel_ptr(int is_double) {
+  return is_double ? (const void*)fft_pass_kernel<double> : (const void*)fft_pass_kernel<float>;
+}
+int fft_size(int is_double) { return is_double ? FftCfg<double>::N : FftCfg<float>::N; }
 int pass_tile_rows(int is_double) { return is_double ? TileCfg<double>::TILE : TileCfg<float>::TILE; }
 const void* pass_kernel_ptr(int is_double) {
   return is_double ? (const void*)pass_kernel<double> : (const void*)pass_kernel<float>;

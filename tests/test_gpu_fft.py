@@ -1,0 +1,110 @@
+"""The overlap-save FFT product pass against the oracle (forced with TOLS_PRODUCT_FFT), and FFT solves.
+
+FFT correlations are accurate normwise: for one tile the error of IDFT(DFT(a) . conj(DFT(b))) is within
+c u log2(N) ||a||_2 ||b||_2 (c a small constant; 8 is used), with ||window||_2 <= sqrt(N) max|y|. Tiles have
+N = 4096 (float32) or 2048 (float64) points and m spans several of them with a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import ar_series
+from tests.helpers import assert_solve_parity
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    return _t
+
+
+@pytest.fixture(scope="module")
+def tols():
+    import paper_2112_12994_gb300 as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def fctx(tols):
+    c = tols.Context(precision=tols.TOLS_FP64, product=tols.TOLS_PRODUCT_FFT)
+    yield c
+    c.close()
+
+
+CASES = [(1, 9 * 2048 + 77), (17, 3 * 4096 + 5), (100, 5 * 4096 + 333), (257, 20_000), (500, 30_000)]
+
+
+@pytest.mark.parametrize("p,n", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fft_gk_pass(torch, tols, fctx, p, n, prec):
+    rng = np.random.default_rng(p * 13 + n)
+    y = ar_series(n, 3, config_id=51, series_index=p).y
+    m = n - p
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    P = tols.TOLS_FP64 if prec == "fp64" else tols.TOLS_MIXED
+    u_eps, N = (U64, 2048) if prec == "fp64" else (U32, 4096)
+    yr = y if prec == "fp64" else y.astype(np.float32).astype(np.float64)
+    v = rng.standard_normal(p)
+    vr = v if prec == "fp64" else v.astype(np.float32).astype(np.float64)
+    u_old = rng.standard_normal(m)
+    uor = u_old if prec == "fp64" else u_old.astype(np.float32).astype(np.float64)
+    c = 0.731
+    cr = c if prec == "fp64" else float(np.float32(c))
+    X, _ = oracle.lag_matrix(yr, p)
+    ref_u = X @ vr - cr * uor
+    d_y = torch.tensor(y, dtype=dt, device="cuda")
+    d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
+    d_uo = torch.tensor(u_old, dtype=dt, device="cuda")
+    d_un = torch.empty(m, dtype=dt, device="cuda")
+    d_t = torch.empty(p, dtype=torch.float64, device="cuda")
+    n2 = tols.toeplitz_ols_gk_pass(fctx, P, d_y, n, p, d_v, d_uo, c, d_un, d_t)
+    u = d_un.cpu().numpy().astype(np.float64)
+    t = d_t.cpu().numpy()
+    k = 8 * u_eps * math.log2(N)
+    win = math.sqrt(N) * np.max(np.abs(yr))
+    bound_u = k * win * np.linalg.norm(vr) + 2 * u_eps * np.abs(cr * uor)
+    assert np.all(np.abs(u - ref_u) <= bound_u)
+    ref_t = X.T @ u
+    tiles = math.ceil(m / (N - ((p + 15) // 16) * 16))
+    bound_t = k * win * math.sqrt(tiles) * np.linalg.norm(u) + (m + p) * u_eps * (np.abs(X.T) @ np.abs(u))
+    assert np.all(np.abs(t - ref_t) <= bound_t)
+    assert n2 == pytest.approx(float(u @ u), rel=64 * u_eps)
+
+
+@pytest.mark.parametrize("p,n", [(10, 10_000), (100, 3 * 2048 + 333), (300, 20_000)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fft_gram(torch, tols, fctx, p, n, prec):
+    y = ar_series(n, 4, config_id=52, series_index=p).y
+    G_ref, h_ref = oracle.gram(y, p)
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_G = torch.empty(p * p, dtype=torch.float64, device="cuda")
+    d_h = torch.empty(p, dtype=torch.float64, device="cuda")
+    P = tols.TOLS_FP64 if prec == "fp64" else tols.TOLS_MIXED
+    tols.toeplitz_ols_gram(fctx, P, d_y, n, p, d_G, d_h)
+    G = d_G.cpu().numpy().reshape(p, p)
+    u_eps, N = (U64, 2048) if prec == "fp64" else (U32, 4096)
+    m = n - p
+    tiles = math.ceil(m / (N - ((p + 1 + 15) // 16) * 16))
+    win = math.sqrt(N) * np.max(np.abs(y))
+    bound = 8 * u_eps * math.log2(N) * win * win * tiles + (4 if prec == "mixed" else 0) * U32 * np.sum(y * y)
+    assert np.max(np.abs(G - G_ref)) <= bound
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,p", [(10_000, 10), (300_000, 100), (60_000, 400)])
+def test_fft_solve_matches_oracle(tols, prec, n, p):
+    s = ar_series(n, p, config_id=53, series_index=p, root_lo=2.0, root_hi=4.0, max_log10_bound=6.0)
+    sol = oracle.ols_qr(s.y, p)
+    P = tols.TOLS_FP64 if prec == "fp64" else tols.TOLS_MIXED
+    with tols.Context(precision=P, product=tols.TOLS_PRODUCT_FFT) as ctx:
+        phi, rnorm, info, rc = tols.toeplitz_ols_solve(ctx, s.y, p, 1e-12)
+    assert rc == tols.TOLS_OK, info
+    assert info["product_used"] == tols.TOLS_PRODUCT_FFT
+    assert_solve_parity(s.y, p, phi, sol, 1e-8 if prec == "fp64" else 1e-6)

@@ -30,7 +30,8 @@ def tols():
 
 @pytest.fixture(scope="module")
 def ctx(tols):
-    c = tols.Context(precision=tols.TOLS_FP64)
+    # the direct (sliding-window) kernels; the FFT kernels are covered in test_gpu_fft.py
+    c = tols.Context(precision=tols.TOLS_FP64, product=tols.TOLS_PRODUCT_DIRECT)
     yield c
     c.close()
 

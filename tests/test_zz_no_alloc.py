@@ -36,10 +36,10 @@ def test_noalloc_pass_matches_context_pass(prec, p, n):
     d_uo = torch.tensor(rng.standard_normal(m), dtype=dt, device="cuda")
     c = 0.731
 
-    # the existing entry point (context, arena) gives the reference
+    # the existing entry point (context, arena) gives the reference, pinned to the same direct-product kernel
     ref_u = torch.empty(m, dtype=dt, device="cuda")
     ref_t = torch.empty(p, dtype=torch.float64, device="cuda")
-    with t.Context() as ctx:
+    with t.Context(product=t.TOLS_PRODUCT_DIRECT) as ctx:
         ref_n2 = t.toeplitz_ols_gk_pass(ctx, P, d_y, n, p, d_v, d_uo, c, ref_u, ref_t)
     ref_u_h = ref_u.cpu().numpy().astype(np.float64)
     ref_t_h = ref_t.cpu().numpy()

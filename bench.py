@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused product pass (toeplitz_ols_gk_pass), float64 then float32")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--only", default="", help="kernel-only: comma list of direct_fp64,direct_fp32,fft_fp64,fft_fp32")
+    ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
     ap.add_argument("--batch-series", type=int, default=1024,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
     ap.add_argument("--serve-requests", type=int, default=400,
@@ -298,17 +300,28 @@ def run_ours(args, wl):
         cnt, ms = prof[key]
         return (ms / cnt if cnt else float("nan")), cnt
 
-    # dominant kernel of the FP64 step and its roofline (float64 FMA units bound it; see the design notes)
+    # dominant kernel of the FP64 step and its roofline (float64 FMA units bound it; see the design notes).
+    # Algorithmic flops per launch: direct products 4 m p (2 m p multiply-adds); overlap-save FFT products
+    # 10 N log2 N per tile (two products, each a forward/inverse real-transform pair of 5 N log2 N).
     dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0), key=lambda k: r64["prof"][k][1])
     avg_ms, cnt = per_launch(r64["prof"], dom)
     lags = p + 1 if dom.endswith("gram") else p
-    flops = (2.0 if dom.endswith("gram") else 4.0) * m * lags
+    fft_used = r64["infos"][-1]["product_used"] == tols.TOLS_PRODUCT_FFT
+    if fft_used and not dom.endswith("gram"):
+        N = 2048
+        L = N - ((lags + 15) // 16) * 16
+        flops = math.ceil(m / L) * 10.0 * N * math.log2(N)
+        kname = f"fft_pass_kernel<double> ({dom})"
+    else:
+        flops = (2.0 if dom.endswith("gram") else 4.0) * m * lags
+        kname = f"pass_kernel<double> ({dom})"
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
     byts_fp64 = 8.0 * n + 16.0 * m
-    roofline = {"bound": "alu", "kernel": f"pass_kernel<double> ({dom})", "achieved": achieved_tf,
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt}
+                "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt,
+                "product": "fft" if fft_used else "direct"}
     mx_dom = "pass_f32_lsqr" if rmx["prof"]["pass_f32_lsqr"][0] else "pass_f32_necorr"
     mx_ms, mx_cnt = per_launch(rmx["prof"], mx_dom)
     byts_mx = 4.0 * n + 8.0 * m
@@ -462,6 +475,8 @@ def run_kernel_only(args, wl):
     import torch
 
     import paper_2112_12994_gb300 as tols
+    if args.p:
+        wl = dict(wl, p=args.p)
     s = make_series(wl)
     n, p = wl["n"], wl["p"]
     m = n - p
@@ -472,24 +487,28 @@ def run_kernel_only(args, wl):
     t = torch.empty(p, dtype=torch.float64, device=dev)
     out = {"kernel_only": True, "workload": wl["desc"], "n": n, "p": p}
     hbm, src = peaks()
-    with tols.Context(precision=tols.TOLS_FP64, cuda_stream=stream.cuda_stream) as ctx:
-        for name, dt, prec, nbytes, flops in (("fp64", torch.float64, tols.TOLS_FP64, 8.0 * n + 16.0 * m, 4.0 * m * p),
-                                              ("fp32", torch.float32, tols.TOLS_MIXED, 4.0 * n + 8.0 * m, 4.0 * m * p)):
-            d_y = torch.tensor(s.y, dtype=dt, device=dev)
-            u0 = torch.tensor(rng.standard_normal(m), dtype=dt, device=dev)
-            u1 = torch.empty(m, dtype=dt, device=dev)
-            times = []
-            for _ in range(args.reps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                tols.toeplitz_ols_gk_pass(ctx, prec, d_y, n, p, v, u0, 0.5, u1, t)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            ms = min(times)
-            out[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm,
-                         "tflops": flops / (ms * 1e-3) / 1e12, "bytes": nbytes}
-            del d_y, u0, u1
+    for prod_name, prod in (("direct", tols.TOLS_PRODUCT_DIRECT), ("fft", tols.TOLS_PRODUCT_FFT)):
+        with tols.Context(precision=tols.TOLS_FP64, product=prod, cuda_stream=stream.cuda_stream) as ctx:
+            for name, dt, prec, nbytes, flops in (("fp64", torch.float64, tols.TOLS_FP64, 8.0 * n + 16.0 * m, 4.0 * m * p),
+                                                  ("fp32", torch.float32, tols.TOLS_MIXED, 4.0 * n + 8.0 * m, 4.0 * m * p)):
+                if args.only and f"{prod_name}_{name}" not in args.only:
+                    continue
+                d_y = torch.tensor(s.y, dtype=dt, device=dev)
+                u0 = torch.tensor(rng.standard_normal(m), dtype=dt, device=dev)
+                u1 = torch.empty(m, dtype=dt, device=dev)
+                times = []
+                for _ in range(args.reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    tols.toeplitz_ols_gk_pass(ctx, prec, d_y, n, p, v, u0, 0.5, u1, t)
+                    e1.record(stream)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = min(times)
+                out[f"{prod_name}_{name}"] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9,
+                                               "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                                               "tflops_equiv": flops / (ms * 1e-3) / 1e12, "bytes": nbytes}
+                del d_y, u0, u1
     out["hbm_peak_gbs"] = hbm
     out["hbm_peak_source"] = src
     print(json.dumps(out), flush=True)

@@ -49,7 +49,7 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -361,16 +361,19 @@ int validate(tols_ctx* ctx, long long n, int p) {
 }
 
 // Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path).
-int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond) {
+int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int spectra = 0, bool converted = false) {
   const int pg = pad_p(w.p + 1);
   if (mixed) {
-    RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
+    if (!converted)
+      RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
     PassArgs<float> a = base_args<float>(w, w.y32, w.n, w.p, pg);
     a.gram = 1;
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    a.fft = choose_fft<float>(ctx, w, w.y32, w.n, w.p, pg, w.p + 1, 1);
+    // with the window spectra at hand the FFT Gram pass needs two transforms per tile: take it
+    a.fft = spectra ? 1 : choose_fft<float>(ctx, w, w.y32, w.n, w.p, pg, w.p + 1, 1);
+    a.use_wspec = spectra;
     RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
   } else {
     PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
@@ -378,7 +381,8 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond) {
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    a.fft = choose_fft<double>(ctx, w, w.y64, w.n, w.p, pg, w.p + 1, 1);
+    a.fft = spectra ? 1 : choose_fft<double>(ctx, w, w.y64, w.n, w.p, pg, w.p + 1, 1);
+    a.use_wspec = spectra;
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
@@ -429,25 +433,47 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   hs.phase = PH_LSQR;
   *ctx->h_state = hs;
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
-  if ((rc = run_setup(ctx, w, mixed, no_precond))) return rc;
+  // products: the direct or FFT kernel per precision; FFT passes use tiles of N - pad_p(p + 1) rows and read
+  // the tile window spectra, transformed once here (before the Gram pass, which reuses them)
+  const int pp = pad_p(p);
+  const int pg = pad_p(p + 1);
+  if (mixed) RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, n, ctx->stream); }));
+  const int fft64 = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
+  const int fft32 = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0) : 0;
+  if (fft64) {
+    RUN(ensure(ctx, ctx->spec64, fft_spectra_bytes(1, n - p, pg)));
+    w.wspec64 = ctx->spec64.p;
+    RUN(run_small(ctx, 12, [&] {
+      return launch_spectra(1, w.y64, n, n - p, pg, w.wspec64, w.tw64, pass_grid_for(ctx, 1, pg, 1), ctx->stream);
+    }));
+  }
+  if (fft32) {
+    RUN(ensure(ctx, ctx->spec32, fft_spectra_bytes(0, n - p, pg)));
+    w.wspec32 = ctx->spec32.p;
+    RUN(run_small(ctx, 12, [&] {
+      return launch_spectra(0, w.y32, n, n - p, pg, w.wspec32, w.tw32, pass_grid_for(ctx, 0, pg, 1), ctx->stream);
+    }));
+  }
+  if ((rc = run_setup(ctx, w, mixed, no_precond, mixed ? fft32 : fft64, true))) return rc;
   if (phi0) {
     CK(cudaMemcpyAsync(w.phi, phi0, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
     RUN(run_small(ctx, 12, [&] { return launch_init_lsqr(w, 1, ctx->stream); }));
   } else {
     RUN(run_small(ctx, 12, [&] { return launch_init_lsqr(w, 0, ctx->stream); }));
   }
-  const int pp = pad_p(p);
-  PassArgs<double> ad = base_args<double>(w, w.y64, n, p, pp);
+  PassArgs<double> ad = base_args<double>(w, w.y64, n, p, fft64 ? pg : pp);
   ad.check_done = 1;
   ad.d = w.d;
-  ad.fft = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
-  PassArgs<float> af = base_args<float>(w, w.y32, n, p, pp);
+  ad.fft = fft64;
+  ad.use_wspec = fft64;
+  PassArgs<float> af = base_args<float>(w, w.y32, n, p, fft32 ? pg : pp);
   af.check_done = 1;
   af.d = w.d;
-  af.fft = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0) : 0;
+  af.fft = fft32;
+  af.use_wspec = fft32;
   ctx->last_fft = mixed ? af.fft : ad.fft;
-  const int gd = pass_grid_for(ctx, 1, pp, ad.fft);
-  const int gf = mixed ? pass_grid_for(ctx, 0, pp, af.fft) : 0;
+  const int gd = pass_grid_for(ctx, 1, ad.p_pad, ad.fft);
+  const int gf = mixed ? pass_grid_for(ctx, 0, af.p_pad, af.fft) : 0;
   const long long max_launch = (long long)(max_iter + 4) * (max_sweeps + 2) * 2 + 16;
   long long launched = 0;
   int burst = 4;
@@ -726,7 +752,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   if (mixed) CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
   else CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
-  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream); }));
+  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream, B.p_pad_max); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
 
   // iterations: a burst of batched passes captured once into a CUDA graph, replayed until all series are done
@@ -1105,7 +1131,7 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
   }
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
   const int cnt = (int)fresh.size();
-  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(a.series, cnt, want, ctx->stream); }));
+  RUN(run_small(ctx, 10, [&] { return launch_precond_batch(a.series, cnt, want, ctx->stream, pmax); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(a.series, cnt, nullptr, ctx->stream); }));
   return TOLS_OK;
 }
@@ -1308,7 +1334,8 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->y64,    &ctx->y32,   &ctx->u0,    &ctx->u1,     &ctx->part,    &ctx->vecs,
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
-                    &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune};
+                    &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
+                    &ctx->spec64};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);

@@ -14,6 +14,10 @@
 // Twiddles come from a table of exp(-2 pi i t / N), t < N, computed on the host in float64.
 #pragma once
 
+// Index into the FFT work arrays: one pad element after every 8, so that the strided writes of the first
+// Stockham stages (stride 8 complex values) land in distinct shared-memory banks.
+__device__ __forceinline__ int pix(int i) { return i + (i >> 3); }
+
 template <typename T>
 struct FftCfg;
 template <>
@@ -115,7 +119,7 @@ __device__ __forceinline__ void fft_stage(const V* __restrict__ in, V* __restric
     const int g = j / Ls;
     V v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+    for (int r = 0; r < R; ++r) v[r] = in[pix(j + r * stride)];
 #pragma unroll
     for (int r = 1; r < R; ++r) {
       V t = tw[r * k * tstep];
@@ -124,7 +128,7 @@ __device__ __forceinline__ void fft_stage(const V* __restrict__ in, V* __restric
     }
     dft_small<V, S, R>(v, inv);
 #pragma unroll
-    for (int q = 0; q < R; ++q) out[g * Ln + k + q * Ls] = v[q];
+    for (int q = 0; q < R; ++q) out[pix(g * Ln + k + q * Ls)] = v[q];
   }
   __syncthreads();
 }
@@ -160,15 +164,23 @@ __device__ __forceinline__ V real_merge(V vf, V vmf, V twf) {
 }
 
 template <typename T>
+struct FftCfg2 {
+  static constexpr int M = FftCfg<T>::N / 2;
+  static constexpr int PADDED = M + M / 8 + 8;   // entries of a padded work array (index pix(f), f <= M)
+};
+
+template <typename T>
 struct FftSmem {
   using V = typename FftCfg<T>::V;
-  V *A, *B, *W, *D;       // M + 1 entries each
+  V *A, *B;               // work arrays, padded (pix)
+  V *W, *D;               // half spectra, M + 1 entries each
   double *tacc, *scratch;
   __device__ FftSmem(unsigned char* raw, int p_pad) {
     constexpr int M = FftCfg<T>::N / 2;
+    constexpr int PADDED = FftCfg2<T>::PADDED;
     A = reinterpret_cast<V*>(raw);
-    B = A + (M + 1);
-    W = B + (M + 1);
+    B = A + PADDED;
+    W = B + PADDED;
     D = W + (M + 1);
     tacc = reinterpret_cast<double*>(D + (M + 1));
     scratch = tacc + p_pad + 16;
@@ -185,49 +197,66 @@ __device__ void fft_d_spectrum(FftSmem<T>& sm, const double* d, double d_scale, 
     V v;
     v.x = k0 < p ? (T)(d_scale * d[p - 1 - k0]) : (T)0;
     v.y = k1 < p ? (T)(d_scale * d[p - 1 - k1]) : (T)0;
-    sm.A[j] = v;
+    sm.A[pix(j)] = v;
   }
   __syncthreads();
   fft_complex<V, T, M>(sm.A, sm.B, tw, false);
-  for (int f = threadIdx.x; f <= M; f += kThreads) sm.D[f] = real_split<V, T>(sm.A[f & (M - 1)], sm.A[(M - f) & (M - 1)], tw[f]);
+  for (int f = threadIdx.x; f <= M; f += kThreads)
+    sm.D[f] = real_split<V, T>(sm.A[pix(f & (M - 1))], sm.A[pix((M - f) & (M - 1))], tw[f]);
   __syncthreads();
 }
 
 // One tile of L rows starting at i0. Accumulates X^T u (lag order) into sm.tacc; returns this thread's ||u||^2.
+// Window spectrum W = RFFT(y[i0 .. i0 + N)) of one tile, into sm.W.
 template <typename T>
-__device__ double fft_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long m, int L, int nlag,
-                           int gram, const T* u_old, T* u_new, double coef, long long i0,
-                           const typename FftCfg<T>::V* tw) {
+__device__ void fft_window_spectrum(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long i0,
+                                    const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
   constexpr int M = FftCfg<T>::N / 2;
-  const T invM = (T)1 / (T)M;
-  const int rows = (int)min((long long)L, m - i0);
-  // window spectrum W = RFFT(y[i0 .. i0 + N))
   for (int j = threadIdx.x; j < M; j += kThreads) {
     const long long g0 = i0 + 2 * j;
     V v;
     v.x = g0 < n ? y[g0] : (T)0;
     v.y = g0 + 1 < n ? y[g0 + 1] : (T)0;
-    sm.A[j] = v;
+    sm.A[pix(j)] = v;
   }
   __syncthreads();
   fft_complex<V, T, M>(sm.A, sm.B, tw, false);
-  for (int f = threadIdx.x; f <= M; f += kThreads) sm.W[f] = real_split<V, T>(sm.A[f & (M - 1)], sm.A[(M - f) & (M - 1)], tw[f]);
+  for (int f = threadIdx.x; f <= M; f += kThreads)
+    sm.W[f] = real_split<V, T>(sm.A[pix(f & (M - 1))], sm.A[pix((M - f) & (M - 1))], tw[f]);
   __syncthreads();
+}
+
+// One tile of L rows starting at i0. Accumulates X^T u (lag order) into sm.tacc; returns this thread's ||u||^2.
+// wsrc: the tile's window spectrum precomputed in global memory (M + 1 entries), or null to transform it here.
+template <typename T>
+__device__ double fft_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long m, int L, int nlag,
+                           int gram, const T* u_old, T* u_new, double coef, long long i0,
+                           const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wsrc) {
+  using V = typename FftCfg<T>::V;
+  constexpr int M = FftCfg<T>::N / 2;
+  const T invM = (T)1 / (T)M;
+  const int rows = (int)min((long long)L, m - i0);
+  if (wsrc) {
+    for (int f = threadIdx.x; f <= M; f += kThreads) sm.W[f] = wsrc[f];
+    __syncthreads();
+  } else {
+    fft_window_spectrum<T>(sm, y, n, i0, tw);
+  }
 
   double n2 = 0.0;
   if (!gram) {
     // X d = IRFFT(W . conj(D)) on rows [0, L)
-    for (int f = threadIdx.x; f <= M; f += kThreads) sm.B[f] = cmulc(sm.W[f], sm.D[f]);
+    for (int f = threadIdx.x; f <= M; f += kThreads) sm.B[pix(f)] = cmulc(sm.W[f], sm.D[f]);
     __syncthreads();
-    for (int f = threadIdx.x; f < M; f += kThreads) sm.A[f] = real_merge<V, T>(sm.B[f], sm.B[M - f], tw[f]);
+    for (int f = threadIdx.x; f < M; f += kThreads) sm.A[pix(f)] = real_merge<V, T>(sm.B[pix(f)], sm.B[pix(M - f)], tw[f]);
     __syncthreads();
     fft_complex<V, T, M>(sm.A, sm.B, tw, true);
     // u = X d - c u_old on the tile's rows, zero elsewhere; packed into B for its forward transform
     T nn = (T)0;
     for (int j = threadIdx.x; j < M; j += kThreads) {
       const int r0 = 2 * j, r1 = 2 * j + 1;
-      const V z = sm.A[j];
+      const V z = sm.A[pix(j)];
       T u0 = (T)0, u1 = (T)0;
       if (r0 < rows) {
         u0 = z.x * invM;
@@ -243,7 +272,7 @@ __device__ double fft_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n,
       V v;
       v.x = u0;
       v.y = u1;
-      sm.B[j] = v;
+      sm.B[pix(j)] = v;
     }
     n2 = (double)nn;
     __syncthreads();
@@ -255,29 +284,29 @@ __device__ double fft_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n,
       V v;
       v.x = r0 < rows ? y[i0 + r0] : (T)0;
       v.y = r1 < rows ? y[i0 + r1] : (T)0;
-      sm.B[j] = v;
+      sm.B[pix(j)] = v;
     }
     __syncthreads();
     fft_complex<V, T, M>(sm.B, sm.A, tw, false);
   }
   // X^T u = IRFFT(W . conj(U)) on lags [0, nlag)
   for (int f = threadIdx.x; f <= M; f += kThreads) {
-    const V uf = real_split<V, T>(sm.B[f & (M - 1)], sm.B[(M - f) & (M - 1)], tw[f]);
-    sm.A[f] = cmulc(sm.W[f], uf);
+    const V uf = real_split<V, T>(sm.B[pix(f & (M - 1))], sm.B[pix((M - f) & (M - 1))], tw[f]);
+    sm.A[pix(f)] = cmulc(sm.W[f], uf);
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < M; f += kThreads) sm.B[f] = real_merge<V, T>(sm.A[f], sm.A[M - f], tw[f]);
+  for (int f = threadIdx.x; f < M; f += kThreads) sm.B[pix(f)] = real_merge<V, T>(sm.A[pix(f)], sm.A[pix(M - f)], tw[f]);
   __syncthreads();
   fft_complex<V, T, M>(sm.B, sm.A, tw, true);
   for (int k = threadIdx.x; k < nlag; k += kThreads) {
-    const V z = sm.B[k >> 1];
+    const V z = sm.B[pix(k >> 1)];
     sm.tacc[k] += (double)(((k & 1) ? z.y : z.x) * invM);
   }
   return n2;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   using V = typename FftCfg<T>::V;
   constexpr int N = FftCfg<T>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,9 +329,12 @@ __global__ void __launch_bounds__(kThreads) fft_pass_kernel(PassArgs<T> a) {
   if (!a.gram) fft_d_spectrum<T>(sm, a.d, a.d_scale, a.p, tw);
   double n2 = 0.0;
   const long long ntiles = (a.m + L - 1) / L;
+  const V* wspec = reinterpret_cast<const V*>(sizeof(T) == 8 ? a.w.wspec64 : a.w.wspec32);
+  if (!a.use_wspec) wspec = nullptr;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    n2 += fft_tile<T>(sm, a.y, a.n, a.m, L, nlag, a.gram, u_old, u_new, coef, tile * L, tw);
+    n2 += fft_tile<T>(sm, a.y, a.n, a.m, L, nlag, a.gram, u_old, u_new, coef, tile * L, tw,
+                      wspec ? wspec + (size_t)tile * (FftCfg<T>::N / 2 + 1) : nullptr);
   }
   __syncthreads();
   const double n2_cta = block_sum(n2, sm.scratch);
@@ -319,5 +351,22 @@ template <typename T>
 static size_t fft_pass_smem(int p_pad) {
   using V = typename FftCfg<T>::V;
   constexpr int M = FftCfg<T>::N / 2;
-  return sizeof(V) * 4 * (size_t)(M + 1) + sizeof(double) * ((size_t)p_pad + 16 + 16);
+  return sizeof(V) * (2 * (size_t)FftCfg2<T>::PADDED + 2 * (size_t)(M + 1)) + sizeof(double) * ((size_t)p_pad + 16 + 16);
+}
+
+// Window spectra of every tile of a series (tiles of L = N - p_pad rows), computed once per solve: y does not
+// change between passes, so the passes read W from here instead of transforming the window again.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) spectrum_kernel(const T* __restrict__ y, long long n, long long m, int L,
+                                                           typename FftCfg<T>::V* __restrict__ out,
+                                                           const typename FftCfg<T>::V* tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int M = FftCfg<T>::N / 2;
+  FftSmem<T> sm(smem_raw, 0);
+  const long long ntiles = (m + L - 1) / L;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    fft_window_spectrum<T>(sm, y, n, tile * L, tw);
+    for (int f = threadIdx.x; f <= M; f += kThreads) out[(size_t)tile * (M + 1) + f] = sm.W[f];
+  }
 }

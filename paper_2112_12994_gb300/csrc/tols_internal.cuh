@@ -82,6 +82,8 @@ struct Work {
   DevState* st;
   const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
+  void* wspec32;          // precomputed window spectra of the float FFT tiles (nullable)
+  void* wspec64;          // precomputed window spectra of the float64 FFT tiles (nullable)
 };
 
 // Arguments of a pass kernel (passed by value).
@@ -106,6 +108,7 @@ struct PassArgs {
   int* worklog;           // nullable: the tail writes 1 + tail + 5 * (T == double) into worklog[work_slot]
   int work_slot;
   int fft;                // 1: overlap-save FFT products (fft_pass_kernel) instead of the direct ones
+  int use_wspec;          // 1: read the tile window spectra from w.wspec32 / w.wspec64
 };
 
 // One series of a batch (device array). Its Work points at the series' own slices of the batch buffers; its
@@ -129,6 +132,9 @@ struct BatchArgs {
 size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
 const void* fft_kernel_ptr(int is_double);
 int fft_size(int is_double);              // N of the real FFT per tile (float 4096, double 2048)
+size_t fft_spectra_bytes(int is_double, long long m, int p_pad);
+cudaError_t launch_spectra(int is_double, const void* y, long long n, long long m, int p_pad, void* out,
+                           const void* tw, int grid, cudaStream_t s);
 int pass_tile_rows(int is_double);
 const void* pass_kernel_ptr(int is_double);
 template <typename T>
@@ -137,7 +143,8 @@ cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s);
 const void* batch_kernel_ptr(int is_double);
-cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s);
+cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s,
+                                 int p_max);
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s);
 cudaError_t launch_finish_batch(const BatchSeries* series, int count, cudaStream_t s);
 cudaError_t launch_convert_batch(const BatchSeries* series, int count, cudaStream_t s);

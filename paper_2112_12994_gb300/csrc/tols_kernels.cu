@@ -835,6 +835,39 @@ const void* fft_kernel_ptr(int is_double) {
   return is_double ? (const void*)fft_pass_kernel<double> : (const void*)fft_pass_kernel<float>;
 }
 int fft_size(int is_double) { return is_double ? FftCfg<double>::N : FftCfg<float>::N; }
+
+template <typename T>
+static size_t spectra_bytes(long long m, int p_pad) {
+  constexpr int N = FftCfg<T>::N;
+  const long long L = N - p_pad;
+  return sizeof(typename FftCfg<T>::V) * (size_t)((m + L - 1) / L) * (N / 2 + 1);
+}
+size_t fft_spectra_bytes(int is_double, long long m, int p_pad) {
+  return is_double ? spectra_bytes<double>(m, p_pad) : spectra_bytes<float>(m, p_pad);
+}
+
+template <typename T>
+static cudaError_t launch_spectra_t(const T* y, long long n, long long m, int p_pad, void* out, const void* tw,
+                                    int grid, cudaStream_t s) {
+  using V = typename FftCfg<T>::V;
+  const size_t smem = sizeof(V) * (2 * (size_t)FftCfg2<T>::PADDED + 2 * (size_t)(FftCfg<T>::N / 2 + 1)) + 512;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(spectrum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  const int L = FftCfg<T>::N - p_pad;
+  const long long ntiles = (m + L - 1) / L;
+  const int g = (int)lmin((long long)grid, ntiles);
+  spectrum_kernel<T><<<g < 1 ? 1 : g, kThreads, smem, s>>>(y, n, m, L, (V*)out, (const V*)tw);
+  return cudaGetLastError();
+}
+cudaError_t launch_spectra(int is_double, const void* y, long long n, long long m, int p_pad, void* out,
+                           const void* tw, int grid, cudaStream_t s) {
+  return is_double ? launch_spectra_t<double>((const double*)y, n, m, p_pad, out, tw, grid, s)
+                   : launch_spectra_t<float>((const float*)y, n, m, p_pad, out, tw, grid, s);
+}
 int pass_tile_rows(int is_double) { return is_double ? TileCfg<double>::TILE : TileCfg<float>::TILE; }
 const void* pass_kernel_ptr(int is_double) {
   return is_double ? (const void*)pass_kernel<double> : (const void*)pass_kernel<float>;
@@ -866,14 +899,26 @@ const void* batch_kernel_ptr(int is_double) {
 // ------------------------------------------------------------------------------------------------------
 // Preconditioner: ||X||_F, a power-iteration estimate of ||X||_2, Cholesky G = R^T R (upper R, in place),
 // M = R^{-1} and M^T (float64 and float copies). One CTA; G is symmetric on entry.
-__device__ void precond_body(const Work& w, int want_precond) {
+__device__ __forceinline__ double* scratch_vec(const Work& w) { return w.t; }  // w.t, w.g: 2 p_pad doubles
+
+// G and R^{-1} are worked on in shared memory when both fit (p <= kPrecondSmemP): the factorisation and the back
+// substitutions are chains of dependent read-modify-writes, which would wait on L2 round trips in global memory.
+constexpr int kPrecondSmemP = 112;
+
+__device__ void precond_body(const Work& w, int want_precond, double* smem) {
   const int p = w.p;
   DevState* st = w.st;
   __shared__ double scratch[16];
   __shared__ int s_fail;
   __shared__ int s_shift;
   __shared__ double s_val[2];
-  double* G = w.G;
+  const bool in_smem = smem && p <= kPrecondSmemP;
+  double* G = in_smem ? smem : w.G;
+  double* Mm = in_smem ? smem + (size_t)p * p : w.M;
+  if (in_smem) {
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.G[q];
+    __syncthreads();
+  }
   // ||X||_F^2 = trace(G)
   double tr = 0.0, dmax = 0.0;
   for (int j = threadIdx.x; j < p; j += kThreads) {
@@ -896,26 +941,56 @@ __device__ void precond_body(const Work& w, int want_precond) {
     dmax = s_val[0];
     __syncthreads();
   }
-  // power iteration on G for lambda_max = ||X||_2^2 (w.t, w.g as work vectors)
-  double* x = w.t;
-  double* yv = w.g;
-  for (int j = threadIdx.x; j < p; j += kThreads) x[j] = 1.0 / sqrt((double)p);
-  __syncthreads();
-  double lam = 0.0;
-  for (int it = 0; it < 24; ++it) {
-    for (int i = threadIdx.x; i < p; i += kThreads) {
-      double acc = 0.0;
-      for (int j = 0; j < p; ++j) acc = fma(G[(size_t)j * p + i], x[j], acc);
-      yv[i] = acc;
-    }
+  // power iteration for lambda_max = ||X||_2^2 on a float copy of G (two digits suffice for the ratio's norm);
+  // the copy lives in the M area, which is free until the factorisation
+  {
+    float* Gf = reinterpret_cast<float*>(Mm);
+    __shared__ float xs[TOLS_MAX_P], ys[TOLS_MAX_P];
+    __shared__ double red3[3 * (kThreads / 32)];
+    for (int q = threadIdx.x; q < p * p; q += kThreads) Gf[q] = (float)G[q];
+    for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = 1.0f;
     __syncthreads();
-    double nrm = sqrt(vec_norm2(yv, p, scratch));
-    double dot = 0.0;
-    for (int j = threadIdx.x; j < p; j += kThreads) dot += x[j] * yv[j];
-    lam = block_sum(dot, scratch);
-    for (int j = threadIdx.x; j < p; j += kThreads) x[j] = nrm > 0 ? yv[j] / nrm : 0.0;
+    double lam = 0.0;
+    for (int it = 0; it < 12; ++it) {
+      double nn = 0.0, dot = 0.0, xx = 0.0;
+      for (int i = threadIdx.x; i < p; i += kThreads) {
+        float a0 = 0.f, a1 = 0.f;
+        int j = 0;
+        for (; j + 1 < p; j += 2) {
+          a0 = fmaf(Gf[j * p + i], xs[j], a0);
+          a1 = fmaf(Gf[(j + 1) * p + i], xs[j + 1], a1);
+        }
+        if (j < p) a0 = fmaf(Gf[j * p + i], xs[j], a0);
+        const float yi = a0 + a1;
+        ys[i] = yi;
+        nn += (double)yi * yi;
+        dot += (double)xs[i] * yi;
+        xx += (double)xs[i] * xs[i];
+      }
+      nn = warp_sum(nn);
+      dot = warp_sum(dot);
+      xx = warp_sum(xx);
+      if ((threadIdx.x & 31) == 0) {
+        red3[threadIdx.x >> 5] = nn;
+        red3[(kThreads / 32) + (threadIdx.x >> 5)] = dot;
+        red3[2 * (kThreads / 32) + (threadIdx.x >> 5)] = xx;
+      }
+      __syncthreads();
+      nn = dot = xx = 0.0;
+      for (int q = 0; q < kThreads / 32; ++q) {
+        nn += red3[q];
+        dot += red3[(kThreads / 32) + q];
+        xx += red3[2 * (kThreads / 32) + q];
+      }
+      lam = xx > 0 ? dot / xx : 0.0;
+      const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+      for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = ys[j] * inv;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s_val[1] = lam;
     __syncthreads();
   }
+  const double lam = s_val[1];
   if (!isfinite(tr) || !isfinite(*w.bnorm2)) {
     if (threadIdx.x == 0) {
       st->status = TOLS_ERR_NONFINITE;
@@ -942,7 +1017,7 @@ __device__ void precond_body(const Work& w, int want_precond) {
   // LSQR from zero, which returns the minimum-norm solution (Thm. "Solution to OLS problem").
   const double ueps = st->mixed ? 5.96e-8 : 1.11e-16;
   if (want_precond) {
-    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) w.M[q] = G[q];  // keep G for a refactor
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) Mm[q] = G[q];  // keep G for a refactor
     __syncthreads();
   }
   if (threadIdx.x == 0) s_shift = 0;
@@ -952,30 +1027,48 @@ __device__ void precond_body(const Work& w, int want_precond) {
     if (attempt == 1) {
       if (threadIdx.x == 0) s_shift = 1;
       lambda = 10.0 * (double)p * ueps * dmax;
-      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.M[q];
+      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = Mm[q];
       __syncthreads();
       for (int j = threadIdx.x; j < p; j += kThreads) G[(size_t)j * p + j] += lambda;
       if (threadIdx.x == 0) s_fail = 0;
       __syncthreads();
     }
     const double tiny = attempt == 0 ? (double)p * ueps * dmax : 1e-3 * lambda;
+    // right-looking: every thread reads the pivot itself (no broadcast step), scales row k by the reciprocal,
+    // then updates the trailing upper triangle column by column, four independent updates at a time
     for (int k = 0; k < p; ++k) {
-      if (threadIdx.x == 0) {
-        const double piv = G[(size_t)k * p + k];
-        if (!(piv > tiny)) s_fail = 1;
-        else G[(size_t)k * p + k] = sqrt(piv);
+      const double piv = G[k * p + k];
+      if (!(piv > tiny)) {
+        if (threadIdx.x == 0) s_fail = 1;
+        break;
       }
+      const double rkk = sqrt(piv);
+      const double inv = 1.0 / rkk;
+      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) G[k * p + j] *= inv;
       __syncthreads();
-      if (s_fail) break;
-      const double rkk = G[(size_t)k * p + k];
-      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) G[(size_t)k * p + j] /= rkk;
-      __syncthreads();
-      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) {
-        const double rkj = G[(size_t)k * p + j];
-        for (int i = k + 1; i <= j; ++i) G[(size_t)i * p + j] -= G[(size_t)k * p + i] * rkj;
+      if (threadIdx.x == 0) G[k * p + k] = rkk;
+      // trailing update G[i][j] -= r_i r_j over k < i <= j < p, spread evenly over every warp: the triangle of
+      // width w = p-k-1 is folded (row a paired with row w-1-a) into ceil(w/2) rows of exactly w+1 entries
+      const double* __restrict__ rowk = G + k * p;
+      const int wd = p - k - 1;
+      const int half = (wd + 1) >> 1;
+      for (int s2 = threadIdx.x; s2 < half * (wd + 1); s2 += kThreads) {
+        const int a = s2 / (wd + 1), b = s2 - a * (wd + 1);
+        int r, c;
+        if (b < wd - a) {
+          r = a;
+          c = a + b;
+        } else {
+          r = wd - 1 - a;
+          if (r <= a) continue;            // the middle row of an odd width is covered by its first half
+          c = r + (b - (wd - a));
+        }
+        const int i = k + 1 + r, j = k + 1 + c;
+        G[i * p + j] = fma(-rowk[i], rowk[j], G[i * p + j]);
       }
       __syncthreads();
     }
+    __syncthreads();
     if (s_fail) {
       if (attempt == 1) break;                     // even the shifted matrix failed: no preconditioner
       if (threadIdx.x == 0) st->singular = 1;      // singular at working precision: refactor with the shift
@@ -1008,24 +1101,35 @@ __device__ void precond_body(const Work& w, int want_precond) {
   }
   const int ok = want_precond && !st->no_precond && !s_fail;
   if (ok) {
-    // M = R^{-1}: column c by back substitution (each thread its own columns)
-    for (int c = threadIdx.x; c < p; c += kThreads) {
-      for (int i = c + 1; i < p; ++i) w.M[(size_t)i * p + c] = 0.0;
-      w.M[(size_t)c * p + c] = 1.0 / G[(size_t)c * p + c];
-      for (int i = c - 1; i >= 0; --i) {
-        double acc = 0.0;
-        for (int l = i + 1; l <= c; ++l) acc = fma(G[(size_t)i * p + l], w.M[(size_t)l * p + c], acc);
-        w.M[(size_t)i * p + c] = -acc / G[(size_t)i * p + i];
+    // M = R^{-1} from R M = I, right-looking: M starts as I; at step i (from p-1 down) row i is final up to the
+    // factor 1/R_ii, and its contribution R_ri M_ic is removed from every row r < i (a rectangle of i x (p-i)
+    // entries, spread evenly over every warp).
+    for (int q = threadIdx.x; q < p * p; q += kThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = p - 1; i >= 0; --i) {
+      const double inv = 1.0 / G[i * p + i];
+      for (int c = i + threadIdx.x; c < p; c += kThreads) Mm[i * p + c] *= inv;
+      __syncthreads();
+      const int wd = p - i;
+      for (int s2 = threadIdx.x; s2 < i * wd; s2 += kThreads) {
+        const int r = s2 / wd, c = i + (s2 - r * wd);
+        Mm[r * p + c] = fma(-G[r * p + i], Mm[i * p + c], Mm[r * p + c]);
       }
+      __syncthreads();
     }
     __syncthreads();
-    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) {
-      const int i = (int)(q / p), j = (int)(q % p);
-      const double mv = w.M[q];
-      w.Mt[(size_t)j * p + i] = mv;
-      w.M32[q] = (float)mv;
-      w.Mt32[(size_t)j * p + i] = (float)mv;
-    }
+    for (int i = 0; i < p; ++i)
+      for (int j = threadIdx.x; j < p; j += kThreads) {
+        const double mv = Mm[i * p + j];
+        if (in_smem) w.M[i * p + j] = mv;
+        w.M32[i * p + j] = (float)mv;
+      }
+    for (int j = 0; j < p; ++j)
+      for (int i = threadIdx.x; i < p; i += kThreads) {
+        const double mv = Mm[i * p + j];
+        w.Mt[j * p + i] = mv;
+        w.Mt32[j * p + i] = (float)mv;
+      }
     if (threadIdx.x == 0) {
       st->precond = 1;
       st->cond_est = s_val[1];
@@ -1036,17 +1140,43 @@ __device__ void precond_body(const Work& w, int want_precond) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond) { precond_body(w, want_precond); }
-__global__ void __launch_bounds__(kThreads) precond_batch_kernel(const BatchSeries* series, int want_precond) {
-  precond_body(series[blockIdx.x].w, want_precond);
+__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond, int use_smem) {
+  extern __shared__ double psm[];
+  precond_body(w, want_precond, use_smem ? psm : nullptr);
+}
+__global__ void __launch_bounds__(kThreads) precond_batch_kernel(const BatchSeries* series, int want_precond,
+                                                                 int use_smem) {
+  extern __shared__ double psm[];
+  precond_body(series[blockIdx.x].w, want_precond, use_smem ? psm : nullptr);
+}
+
+static size_t precond_smem(int p_max) {
+  const int q = p_max < kPrecondSmemP ? p_max : kPrecondSmemP;
+  return sizeof(double) * 2 * (size_t)q * q;
+}
+static cudaError_t precond_config() {
+  static int done = 0;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(precond_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  if (e == cudaSuccess) done = 1;
+  return e;
 }
 
 cudaError_t launch_precond(Work w, int want_precond, cudaStream_t s) {
-  precond_kernel<<<1, kThreads, 0, s>>>(w, want_precond);
+  cudaError_t e = precond_config();
+  if (e != cudaSuccess) return e;
+  const int use = w.p <= kPrecondSmemP;
+  precond_kernel<<<1, kThreads, use ? precond_smem(w.p) : 0, s>>>(w, want_precond, use);
   return cudaGetLastError();
 }
-cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s) {
-  precond_batch_kernel<<<count, kThreads, 0, s>>>(series, want_precond);
+// Batched: series with p <= kPrecondSmemP work in shared memory sized for the largest such p in the batch.
+cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s,
+                                 int p_max) {
+  cudaError_t e = precond_config();
+  if (e != cudaSuccess) return e;
+  precond_batch_kernel<<<count, kThreads, precond_smem(p_max), s>>>(series, want_precond, 1);
   return cudaGetLastError();
 }
 
@@ -1065,13 +1195,30 @@ __device__ bool mixed_hopeless(DevState* st) {
   return true;
 }
 
+// Start of a solve. Float64 with a trustworthy (unshifted) Cholesky factor: start from the semi-normal-equation solution
+// phi0 = R^{-1} R^{-T} X^T b (O(p^2)) and let a float64 check pass decide whether LSQR on the residual is needed.
+// Otherwise (mixed precision, or no factor): LSQR from zero on b.
+__device__ void start_solve(const Work& w, DevState* st, double* scratch) {
+  for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
+  __syncthreads();
+  if (!st->mixed && st->precond && !st->shifted) {
+    apply_Mt(w, 1, 0, w.h, w.t);
+    __syncthreads();
+    apply_M_exact(w, 1, 0, w.t, w.phi);
+    __syncthreads();
+    schedule_check(w, st, scratch);
+    return;
+  }
+  start_lsqr(w, st, w.h, st->bnorm, scratch);
+}
+
 __global__ void __launch_bounds__(kThreads) init_lsqr_kernel(Work w) {
   __shared__ double scratch[16];
   DevState* st = w.st;
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
   if (mixed_hopeless(st)) return;
-  start_lsqr(w, st, w.h, st->bnorm, scratch);
+  start_solve(w, st, scratch);
 }
 
 // Warm start: phi already holds a guess; the first pass is a residual check.
@@ -1094,7 +1241,7 @@ __global__ void __launch_bounds__(kThreads) init_lsqr_batch_kernel(const BatchSe
     if (threadIdx.x == 0 && done) atomicAdd(done, 1u);
     return;
   }
-  start_lsqr(w, st, w.h, st->bnorm, scratch);
+  start_solve(w, st, scratch);
 }
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s) {
   init_lsqr_batch_kernel<<<count, kThreads, 0, s>>>(series, done);

@@ -221,6 +221,20 @@ int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
   return ctx->grid[slot];
 }
 
+// Doubled window spectra of series y (tiles of N - p_pad rows) in the context's buffer for that precision, which
+// every FFT pass reads. form: transform them here (spectrum_kernel); else only make room (a Gram pass fills it).
+int fft_spectra(tols_ctx* ctx, Work& w, int is_double, const void* y, long long n, long long m, int p_pad, bool form) {
+  DevBuf& b = is_double ? ctx->spec64 : ctx->spec32;
+  RUN(ensure(ctx, b, fft_spectra_bytes(is_double, m, p_pad)));
+  if (is_double) w.wspec64 = b.p;
+  else w.wspec32 = b.p;
+  if (!form) return TOLS_OK;
+  return run_small(ctx, 12, [&] {
+    return launch_spectra(is_double, y, n, m, p_pad, b.p, is_double ? w.tw64 : w.tw32,
+                          pass_grid_for(ctx, is_double, p_pad, 1), ctx->stream);
+  });
+}
+
 // Product kernel for a pass over series y (T = float or double): the sliding-window direct products or the
 // overlap-save FFT. DIRECT / FFT force one; AUTO times both once per (precision, p_pad) on the series at hand
 // when it is long enough for the choice to matter (cached in the context), else picks by p.
@@ -237,6 +251,8 @@ int choose_fft(tols_ctx* ctx, const Work& w, const T* y, long long n, int p, int
   const int guess = p_pad >= (is_double ? 32 : 64);
   if (m < (1 << 20) || ensure(ctx, ctx->tune, sizeof(double) * (4 * (size_t)p_pad + 64)) != TOLS_OK) return guess;
   double* sc = (double*)ctx->tune.p;
+  Work wf = w;                    // the FFT pass reads (or, for the Gram, writes) the window spectra
+  if (fft_spectra(ctx, wf, is_double, y, n, m, p_pad, !gram) != TOLS_OK) return guess;
   PassArgs<T> a;
   memset(&a, 0, sizeof a);
   a.y = y;
@@ -258,6 +274,7 @@ int choose_fft(tols_ctx* ctx, const Work& w, const T* y, long long n, int p, int
   float best[2] = {0.f, 0.f};
   for (int f = 0; f < 2; ++f) {
     a.fft = f;
+    a.w = f ? wf : w;
     const int grid = pass_grid_for(ctx, is_double, p_pad, f);
     launch_pass<T>(a, grid, ctx->stream);                 // warm-up
     cudaEventRecord(e0, ctx->stream);
@@ -360,8 +377,9 @@ int validate(tols_ctx* ctx, long long n, int p) {
   return TOLS_OK;
 }
 
-// Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path).
-int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int spectra = 0, bool converted = false) {
+// Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path). fft: the Gram pass uses the FFT
+// kernel and writes the window spectra of its precision (room made by fft_spectra).
+int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, bool converted = false) {
   const int pg = pad_p(w.p + 1);
   if (mixed) {
     if (!converted)
@@ -371,9 +389,7 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int spectra =
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    // with the window spectra at hand the FFT Gram pass needs two transforms per tile: take it
-    a.fft = spectra ? 1 : choose_fft<float>(ctx, w, w.y32, w.n, w.p, pg, w.p + 1, 1);
-    a.use_wspec = spectra;
+    a.fft = fft;
     RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
   } else {
     PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
@@ -381,8 +397,7 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int spectra =
     a.nlag = w.p + 1;
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
-    a.fft = spectra ? 1 : choose_fft<double>(ctx, w, w.y64, w.n, w.p, pg, w.p + 1, 1);
-    a.use_wspec = spectra;
+    a.fft = fft;
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
   const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
@@ -433,27 +448,16 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   hs.phase = PH_LSQR;
   *ctx->h_state = hs;
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
-  // products: the direct or FFT kernel per precision; FFT passes use tiles of N - pad_p(p + 1) rows and read
-  // the tile window spectra, transformed once here (before the Gram pass, which reuses them)
+  // products: the direct or FFT kernel per precision. FFT passes use tiles of N - pad_p(p + 1) rows and read
+  // the tile window spectra: the Gram pass of the same precision forms them; the float64 spectra of a mixed
+  // solve come from spectrum_kernel.
   const int pp = pad_p(p);
   const int pg = pad_p(p + 1);
   if (mixed) RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, n, ctx->stream); }));
   const int fft64 = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
   const int fft32 = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0) : 0;
-  if (fft64) {
-    RUN(ensure(ctx, ctx->spec64, fft_spectra_bytes(1, n - p, pg)));
-    w.wspec64 = ctx->spec64.p;
-    RUN(run_small(ctx, 12, [&] {
-      return launch_spectra(1, w.y64, n, n - p, pg, w.wspec64, w.tw64, pass_grid_for(ctx, 1, pg, 1), ctx->stream);
-    }));
-  }
-  if (fft32) {
-    RUN(ensure(ctx, ctx->spec32, fft_spectra_bytes(0, n - p, pg)));
-    w.wspec32 = ctx->spec32.p;
-    RUN(run_small(ctx, 12, [&] {
-      return launch_spectra(0, w.y32, n, n - p, pg, w.wspec32, w.tw32, pass_grid_for(ctx, 0, pg, 1), ctx->stream);
-    }));
-  }
+  if (fft64) RUN(fft_spectra(ctx, w, 1, w.y64, n, n - p, pg, mixed));
+  if (fft32) RUN(fft_spectra(ctx, w, 0, w.y32, n, n - p, pg, false));
   if ((rc = run_setup(ctx, w, mixed, no_precond, mixed ? fft32 : fft64, true))) return rc;
   if (phi0) {
     CK(cudaMemcpyAsync(w.phi, phi0, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -465,12 +469,10 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   ad.check_done = 1;
   ad.d = w.d;
   ad.fft = fft64;
-  ad.use_wspec = fft64;
   PassArgs<float> af = base_args<float>(w, w.y32, n, p, fft32 ? pg : pp);
   af.check_done = 1;
   af.d = w.d;
   af.fft = fft32;
-  af.use_wspec = fft32;
   ctx->last_fft = mixed ? af.fft : ad.fft;
   const int gd = pass_grid_for(ctx, 1, ad.p_pad, ad.fft);
   const int gf = mixed ? pass_grid_for(ctx, 0, af.p_pad, af.fft) : 0;
@@ -1533,6 +1535,10 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     a.out_t = d_xtu;
     a.out_n2 = d_n2;
     a.fft = choose_fft<double>(ctx, w, (const double*)d_y, n, p, pp, p, 0);
+    if (a.fft) {
+      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true));
+      a.w.wspec64 = w.wspec64;
+    }
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
   } else {
     PassArgs<float> a = base_args<float>(w, (const float*)d_y, n, p, pp);
@@ -1544,6 +1550,10 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     a.out_t = d_xtu;
     a.out_n2 = d_n2;
     a.fft = choose_fft<float>(ctx, w, (const float*)d_y, n, p, pp, p, 0);
+    if (a.fft) {
+      RUN(fft_spectra(ctx, w, 0, d_y, n, n - p, pp, true));
+      a.w.wspec32 = w.wspec32;
+    }
     RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pp, a.fft)));
   }
   double h = 0.0;
@@ -1574,6 +1584,10 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
     a.fft = choose_fft<float>(ctx, w, w.y32, n, p, pg, p + 1, 1);
+    if (a.fft) {
+      RUN(fft_spectra(ctx, w, 0, w.y32, n, n - p, pg, false));
+      a.w.wspec32 = w.wspec32;
+    }
     RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
   } else {
     PassArgs<double> a = base_args<double>(w, d_y, n, p, pg);
@@ -1582,6 +1596,10 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
     a.tail = TAIL_GRAM;
     a.out_n2 = w.bnorm2;
     a.fft = choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
+    if (a.fft) {
+      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pg, false));
+      a.w.wspec64 = w.wspec64;
+    }
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
   double h = 0.0;
@@ -1628,6 +1646,10 @@ int toeplitz_ols_residual(tols_ctx* ctx, const double* d_y, long long n, int p, 
   a.out_t = d_g;
   a.out_n2 = d_n2;
   a.fft = choose_fft<double>(ctx, w, d_y, n, p, pp, p, 0);
+  if (a.fft) {
+    RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true));
+    a.w.wspec64 = w.wspec64;
+  }
   RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
   double h = 0.0;
   CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

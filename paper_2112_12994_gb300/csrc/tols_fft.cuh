@@ -5,13 +5,17 @@
 // rows, which never wrap inside the rows and lags used:
 //   (X d)[i0 + r] = sum_{k<p} w[r + k] dr[k]          = IDFT(W . conj(DR))[r],   r < L
 //   tk[k]         = sum_{r<L} u[r] w[r + k]             = IDFT(W . conj(U))[k],    k < nlag
-// with w the window y[i0 .. i0+N), dr the lag-reversed d, u the tile's fresh u (zero beyond its rows). Per tile:
-// one forward real FFT of the window, one inverse for X d, one forward of u, one inverse for X^T u; the spectrum
-// of dr is formed once per CTA and launch.
+// with w the window y[i0 .. i0+N) (zero past the end of y), dr the lag-reversed d, u the tile's fresh u (zero
+// beyond its rows). The window spectra W of all tiles are formed once per solve (by the Gram pass, or by
+// spectrum_kernel) and read from global memory. Per tile a pass runs one inverse transform (X d) and one forward
+// transform (u). The X^T u products are linear in the spectra, so each CTA sums W . conj(U) over its tiles and
+// transforms back once, at its end; the spectrum of dr is formed once per CTA and launch.
 //
 // A real N-point FFT is an N/2-point complex FFT of the packed pairs (w[2j], w[2j+1]) plus an O(N) split; the
 // complex FFT is a radix-8 (then 4, 2) Stockham autosort in shared memory, one butterfly per thread per stage.
-// Twiddles come from a table of exp(-2 pi i t / N), t < N, computed on the host in float64.
+// Twiddles come from a table of exp(-2 pi i t / N), t < N, computed on the host in float64. Half spectra are
+// kept doubled (2W, 2U, 2D): the split and merge then need no halving, and every product of two of them and its
+// merge carry a factor 8, removed with the 1 / (8 M) scale of the inverse transform (all powers of two: exact).
 #pragma once
 
 // Index into the FFT work arrays: one pad element after every 8, so that the strided writes of the first
@@ -144,23 +148,33 @@ __device__ void fft_complex(V* a, V* b, const V* tw, bool inv) {
   else fft_stage<V, S, 2, M>(b, a, 512, tw, inv);
 }
 
-// Split of the packed complex transform Z of a real sequence into its half spectrum:
-//   X[f] = (Z[f] + conj(Z[M-f])) / 2 - i w^f (Z[f] - conj(Z[M-f])) / 2,   w = exp(-2 pi i / N), Z[M] = Z[0].
+// Split of the packed complex transform Z of a real sequence into its doubled half spectrum, two bins at a time:
+//   a = Z[f] + conj(Z[M-f]),  b = Z[f] - conj(Z[M-f]),  s = -i w^f b   (w = exp(-2 pi i / N), Z[M] = Z[0])
+//   2X[f] = a + s,   2X[M-f] = conj(a - s).
 template <typename V, typename S>
-__device__ __forceinline__ V real_split(V zf, V zmf, V twf) {
-  const V c = cconj(zmf);
-  const V e = cscale(cadd(zf, c), (S)0.5);
-  const V o = cscale(csub(zf, c), (S)0.5);
-  return cadd(e, cmul(twf, cmul_mi(o, false)));
+__device__ __forceinline__ void split2(V zf, V zmf, V twf, V& xf, V& xmf) {
+  const S ax = zf.x + zmf.x, ay = zf.y - zmf.y;
+  const S bx = zf.x - zmf.x, by = zf.y + zmf.y;
+  const S tbx = twf.x * bx - twf.y * by;   // w^f b
+  const S tby = twf.x * by + twf.y * bx;
+  xf.x = ax + tby;                         // s = tby - i tbx
+  xf.y = ay - tbx;
+  xmf.x = ax - tby;
+  xmf.y = -(ay + tbx);
 }
-// Inverse: from a Hermitian half spectrum V (f in [0, M]) to the packed complex input of an inverse M-point FFT:
-//   Z[f] = (V[f] + conj(V[M-f])) / 2 + i conj(w^f) (V[f] - conj(V[M-f])) / 2.
+// Inverse: from a doubled Hermitian half spectrum V (bins f and M-f) to the doubled packed input of an inverse
+// M-point FFT:  a = V[f] + conj(V[M-f]),  b = V[f] - conj(V[M-f]),  q = i conj(w^f) b;
+//   2Z[f] = a + q,   2Z[M-f] = conj(a - q).
 template <typename V, typename S>
-__device__ __forceinline__ V real_merge(V vf, V vmf, V twf) {
-  const V c = cconj(vmf);
-  const V e = cscale(cadd(vf, c), (S)0.5);
-  const V o = cscale(csub(vf, c), (S)0.5);
-  return cadd(e, cmul_mi(cmul(cconj(twf), o), true));
+__device__ __forceinline__ void merge2(V vf, V vmf, V twf, V& zf, V& zmf) {
+  const S ax = vf.x + vmf.x, ay = vf.y - vmf.y;
+  const S bx = vf.x - vmf.x, by = vf.y + vmf.y;
+  const S cbx = twf.x * bx + twf.y * by;   // conj(w^f) b
+  const S cby = twf.x * by - twf.y * bx;
+  zf.x = ax - cby;                         // q = -cby + i cbx
+  zf.y = ay + cbx;
+  zmf.x = ax + cby;
+  zmf.y = -(ay - cbx);
 }
 
 template <typename T>
@@ -169,25 +183,62 @@ struct FftCfg2 {
   static constexpr int PADDED = M + M / 8 + 8;   // entries of a padded work array (index pix(f), f <= M)
 };
 
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Gram pass: below this many multiply-adds per tile (p_pad x nlag) the lag sums come from |W|^2 plus direct
+// corrections (one transform per tile); above it from W . conj(B) with B the tile's row block (two transforms).
+template <typename T>
+struct GramCfg {
+  static constexpr long long kDirectMax = sizeof(T) == 8 ? 24576 : 65536;
+};
+
+// Shared memory of the FFT kernels: work arrays A, B (padded), the doubled spectrum D of the lag-reversed d,
+// the CTA's accumulated spectrum S (float64), the Gram pass's window segments ext[2 p_pad], tacc, scratch.
 template <typename T>
 struct FftSmem {
   using V = typename FftCfg<T>::V;
-  V *A, *B;               // work arrays, padded (pix)
-  V *W, *D;               // half spectra, M + 1 entries each
+  static constexpr int M = FftCfg<T>::N / 2;
+  static constexpr int PADDED = FftCfg2<T>::PADDED;
+  V *A, *B, *D;
+  double2* S;
+  T* ext;
   double *tacc, *scratch;
+  __host__ __device__ static size_t bytes(int p_pad) {
+    return round16(sizeof(V) * (2 * (size_t)PADDED + (M + 1))) + sizeof(double2) * (M + 1) +
+           round16(sizeof(T) * 2 * (size_t)p_pad) + sizeof(double) * ((size_t)p_pad + 16 + 16);
+  }
   __device__ FftSmem(unsigned char* raw, int p_pad) {
-    constexpr int M = FftCfg<T>::N / 2;
-    constexpr int PADDED = FftCfg2<T>::PADDED;
     A = reinterpret_cast<V*>(raw);
     B = A + PADDED;
-    W = B + PADDED;
-    D = W + (M + 1);
-    tacc = reinterpret_cast<double*>(D + (M + 1));
+    D = B + PADDED;
+    unsigned char* q = raw + round16(sizeof(V) * (2 * (size_t)PADDED + (M + 1)));
+    S = reinterpret_cast<double2*>(q);
+    q += sizeof(double2) * (M + 1);
+    ext = reinterpret_cast<T*>(q);
+    q += round16(sizeof(T) * 2 * (size_t)p_pad);
+    tacc = reinterpret_cast<double*>(q);
     scratch = tacc + p_pad + 16;
   }
 };
 
-// Spectrum of the lag-reversed d (scaled), into sm.D.
+// Window y[i0 .. i0+N) (zero past n), packed in pairs, into sm.A; then its complex transform (result in sm.A).
+template <typename T>
+__device__ void fft_window(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long i0,
+                           const typename FftCfg<T>::V* tw) {
+  using V = typename FftCfg<T>::V;
+  constexpr int M = FftCfg<T>::N / 2;
+  for (int j = threadIdx.x; j < M; j += kThreads) {
+    const long long g0 = i0 + 2 * j;
+    V v;
+    v.x = g0 < n ? y[g0] : (T)0;
+    v.y = g0 + 1 < n ? y[g0 + 1] : (T)0;
+    sm.A[pix(j)] = v;
+  }
+  __syncthreads();
+  fft_complex<V, T, M>(sm.A, sm.B, tw, false);
+}
+
+// Doubled spectrum of the lag-reversed, scaled d, into sm.D.
 template <typename T>
 __device__ void fft_d_spectrum(FftSmem<T>& sm, const double* d, double d_scale, int p, const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
@@ -201,114 +252,163 @@ __device__ void fft_d_spectrum(FftSmem<T>& sm, const double* d, double d_scale, 
   }
   __syncthreads();
   fft_complex<V, T, M>(sm.A, sm.B, tw, false);
-  for (int f = threadIdx.x; f <= M; f += kThreads)
-    sm.D[f] = real_split<V, T>(sm.A[pix(f & (M - 1))], sm.A[pix((M - f) & (M - 1))], tw[f]);
-  __syncthreads();
-}
-
-// One tile of L rows starting at i0. Accumulates X^T u (lag order) into sm.tacc; returns this thread's ||u||^2.
-// Window spectrum W = RFFT(y[i0 .. i0 + N)) of one tile, into sm.W.
-template <typename T>
-__device__ void fft_window_spectrum(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long i0,
-                                    const typename FftCfg<T>::V* tw) {
-  using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
-  for (int j = threadIdx.x; j < M; j += kThreads) {
-    const long long g0 = i0 + 2 * j;
-    V v;
-    v.x = g0 < n ? y[g0] : (T)0;
-    v.y = g0 + 1 < n ? y[g0 + 1] : (T)0;
-    sm.A[pix(j)] = v;
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V xf, xm;
+    split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
+    sm.D[f] = xf;
+    sm.D[M - f] = xm;
   }
   __syncthreads();
-  fft_complex<V, T, M>(sm.A, sm.B, tw, false);
-  for (int f = threadIdx.x; f <= M; f += kThreads)
-    sm.W[f] = real_split<V, T>(sm.A[pix(f & (M - 1))], sm.A[pix((M - f) & (M - 1))], tw[f]);
-  __syncthreads();
 }
 
-// One tile of L rows starting at i0. Accumulates X^T u (lag order) into sm.tacc; returns this thread's ||u||^2.
-// wsrc: the tile's window spectrum precomputed in global memory (M + 1 entries), or null to transform it here.
+template <typename V>
+__device__ __forceinline__ void acc_add(double2& s, V v) {
+  s.x += (double)v.x;
+  s.y += (double)v.y;
+}
+
+// One tile of L rows starting at i0 of a product pass: u = X d - c u_old on the tile's rows (stored when u_new
+// is given), and W . conj(U) added into the CTA's spectrum sm.S. wt: the tile's doubled window spectrum
+// (M + 1 entries, global). Returns this thread's part of ||u||^2.
 template <typename T>
-__device__ double fft_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long m, int L, int nlag,
-                           int gram, const T* u_old, T* u_new, double coef, long long i0,
-                           const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wsrc) {
+__device__ double fft_tile(FftSmem<T>& sm, long long m, int L, const T* u_old, T* u_new, double coef, long long i0,
+                           const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wt) {
   using V = typename FftCfg<T>::V;
   constexpr int M = FftCfg<T>::N / 2;
-  const T invM = (T)1 / (T)M;
+  const T sc = (T)(1.0 / (8.0 * M));
   const int rows = (int)min((long long)L, m - i0);
-  if (wsrc) {
-    for (int f = threadIdx.x; f <= M; f += kThreads) sm.W[f] = wsrc[f];
-    __syncthreads();
-  } else {
-    fft_window_spectrum<T>(sm, y, n, i0, tw);
+  // X d = IRFFT(W . conj(D)) on rows [0, L)
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V zf, zm;
+    merge2<V, T>(cmulc(wt[f], sm.D[f]), cmulc(wt[M - f], sm.D[M - f]), tw[f], zf, zm);
+    sm.A[pix(f)] = zf;
+    if (f != 0 && f != M / 2) sm.A[pix(M - f)] = zm;
   }
+  __syncthreads();
+  fft_complex<V, T, M>(sm.A, sm.B, tw, true);
+  // u = X d - c u_old on the tile's rows, zero elsewhere; packed into B for its forward transform
+  T nn = (T)0;
+  for (int j = threadIdx.x; j < M; j += kThreads) {
+    const int r0 = 2 * j, r1 = 2 * j + 1;
+    const V z = sm.A[pix(j)];
+    T u0 = (T)0, u1 = (T)0;
+    if (r0 < rows) {
+      u0 = z.x * sc;
+      if (u_old) u0 = fma((T)(-coef), u_old[i0 + r0], u0);
+      if (u_new) u_new[i0 + r0] = u0;
+    }
+    if (r1 < rows) {
+      u1 = z.y * sc;
+      if (u_old) u1 = fma((T)(-coef), u_old[i0 + r1], u1);
+      if (u_new) u_new[i0 + r1] = u1;
+    }
+    nn = fma(u0, u0, fma(u1, u1, nn));
+    V v;
+    v.x = u0;
+    v.y = u1;
+    sm.B[pix(j)] = v;
+  }
+  __syncthreads();
+  fft_complex<V, T, M>(sm.B, sm.A, tw, false);
+  // S += W . conj(U)
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V uf, um;
+    split2<V, T>(sm.B[pix(f)], sm.B[pix((M - f) & (M - 1))], tw[f], uf, um);
+    acc_add(sm.S[f], cmulc(wt[f], uf));
+    if (f != M / 2) acc_add(sm.S[M - f], cmulc(wt[M - f], um));
+  }
+  return (double)nn;
+}
 
-  double n2 = 0.0;
-  if (!gram) {
-    // X d = IRFFT(W . conj(D)) on rows [0, L)
-    for (int f = threadIdx.x; f <= M; f += kThreads) sm.B[pix(f)] = cmulc(sm.W[f], sm.D[f]);
-    __syncthreads();
-    for (int f = threadIdx.x; f < M; f += kThreads) sm.A[pix(f)] = real_merge<V, T>(sm.B[pix(f)], sm.B[pix(M - f)], tw[f]);
-    __syncthreads();
-    fft_complex<V, T, M>(sm.A, sm.B, tw, true);
-    // u = X d - c u_old on the tile's rows, zero elsewhere; packed into B for its forward transform
-    T nn = (T)0;
-    for (int j = threadIdx.x; j < M; j += kThreads) {
-      const int r0 = 2 * j, r1 = 2 * j + 1;
-      const V z = sm.A[pix(j)];
-      T u0 = (T)0, u1 = (T)0;
-      if (r0 < rows) {
-        u0 = z.x * invM;
-        if (u_old) u0 = fma((T)(-coef), u_old[i0 + r0], u0);
-        if (u_new) u_new[i0 + r0] = u0;
-      }
-      if (r1 < rows) {
-        u1 = z.y * invM;
-        if (u_old) u1 = fma((T)(-coef), u_old[i0 + r1], u1);
-        if (u_new) u_new[i0 + r1] = u1;
-      }
-      nn = fma(u0, u0, fma(u1, u1, nn));
-      V v;
-      v.x = u0;
-      v.y = u1;
-      sm.B[pix(j)] = v;
+// One tile of the Gram pass: the tile's doubled window spectrum into wt (global), and the lag sums
+// sum_{r < rows} y[i0 + r] y[i0 + r + k], k < nlag, into the CTA's state:
+//   corr: S += |W|^2 (circular autocorrelation of the window) and tacc -= its pairs that start in the window's
+//         last p_pad samples: sum_{j < p_pad} ext[j] ext[j + k], ext = (window tail, window head); the last
+//         tile also drops its pairs that start at rows >= m.
+//   else: S += W . conj(B), B the spectrum of the tile's row block (zero beyond its rows).
+template <typename T>
+__device__ void fft_gram_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long m, int L, int p_pad,
+                              int nlag, long long i0, const typename FftCfg<T>::V* tw,
+                              typename FftCfg<T>::V* __restrict__ wt, bool corr) {
+  using V = typename FftCfg<T>::V;
+  constexpr int M = FftCfg<T>::N / 2;
+  const int rows = (int)min((long long)L, m - i0);
+  if (corr) {
+    for (int j = threadIdx.x; j < 2 * p_pad; j += kThreads) {
+      const long long g = j < p_pad ? i0 + L + j : i0 + (j - p_pad);
+      sm.ext[j] = g < n ? y[g] : (T)0;
     }
-    n2 = (double)nn;
-    __syncthreads();
-    fft_complex<V, T, M>(sm.B, sm.A, tw, false);
-  } else {
-    // Gram lag sums: u = y itself on the tile's rows
-    for (int j = threadIdx.x; j < M; j += kThreads) {
-      const int r0 = 2 * j, r1 = 2 * j + 1;
-      V v;
-      v.x = r0 < rows ? y[i0 + r0] : (T)0;
-      v.y = r1 < rows ? y[i0 + r1] : (T)0;
-      sm.B[pix(j)] = v;
-    }
-    __syncthreads();
-    fft_complex<V, T, M>(sm.B, sm.A, tw, false);
   }
-  // X^T u = IRFFT(W . conj(U)) on lags [0, nlag)
-  for (int f = threadIdx.x; f <= M; f += kThreads) {
-    const V uf = real_split<V, T>(sm.B[pix(f & (M - 1))], sm.B[pix((M - f) & (M - 1))], tw[f]);
-    sm.A[pix(f)] = cmulc(sm.W[f], uf);
+  fft_window<T>(sm, y, n, i0, tw);
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V xf, xm;
+    split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
+    wt[f] = xf;
+    wt[M - f] = xm;
+    if (corr) {
+      sm.S[f].x += (double)xf.x * xf.x + (double)xf.y * xf.y;
+      if (f != M / 2) sm.S[M - f].x += (double)xm.x * xm.x + (double)xm.y * xm.y;
+    }
+  }
+  if (corr) {
+    for (int k = threadIdx.x; k < nlag; k += kThreads) {
+      double c = 0.0;
+      for (int j = 0; j < p_pad; ++j) c = fma((double)sm.ext[j], (double)sm.ext[j + k], c);
+      if (rows < L) {
+        const long long hi = min(i0 + L, n - k);
+        for (long long i = m; i < hi; ++i) c = fma((double)y[i], (double)y[i + k], c);
+      }
+      sm.tacc[k] -= c;
+    }
+    return;
+  }
+  // row block spectrum B (sm.B is free: the window transform ended in sm.A)
+  for (int j = threadIdx.x; j < M; j += kThreads) {
+    const int r0 = 2 * j, r1 = 2 * j + 1;
+    V v;
+    v.x = r0 < rows ? y[i0 + r0] : (T)0;
+    v.y = r1 < rows ? y[i0 + r1] : (T)0;
+    sm.B[pix(j)] = v;
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < M; f += kThreads) sm.B[pix(f)] = real_merge<V, T>(sm.A[pix(f)], sm.A[pix(M - f)], tw[f]);
+  fft_complex<V, T, M>(sm.B, sm.A, tw, false);
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V bf, bm;
+    split2<V, T>(sm.B[pix(f)], sm.B[pix((M - f) & (M - 1))], tw[f], bf, bm);
+    acc_add(sm.S[f], cmulc(wt[f], bf));      // wt[f], wt[M - f]: written by this thread above
+    if (f != M / 2) acc_add(sm.S[M - f], cmulc(wt[M - f], bm));
+  }
+}
+
+// End of a CTA's tiles: tacc[k] += IRFFT(S)[k], k < nlag (S holds 4x the true spectrum: scale 1 / (8 M)).
+template <typename T>
+__device__ void fft_finish_lags(FftSmem<T>& sm, int nlag, const typename FftCfg<T>::V* tw) {
+  using V = typename FftCfg<T>::V;
+  constexpr int M = FftCfg<T>::N / 2;
+  for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+    V vf, vm, zf, zm;
+    vf.x = (T)sm.S[f].x;
+    vf.y = (T)sm.S[f].y;
+    vm.x = (T)sm.S[M - f].x;
+    vm.y = (T)sm.S[M - f].y;
+    merge2<V, T>(vf, vm, tw[f], zf, zm);
+    sm.A[pix(f)] = zf;
+    if (f != 0 && f != M / 2) sm.A[pix(M - f)] = zm;
+  }
   __syncthreads();
-  fft_complex<V, T, M>(sm.B, sm.A, tw, true);
+  fft_complex<V, T, M>(sm.A, sm.B, tw, true);
+  const double sc = 1.0 / (8.0 * M);
   for (int k = threadIdx.x; k < nlag; k += kThreads) {
-    const V z = sm.B[pix(k >> 1)];
-    sm.tacc[k] += (double)(((k & 1) ? z.y : z.x) * invM);
+    const V z = sm.A[pix(k >> 1)];
+    sm.tacc[k] += (double)((k & 1) ? z.y : z.x) * sc;
   }
-  return n2;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   using V = typename FftCfg<T>::V;
   constexpr int N = FftCfg<T>::N;
+  constexpr int M = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
   int tail = a.tail;
@@ -323,19 +423,23 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   const int p_pad = a.p_pad, nlag = a.nlag;
   const int L = N - p_pad;
   const V* tw = reinterpret_cast<const V*>(sizeof(T) == 8 ? a.w.tw64 : a.w.tw32);
+  V* wspec = reinterpret_cast<V*>(sizeof(T) == 8 ? a.w.wspec64 : a.w.wspec32);
   FftSmem<T> sm(smem_raw, p_pad);
   const int tid = threadIdx.x;
   for (int k = tid; k < p_pad + 16; k += kThreads) sm.tacc[k] = 0.0;
-  if (!a.gram) fft_d_spectrum<T>(sm, a.d, a.d_scale, a.p, tw);
-  double n2 = 0.0;
+  for (int f = tid; f <= M; f += kThreads) sm.S[f] = make_double2(0.0, 0.0);
   const long long ntiles = (a.m + L - 1) / L;
-  const V* wspec = reinterpret_cast<const V*>(sizeof(T) == 8 ? a.w.wspec64 : a.w.wspec32);
-  if (!a.use_wspec) wspec = nullptr;
+  const bool corr = a.gram && (long long)p_pad * nlag <= GramCfg<T>::kDirectMax;
+  if (!a.gram && blockIdx.x < ntiles) fft_d_spectrum<T>(sm, a.d, a.d_scale, a.p, tw);
+  double n2 = 0.0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    n2 += fft_tile<T>(sm, a.y, a.n, a.m, L, nlag, a.gram, u_old, u_new, coef, tile * L, tw,
-                      wspec ? wspec + (size_t)tile * (FftCfg<T>::N / 2 + 1) : nullptr);
+    V* wt = wspec + (size_t)tile * (M + 1);
+    if (a.gram) fft_gram_tile<T>(sm, a.y, a.n, a.m, L, p_pad, nlag, tile * L, tw, wt, corr);
+    else n2 += fft_tile<T>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt);
   }
+  __syncthreads();
+  if (blockIdx.x < ntiles) fft_finish_lags<T>(sm, nlag, tw);
   __syncthreads();
   const double n2_cta = block_sum(n2, sm.scratch);
   for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
@@ -349,24 +453,29 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
 
 template <typename T>
 static size_t fft_pass_smem(int p_pad) {
-  using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
-  return sizeof(V) * (2 * (size_t)FftCfg2<T>::PADDED + 2 * (size_t)(M + 1)) + sizeof(double) * ((size_t)p_pad + 16 + 16);
+  return FftSmem<T>::bytes(p_pad);
 }
 
-// Window spectra of every tile of a series (tiles of L = N - p_pad rows), computed once per solve: y does not
-// change between passes, so the passes read W from here instead of transforming the window again.
+// Doubled window spectra of every tile of a series (tiles of L = N - p_pad rows), for passes whose Gram pass did
+// not form them (another precision's Gram pass, or a single product pass): y does not change between passes.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) spectrum_kernel(const T* __restrict__ y, long long n, long long m, int L,
                                                            typename FftCfg<T>::V* __restrict__ out,
                                                            const typename FftCfg<T>::V* tw) {
+  using V = typename FftCfg<T>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int M = FftCfg<T>::N / 2;
   FftSmem<T> sm(smem_raw, 0);
   const long long ntiles = (m + L - 1) / L;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    fft_window_spectrum<T>(sm, y, n, tile * L, tw);
-    for (int f = threadIdx.x; f <= M; f += kThreads) out[(size_t)tile * (M + 1) + f] = sm.W[f];
+    fft_window<T>(sm, y, n, tile * L, tw);
+    V* wt = out + (size_t)tile * (M + 1);
+    for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
+      V xf, xm;
+      split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
+      wt[f] = xf;
+      wt[M - f] = xm;
+    }
   }
 }

@@ -82,8 +82,8 @@ struct Work {
   DevState* st;
   const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
-  void* wspec32;          // precomputed window spectra of the float FFT tiles (nullable)
-  void* wspec64;          // precomputed window spectra of the float64 FFT tiles (nullable)
+  void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
+  void* wspec64;          // the same for the float64 FFT tiles
 };
 
 // Arguments of a pass kernel (passed by value).
@@ -108,7 +108,6 @@ struct PassArgs {
   int* worklog;           // nullable: the tail writes 1 + tail + 5 * (T == double) into worklog[work_slot]
   int work_slot;
   int fft;                // 1: overlap-save FFT products (fft_pass_kernel) instead of the direct ones
-  int use_wspec;          // 1: read the tile window spectra from w.wspec32 / w.wspec64
 };
 
 // One series of a batch (device array). Its Work points at the series' own slices of the batch buffers; its

@@ -850,7 +850,7 @@ template <typename T>
 static cudaError_t launch_spectra_t(const T* y, long long n, long long m, int p_pad, void* out, const void* tw,
                                     int grid, cudaStream_t s) {
   using V = typename FftCfg<T>::V;
-  const size_t smem = sizeof(V) * (2 * (size_t)FftCfg2<T>::PADDED + 2 * (size_t)(FftCfg<T>::N / 2 + 1)) + 512;
+  const size_t smem = round16(sizeof(V) * 2 * (size_t)FftCfg2<T>::PADDED);   // the work arrays A, B only
   static int configured = 0;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(spectrum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

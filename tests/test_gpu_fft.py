@@ -78,7 +78,7 @@ def test_fft_gk_pass(torch, tols, fctx, p, n, prec):
     assert n2 == pytest.approx(float(u @ u), rel=64 * u_eps)
 
 
-@pytest.mark.parametrize("p,n", [(10, 10_000), (100, 3 * 2048 + 333), (300, 20_000)])
+@pytest.mark.parametrize("p,n", [(10, 10_000), (20, 1000), (50, 2100), (100, 3 * 2048 + 333), (300, 20_000)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_fft_gram(torch, tols, fctx, p, n, prec):
     y = ar_series(n, 4, config_id=52, series_index=p).y

@@ -314,8 +314,13 @@ def run_ours(args, wl):
     barrier()
     e2e_ms = max_over_ranks(sum(e2e_times))
 
-    batched = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world) if batch_in else None
-    serving = run_serving(tols, serve_in, args) if serve_in else None
+    batched = batched_mixed = serving = None
+    if batch_in:
+        batched = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world, tols.TOLS_FP64)
+        batched_mixed = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world,
+                                    tols.TOLS_MIXED)
+    if serve_in:
+        serving = run_serving(tols, serve_in, args)
 
     hbm_peak, hbm_src = peaks()
     r64, rmx = results["fp64"], results["mixed"]
@@ -384,6 +389,7 @@ def run_ours(args, wl):
            "e2e": {"value": whole_job_rate(world, K, e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
                    "d2h_bytes_per_step": 8 * p},
            "batched": batched,
+           "batched_mixed": batched_mixed,
            "serving": serving,
            "gpu_launches": int(r64["launches"] + rmx["launches"]),
            "clocks": r64["clocks"],
@@ -410,16 +416,17 @@ def run_ours(args, wl):
     ranks.close()
 
 
-def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world):
-    """Many series of uneven length in one batched solve (mixed precision), series resident in HBM."""
+def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world, prec):
+    """Many series of uneven length in one batched solve, series resident in HBM."""
     import numpy as np
     ys, ps = batch_in
     d_ys = [torch.tensor(y, dtype=torch.float64, device=dev) for y in ys]
     d_phi = torch.empty(sum(ps), dtype=torch.float64, device=dev)
     steps = max(2, min(args.steps, 5))
-    out = {"series": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "mixed",
+    out = {"series": len(ys), "sum_n": int(sum(y.size for y in ys)),
+           "precision": "fp64" if prec == tols.TOLS_FP64 else "mixed",
            "workload": "n log-uniform in [1e4, 1e6], p uniform in [5, 200], roots |r| in U[1.2, 3], N(0,1)"}
-    with tols.Context(precision=tols.TOLS_MIXED, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
+    with tols.Context(precision=prec, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
         tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)       # warm-up
         tols.toeplitz_ols_profile(ctx, True)
         barrier()
@@ -443,6 +450,7 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
                 "statuses_not_converged": int(sum(1 for x in status if x == 1)),
                 "fp64_fallbacks": int(sum(1 for i in infos if i["precision_used"] == 0)),
                 "mean_iters": float(np.mean([i["iters"] for i in infos])),
+                "max_iters": int(max(i["iters"] for i in infos)),
                 "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches),
                 "f32_lsqr_pass_launches": f32[0], "f32_lsqr_pass_ms": f32[1]})
     # accuracy on a few series against the oracle (timed as the CPU baseline of this workload)
@@ -466,13 +474,13 @@ def run_serving(tols, serve_in, args):
     """Continuous batching: saturation throughput, then Poisson arrivals at half of it; p50/p99 latency."""
     import numpy as np
     ys, ps = serve_in
-    res = {"requests": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "mixed",
+    res = {"requests": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "fp64",
            "workload": "n log-uniform in [1e3, 1e7], p log-uniform in [1, 300], roots |r| in U[1.2, 3], N(0,1)"}
 
     def run(rate):
         rng = np.random.default_rng(5)
         arrivals = np.zeros(len(ys)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, size=len(ys)))
-        with tols.Server(precision=tols.TOLS_MIXED, burst=4) as srv:
+        with tols.Server(precision=tols.TOLS_FP64, burst=4) as srv:
             t0 = time.perf_counter()
             nxt, done, lat = 0, [], []
             while len(done) < len(ys):

@@ -51,7 +51,13 @@ typedef enum {
 
 typedef enum {
   TOLS_PRECOND_NONE = 0,      /* plain LSQR on X                                                           */
-  TOLS_PRECOND_GRAM_CHOL = 1  /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X          */
+  TOLS_PRECOND_GRAM_CHOL = 1, /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X. A float64
+                                 solve whose factor is not trustworthy (kappa(R)^2 u > 1/4) switches to
+                                 TOLS_PRECOND_SAMPLED_QR by itself (p <= 256, n - p >= 4p)                      */
+  TOLS_PRECOND_SAMPLED_QR = 2 /* LSQR on X R^{-1}, R from a float64 Householder QR of 4p rows of X sampled
+                                 evenly (the row-sampling idea of Section 3.1 used as a preconditioner; errors
+                                 of order kappa u instead of kappa^2 u). float64 solves, p <= 256, n - p >= 4p;
+                                 otherwise the Gram factor is used                                             */
 } tols_precond;
 
 typedef enum {
@@ -77,7 +83,8 @@ typedef struct {
   int iters;              /* LSQR iterations (FP64) or inner iterations over all sweeps (mixed)             */
   int sweeps;             /* float64 residual passes made                                                   */
   int precision_used;     /* tols_precision actually used (mixed falls back to FP64 when kappa is too big)  */
-  int precond_used;       /* tols_precond actually used (falls back to NONE if the Gram matrix is singular) */
+  int precond_used;       /* tols_precond actually used (SAMPLED_QR for an ill-conditioned float64 solve,
+                             NONE if no factor could be formed)                                               */
   int product_used;       /* tols_product actually used                                                     */
   double ne_ratio;        /* ||X^T r|| / (||X||_2est ||r||), r = b - X phi, from a float64 pass             */
   double rnorm;           /* ||b - X phi||_2 from the same pass                                             */

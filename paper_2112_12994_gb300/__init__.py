@@ -34,6 +34,7 @@ TOLS_FP64 = 0
 TOLS_MIXED = 1
 TOLS_PRECOND_NONE = 0
 TOLS_PRECOND_GRAM_CHOL = 1
+TOLS_PRECOND_SAMPLED_QR = 2
 TOLS_PRODUCT_AUTO = 0
 TOLS_PRODUCT_DIRECT = 1
 TOLS_PRODUCT_FFT = 2

@@ -340,11 +340,14 @@ int prepare_work(tols_ctx* ctx, const double* y64, long long n, int p, bool mixe
   w.best = q; q += pp;
   w.bnorm2 = q; q += pp;
   const size_t pq = (size_t)p * p;
-  if ((rc = ensure(ctx, ctx->mats, sizeof(double) * 3 * pq + sizeof(float) * 2 * pq + 1024))) return rc;
+  const size_t qrd = qr_scratch_doubles(p);
+  if ((rc = ensure(ctx, ctx->mats, sizeof(double) * (3 * pq + qrd) + sizeof(float) * 2 * pq + 1024))) return rc;
   q = (double*)ctx->mats.p;
   w.G = q; q += pq;
   w.M = q; q += pq;
   w.Mt = q; q += pq;
+  w.qr = qrd ? q : nullptr;
+  q += qrd;
   float* f = (float*)q;
   w.M32 = f; f += pq;
   w.Mt32 = f;
@@ -400,7 +403,7 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, 
     a.fft = fft;
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
-  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
+  const int want = no_precond ? 0 : ctx->cfg.precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
   return TOLS_OK;
 }
@@ -621,7 +624,8 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
     B.off_phi.push_back(B.phi_doubles);
     B.phi_doubles += (size_t)p[k];
     B.off_mat.push_back(B.mat_bytes);
-    B.mat_bytes += align_up(sizeof(double) * 3 * (size_t)p[k] * p[k] + sizeof(float) * 2 * (size_t)p[k] * p[k], 256);
+    B.mat_bytes += align_up(sizeof(double) * (3 * (size_t)p[k] * p[k] + qr_scratch_doubles(p[k])) +
+                            sizeof(float) * 2 * (size_t)p[k] * p[k], 256);
     B.tiles_f += ntf;
     B.tiles_d += ntd;
     B.p_pad_max = std::max(B.p_pad_max, pp1);
@@ -703,7 +707,8 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.G = (double*)mb;
     w.M = w.G + pq;
     w.Mt = w.M + pq;
-    w.M32 = (float*)(w.Mt + pq);
+    w.qr = qr_scratch_doubles(p) ? w.Mt + pq : nullptr;
+    w.M32 = (float*)(w.Mt + pq + qr_scratch_doubles(p));
     w.Mt32 = w.M32 + pq;
     w.st = (DevState*)ctx->b_state.p + k;
     S.tile0_f = tf;               // index in the float tile list
@@ -753,7 +758,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   ctx->launch_total++;
   if (mixed) CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
   else CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
-  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL && !no_precond;
+  const int want = no_precond ? 0 : ctx->cfg.precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream, B.p_pad_max); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
 
@@ -939,7 +944,7 @@ size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
   char* u1 = take(es * (size_t)m);
   char* part = take(sizeof(double) * (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr));
   char* vec = take(sizeof(double) * (9 * pp1 + (size_t)p));
-  char* mat = take(sizeof(double) * 3 * (size_t)p * p + sizeof(float) * 2 * (size_t)p * p);
+  char* mat = take(sizeof(double) * (3 * (size_t)p * p + qr_scratch_doubles(p)) + sizeof(float) * 2 * (size_t)p * p);
   if (base && w) {
     memset(w, 0, sizeof *w);
     w->n = n;
@@ -972,7 +977,8 @@ size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
     w->G = (double*)mat;
     w->M = w->G + pq;
     w->Mt = w->M + pq;
-    w->M32 = (float*)(w->Mt + pq);
+    w->qr = qr_scratch_doubles(p) ? w->Mt + pq : nullptr;
+    w->M32 = (float*)(w->Mt + pq + qr_scratch_doubles(p));
     w->Mt32 = w->M32 + pq;
   }
   return off;
@@ -1131,7 +1137,7 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
     ctx->launch_total++;
     CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
   }
-  const int want = ctx->cfg.precond == TOLS_PRECOND_GRAM_CHOL;
+  const int want = ctx->cfg.precond;
   const int cnt = (int)fresh.size();
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(a.series, cnt, want, ctx->stream, pmax); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(a.series, cnt, nullptr, ctx->stream); }));
@@ -1269,7 +1275,8 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
   if (cfg) c = *cfg;
   else toeplitz_ols_config_default(&c);
   if (c.precision != TOLS_FP64 && c.precision != TOLS_MIXED) return TOLS_ERR_ARG;
-  if (c.precond != TOLS_PRECOND_NONE && c.precond != TOLS_PRECOND_GRAM_CHOL) return TOLS_ERR_ARG;
+  if (c.precond != TOLS_PRECOND_NONE && c.precond != TOLS_PRECOND_GRAM_CHOL && c.precond != TOLS_PRECOND_SAMPLED_QR)
+    return TOLS_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= c.device || c.device < 0) {
     cudaGetLastError();

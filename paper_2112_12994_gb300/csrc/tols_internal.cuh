@@ -22,6 +22,13 @@ constexpr int kMaxGroups = (kMaxGrid + kGroup - 1) / kGroup;
 // Round p up to the lag-chunk granularity used by the direct kernels.
 __host__ __device__ constexpr int pad_p(int p) { return (p + 15) & ~15; }
 
+// Sampled-row QR preconditioner: orders it serves and rows sampled per coefficient; its scratch (doubles).
+constexpr int kQrMaxP = 256;
+constexpr int kQrRowsPerP = 4;
+__host__ __device__ constexpr size_t qr_scratch_doubles(int p) {
+  return p <= kQrMaxP ? (size_t)kQrRowsPerP * p * p : 0;
+}
+
 // What the last CTA of a pass does after the grid-wide reduction (see tails in tols_kernels.cu).
 enum TailMode : int {
   TAIL_STORE = 0,    // write the reduced X^T u and ||u||^2 to out_t / out_n2
@@ -50,12 +57,15 @@ struct DevState {
   // norms
   double anorm_f, anorm_2, ne_ratio, rnorm, ne_best, rnorm_best;
   double tol, tol_inner, est_ratio, cond_est;
-  int iter, max_iter, iter_cap, inner_iter, total_iter, sweeps, max_sweeps;
+  double est_best;   // best (halving) value of the inner solve's stopping estimate, at inner iteration iter_best
+  double phibar_mark;  // LSQR residual-norm estimate at the last iteration that made progress
+  int iter, max_iter, iter_cap, inner_iter, total_iter, sweeps, max_sweeps, iter_best;
   int phase, status, precond, mixed, mixed_ok;
   int done;          // 1 => every pass kernel returns at once
   int singular;      // the Gram matrix was singular at working precision
   int compatible;    // a check found ||r|| <= tol ||b||
   int shifted;       // the Cholesky factor needed the diagonal shift
+  int trusted;       // unshifted factor with kappa(R)^2 u <= 1/4 (semi-normal-equation start, float refinement)
   int no_precond;    // set by the host: plain LSQR (minimum-norm repeat of a rank-deficient problem)
 };
 
@@ -79,6 +89,7 @@ struct Work {
   float* M32;             // float copies for the mixed path
   float* Mt32;
   double* bnorm2;         // device scalar ||b||^2 written by the Gram pass
+  double* qr;             // (nullable) 4p x p float64 scratch for the sampled-row QR preconditioner (p <= 256)
   DevState* st;
   const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)

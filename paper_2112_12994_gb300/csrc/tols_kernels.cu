@@ -172,6 +172,14 @@ __device__ double vec_norm2(const double* a, int p, double* scratch) {
 // Solver tails. Run by the last CTA of a pass with tk[k] = sum_i u_new[i] y[i+k] (k in [0, nlag)) in shared
 // memory and n2 = ||u_new||^2. They update DevState and the p-vectors for the next launch.
 
+// An inner solve (LSQR or the correction solve) stops when its stopping estimate has not halved for this many
+// iterations: it has reached what the arithmetic (or the preconditioner) lets it reach, and the float64 check
+// decides what comes next.
+constexpr int kStallIters = 20;
+// With the sampled-QR preconditioner kappa(X R^{-1}) is a small constant (about 3): a sweep that has not
+// converged in this many iterations has met the limit of float64 arithmetic (kappa(X) u ~ 1).
+constexpr int kQrIterCap = 100;
+
 // After LSQR or the correction solve has finished: the next pass is a float64 residual check with
 // d = -phi and u_old = b, c = -1, so that u_new = b - X phi.
 __device__ void schedule_check(const Work& w, DevState* st, double* scratch) {
@@ -211,6 +219,9 @@ __device__ void start_lsqr(const Work& w, DevState* st, const double* g, double 
     st->rhobar = alpha;
     st->anorm2 = 0.0;
     st->iter = 0;
+    st->est_best = 1e300;
+    st->iter_best = 0;
+    st->phibar_mark = beta1;
     st->coef = beta1 > 0 ? alpha / beta1 : 0.0;
     st->phase = PH_LSQR;
   }
@@ -242,6 +253,8 @@ __device__ void start_necorr(const Work& w, DevState* st, double* scratch) {
     st->coef = 0.0;
     st->anorm2 = 0.0;
     st->inner_iter = 0;
+    st->est_best = 1e300;
+    st->iter_best = 0;
     st->phase = PH_NECORR;
   }
   __syncthreads();
@@ -289,9 +302,18 @@ __device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double 
   // order u ||b||); LSQR's estimate of ||r|| is phibar
   const double floor64 = new_phibar > 0 ? 1e-15 * sqrt((double)p) * st->bnorm / new_phibar : 0.0;
   const double tolA = st->mixed ? st->tol_inner : fmax(st->est_ratio, floor64);
-  // Paige-Saunders stopping tests: ||A^T r|| <= tol ||A|| ||r||, or a compatible system ||r|| <= tol ||rhs||
+  double est_best = st->est_best;
+  int iter_best = st->iter_best;
+  // progress: the ratio estimate halved, or the residual norm estimate still falls (relative 1e-10)
+  const bool progress = ratio < 0.5 * est_best || new_phibar < (1.0 - 1e-10) * st->phibar_mark;
+  if (progress) {
+    est_best = fmin(ratio, est_best);
+    iter_best = iter;
+  }
+  // Paige-Saunders stopping tests: ||A^T r|| <= tol ||A|| ||r||, or a compatible system ||r|| <= tol ||rhs||;
+  // or no progress for kStallIters iterations
   const bool stop = (ratio <= tolA) || (new_phibar <= tolA * st->beta1) || (beta == 0.0) || (alpha == 0.0) ||
-                    (iter >= st->iter_cap) ||
+                    (iter >= st->iter_cap) || (iter - iter_best >= kStallIters) ||
                     (st->total_iter + 1 >= 64 * st->max_iter);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -301,6 +323,9 @@ __device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double 
     st->phibar = new_phibar;
     st->anorm2 = anorm2;
     st->iter = iter;
+    st->est_best = est_best;
+    st->iter_best = iter_best;
+    if (progress) st->phibar_mark = new_phibar;
     st->total_iter += 1;
     st->coef = beta > 0 ? alpha / beta : 0.0;
   }
@@ -345,8 +370,15 @@ __device__ void tail_necorr(const Work& w, DevState* st, const double* tk, doubl
   __syncthreads();
   const double resid = fabs(theta_next * f);
   const int it = st->inner_iter + 1;
+  double est_best = st->est_best;
+  int iter_best = st->iter_best;
+  if (resid < 0.5 * est_best) {
+    est_best = resid;
+    iter_best = it;
+  }
   const bool stop = rho == 0.0 || theta_next == 0.0 || resid <= st->tol_inner * st->theta1 ||
-                    it >= st->iter_cap || (st->total_iter + 1 >= 64 * st->max_iter);
+                    it >= st->iter_cap || (it - iter_best >= kStallIters) ||
+                    (st->total_iter + 1 >= 64 * st->max_iter);
   __syncthreads();
   if (threadIdx.x == 0) {
     st->anorm2 += theta * theta + rho * rho;
@@ -354,6 +386,8 @@ __device__ void tail_necorr(const Work& w, DevState* st, const double* tk, doubl
     st->rho = rho;
     st->theta = theta_next;
     st->inner_iter = it;
+    st->est_best = est_best;
+    st->iter_best = iter_best;
     st->total_iter += 1;
     st->coef = rho > 0 ? theta_next / rho : 0.0;
   }
@@ -378,6 +412,10 @@ __device__ void tail_check(const Work& w, DevState* st, const double* tk, double
   const double gn = sqrt(vec_norm2(w.g, p, scratch));
   const double ne = (rnorm > 0 && st->anorm_2 > 0) ? gn / (st->anorm_2 * rnorm) : 0.0;
   const double prev = st->ne_ratio;
+  // the residual norm still falls (by 1 % or more) since the last check: each sweep of LSQR on the residual can
+  // resolve it only to about kappa(X) u relative, so an ill-conditioned solve needs several sweeps even while its
+  // ratio stays high
+  const bool r_progress = st->sweeps >= 1 && rnorm < 0.99 * st->rnorm;
   const int sweeps = st->sweeps + 1;
   const bool better = ne < st->ne_best;
   if (better)
@@ -400,7 +438,7 @@ __device__ void tail_check(const Work& w, DevState* st, const double* tk, double
   if (threadIdx.x == 0 && rnorm <= st->tol * st->bnorm) st->compatible = 1;
   if (ne <= st->tol || rnorm <= st->tol * st->bnorm) next = 0;           // converged (or compatible)
   else if (sweeps >= st->max_sweeps || st->total_iter >= 64 * st->max_iter) next = 1;  // give up
-  else if (sweeps >= 2 && ne > 0.5 * prev) {                              // no progress since the last check
+  else if (sweeps >= 2 && ne > 0.5 * prev && !r_progress) {              // no progress since the last check
     next = (st->mixed && ne > 10.0 * floor64) ? 2 : 1;                   // mixed: float cannot refine it
   } else if (st->mixed && sweeps == 1 && ne > 1e-2) {
     next = 2;                                                             // float LSQR gained < 2 digits
@@ -422,6 +460,7 @@ __device__ void tail_check(const Work& w, DevState* st, const double* tk, double
     if (threadIdx.x == 0) {
       st->est_ratio = fmax(st->est_ratio * 0.01, 1e-16);
       st->iter_cap = min(st->max_iter, max(2 * st->iter + 10, 20));
+      if (st->precond == 2) st->iter_cap = min(st->iter_cap, kQrIterCap);
     }
     __syncthreads();
     start_lsqr(w, st, w.g, rnorm, scratch);
@@ -905,6 +944,79 @@ __device__ __forceinline__ double* scratch_vec(const Work& w) { return w.t; }  /
 // substitutions are chains of dependent read-modify-writes, which would wait on L2 round trips in global memory.
 constexpr int kPrecondSmemP = 112;
 
+// Sampled-row QR (Section 3.1: a least-squares problem on sampled rows of X): c = kQrRowsPerP p rows of X,
+// evenly spaced (row i_k = floor((k + 1/2) m / c)), gathered into w.qr (c x p, row-major), then Householder QR
+// in float64. R (upper triangular, p x p, row-major) is written to R. Returns false when a column of the sample
+// is (numerically) dependent on the others, i.e. R would be singular.
+__device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, double* qpart, double* scratch) {
+  const int p = w.p;
+  const long long m = w.m;
+  const int c = kQrRowsPerP * p;
+  double* A = w.qr;
+  const double* y = w.y64;
+  for (long long q = threadIdx.x; q < (long long)c * p; q += kThreads) {
+    const int i = (int)(q / p), j = (int)(q - (long long)i * p);
+    const long long row = ((2LL * i + 1) * m) / (2LL * c);
+    A[q] = y[p + row - j - 1];
+  }
+  for (long long q = threadIdx.x; q < (long long)p * p; q += kThreads) R[q] = 0.0;
+  __syncthreads();
+  double amax = 0.0;   // largest |R_kk| so far, for the rank test
+  bool full_rank = true;
+  for (int k = 0; k < p; ++k) {
+    // Householder vector of column k below the diagonal: v = x - alpha e_k, alpha = -sign(x_k) ||x||
+    double s = 0.0;
+    for (int i = k + threadIdx.x; i < c; i += kThreads) {
+      const double a = A[(size_t)i * p + k];
+      qv[i] = a;
+      s = fma(a, a, s);
+    }
+    s = block_sum(s, scratch);                      // synchronises: qv complete
+    const double x0 = qv[k];
+    const double nrm = sqrt(s);
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    const double vk = x0 - alpha;
+    const double vtv = s - x0 * x0 + vk * vk;
+    amax = fmax(amax, nrm);
+    if (!(nrm > 1e-13 * amax)) full_rank = false;
+    const int ncol = p - k - 1;
+    if (vtv > 0.0 && ncol > 0) {
+      const double beta = 2.0 / vtv;
+      __syncthreads();
+      if (threadIdx.x == 0) qv[k] = vk;
+      __syncthreads();
+      // qw_j = beta sum_{i >= k} v_i A[i][j] for the trailing columns: (column, row-slice) pairs over the CTA
+      const int nsplit = max(1, min(kThreads / ncol, c - k));
+      for (int t = threadIdx.x; t < ncol * nsplit; t += kThreads) {
+        const int jj = t % ncol, r0 = t / ncol;
+        const int j = k + 1 + jj;
+        double acc = 0.0;
+        for (int i = k + r0; i < c; i += nsplit) acc = fma(qv[i], A[(size_t)i * p + j], acc);
+        qpart[t] = acc;
+      }
+      __syncthreads();
+      for (int jj = threadIdx.x; jj < ncol; jj += kThreads) {
+        double acc = 0.0;
+        for (int r0 = 0; r0 < nsplit; ++r0) acc += qpart[r0 * ncol + jj];
+        qw[jj] = beta * acc;
+      }
+      __syncthreads();
+      // A[i][j] -= v_i qw_j over the trailing block
+      const long long tot = (long long)(c - k) * ncol;
+      for (long long q = threadIdx.x; q < tot; q += kThreads) {
+        const int i = k + (int)(q / ncol), jj = (int)(q - (long long)(q / ncol) * ncol);
+        const size_t idx = (size_t)i * p + (k + 1 + jj);
+        A[idx] = fma(-qv[i], qw[jj], A[idx]);
+      }
+      __syncthreads();
+    }
+    // row k of R: alpha on the diagonal, the transformed row k beyond it
+    for (int j = k + threadIdx.x; j < p; j += kThreads) R[(size_t)k * p + j] = j == k ? alpha : A[(size_t)k * p + j];
+    __syncthreads();
+  }
+  return full_rank;
+}
+
 __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   const int p = w.p;
   DevState* st = w.st;
@@ -912,9 +1024,15 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   __shared__ int s_fail;
   __shared__ int s_shift;
   __shared__ double s_val[2];
+  __shared__ float xs[TOLS_MAX_P], ys[TOLS_MAX_P], zs[TOLS_MAX_P];
+  __shared__ double red3[3 * (kThreads / 32)];
+  __shared__ double qv[kQrRowsPerP * kQrMaxP], qw[kQrMaxP], qpart[kThreads];
   const bool in_smem = smem && p <= kPrecondSmemP;
   double* G = in_smem ? smem : w.G;
   double* Mm = in_smem ? smem + (size_t)p * p : w.M;
+  // the Gram matrix is kept for a refactorisation: in w.G when the work is in shared memory, else in w.Mt
+  // (written only at the end)
+  const double* Gsave = in_smem ? w.G : w.Mt;
   if (in_smem) {
     for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.G[q];
     __syncthreads();
@@ -941,16 +1059,32 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     dmax = s_val[0];
     __syncthreads();
   }
+  // Sums over the CTA of three per-thread values (into nn, dot, xx; every thread gets them).
+  auto sum3 = [&](double& nn, double& dot, double& xx) {
+    nn = warp_sum(nn);
+    dot = warp_sum(dot);
+    xx = warp_sum(xx);
+    if ((threadIdx.x & 31) == 0) {
+      red3[threadIdx.x >> 5] = nn;
+      red3[(kThreads / 32) + (threadIdx.x >> 5)] = dot;
+      red3[2 * (kThreads / 32) + (threadIdx.x >> 5)] = xx;
+    }
+    __syncthreads();
+    nn = dot = xx = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) {
+      nn += red3[q];
+      dot += red3[(kThreads / 32) + q];
+      xx += red3[2 * (kThreads / 32) + q];
+    }
+  };
   // power iteration for lambda_max = ||X||_2^2 on a float copy of G (two digits suffice for the ratio's norm);
-  // the copy lives in the M area, which is free until the factorisation
+  // the copy lives in the M area, which is free until the inverse
+  double lam = 0.0;
   {
     float* Gf = reinterpret_cast<float*>(Mm);
-    __shared__ float xs[TOLS_MAX_P], ys[TOLS_MAX_P];
-    __shared__ double red3[3 * (kThreads / 32)];
     for (int q = threadIdx.x; q < p * p; q += kThreads) Gf[q] = (float)G[q];
     for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = 1.0f;
     __syncthreads();
-    double lam = 0.0;
     for (int it = 0; it < 12; ++it) {
       double nn = 0.0, dot = 0.0, xx = 0.0;
       for (int i = threadIdx.x; i < p; i += kThreads) {
@@ -967,30 +1101,13 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
         dot += (double)xs[i] * yi;
         xx += (double)xs[i] * xs[i];
       }
-      nn = warp_sum(nn);
-      dot = warp_sum(dot);
-      xx = warp_sum(xx);
-      if ((threadIdx.x & 31) == 0) {
-        red3[threadIdx.x >> 5] = nn;
-        red3[(kThreads / 32) + (threadIdx.x >> 5)] = dot;
-        red3[2 * (kThreads / 32) + (threadIdx.x >> 5)] = xx;
-      }
-      __syncthreads();
-      nn = dot = xx = 0.0;
-      for (int q = 0; q < kThreads / 32; ++q) {
-        nn += red3[q];
-        dot += red3[(kThreads / 32) + q];
-        xx += red3[2 * (kThreads / 32) + q];
-      }
+      sum3(nn, dot, xx);
       lam = xx > 0 ? dot / xx : 0.0;
       const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
       for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = ys[j] * inv;
       __syncthreads();
     }
-    if (threadIdx.x == 0) s_val[1] = lam;
-    __syncthreads();
   }
-  const double lam = s_val[1];
   if (!isfinite(tr) || !isfinite(*w.bnorm2)) {
     if (threadIdx.x == 0) {
       st->status = TOLS_ERR_NONFINITE;
@@ -1009,25 +1126,106 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   }
   __syncthreads();
 
-  // Cholesky G = R^T R on the upper triangle (right-looking), first without a shift. If a pivot falls to
-  // rounding level (<= p u max_j G_jj, u of the precision G was formed in: G singular at working precision) or
-  // the factor is not trustworthy (kappa(R)^2 u > 1, or > 1e-3 for the float Gram), G is refactored with the shift
-  // lambda = 10 p u max_j G_jj, which bounds kappa(X R^{-1}) by about sqrt(lambda) kappa(X). A singular G is
-  // flagged: if the solve then turns out compatible (an exactly rank-deficient X), the host repeats it with plain
-  // LSQR from zero, which returns the minimum-norm solution (Thm. "Solution to OLS problem").
+  // Cholesky G = R^T R on the upper triangle (right-looking), first without a shift, then M = R^{-1}. If a pivot
+  // falls to rounding level (<= p u max_j G_jj, u of the precision G was formed in: G singular at working
+  // precision), G is refactored with the shift lambda = 10 p u max_j G_jj, which bounds kappa(X R^{-1}) by about
+  // sqrt(lambda) kappa(X). A singular G is flagged: if the solve then turns out compatible (an exactly
+  // rank-deficient X), the host repeats it with plain LSQR from zero, which returns the minimum-norm solution
+  // (Thm. "Solution to OLS problem"). kappa(R) = ||X||_2 ||R^{-1}||_2 is estimated by power iteration; a factor
+  // with kappa(R)^2 u > 1/4 still preconditions LSQR (better than a shifted one) but is not trusted for the
+  // semi-normal-equation start, nor for refinement with float products.
   const double ueps = st->mixed ? 5.96e-8 : 1.11e-16;
-  if (want_precond) {
-    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) Mm[q] = G[q];  // keep G for a refactor
+  if (want_precond && !in_smem) {
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) w.Mt[q] = G[q];
     __syncthreads();
   }
   if (threadIdx.x == 0) s_shift = 0;
   __syncthreads();
+  // M = R^{-1} (R upper triangular in G) and kappa(R) = ||X||_2 ||R^{-1}||_2.
+  auto invert_and_estimate = [&]() -> double {
+    // M = R^{-1} from R M = I, right-looking: M starts as I; at step i (from p-1 down) row i is final up to the
+    // factor 1/R_ii, and its contribution R_ri M_ic is removed from every row r < i (a rectangle of i x (p-i)
+    // entries, spread evenly over every warp).
+    for (int q = threadIdx.x; q < p * p; q += kThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = p - 1; i >= 0; --i) {
+      const double inv = 1.0 / G[i * p + i];
+      for (int c = i + threadIdx.x; c < p; c += kThreads) Mm[i * p + c] *= inv;
+      __syncthreads();
+      const int wd = p - i;
+      for (int s2 = threadIdx.x; s2 < i * wd; s2 += kThreads) {
+        const int r = s2 / wd, c = i + (s2 - r * wd);
+        Mm[r * p + c] = fma(-G[r * p + i], Mm[i * p + c], Mm[r * p + c]);
+      }
+      __syncthreads();
+    }
+    // ||R^{-1}||_2^2 = lambda_max(M^T M): power iteration on a float copy of M in the area of R (not needed
+    // any more)
+    {
+      float* Mf = reinterpret_cast<float*>(G);
+      for (int q = threadIdx.x; q < p * p; q += kThreads) Mf[q] = (float)Mm[q];
+      for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = 1.0f;
+      __syncthreads();
+      double lamM = 0.0;
+      for (int it = 0; it < 8; ++it) {
+        for (int i = threadIdx.x; i < p; i += kThreads) {         // ys = M xs (upper triangular rows)
+          float a0 = 0.f, a1 = 0.f;
+          int j = i;
+          for (; j + 1 < p; j += 2) {
+            a0 = fmaf(Mf[i * p + j], xs[j], a0);
+            a1 = fmaf(Mf[i * p + j + 1], xs[j + 1], a1);
+          }
+          if (j < p) a0 = fmaf(Mf[i * p + j], xs[j], a0);
+          ys[i] = a0 + a1;
+        }
+        __syncthreads();
+        double nn = 0.0, dot = 0.0, xx = 0.0;
+        for (int j = threadIdx.x; j < p; j += kThreads) {         // zs = M^T ys (columns)
+          float b0 = 0.f, b1 = 0.f;
+          int i = 0;
+          for (; i + 1 <= j; i += 2) {
+            b0 = fmaf(Mf[i * p + j], ys[i], b0);
+            b1 = fmaf(Mf[(i + 1) * p + j], ys[i + 1], b1);
+          }
+          if (i <= j) b0 = fmaf(Mf[i * p + j], ys[i], b0);
+          const float zj = b0 + b1;
+          zs[j] = zj;
+          nn += (double)zj * zj;
+          dot += (double)xs[j] * zj;
+          xx += (double)xs[j] * xs[j];
+        }
+        sum3(nn, dot, xx);
+        lamM = xx > 0 ? dot / xx : 0.0;
+        const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
+        for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = zs[j] * inv;
+        __syncthreads();
+      }
+      return sqrt(fmax(lam, 0.0)) * sqrt(fmax(lamM, 0.0));
+    }
+  };
+  // Copies of M into the float64 / float matrices the solve reads (M and M^T).
+  auto store = [&]() {
+    for (int i = 0; i < p; ++i)
+      for (int j = threadIdx.x; j < p; j += kThreads) {
+        const double mv = Mm[i * p + j];
+        if (in_smem) w.M[i * p + j] = mv;
+        w.M32[i * p + j] = (float)mv;
+      }
+    for (int j = 0; j < p; ++j)
+      for (int i = threadIdx.x; i < p; i += kThreads) {
+        const double mv = Mm[i * p + j];
+        w.Mt[j * p + i] = mv;
+        w.Mt32[j * p + i] = (float)mv;
+      }
+    __syncthreads();
+  };
+  double cond = 0.0;
   for (int attempt = 0; attempt < 2 && want_precond && !st->no_precond; ++attempt) {
     double lambda = 0.0;
     if (attempt == 1) {
       if (threadIdx.x == 0) s_shift = 1;
       lambda = 10.0 * (double)p * ueps * dmax;
-      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = Mm[q];
+      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = Gsave[q];
       __syncthreads();
       for (int j = threadIdx.x; j < p; j += kThreads) G[(size_t)j * p + j] += lambda;
       if (threadIdx.x == 0) s_fail = 0;
@@ -1035,7 +1233,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     }
     const double tiny = attempt == 0 ? (double)p * ueps * dmax : 1e-3 * lambda;
     // right-looking: every thread reads the pivot itself (no broadcast step), scales row k by the reciprocal,
-    // then updates the trailing upper triangle column by column, four independent updates at a time
+    // then updates the trailing upper triangle
     for (int k = 0; k < p; ++k) {
       const double piv = G[k * p + k];
       if (!(piv > tiny)) {
@@ -1075,68 +1273,35 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
       __syncthreads();
       continue;
     }
-    // kappa(R) >= max R_jj / min R_jj
-    double rmax = 0.0, rmin = 1e300;
-    for (int j = threadIdx.x; j < p; j += kThreads) {
-      rmax = fmax(rmax, G[(size_t)j * p + j]);
-      rmin = fmin(rmin, G[(size_t)j * p + j]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) { scratch[threadIdx.x >> 5] = rmax; scratch[8 + (threadIdx.x >> 5)] = rmin; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 1e300;
-      for (int q = 0; q < kThreads / 32; ++q) { a = fmax(a, scratch[q]); b = fmin(b, scratch[8 + q]); }
-      s_val[1] = b > 0 ? a / b : 1e300;
-    }
-    __syncthreads();
-    const double cond = s_val[1];
-    // unshifted factor trustworthy: a float64 factor still preconditions well while kappa(R)^2 u <= 1; the float
-    // Gram of the mixed path must also let float refinement contract, which needs kappa^2 u32 well below 1
-    if (attempt == 0 && cond * cond * ueps <= (st->mixed ? 1e-3 : 1.0)) break;
+    cond = invert_and_estimate();
+    break;
   }
   const int ok = want_precond && !st->no_precond && !s_fail;
-  if (ok) {
-    // M = R^{-1} from R M = I, right-looking: M starts as I; at step i (from p-1 down) row i is final up to the
-    // factor 1/R_ii, and its contribution R_ri M_ic is removed from every row r < i (a rectangle of i x (p-i)
-    // entries, spread evenly over every warp).
-    for (int q = threadIdx.x; q < p * p; q += kThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int i = p - 1; i >= 0; --i) {
-      const double inv = 1.0 / G[i * p + i];
-      for (int c = i + threadIdx.x; c < p; c += kThreads) Mm[i * p + c] *= inv;
-      __syncthreads();
-      const int wd = p - i;
-      for (int s2 = threadIdx.x; s2 < i * wd; s2 += kThreads) {
-        const int r = s2 / wd, c = i + (s2 - r * wd);
-        Mm[r * p + c] = fma(-G[r * p + i], Mm[i * p + c], Mm[r * p + c]);
-      }
-      __syncthreads();
+  const bool trusted = ok && !s_shift && cond * cond * ueps <= 0.25;
+  if (ok) store();
+  // A float64 solve whose Gram factor is not trusted (or that asks for it): precondition with the R factor of a
+  // Householder QR of rows of X sampled evenly, the row-sampling idea of Section 3.1 put to use as a
+  // preconditioner. R from QR carries errors of order kappa u, not kappa^2 u, so LSQR on X R^{-1} converges in
+  // a few tens of iterations up to kappa(X) ~ 1/u. The Gram factor stays if the sample is rank deficient.
+  bool qr_used = false;
+  if (want_precond && !st->no_precond && !st->mixed && (want_precond == 2 || !trusted) && w.qr &&
+      p <= kQrMaxP && w.m >= (long long)kQrRowsPerP * p) {
+    if (sampled_qr(w, G, qv, qw, qpart, scratch)) {
+      cond = invert_and_estimate();
+      store();
+      qr_used = true;
     }
-    __syncthreads();
-    for (int i = 0; i < p; ++i)
-      for (int j = threadIdx.x; j < p; j += kThreads) {
-        const double mv = Mm[i * p + j];
-        if (in_smem) w.M[i * p + j] = mv;
-        w.M32[i * p + j] = (float)mv;
-      }
-    for (int j = 0; j < p; ++j)
-      for (int i = threadIdx.x; i < p; i += kThreads) {
-        const double mv = Mm[i * p + j];
-        w.Mt[j * p + i] = mv;
-        w.Mt32[j * p + i] = (float)mv;
-      }
-    if (threadIdx.x == 0) {
-      st->precond = 1;
-      st->cond_est = s_val[1];
-      st->shifted = s_shift;
+  }
+  if (threadIdx.x == 0) {
+    if (ok || qr_used) {
+      st->precond = qr_used ? 2 : 1;
+      st->cond_est = cond;
+      st->shifted = qr_used ? 0 : s_shift;
+      st->trusted = qr_used ? 0 : trusted;
+    } else {
+      st->precond = 0;
+      st->cond_est = 0.0;
     }
-  } else {
-    if (threadIdx.x == 0) { st->precond = 0; st->cond_est = 0.0; }
   }
 }
 
@@ -1157,9 +1322,11 @@ static size_t precond_smem(int p_max) {
 static cudaError_t precond_config() {
   static int done = 0;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  // dynamic plus static shared memory must stay within the per-CTA limit: ask for exactly the largest need
+  const int bytes = (int)precond_smem(kPrecondSmemP);
+  cudaError_t e = cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(precond_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    e = cudaFuncSetAttribute(precond_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess) done = 1;
   return e;
 }
@@ -1181,10 +1348,10 @@ cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_
 }
 
 // LSQR start on rhs = b with X^T b = h and ||b|| = bnorm (already in state).
-// A mixed solve whose float Gram matrix needed the shifted factorisation (kappa(R)^2 u32 > 1e-3, or singular)
-// cannot be refined with float products: it is handed back to the float64 path at once.
+// A mixed solve whose float Gram factor is not trusted (kappa(R)^2 u32 > 1/4, shifted or singular) cannot be
+// refined with float products: it is handed back to the float64 path at once.
 __device__ bool mixed_hopeless(DevState* st) {
-  if (!(st->mixed && (st->shifted || st->singular))) return false;
+  if (!(st->mixed && ((st->precond && !st->trusted) || st->singular))) return false;
   if (threadIdx.x == 0) {
     st->mixed_ok = 0;
     st->status = TOLS_NOT_CONVERGED;
@@ -1195,13 +1362,14 @@ __device__ bool mixed_hopeless(DevState* st) {
   return true;
 }
 
-// Start of a solve. Float64 with a trustworthy (unshifted) Cholesky factor: start from the semi-normal-equation solution
+// Start of a solve. Float64 with a trusted (unshifted, kappa(R)^2 u <= 1/4) Cholesky factor: start from the semi-normal-equation solution
 // phi0 = R^{-1} R^{-T} X^T b (O(p^2)) and let a float64 check pass decide whether LSQR on the residual is needed.
 // Otherwise (mixed precision, or no factor): LSQR from zero on b.
 __device__ void start_solve(const Work& w, DevState* st, double* scratch) {
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
-  if (!st->mixed && st->precond && !st->shifted) {
+  if (st->precond == 2 && threadIdx.x == 0) st->iter_cap = min(st->iter_cap, kQrIterCap);
+  if (!st->mixed && st->precond && st->trusted) {
     apply_Mt(w, 1, 0, w.h, w.t);
     __syncthreads();
     apply_M_exact(w, 1, 0, w.t, w.phi);

@@ -158,3 +158,38 @@ def test_ill_conditioned_reaches_the_float64_floor(tols, ctx, prec, p, idx, grad
         assert ne <= max(1e-12, 10 * sol.ne_ratio), (ne, sol.ne_ratio, info)
     assert abs(rn - sol.rnorm) <= 1e-9 * sol.rnorm, (rn, sol.rnorm, info)
     assert info["iters"] <= 64 * (4 * p + 200)
+
+
+@pytest.mark.parametrize("n,p,lo,hi", [(10_000, 10, 1.2, 3.0), (20_000, 57, 1.2, 3.0), (50_000, 200, 2.0, 4.0)])
+def test_sampled_qr_preconditioner(tols, n, p, lo, hi):
+    # TOLS_PRECOND_SAMPLED_QR asked for: R from the QR of 4p evenly sampled rows, LSQR from zero on X R^{-1}
+    s = ar_series(n, p, config_id=71, series_index=p, root_lo=lo, root_hi=hi, max_log10_bound=6.0)
+    sol = oracle.ols_qr(s.y, p)
+    with tols.Context(precision=tols.TOLS_FP64, precond=tols.TOLS_PRECOND_SAMPLED_QR) as c:
+        phi, rnorm, info, rc = tols.toeplitz_ols_solve(c, s.y, p, 1e-12)
+    assert rc == tols.TOLS_OK, info
+    assert info["precond_used"] == tols.TOLS_PRECOND_SAMPLED_QR
+    # kappa(X R^{-1}) is a small constant: LSQR needs a few tens of iterations, not hundreds
+    assert info["iters"] <= 120, info
+    assert_solve_parity(s.y, p, phi, sol, 1e-8)
+
+
+@pytest.mark.parametrize("k", [19, 43])
+def test_ill_conditioned_switches_to_sampled_qr(tols, k):
+    # series of the batched workload (n log-uniform in [1e4, 1e6], p in [5, 200], roots |r| in U[1.2, 3]) with
+    # kappa(X) ~ 1e11 .. 1e12: the Gram factor is not trustworthy (kappa^2 u >> 1), the float64 solve switches to
+    # the sampled-QR preconditioner, and ends near the attainable float64 floor (the oracle's own ratio is
+    # 4e-6 .. 6e-6) within a bounded number of iterations, with a residual norm no larger than the oracle's.
+    from synthetic import batch_shapes
+    bn, bp = batch_shapes(256, config_id=4, n_lo=1e4, n_hi=1e6, p_lo=5, p_hi=200)
+    n, p = int(bn[k]), int(bp[k])
+    s = ar_series(n, p, config_id=4, series_index=k, root_lo=1.2, root_hi=3.0)
+    sol = oracle.ols_qr(s.y, p)
+    with tols.Context(precision=tols.TOLS_FP64) as c:
+        phi, rnorm, info, rc = tols.toeplitz_ols_solve(c, s.y, p, 1e-10)
+    assert rc in (tols.TOLS_OK, tols.TOLS_NOT_CONVERGED)
+    assert info["precond_used"] == tols.TOLS_PRECOND_SAMPLED_QR, info
+    assert info["iters"] <= 300, info
+    rn, _, ne = oracle.residual_check(s.y, p, phi, norm2=sol.norm2)
+    assert rn <= sol.rnorm * (1 + 1e-9), (rn, sol.rnorm, info)
+    assert ne <= 10 * sol.ne_ratio, (ne, sol.ne_ratio, info)

@@ -333,17 +333,22 @@ def run_ours(args, wl):
         return (ms / cnt if cnt else float("nan")), cnt
 
     # dominant kernel of the FP64 step and its roofline (float64 FMA units bound it; see the design notes).
-    # Algorithmic flops per launch: direct products 4 m p (2 m p multiply-adds); overlap-save FFT products
-    # 10 N log2 N per tile (two products, each a forward/inverse real-transform pair of 5 N log2 N).
+    # Flops per launch: direct products 4 m p (2 m p multiply-adds). Overlap-save FFT pass: per tile of
+    # L = N - pad16(p + 1) rows one inverse and one forward real N-point transform, 2 x 2.5 N log2 N (the window
+    # spectra are formed once per solve, the X^T u spectra are summed per CTA and transformed back once).
     dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0 and k.startswith("pass_")),
               key=lambda k: r64["prof"][k][1])
     avg_ms, cnt = per_launch(r64["prof"], dom)
     lags = p + 1 if dom.endswith("gram") else p
     fft_used = r64["infos"][-1]["product_used"] == tols.TOLS_PRODUCT_FFT
-    if fft_used and not dom.endswith("gram"):
+    if fft_used:
         N = 2048
-        L = N - ((lags + 15) // 16) * 16
-        flops = math.ceil(m / L) * 10.0 * N * math.log2(N)
+        pg = ((p + 1 + 15) // 16) * 16
+        tiles = math.ceil(m / (N - pg))
+        if dom.endswith("gram"):    # one forward transform per tile plus the direct edge corrections
+            flops = tiles * (2.5 * N * math.log2(N) + 2.0 * pg * (p + 1))
+        else:
+            flops = tiles * 5.0 * N * math.log2(N)
         kname = f"fft_pass_kernel<double> ({dom})"
     else:
         flops = (2.0 if dom.endswith("gram") else 4.0) * m * lags

@@ -111,24 +111,26 @@ __device__ __forceinline__ void dft_small(V* v, bool inv) {
 }
 
 // One Stockham radix-R stage over M points (in -> out): sub-transforms of length Ls grow to Ls * R.
-// tw: exp(-2 pi i t / (2M)), t < 2M; omega_M^s = tw[2s].
-template <typename V, typename S, int R, int M>
-__device__ __forceinline__ void fft_stage(const V* __restrict__ in, V* __restrict__ out, int Ls,
+// tw: exp(-2 pi i t / (2M)), t < 2M; omega_M^s = tw[2s]. The first stage (Ls = 1) has only unit twiddles.
+template <typename V, typename S, int R, int M, int Ls>
+__device__ __forceinline__ void fft_stage(const V* __restrict__ in, V* __restrict__ out,
                                           const V* __restrict__ tw, bool inv) {
   constexpr int stride = M / R;
-  const int Ln = Ls * R;
-  const int tstep = 2 * (M / Ln);
+  constexpr int Ln = Ls * R;
+  constexpr int tstep = 2 * (M / Ln);
   for (int j = threadIdx.x; j < stride; j += kThreads) {
     const int k = j & (Ls - 1);
     const int g = j / Ls;
     V v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[pix(j + r * stride)];
+    if (Ls > 1) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      V t = tw[r * k * tstep];
-      if (inv) t.y = -t.y;
-      v[r] = cmul(v[r], t);
+      for (int r = 1; r < R; ++r) {
+        V t = tw[r * k * tstep];
+        if (inv) t.y = -t.y;
+        v[r] = cmul(v[r], t);
+      }
     }
     dft_small<V, S, R>(v, inv);
 #pragma unroll
@@ -141,11 +143,11 @@ __device__ __forceinline__ void fft_stage(const V* __restrict__ in, V* __restric
 template <typename V, typename S, int M>
 __device__ void fft_complex(V* a, V* b, const V* tw, bool inv) {
   static_assert(M == 2048 || M == 1024, "plans for M = 2048 (8,8,8,4) and M = 1024 (8,8,8,2)");
-  fft_stage<V, S, 8, M>(a, b, 1, tw, inv);
-  fft_stage<V, S, 8, M>(b, a, 8, tw, inv);
-  fft_stage<V, S, 8, M>(a, b, 64, tw, inv);
-  if (M == 2048) fft_stage<V, S, 4, M>(b, a, 512, tw, inv);
-  else fft_stage<V, S, 2, M>(b, a, 512, tw, inv);
+  fft_stage<V, S, 8, M, 1>(a, b, tw, inv);
+  fft_stage<V, S, 8, M, 8>(b, a, tw, inv);
+  fft_stage<V, S, 8, M, 64>(a, b, tw, inv);
+  if (M == 2048) fft_stage<V, S, 4, M, 512>(b, a, tw, inv);
+  else fft_stage<V, S, 2, M, 512>(b, a, tw, inv);
 }
 
 // Split of the packed complex transform Z of a real sequence into its doubled half spectrum, two bins at a time:

@@ -103,6 +103,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum over the 256 threads of a CTA; every thread gets the result. scratch: >= 8 doubles of shared memory.
+template <int NT = kThreads>
 __device__ double block_sum(double v, double* scratch) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -111,7 +112,7 @@ __device__ double block_sum(double v, double* scratch) {
   __syncthreads();
   double r = 0.0;
 #pragma unroll
-  for (int k = 0; k < kThreads / 32; ++k) r += scratch[k];
+  for (int k = 0; k < NT / 32; ++k) r += scratch[k];
   __syncthreads();
   return r;
 }
@@ -948,30 +949,34 @@ constexpr int kPrecondSmemP = 112;
 // evenly spaced (row i_k = floor((k + 1/2) m / c)), gathered into w.qr (c x p, row-major), then Householder QR
 // in float64. R (upper triangular, p x p, row-major) is written to R. Returns false when a column of the sample
 // is (numerically) dependent on the others, i.e. R would be singular.
+// The preconditioner runs one CTA per series; 16 warps (4 per SM sub-partition) hide the latency of its chains of
+// dependent shared-memory and FP64 operations better than 8.
+constexpr int kPcThreads = 512;
+
 __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, double* qpart, double* scratch) {
   const int p = w.p;
   const long long m = w.m;
   const int c = kQrRowsPerP * p;
   double* A = w.qr;
   const double* y = w.y64;
-  for (long long q = threadIdx.x; q < (long long)c * p; q += kThreads) {
+  for (long long q = threadIdx.x; q < (long long)c * p; q += kPcThreads) {
     const int i = (int)(q / p), j = (int)(q - (long long)i * p);
     const long long row = ((2LL * i + 1) * m) / (2LL * c);
     A[q] = y[p + row - j - 1];
   }
-  for (long long q = threadIdx.x; q < (long long)p * p; q += kThreads) R[q] = 0.0;
+  for (long long q = threadIdx.x; q < (long long)p * p; q += kPcThreads) R[q] = 0.0;
   __syncthreads();
   double amax = 0.0;   // largest |R_kk| so far, for the rank test
   bool full_rank = true;
   for (int k = 0; k < p; ++k) {
     // Householder vector of column k below the diagonal: v = x - alpha e_k, alpha = -sign(x_k) ||x||
     double s = 0.0;
-    for (int i = k + threadIdx.x; i < c; i += kThreads) {
+    for (int i = k + threadIdx.x; i < c; i += kPcThreads) {
       const double a = A[(size_t)i * p + k];
       qv[i] = a;
       s = fma(a, a, s);
     }
-    s = block_sum(s, scratch);                      // synchronises: qv complete
+    s = block_sum<kPcThreads>(s, scratch);                      // synchronises: qv complete
     const double x0 = qv[k];
     const double nrm = sqrt(s);
     const double alpha = x0 >= 0.0 ? -nrm : nrm;
@@ -986,8 +991,8 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       if (threadIdx.x == 0) qv[k] = vk;
       __syncthreads();
       // qw_j = beta sum_{i >= k} v_i A[i][j] for the trailing columns: (column, row-slice) pairs over the CTA
-      const int nsplit = max(1, min(kThreads / ncol, c - k));
-      for (int t = threadIdx.x; t < ncol * nsplit; t += kThreads) {
+      const int nsplit = max(1, min(kPcThreads / ncol, c - k));
+      for (int t = threadIdx.x; t < ncol * nsplit; t += kPcThreads) {
         const int jj = t % ncol, r0 = t / ncol;
         const int j = k + 1 + jj;
         double acc = 0.0;
@@ -995,7 +1000,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
         qpart[t] = acc;
       }
       __syncthreads();
-      for (int jj = threadIdx.x; jj < ncol; jj += kThreads) {
+      for (int jj = threadIdx.x; jj < ncol; jj += kPcThreads) {
         double acc = 0.0;
         for (int r0 = 0; r0 < nsplit; ++r0) acc += qpart[r0 * ncol + jj];
         qw[jj] = beta * acc;
@@ -1003,7 +1008,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       __syncthreads();
       // A[i][j] -= v_i qw_j over the trailing block
       const long long tot = (long long)(c - k) * ncol;
-      for (long long q = threadIdx.x; q < tot; q += kThreads) {
+      for (long long q = threadIdx.x; q < tot; q += kPcThreads) {
         const int i = k + (int)(q / ncol), jj = (int)(q - (long long)(q / ncol) * ncol);
         const size_t idx = (size_t)i * p + (k + 1 + jj);
         A[idx] = fma(-qv[i], qw[jj], A[idx]);
@@ -1011,7 +1016,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       __syncthreads();
     }
     // row k of R: alpha on the diagonal, the transformed row k beyond it
-    for (int j = k + threadIdx.x; j < p; j += kThreads) R[(size_t)k * p + j] = j == k ? alpha : A[(size_t)k * p + j];
+    for (int j = k + threadIdx.x; j < p; j += kPcThreads) R[(size_t)k * p + j] = j == k ? alpha : A[(size_t)k * p + j];
     __syncthreads();
   }
   return full_rank;
@@ -1025,8 +1030,8 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   __shared__ int s_shift;
   __shared__ double s_val[2];
   __shared__ float xs[TOLS_MAX_P], ys[TOLS_MAX_P], zs[TOLS_MAX_P];
-  __shared__ double red3[3 * (kThreads / 32)];
-  __shared__ double qv[kQrRowsPerP * kQrMaxP], qw[kQrMaxP], qpart[kThreads];
+  __shared__ float red2[2 * (kPcThreads / 32)];
+  __shared__ double qv[kQrRowsPerP * kQrMaxP], qw[kQrMaxP], qpart[kPcThreads];
   const bool in_smem = smem && p <= kPrecondSmemP;
   double* G = in_smem ? smem : w.G;
   double* Mm = in_smem ? smem + (size_t)p * p : w.M;
@@ -1034,16 +1039,17 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   // (written only at the end)
   const double* Gsave = in_smem ? w.G : w.Mt;
   if (in_smem) {
-    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = w.G[q];
+#pragma unroll 4
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) G[q] = w.G[q];
     __syncthreads();
   }
   // ||X||_F^2 = trace(G)
   double tr = 0.0, dmax = 0.0;
-  for (int j = threadIdx.x; j < p; j += kThreads) {
+  for (int j = threadIdx.x; j < p; j += kPcThreads) {
     tr += G[(size_t)j * p + j];
     dmax = fmax(dmax, G[(size_t)j * p + j]);
   }
-  tr = block_sum(tr, scratch);
+  tr = block_sum<kPcThreads>(tr, scratch);
   // block max of the diagonal
   {
     double v = dmax;
@@ -1052,42 +1058,53 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double r = 0.0;
-      for (int k = 0; k < kThreads / 32; ++k) r = fmax(r, scratch[k]);
+      for (int k = 0; k < kPcThreads / 32; ++k) r = fmax(r, scratch[k]);
       s_val[0] = r;
     }
     __syncthreads();
     dmax = s_val[0];
     __syncthreads();
   }
-  // Sums over the CTA of three per-thread values (into nn, dot, xx; every thread gets them).
-  auto sum3 = [&](double& nn, double& dot, double& xx) {
-    nn = warp_sum(nn);
-    dot = warp_sum(dot);
-    xx = warp_sum(xx);
+  // Sums over the CTA of two per-thread float values (every thread gets them).
+  auto sum2 = [&](float& dot, float& xx) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
     if ((threadIdx.x & 31) == 0) {
-      red3[threadIdx.x >> 5] = nn;
-      red3[(kThreads / 32) + (threadIdx.x >> 5)] = dot;
-      red3[2 * (kThreads / 32) + (threadIdx.x >> 5)] = xx;
+      red2[threadIdx.x >> 5] = dot;
+      red2[(kPcThreads / 32) + (threadIdx.x >> 5)] = xx;
     }
     __syncthreads();
-    nn = dot = xx = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) {
-      nn += red3[q];
-      dot += red3[(kThreads / 32) + q];
-      xx += red3[2 * (kThreads / 32) + q];
+    dot = xx = 0.f;
+    for (int q = 0; q < kPcThreads / 32; ++q) {
+      dot += red2[q];
+      xx += red2[(kPcThreads / 32) + q];
     }
   };
   // power iteration for lambda_max = ||X||_2^2 on a float copy of G (two digits suffice for the ratio's norm);
-  // the copy lives in the M area, which is free until the inverse
+  // the copy lives in the M area, which is free until the factorisation
   double lam = 0.0;
   {
     float* Gf = reinterpret_cast<float*>(Mm);
-    for (int q = threadIdx.x; q < p * p; q += kThreads) Gf[q] = (float)G[q];
-    for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = 1.0f;
+    // G is symmetric: convert its upper triangle and mirror it (float64 -> float conversions use the FP64 pipe)
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
+      const int i = q / p, j = q - i * p;
+      if (i <= j) {
+        const float g = (float)G[q];
+        Gf[q] = g;
+        Gf[j * p + i] = g;
+      }
+    }
+    for (int j = threadIdx.x; j < p; j += kPcThreads) xs[j] = 1.0f;
     __syncthreads();
-    for (int it = 0; it < 12; ++it) {
-      double nn = 0.0, dot = 0.0, xx = 0.0;
-      for (int i = threadIdx.x; i < p; i += kThreads) {
+    // float arithmetic throughout (FP64 instructions, divisions above all, are expensive here); the next
+    // iterate is y scaled by xx / dot, the inverse Rayleigh quotient, which keeps its norm near the first one's
+    float dot = 0.f, xx = 0.f;
+    for (int it = 0; it < 8; ++it) {
+      dot = 0.f;
+      xx = 0.f;
+      for (int i = threadIdx.x; i < p; i += kPcThreads) {      // ys = G xs (column i of the symmetric G)
         float a0 = 0.f, a1 = 0.f;
         int j = 0;
         for (; j + 1 < p; j += 2) {
@@ -1097,16 +1114,15 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
         if (j < p) a0 = fmaf(Gf[j * p + i], xs[j], a0);
         const float yi = a0 + a1;
         ys[i] = yi;
-        nn += (double)yi * yi;
-        dot += (double)xs[i] * yi;
-        xx += (double)xs[i] * xs[i];
+        dot = fmaf(xs[i], yi, dot);
+        xx = fmaf(xs[i], xs[i], xx);
       }
-      sum3(nn, dot, xx);
-      lam = xx > 0 ? dot / xx : 0.0;
-      const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
-      for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = ys[j] * inv;
+      sum2(dot, xx);
+      const float scale = dot > 0.f ? xx / dot : 0.f;
+      for (int j = threadIdx.x; j < p; j += kPcThreads) xs[j] = ys[j] * scale;
       __syncthreads();
     }
+    lam = xx > 0.f ? (double)dot / (double)xx : 0.0;
   }
   if (!isfinite(tr) || !isfinite(*w.bnorm2)) {
     if (threadIdx.x == 0) {
@@ -1136,87 +1152,96 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   // semi-normal-equation start, nor for refinement with float products.
   const double ueps = st->mixed ? 5.96e-8 : 1.11e-16;
   if (want_precond && !in_smem) {
-    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) w.Mt[q] = G[q];
+    for (size_t q = threadIdx.x; q < (size_t)p * p; q += kPcThreads) w.Mt[q] = G[q];
     __syncthreads();
   }
   if (threadIdx.x == 0) s_shift = 0;
   __syncthreads();
-  // M = R^{-1} (R upper triangular in G) and kappa(R) = ||X||_2 ||R^{-1}||_2.
+  // ||R^{-1}||_2^2 = lambda_max(M^T M) (M in Mm): power iteration on a float copy of M's upper triangle in the
+  // area of R (not needed any more), rows padded to p + 1 entries so that both row and column walks are free of
+  // bank conflicts; returns kappa(R) = ||X||_2 ||R^{-1}||_2.
+  auto estimate = [&]() -> double {
+    float* Mf = reinterpret_cast<float*>(G);
+    const int ld = p + 1;
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
+      const int i = q / p, j = q - i * p;
+      if (i <= j) Mf[i * ld + j] = (float)Mm[q];
+    }
+    for (int j = threadIdx.x; j < p; j += kPcThreads) xs[j] = 1.0f;
+    __syncthreads();
+    float dot = 0.f, xx = 0.f;
+    for (int it = 0; it < 6; ++it) {
+      for (int i = threadIdx.x; i < p; i += kPcThreads) {        // ys = M xs (rows)
+        float a0 = 0.f, a1 = 0.f;
+        int j = i;
+        for (; j + 1 < p; j += 2) {
+          a0 = fmaf(Mf[i * ld + j], xs[j], a0);
+          a1 = fmaf(Mf[i * ld + j + 1], xs[j + 1], a1);
+        }
+        if (j < p) a0 = fmaf(Mf[i * ld + j], xs[j], a0);
+        ys[i] = a0 + a1;
+      }
+      __syncthreads();
+      dot = 0.f;
+      xx = 0.f;
+      for (int j = threadIdx.x; j < p; j += kPcThreads) {        // zs = M^T ys (columns)
+        float b0 = 0.f, b1 = 0.f;
+        int i = 0;
+        for (; i + 1 <= j; i += 2) {
+          b0 = fmaf(Mf[i * ld + j], ys[i], b0);
+          b1 = fmaf(Mf[(i + 1) * ld + j], ys[i + 1], b1);
+        }
+        if (i <= j) b0 = fmaf(Mf[i * ld + j], ys[i], b0);
+        const float zj = b0 + b1;
+        zs[j] = zj;
+        dot = fmaf(xs[j], zj, dot);
+        xx = fmaf(xs[j], xs[j], xx);
+      }
+      sum2(dot, xx);
+      const float scale = dot > 0.f ? xx / dot : 0.f;
+      for (int j = threadIdx.x; j < p; j += kPcThreads) xs[j] = zs[j] * scale;
+      __syncthreads();
+    }
+    const double lamM = xx > 0.f ? (double)dot / (double)xx : 0.0;
+    return sqrt(fmax(lam, 0.0)) * sqrt(fmax(lamM, 0.0));
+  };
+  // M = R^{-1} (R upper triangular in G), then kappa(R) = ||X||_2 ||R^{-1}||_2.
   auto invert_and_estimate = [&]() -> double {
     // M = R^{-1} from R M = I, right-looking: M starts as I; at step i (from p-1 down) row i is final up to the
     // factor 1/R_ii, and its contribution R_ri M_ic is removed from every row r < i (a rectangle of i x (p-i)
     // entries, spread evenly over every warp).
-    for (int q = threadIdx.x; q < p * p; q += kThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
+    // (used after the sampled QR, p <= kQrMaxP: the reciprocals of the diagonal go to qw, one division each)
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
+    for (int j = threadIdx.x; j < p; j += kPcThreads) qw[j] = 1.0 / G[j * p + j];
     __syncthreads();
     for (int i = p - 1; i >= 0; --i) {
-      const double inv = 1.0 / G[i * p + i];
-      for (int c = i + threadIdx.x; c < p; c += kThreads) Mm[i * p + c] *= inv;
+      const double inv = qw[i];
+      for (int c = i + threadIdx.x; c < p; c += kPcThreads) Mm[i * p + c] *= inv;
       __syncthreads();
       const int wd = p - i;
-      for (int s2 = threadIdx.x; s2 < i * wd; s2 += kThreads) {
+      for (int s2 = threadIdx.x; s2 < i * wd; s2 += kPcThreads) {
         const int r = s2 / wd, c = i + (s2 - r * wd);
         Mm[r * p + c] = fma(-G[r * p + i], Mm[i * p + c], Mm[r * p + c]);
       }
       __syncthreads();
     }
-    // ||R^{-1}||_2^2 = lambda_max(M^T M): power iteration on a float copy of M in the area of R (not needed
-    // any more)
-    {
-      float* Mf = reinterpret_cast<float*>(G);
-      for (int q = threadIdx.x; q < p * p; q += kThreads) Mf[q] = (float)Mm[q];
-      for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = 1.0f;
-      __syncthreads();
-      double lamM = 0.0;
-      for (int it = 0; it < 8; ++it) {
-        for (int i = threadIdx.x; i < p; i += kThreads) {         // ys = M xs (upper triangular rows)
-          float a0 = 0.f, a1 = 0.f;
-          int j = i;
-          for (; j + 1 < p; j += 2) {
-            a0 = fmaf(Mf[i * p + j], xs[j], a0);
-            a1 = fmaf(Mf[i * p + j + 1], xs[j + 1], a1);
-          }
-          if (j < p) a0 = fmaf(Mf[i * p + j], xs[j], a0);
-          ys[i] = a0 + a1;
-        }
-        __syncthreads();
-        double nn = 0.0, dot = 0.0, xx = 0.0;
-        for (int j = threadIdx.x; j < p; j += kThreads) {         // zs = M^T ys (columns)
-          float b0 = 0.f, b1 = 0.f;
-          int i = 0;
-          for (; i + 1 <= j; i += 2) {
-            b0 = fmaf(Mf[i * p + j], ys[i], b0);
-            b1 = fmaf(Mf[(i + 1) * p + j], ys[i + 1], b1);
-          }
-          if (i <= j) b0 = fmaf(Mf[i * p + j], ys[i], b0);
-          const float zj = b0 + b1;
-          zs[j] = zj;
-          nn += (double)zj * zj;
-          dot += (double)xs[j] * zj;
-          xx += (double)xs[j] * xs[j];
-        }
-        sum3(nn, dot, xx);
-        lamM = xx > 0 ? dot / xx : 0.0;
-        const float inv = nn > 0 ? (float)(1.0 / sqrt(nn)) : 0.f;
-        for (int j = threadIdx.x; j < p; j += kThreads) xs[j] = zs[j] * inv;
-        __syncthreads();
-      }
-      return sqrt(fmax(lam, 0.0)) * sqrt(fmax(lamM, 0.0));
-    }
+    return estimate();
   };
   // Copies of M into the float64 / float matrices the solve reads (M and M^T).
+  // The float copies serve only the mixed path.
   auto store = [&]() {
-    for (int i = 0; i < p; ++i)
-      for (int j = threadIdx.x; j < p; j += kThreads) {
-        const double mv = Mm[i * p + j];
-        if (in_smem) w.M[i * p + j] = mv;
-        w.M32[i * p + j] = (float)mv;
+    const bool mixed = st->mixed;
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
+      const int i = q / p, j = q - i * p;
+      const double mv = Mm[q];                  // M[i][j]
+      const double tv = Mm[j * p + i];          // M[j][i] = M^T[i][j]
+      if (in_smem) w.M[q] = mv;
+      w.Mt[q] = tv;
+      if (mixed) {
+        w.M32[q] = (float)mv;
+        w.Mt32[q] = (float)tv;
       }
-    for (int j = 0; j < p; ++j)
-      for (int i = threadIdx.x; i < p; i += kThreads) {
-        const double mv = Mm[i * p + j];
-        w.Mt[j * p + i] = mv;
-        w.Mt32[j * p + i] = (float)mv;
-      }
+    }
     __syncthreads();
   };
   double cond = 0.0;
@@ -1225,24 +1250,38 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     if (attempt == 1) {
       if (threadIdx.x == 0) s_shift = 1;
       lambda = 10.0 * (double)p * ueps * dmax;
-      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kThreads) G[q] = Gsave[q];
+      for (size_t q = threadIdx.x; q < (size_t)p * p; q += kPcThreads) G[q] = Gsave[q];
       __syncthreads();
-      for (int j = threadIdx.x; j < p; j += kThreads) G[(size_t)j * p + j] += lambda;
+      for (int j = threadIdx.x; j < p; j += kPcThreads) G[(size_t)j * p + j] += lambda;
       if (threadIdx.x == 0) s_fail = 0;
       __syncthreads();
     }
     const double tiny = attempt == 0 ? (double)p * ueps * dmax : 1e-3 * lambda;
     // right-looking: every thread reads the pivot itself (no broadcast step), scales row k by the reciprocal,
-    // then updates the trailing upper triangle
-    for (int k = 0; k < p; ++k) {
-      const double piv = G[k * p + k];
+    // then updates the trailing upper triangle. The same elimination applied to B = I (rows scaled by 1/R_kk,
+    // row k subtracted R_ki times from every row i > k) leaves B = L^{-1} = (R^{-1})^T, lower triangular, in Mm:
+    // the inverse comes out of the same p steps instead of p more.
+    double* B = Mm;
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) B[q] = (q / p == q % p) ? 1.0 : 0.0;
+    // Thread 0 forms each pivot's square root and reciprocal once, one step ahead (it also owns the update of
+    // the next diagonal entry): float64 square roots and divisions are long instruction sequences on the FP64
+    // pipe, which every warp would otherwise repeat.
+    if (threadIdx.x == 0) {
+      const double piv = G[0];
       if (!(piv > tiny)) {
-        if (threadIdx.x == 0) s_fail = 1;
-        break;
+        s_fail = 1;
+      } else {
+        s_val[0] = sqrt(piv);
+        s_val[1] = 1.0 / s_val[0];
       }
-      const double rkk = sqrt(piv);
-      const double inv = 1.0 / rkk;
-      for (int j = k + 1 + threadIdx.x; j < p; j += kThreads) G[k * p + j] *= inv;
+    }
+    __syncthreads();
+    for (int k = 0; k < p; ++k) {
+      if (s_fail) break;
+      const double rkk = s_val[0];
+      const double inv = s_val[1];
+      for (int j = k + 1 + threadIdx.x; j < p; j += kPcThreads) G[k * p + j] *= inv;
+      for (int c = threadIdx.x; c <= k; c += kPcThreads) B[k * p + c] *= inv;
       __syncthreads();
       if (threadIdx.x == 0) G[k * p + k] = rkk;
       // trailing update G[i][j] -= r_i r_j over k < i <= j < p, spread evenly over every warp: the triangle of
@@ -1250,7 +1289,20 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
       const double* __restrict__ rowk = G + k * p;
       const int wd = p - k - 1;
       const int half = (wd + 1) >> 1;
-      for (int s2 = threadIdx.x; s2 < half * (wd + 1); s2 += kThreads) {
+      // entry (k+1, k+1), the next pivot, is thread 0's (s2 = 0 of the fold)
+      if (threadIdx.x == 0 && wd > 0) {
+        const int d = (k + 1) * p + (k + 1);
+        const double piv = fma(-rowk[k + 1], rowk[k + 1], G[d]);
+        G[d] = piv;
+        if (!(piv > tiny)) {
+          s_fail = 1;
+        } else {
+          s_val[0] = sqrt(piv);
+          s_val[1] = 1.0 / s_val[0];
+        }
+      }
+      for (int s2 = threadIdx.x; s2 < half * (wd + 1); s2 += kPcThreads) {
+        if (s2 == 0) continue;
         const int a = s2 / (wd + 1), b = s2 - a * (wd + 1);
         int r, c;
         if (b < wd - a) {
@@ -1264,6 +1316,13 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
         const int i = k + 1 + r, j = k + 1 + c;
         G[i * p + j] = fma(-rowk[i], rowk[j], G[i * p + j]);
       }
+      // B[i][c] -= R_ki B[k][c] over the rectangle k < i < p, c <= k
+      const int kc = k + 1;
+      for (int s2 = threadIdx.x; s2 < wd * kc; s2 += kPcThreads) {
+        const int r = s2 / kc, c = s2 - r * kc;
+        const int i = k + 1 + r;
+        B[i * p + c] = fma(-rowk[i], B[k * p + c], B[i * p + c]);
+      }
       __syncthreads();
     }
     __syncthreads();
@@ -1273,7 +1332,16 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
       __syncthreads();
       continue;
     }
-    cond = invert_and_estimate();
+    // M = B^T, in place (Mm then holds M = R^{-1}, upper triangular)
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
+      const int i = q / p, j = q - i * p;
+      if (i < j) {
+        Mm[i * p + j] = Mm[j * p + i];
+        Mm[j * p + i] = 0.0;
+      }
+    }
+    __syncthreads();
+    cond = estimate();
     break;
   }
   const int ok = want_precond && !st->no_precond && !s_fail;
@@ -1305,11 +1373,11 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) precond_kernel(Work w, int want_precond, int use_smem) {
+__global__ void __launch_bounds__(kPcThreads, 1) precond_kernel(Work w, int want_precond, int use_smem) {
   extern __shared__ double psm[];
   precond_body(w, want_precond, use_smem ? psm : nullptr);
 }
-__global__ void __launch_bounds__(kThreads) precond_batch_kernel(const BatchSeries* series, int want_precond,
+__global__ void __launch_bounds__(kPcThreads, 1) precond_batch_kernel(const BatchSeries* series, int want_precond,
                                                                  int use_smem) {
   extern __shared__ double psm[];
   precond_body(series[blockIdx.x].w, want_precond, use_smem ? psm : nullptr);
@@ -1335,7 +1403,7 @@ cudaError_t launch_precond(Work w, int want_precond, cudaStream_t s) {
   cudaError_t e = precond_config();
   if (e != cudaSuccess) return e;
   const int use = w.p <= kPrecondSmemP;
-  precond_kernel<<<1, kThreads, use ? precond_smem(w.p) : 0, s>>>(w, want_precond, use);
+  precond_kernel<<<1, kPcThreads, use ? precond_smem(w.p) : 0, s>>>(w, want_precond, use);
   return cudaGetLastError();
 }
 // Batched: series with p <= kPrecondSmemP work in shared memory sized for the largest such p in the batch.
@@ -1343,7 +1411,7 @@ cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_
                                  int p_max) {
   cudaError_t e = precond_config();
   if (e != cudaSuccess) return e;
-  precond_batch_kernel<<<count, kThreads, precond_smem(p_max), s>>>(series, want_precond, 1);
+  precond_batch_kernel<<<count, kPcThreads, precond_smem(p_max), s>>>(series, want_precond, 1);
   return cudaGetLastError();
 }
 

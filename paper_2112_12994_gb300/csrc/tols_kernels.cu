@@ -949,6 +949,32 @@ constexpr int kPrecondSmemP = 112;
 // evenly spaced (row i_k = floor((k + 1/2) m / c)), gathered into w.qr (c x p, row-major), then Householder QR
 // in float64. R (upper triangular, p x p, row-major) is written to R. Returns false when a column of the sample
 // is (numerically) dependent on the others, i.e. R would be singular.
+// 1/sqrt(x) for x > 0 in float64 by Newton-Raphson for f(r) = 1/r^2 - x (r <- r (3 - x r^2) / 2), started from
+// the float reciprocal square root: two steps take the 24-bit start to full float64 accuracy (quadratic
+// convergence). A short chain of FP64 operations, where sqrt followed by a division is a long one.
+// x is first scaled by an even power of two into [1, 4) (exponent arithmetic on the bits), so the float start
+// never overflows or underflows.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return 1.0 / sqrt(x);         // zero, subnormal, inf, nan: the plain way
+  const int kk = (ef - 1023) >> 1;                           // x = xs 4^kk, xs in [1, 4)
+  const double xs = __longlong_as_double(bits - ((long long)(2 * kk) << 52));
+  double r = (double)rsqrtf((float)xs);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)kk << 52));   // r 2^-kk
+}
+
+// s / d by multiplication with magic = ceil(2^32 / d) = (2^32 - 1) / d + 1 (division by an invariant integer,
+// Granlund & Montgomery 1994): exact while s d < 2^32, integer instructions only (the general division
+// sequence goes through float conversions, which are slow here).
+// d = 1 has no 32-bit magic (2^32): its magic is 0 and small_div returns s itself.
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return d > 1u ? 0xffffffffu / d + 1u : 0u; }
+__device__ __forceinline__ int small_div(int s, unsigned magic) {
+  return magic ? (int)__umulhi((unsigned)s, magic) : s;
+}
+
 // The preconditioner runs one CTA per series; 16 warps (4 per SM sub-partition) hide the latency of its chains of
 // dependent shared-memory and FP64 operations better than 8.
 constexpr int kPcThreads = 512;
@@ -959,12 +985,13 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
   const int c = kQrRowsPerP * p;
   double* A = w.qr;
   const double* y = w.y64;
-  for (long long q = threadIdx.x; q < (long long)c * p; q += kPcThreads) {
-    const int i = (int)(q / p), j = (int)(q - (long long)i * p);
+  // gather: one row per warp at a time, its lanes along the row (one 64-bit division per row, not per entry)
+  for (int i = threadIdx.x >> 5; i < c; i += kPcThreads / 32) {
     const long long row = ((2LL * i + 1) * m) / (2LL * c);
-    A[q] = y[p + row - j - 1];
+    const double* yr = y + p + row - 1;              // X[row][j] = y[p + row - j - 1]
+    for (int j = threadIdx.x & 31; j < p; j += 32) A[(size_t)i * p + j] = yr[-j];
   }
-  for (long long q = threadIdx.x; q < (long long)p * p; q += kPcThreads) R[q] = 0.0;
+  for (int q = threadIdx.x; q < p * p; q += kPcThreads) R[q] = 0.0;
   __syncthreads();
   double amax = 0.0;   // largest |R_kk| so far, for the rank test
   bool full_rank = true;
@@ -993,7 +1020,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       // qw_j = beta sum_{i >= k} v_i A[i][j] for the trailing columns: (column, row-slice) pairs over the CTA
       const int nsplit = max(1, min(kPcThreads / ncol, c - k));
       for (int t = threadIdx.x; t < ncol * nsplit; t += kPcThreads) {
-        const int jj = t % ncol, r0 = t / ncol;
+        const int r0 = t / ncol, jj = t - r0 * ncol;      // t < kPcThreads: one division per thread
         const int j = k + 1 + jj;
         double acc = 0.0;
         for (int i = k + r0; i < c; i += nsplit) acc = fma(qv[i], A[(size_t)i * p + j], acc);
@@ -1006,12 +1033,13 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
         qw[jj] = beta * acc;
       }
       __syncthreads();
-      // A[i][j] -= v_i qw_j over the trailing block
-      const long long tot = (long long)(c - k) * ncol;
-      for (long long q = threadIdx.x; q < tot; q += kPcThreads) {
-        const int i = k + (int)(q / ncol), jj = (int)(q - (long long)(q / ncol) * ncol);
-        const size_t idx = (size_t)i * p + (k + 1 + jj);
-        A[idx] = fma(-qv[i], qw[jj], A[idx]);
+      // A[i][j] -= v_i qw_j over the trailing block ((c - k) ncol < 4 p^2 entries: q ncol < 2^32)
+      const int tot = (c - k) * ncol;
+      const unsigned nmag = div_magic((unsigned)ncol);
+      for (int q = threadIdx.x; q < tot; q += kPcThreads) {
+        const int r = small_div(q, nmag), jj = q - r * ncol;
+        const size_t idx = (size_t)(k + r) * p + (k + 1 + jj);
+        A[idx] = fma(-qv[k + r], qw[jj], A[idx]);
       }
       __syncthreads();
     }
@@ -1024,6 +1052,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
 
 __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   const int p = w.p;
+  const unsigned pmag = div_magic((unsigned)p);   // q / p for q < p^2 (q p < 2^32 for p <= 1024)
   DevState* st = w.st;
   __shared__ double scratch[16];
   __shared__ int s_fail;
@@ -1031,6 +1060,8 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   __shared__ double s_val[2];
   __shared__ float xs[TOLS_MAX_P], ys[TOLS_MAX_P], zs[TOLS_MAX_P];
   __shared__ float red2[2 * (kPcThreads / 32)];
+  __shared__ unsigned s_mag[TOLS_MAX_P + 2];       // div_magic(d), d = 0 .. p + 1, formed once (a division each)
+  for (int d = threadIdx.x; d <= p + 1; d += kPcThreads) s_mag[d] = d > 0 ? div_magic((unsigned)d) : 0u;
   __shared__ double qv[kQrRowsPerP * kQrMaxP], qw[kQrMaxP], qpart[kPcThreads];
   const bool in_smem = smem && p <= kPrecondSmemP;
   double* G = in_smem ? smem : w.G;
@@ -1089,7 +1120,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     float* Gf = reinterpret_cast<float*>(Mm);
     // G is symmetric: convert its upper triangle and mirror it (float64 -> float conversions use the FP64 pipe)
     for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
-      const int i = q / p, j = q - i * p;
+      const int i = small_div(q, pmag), j = q - i * p;
       if (i <= j) {
         const float g = (float)G[q];
         Gf[q] = g;
@@ -1164,7 +1195,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     float* Mf = reinterpret_cast<float*>(G);
     const int ld = p + 1;
     for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
-      const int i = q / p, j = q - i * p;
+      const int i = small_div(q, pmag), j = q - i * p;
       if (i <= j) Mf[i * ld + j] = (float)Mm[q];
     }
     for (int j = threadIdx.x; j < p; j += kPcThreads) xs[j] = 1.0f;
@@ -1211,7 +1242,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     // factor 1/R_ii, and its contribution R_ri M_ic is removed from every row r < i (a rectangle of i x (p-i)
     // entries, spread evenly over every warp).
     // (used after the sampled QR, p <= kQrMaxP: the reciprocals of the diagonal go to qw, one division each)
-    for (int q = threadIdx.x; q < p * p; q += kPcThreads) Mm[q] = (q / p == q % p) ? 1.0 : 0.0;
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) Mm[q] = (q == small_div(q, pmag) * (p + 1)) ? 1.0 : 0.0;
     for (int j = threadIdx.x; j < p; j += kPcThreads) qw[j] = 1.0 / G[j * p + j];
     __syncthreads();
     for (int i = p - 1; i >= 0; --i) {
@@ -1219,8 +1250,9 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
       for (int c = i + threadIdx.x; c < p; c += kPcThreads) Mm[i * p + c] *= inv;
       __syncthreads();
       const int wd = p - i;
+      const unsigned wmag = div_magic((unsigned)wd);
       for (int s2 = threadIdx.x; s2 < i * wd; s2 += kPcThreads) {
-        const int r = s2 / wd, c = i + (s2 - r * wd);
+        const int r = small_div(s2, wmag), c = i + (s2 - r * wd);
         Mm[r * p + c] = fma(-G[r * p + i], Mm[i * p + c], Mm[r * p + c]);
       }
       __syncthreads();
@@ -1232,7 +1264,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   auto store = [&]() {
     const bool mixed = st->mixed;
     for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
-      const int i = q / p, j = q - i * p;
+      const int i = small_div(q, pmag), j = q - i * p;
       const double mv = Mm[q];                  // M[i][j]
       const double tv = Mm[j * p + i];          // M[j][i] = M^T[i][j]
       if (in_smem) w.M[q] = mv;
@@ -1262,7 +1294,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     // row k subtracted R_ki times from every row i > k) leaves B = L^{-1} = (R^{-1})^T, lower triangular, in Mm:
     // the inverse comes out of the same p steps instead of p more.
     double* B = Mm;
-    for (int q = threadIdx.x; q < p * p; q += kPcThreads) B[q] = (q / p == q % p) ? 1.0 : 0.0;
+    for (int q = threadIdx.x; q < p * p; q += kPcThreads) B[q] = (q == small_div(q, pmag) * (p + 1)) ? 1.0 : 0.0;
     // Thread 0 forms each pivot's square root and reciprocal once, one step ahead (it also owns the update of
     // the next diagonal entry): float64 square roots and divisions are long instruction sequences on the FP64
     // pipe, which every warp would otherwise repeat.
@@ -1271,8 +1303,9 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
       if (!(piv > tiny)) {
         s_fail = 1;
       } else {
-        s_val[0] = sqrt(piv);
-        s_val[1] = 1.0 / s_val[0];
+        const double r = rsqrt_newton(piv);
+        s_val[0] = piv * r;
+        s_val[1] = r;
       }
     }
     __syncthreads();
@@ -1297,13 +1330,19 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
         if (!(piv > tiny)) {
           s_fail = 1;
         } else {
-          s_val[0] = sqrt(piv);
-          s_val[1] = 1.0 / s_val[0];
+          const double r = rsqrt_newton(piv);
+          s_val[0] = piv * r;
+          s_val[1] = r;
         }
       }
-      for (int s2 = threadIdx.x; s2 < half * (wd + 1); s2 += kPcThreads) {
+      // then every other entry of the fold, and the B rectangle B[i][c] -= R_ki B[k][c] (k < i < p, c <= k),
+      // shared by warps 1 .. 15: warp 0 runs only thread 0's pivot chain (its other lanes would otherwise wait
+      // behind that divergent branch before starting their share)
+      const unsigned wmag = s_mag[wd + 1];
+      const int t1 = (int)threadIdx.x - 32;
+      for (int s2 = t1 < 0 ? 0x7fffffff : t1; s2 < half * (wd + 1); s2 += kPcThreads - 32) {
         if (s2 == 0) continue;
-        const int a = s2 / (wd + 1), b = s2 - a * (wd + 1);
+        const int a = small_div(s2, wmag), b = s2 - a * (wd + 1);
         int r, c;
         if (b < wd - a) {
           r = a;
@@ -1316,10 +1355,10 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
         const int i = k + 1 + r, j = k + 1 + c;
         G[i * p + j] = fma(-rowk[i], rowk[j], G[i * p + j]);
       }
-      // B[i][c] -= R_ki B[k][c] over the rectangle k < i < p, c <= k
       const int kc = k + 1;
-      for (int s2 = threadIdx.x; s2 < wd * kc; s2 += kPcThreads) {
-        const int r = s2 / kc, c = s2 - r * kc;
+      const unsigned kmag = s_mag[kc];
+      for (int s2 = t1 < 0 ? 0x7fffffff : t1; s2 < wd * kc; s2 += kPcThreads - 32) {
+        const int r = small_div(s2, kmag), c = s2 - r * kc;
         const int i = k + 1 + r;
         B[i * p + c] = fma(-rowk[i], B[k * p + c], B[i * p + c]);
       }
@@ -1334,7 +1373,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     }
     // M = B^T, in place (Mm then holds M = R^{-1}, upper triangular)
     for (int q = threadIdx.x; q < p * p; q += kPcThreads) {
-      const int i = q / p, j = q - i * p;
+      const int i = small_div(q, pmag), j = q - i * p;
       if (i < j) {
         Mm[i * p + j] = Mm[j * p + i];
         Mm[j * p + i] = 0.0;

@@ -57,6 +57,7 @@ struct DevState {
   // norms
   double anorm_f, anorm_2, ne_ratio, rnorm, ne_best, rnorm_best;
   double tol, tol_inner, est_ratio, cond_est;
+  double kappa_est;  // estimate of kappa(X) (sampled-QR preconditioner: cond_est sqrt(c / m), c the rows sampled)
   double est_best;   // best (halving) value of the inner solve's stopping estimate, at inner iteration iter_best
   double phibar_mark;  // LSQR residual-norm estimate at the last iteration that made progress
   int iter, max_iter, iter_cap, inner_iter, total_iter, sweeps, max_sweeps, iter_best;

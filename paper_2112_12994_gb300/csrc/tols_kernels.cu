@@ -302,7 +302,11 @@ __device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double 
   // the float64 floor of the ratio is about u sqrt(p) ||b|| / ||r|| (r = b - X phi carries an absolute error of
   // order u ||b||); LSQR's estimate of ||r|| is phibar
   const double floor64 = new_phibar > 0 ? 1e-15 * sqrt((double)p) * st->bnorm / new_phibar : 0.0;
-  const double tolA = st->mixed ? st->tol_inner : fmax(st->est_ratio, floor64);
+  // with the sampled-QR preconditioner a sweep resolves the residual only to about kappa(X) u relative (each
+  // later sweep starts from the float64 residual): asking LSQR for more spends iterations the next check would
+  // not see
+  const double floor_qr = st->precond == 2 ? 0.5 * st->kappa_est * 1.11e-16 : 0.0;
+  const double tolA = st->mixed ? st->tol_inner : fmax(fmax(st->est_ratio, floor64), floor_qr);
   double est_best = st->est_best;
   int iter_best = st->iter_best;
   // progress: the ratio estimate halved, or the residual norm estimate still falls (relative 1e-10)
@@ -439,7 +443,7 @@ __device__ void tail_check(const Work& w, DevState* st, const double* tk, double
   if (threadIdx.x == 0 && rnorm <= st->tol * st->bnorm) st->compatible = 1;
   if (ne <= st->tol || rnorm <= st->tol * st->bnorm) next = 0;           // converged (or compatible)
   else if (sweeps >= st->max_sweeps || st->total_iter >= 64 * st->max_iter) next = 1;  // give up
-  else if (sweeps >= 2 && ne > 0.5 * prev && !r_progress) {              // no progress since the last check
+  else if (sweeps >= 2 && ne > 0.7 * prev && !r_progress) {              // no progress since the last check
     next = (st->mixed && ne > 10.0 * floor64) ? 2 : 1;                   // mixed: float cannot refine it
   } else if (st->mixed && sweeps == 1 && ne > 1e-2) {
     next = 2;                                                             // float LSQR gained < 2 digits
@@ -1403,6 +1407,9 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
     if (ok || qr_used) {
       st->precond = qr_used ? 2 : 1;
       st->cond_est = cond;
+      // the sampled R is about sqrt(c / m) times the full one, so ||X||_2 ||R_s^{-1}||_2 overstates kappa(X) by
+      // sqrt(m / c)
+      st->kappa_est = qr_used ? cond * sqrt((double)(kQrRowsPerP * p) / (double)w.m) : cond;
       st->shifted = qr_used ? 0 : s_shift;
       st->trusted = qr_used ? 0 : trusted;
     } else {

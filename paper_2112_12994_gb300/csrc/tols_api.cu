@@ -49,7 +49,7 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -589,16 +589,23 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct BatchPlan {
   std::vector<int> idx;                      // caller index of every valid series
   std::vector<const double*> y_dev;          // device series given by the caller (else packed in b_y64)
-  std::vector<long long> n, m, off_y, off_u, off_part, off_cnt, ntd, ntf;
+  std::vector<long long> n, m, off_y, off_u, off_part, off_cnt, ntd, ntf, ntx;
   std::vector<int> p;
-  std::vector<size_t> off_vec, off_phi, off_mat;
+  std::vector<char> fft;                     // float64 FFT products (batch_fft_series)
+  std::vector<size_t> off_vec, off_phi, off_mat, off_spec;
   size_t y_elems = 0, u_elems = 0, part_doubles = 0, cnt_uints = 0, vec_doubles = 0, phi_doubles = 0,
-         mat_bytes = 0;
-  long long tiles_f = 0, tiles_d = 0;
-  int p_pad_max = 16;
+         mat_bytes = 0, spec_doubles = 0;
+  long long tiles_f = 0, tiles_d = 0, tiles_x = 0;
+  int p_pad_max = 16, p_pad_max_x = 16;
 };
 
-void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status) {
+// Partial-sum slots (and arrival units) of a batched series: one per tile of the product kernel it uses.
+long long batch_units(long long m, int p, bool fx) {
+  return fx ? batch_fft_tiles(m, p) : (m + kTileD - 1) / kTileD;
+}
+
+void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status, bool mixed,
+                bool allow_fft = true) {
   for (int k = 0; k < count; ++k) {
     if (p[k] < 1 || p[k] > TOLS_MAX_P || n[k] <= p[k]) { status[k] = TOLS_ERR_ARG; continue; }
     const long long nn = n[k], mm = nn - p[k];
@@ -611,12 +618,19 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
     B.y_elems += align_up((size_t)nn, 64);
     B.off_u.push_back((long long)B.u_elems);
     B.u_elems += align_up((size_t)mm, 64);
-    const long long ntd = (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
-    const long long ngr = (ntd + kGroup - 1) / kGroup;
+    const bool fx = allow_fft && batch_fft_series(p[k], mixed);
+    const long long ntd = fx ? 0 : (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
+    const long long ntx = fx ? batch_fft_tiles(mm, p[k]) : 0;
+    const long long nun = batch_units(mm, p[k], fx);
+    const long long ngr = (nun + kGroup - 1) / kGroup;
+    B.fft.push_back(fx ? 1 : 0);
     B.ntd.push_back(ntd);
     B.ntf.push_back(ntf);
+    B.ntx.push_back(ntx);
+    B.off_spec.push_back(B.spec_doubles);
+    if (fx) B.spec_doubles += batch_fft_spectra_doubles(mm, p[k]) + 2 * (kBatchFftN / 2 + 1);
     B.off_part.push_back((long long)B.part_doubles);
-    B.part_doubles += (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr);
+    B.part_doubles += (size_t)(nun * pp1 + nun + ngr * pp1 + ngr);
     B.off_cnt.push_back((long long)B.cnt_uints);
     B.cnt_uints += (size_t)align_up((size_t)ngr + 1, 4);
     B.off_vec.push_back(B.vec_doubles);
@@ -628,7 +642,9 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
                             sizeof(float) * 2 * (size_t)p[k] * p[k], 256);
     B.tiles_f += ntf;
     B.tiles_d += ntd;
+    B.tiles_x += ntx;
     B.p_pad_max = std::max(B.p_pad_max, pp1);
+    if (fx) B.p_pad_max_x = std::max(B.p_pad_max_x, pp1);
   }
 }
 
@@ -637,6 +653,15 @@ int batch_grid(tols_ctx* ctx, int is_double, int p_pad) {
   cudaFuncSetAttribute(batch_kernel_ptr(is_double), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(is_double), kThreads,
                                                     pass_smem_bytes(is_double, p_pad)) != cudaSuccess || nb < 1)
+    nb = 1;
+  return ctx->sms * std::min(nb, 4);
+}
+
+int batch_fft_grid(tols_ctx* ctx, int p_pad) {
+  int nb = 0;
+  cudaFuncSetAttribute(batch_fft_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fft_kernel_ptr(), kThreads, batch_fft_smem(p_pad)) !=
+          cudaSuccess || nb < 1)
     nb = 1;
   return ctx->sms * std::min(nb, 4);
 }
@@ -658,7 +683,8 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   if ((rc = ensure(ctx, ctx->b_mats, B.mat_bytes))) return rc;
   if ((rc = ensure(ctx, ctx->b_state, sizeof(DevState) * cnt))) return rc;
   if ((rc = ensure(ctx, ctx->b_series, sizeof(BatchSeries) * cnt))) return rc;
-  if ((rc = ensure(ctx, ctx->b_tiles, sizeof(int) * (size_t)(B.tiles_f + B.tiles_d)))) return rc;
+  if ((rc = ensure(ctx, ctx->b_tiles, sizeof(int) * (size_t)(B.tiles_f + B.tiles_d + B.tiles_x)))) return rc;
+  if (B.spec_doubles && (rc = ensure(ctx, ctx->b_spec, sizeof(double) * B.spec_doubles))) return rc;
   (void)fresh_cnt;
   // counters (and the done counter after them) start at zero; every pass leaves the counters at zero
   unsigned int* d_done = (unsigned int*)ctx->b_cnt.p + B.cnt_uints;
@@ -667,9 +693,9 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   const int max_iter_cfg = ctx->cfg.max_iter;
   const int max_sweeps = ctx->cfg.max_sweeps > 0 ? ctx->cfg.max_sweeps : 6;
   std::vector<BatchSeries> hs(cnt);
-  std::vector<int> tiles((size_t)(B.tiles_f + B.tiles_d));
+  std::vector<int> tiles((size_t)(B.tiles_f + B.tiles_d + B.tiles_x));
   states.assign(cnt, DevState{});
-  long long tf = 0, td = 0;
+  long long tf = 0, td = 0, tx = 0;
   for (int k = 0; k < cnt; ++k) {
     BatchSeries& S = hs[k];
     memset(&S, 0, sizeof S);
@@ -685,9 +711,9 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.U[0] = (char*)ctx->b_u0.p + ues * B.off_u[k];
     w.U[1] = (char*)ctx->b_u1.p + ues * B.off_u[k];
     double* q = (double*)ctx->b_part.p + B.off_part[k];
-    const long long ntd = B.ntd[k], ngr = (ntd + kGroup - 1) / kGroup;
-    w.part_t = q; q += ntd * pp1;
-    w.part_n2 = q; q += ntd;
+    const long long nun = batch_units(B.m[k], p, B.fft[k]), ngr = (nun + kGroup - 1) / kGroup;
+    w.part_t = q; q += nun * pp1;
+    w.part_n2 = q; q += nun;
     w.grp_t = q; q += ngr * pp1;
     w.grp_n2 = q;
     w.counters = (unsigned int*)ctx->b_cnt.p + B.off_cnt[k];
@@ -711,9 +737,19 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.M32 = (float*)(w.Mt + pq + qr_scratch_doubles(p));
     w.Mt32 = w.M32 + pq;
     w.st = (DevState*)ctx->b_state.p + k;
+    w.tw64 = ctx->tw64;
+    w.tw32 = ctx->tw32;
+    if (B.fft[k]) {
+      double* sp = (double*)ctx->b_spec.p + B.off_spec[k];
+      w.wspec64 = sp;
+      w.dspec64 = sp + batch_fft_spectra_doubles(B.m[k], p);
+    }
     S.tile0_f = tf;               // index in the float tile list
+    S.tile0_x = tx;               // index in the FFT tile list (stored after the float and double lists)
     for (long long t = 0; t < B.ntf[k]; ++t) tiles[(size_t)(tf + t)] = k;
     for (long long t = 0; t < B.ntd[k]; ++t) tiles[(size_t)(B.tiles_f + td + t)] = k;
+    for (long long t = 0; t < B.ntx[k]; ++t) tiles[(size_t)(B.tiles_f + B.tiles_d + tx + t)] = k;
+    tx += B.ntx[k];
     tf += B.ntf[k];
     td += B.ntd[k];
     S.tile0_d = td - B.ntd[k];   // index in the double tile list (stored after the float list)
@@ -742,8 +778,10 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   a.series = d_series;
   a.tile_series_f = (const int*)ctx->b_tiles.p;
   a.tile_series_d = (const int*)ctx->b_tiles.p + B.tiles_f;
+  a.tile_series_x = (const int*)ctx->b_tiles.p + B.tiles_f + B.tiles_d;
   a.tiles_f = B.tiles_f;
   a.tiles_d = B.tiles_d;
+  a.tiles_x = B.tiles_x;
   a.done_count = d_done;
   const int gf = batch_grid(ctx, 0, B.p_pad_max), gd = batch_grid(ctx, 1, B.p_pad_max);
 
@@ -755,9 +793,17 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     RUN(run_small(ctx, 11, [&] { return launch_convert_batch(d_series, cnt, ctx->stream); }));
   BatchArgs ag = a;
   ag.gram = 1;
-  ctx->launch_total++;
-  if (mixed) CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
-  else CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
+  const int gx = B.tiles_x ? batch_fft_grid(ctx, B.p_pad_max_x) : 0;
+  // launches per solver pass: float (mixed) or the FFT pair (d spectra, FFT pass) and/or the direct float64 pass
+  const int per_pass = mixed ? 1 : (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0);
+  ctx->launch_total += mixed ? 1 : (B.tiles_x ? 1 : 0) + (B.tiles_d ? 1 : 0);
+  if (mixed) {
+    CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
+  } else {
+    // the FFT series' Gram pass also forms their window spectra
+    if (B.tiles_x) CK(launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream));
+    if (B.tiles_d) CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
+  }
   const int want = no_precond ? 0 : ctx->cfg.precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream, B.p_pad_max); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
@@ -767,9 +813,16 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   cudaGraphExec_t exec = nullptr;
   auto enqueue_burst = [&]() -> int {
     for (int k = 0; k < burst; ++k) {
-      ctx->launch_total++;
-      CK(mixed ? launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream)
-               : launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+      ctx->launch_total += per_pass;
+      if (mixed) {
+        CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
+      } else {
+        if (B.tiles_x) {
+          CK(launch_batch_dspec(d_series, cnt, ctx->stream));
+          CK(launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream));
+        }
+        if (B.tiles_d) CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+      }
     }
     if (mixed) {
       ctx->launch_total++;
@@ -797,7 +850,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   int out = TOLS_OK;
   for (long long round = 0;; ++round) {
     if (exec) {
-      ctx->launch_total += burst + (mixed ? 1 : 0);
+      ctx->launch_total += burst * per_pass + (mixed ? 1 : 0);
       cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
       if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "cudaGraphLaunch", e); break; }
     } else if ((out = enqueue_burst())) {
@@ -829,7 +882,7 @@ BatchPlan sub_plan(tols_ctx* ctx, const BatchPlan& B, const std::vector<int>& wh
     p.push_back(B.p[k]);
   }
   std::vector<int> st(which.size(), TOLS_OK);
-  plan_batch(S, (int)which.size(), n.data(), p.data(), st);
+  plan_batch(S, (int)which.size(), n.data(), p.data(), st, false, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
   for (int k : which)
     S.y_dev.push_back(B.y_dev.empty() ? (const double*)ctx->b_y64.p + B.off_y[k] : B.y_dev[k]);
   return S;
@@ -928,7 +981,8 @@ class ArenaAlloc {
 size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
   const long long m = n - p;
   const size_t pp1 = (size_t)pad_p(p + 1);
-  const long long ntd = (m + kTileD - 1) / kTileD, ngr = (ntd + kGroup - 1) / kGroup;
+  const bool fx = batch_fft_series(p, mixed);
+  const long long ntd = batch_units(m, p, fx), ngr = (ntd + kGroup - 1) / kGroup;
   const size_t es = mixed ? sizeof(float) : sizeof(double);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -945,6 +999,8 @@ size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
   char* part = take(sizeof(double) * (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr));
   char* vec = take(sizeof(double) * (9 * pp1 + (size_t)p));
   char* mat = take(sizeof(double) * (3 * (size_t)p * p + qr_scratch_doubles(p)) + sizeof(float) * 2 * (size_t)p * p);
+  // window spectra of the FFT tiles and the spectrum of d (float64 requests with FFT products)
+  char* spec = fx ? take(sizeof(double) * (batch_fft_spectra_doubles(m, p) + 2 * (kBatchFftN / 2 + 1))) : nullptr;
   if (base && w) {
     memset(w, 0, sizeof *w);
     w->n = n;
@@ -980,6 +1036,10 @@ size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
     w->qr = qr_scratch_doubles(p) ? w->Mt + pq : nullptr;
     w->M32 = (float*)(w->Mt + pq + qr_scratch_doubles(p));
     w->Mt32 = w->M32 + pq;
+    if (spec) {
+      w->wspec64 = spec;
+      w->dspec64 = (double*)spec + batch_fft_spectra_doubles(m, p);
+    }
   }
   return off;
 }
@@ -1054,24 +1114,31 @@ int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, i
   tols_ctx* ctx = srv->ctx;
   const int cnt = (int)list.size();
   std::vector<BatchSeries> hs(cnt);
-  long long tf = 0, td = 0;
+  long long tf = 0, td = 0, tx = 0;
   p_pad_max = 16;
   for (int k = 0; k < cnt; ++k) {
     const Work& w = srv->active[list[k]].w;
     memset(&hs[k], 0, sizeof(BatchSeries));
     hs[k].w = w;
+    hs[k].w.tw64 = ctx->tw64;
+    hs[k].w.tw32 = ctx->tw32;
     hs[k].tile0_f = tf;
     hs[k].tile0_d = td;
+    hs[k].tile0_x = tx;
     tf += (w.m + kTileF - 1) / kTileF;
-    td += (w.m + kTileD - 1) / kTileD;
+    if (w.dspec64) tx += batch_fft_tiles(w.m, w.p);
+    else td += (w.m + kTileD - 1) / kTileD;
     p_pad_max = std::max(p_pad_max, pad_p(w.p + 1));
   }
-  std::vector<int> tiles((size_t)(tf + td));
+  std::vector<int> tiles((size_t)(tf + td + tx));
   for (int k = 0; k < cnt; ++k) {
     const Work& w = hs[k].w;
-    const long long ntf = (w.m + kTileF - 1) / kTileF, ntd = (w.m + kTileD - 1) / kTileD;
+    const long long ntf = (w.m + kTileF - 1) / kTileF;
+    const long long ntd = w.dspec64 ? 0 : (w.m + kTileD - 1) / kTileD;
+    const long long ntx = w.dspec64 ? batch_fft_tiles(w.m, w.p) : 0;
     for (long long t = 0; t < ntf; ++t) tiles[(size_t)(hs[k].tile0_f + t)] = k;
     for (long long t = 0; t < ntd; ++t) tiles[(size_t)(tf + hs[k].tile0_d + t)] = k;
+    for (long long t = 0; t < ntx; ++t) tiles[(size_t)(tf + td + hs[k].tile0_x + t)] = k;
   }
   int rc;
   if ((rc = ensure(ctx, srv->table, sizeof(BatchSeries) * std::max(cnt, 1)))) return rc;
@@ -1082,8 +1149,10 @@ int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, i
   a.series = (const BatchSeries*)srv->table.p;
   a.tile_series_f = (const int*)srv->tiles.p;
   a.tile_series_d = (const int*)srv->tiles.p + tf;
+  a.tile_series_x = (const int*)srv->tiles.p + tf + td;
   a.tiles_f = tf;
   a.tiles_d = td;
+  a.tiles_x = tx;
   // the host vectors must outlive the copies: pageable-memory copies are staged before they return
   return TOLS_OK;
 }
@@ -1103,8 +1172,8 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
     st.no_precond = r.no_precond ? 1 : 0;
     CK(cudaMemcpyAsync((void*)a.w.y64, r.y.data(), sizeof(double) * (size_t)r.n, cudaMemcpyHostToDevice,
                        ctx->stream));
-    CK(cudaMemsetAsync(a.w.counters, 0, sizeof(unsigned) * (size_t)((((r.n - r.p) + kTileD - 1) / kTileD + kGroup - 1) / kGroup + 1),
-                       ctx->stream));
+    const long long nun = batch_units(r.n - r.p, r.p, a.w.dspec64 != nullptr);
+    CK(cudaMemsetAsync(a.w.counters, 0, sizeof(unsigned) * (size_t)((nun + kGroup - 1) / kGroup + 1), ctx->stream));
     CK(cudaMemcpyAsync(a.w.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
     a.req = std::move(r);
     srv->queue.pop_front();
@@ -1134,8 +1203,15 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
     CK(launch_batch_pass<float>(ag, batch_grid(ctx, 0, pmax), pmax, ctx->stream));
   }
   if (any_fp64) {
-    ctx->launch_total++;
-    CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
+    // the FFT requests' Gram pass also forms their window spectra
+    if (a.tiles_x) {
+      ctx->launch_total++;
+      CK(launch_batch_fft(ag, batch_fft_grid(ctx, pmax), pmax, ctx->stream));
+    }
+    if (a.tiles_d) {
+      ctx->launch_total++;
+      CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
+    }
   }
   const int want = ctx->cfg.precond;
   const int cnt = (int)fresh.size();
@@ -1163,6 +1239,7 @@ int server_round(tols_server* srv) {
   int pmax = 16;
   RUN(upload_table(srv, all, a, pmax));
   const int gf = batch_grid(ctx, 0, pmax), gd = batch_grid(ctx, 1, pmax);
+  const int gx = a.tiles_x ? batch_fft_grid(ctx, pmax) : 0;
   bool any_mixed = false;
   for (const SrvActive& A : srv->active) any_mixed |= A.req.mixed;
   // float passes serve the mixed requests' iterations, double passes the float64 requests' iterations and every
@@ -1172,8 +1249,15 @@ int server_round(tols_server* srv) {
       ctx->launch_total++;
       CK(launch_batch_pass<float>(a, gf, pmax, ctx->stream));
     }
-    ctx->launch_total++;
-    CK(launch_batch_pass<double>(a, gd, pmax, ctx->stream));
+    if (a.tiles_x) {
+      ctx->launch_total += 2;
+      CK(launch_batch_dspec(a.series, cnt, ctx->stream));
+      CK(launch_batch_fft(a, gx, pmax, ctx->stream));
+    }
+    if (a.tiles_d) {
+      ctx->launch_total++;
+      CK(launch_batch_pass<double>(a, gd, pmax, ctx->stream));
+    }
   }
   RUN(run_small(ctx, 12, [&] { return launch_finish_batch(a.series, cnt, ctx->stream); }));
   int rc;
@@ -1344,7 +1428,7 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
                     &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
-                    &ctx->spec64};
+                    &ctx->spec64, &ctx->b_spec};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -1389,7 +1473,7 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
   if (tol <= 0) tol = 1e-12;
   std::vector<int> status(count, TOLS_OK);
   BatchPlan B;
-  plan_batch(B, count, n, p, status);
+  plan_batch(B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
   for (int k : B.idx)
     if (!y[k] || !phi[k]) return fail(ctx, TOLS_ERR_ARG, "null series or phi pointer");
   int rc;
@@ -1443,7 +1527,7 @@ int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* co
   if (tol <= 0) tol = 1e-12;
   std::vector<int> status(count, TOLS_OK);
   BatchPlan B;
-  plan_batch(B, count, n, p, status);
+  plan_batch(B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
   for (int k : B.idx) {
     if (!d_y[k]) return fail(ctx, TOLS_ERR_ARG, "null device series pointer");
     B.y_dev.push_back(d_y[k]);

@@ -96,6 +96,7 @@ struct Work {
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
   void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
   void* wspec64;          // the same for the float64 FFT tiles
+  void* dspec64;          // (batched float64 FFT series) doubled spectrum of the lag-reversed d, N/2 + 1 entries
 };
 
 // Arguments of a pass kernel (passed by value).
@@ -127,6 +128,7 @@ struct PassArgs {
 struct BatchSeries {
   Work w;
   long long tile0_f, tile0_d;   // first index of this series in the float / double tile lists
+  long long tile0_x;            // first index in the float64 FFT tile list (series with w.dspec64 set)
 };
 
 // Arguments of a batched pass launch.
@@ -135,9 +137,24 @@ struct BatchArgs {
   const int* tile_series_f;     // float tile list: tile -> series
   const int* tile_series_d;     // double tile list: tile -> series
   long long tiles_f, tiles_d;
+  const int* tile_series_x;     // float64 FFT tile list: tile -> series
+  long long tiles_x;
   int gram;                     // 1: Gram lag-sum pass (TAIL_GRAM) instead of a solver pass
   unsigned int* done_count;     // incremented once per series that reaches PH_DONE
 };
+
+// Batched float64 series with p_pad(p + 1) in [32, 1024) take the overlap-save FFT products (N = 2,048, tiles of
+// 2,048 - pad_p(p + 1) rows); the others, and every series of a mixed batch, the direct products.
+constexpr int kBatchFftN = 2048;
+__host__ __device__ constexpr bool batch_fft_series(int p, bool mixed) {
+  return !mixed && pad_p(p + 1) >= 32 && pad_p(p + 1) < kBatchFftN / 2;
+}
+__host__ __device__ constexpr long long batch_fft_tiles(long long m, int p) {
+  return (m + (kBatchFftN - pad_p(p + 1)) - 1) / (kBatchFftN - pad_p(p + 1));
+}
+__host__ __device__ constexpr size_t batch_fft_spectra_doubles(long long m, int p) {
+  return (size_t)batch_fft_tiles(m, p) * (kBatchFftN / 2 + 1) * 2;
+}
 
 // Launch helpers (tols_kernels.cu).
 size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
@@ -154,6 +171,10 @@ cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s);
 template <typename T>
 cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s);
 const void* batch_kernel_ptr(int is_double);
+cudaError_t launch_batch_fft(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s);
+cudaError_t launch_batch_dspec(const BatchSeries* series, int count, cudaStream_t s);
+const void* batch_fft_kernel_ptr();
+size_t batch_fft_smem(int p_pad_max);
 cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_precond, cudaStream_t s,
                                  int p_max);
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s);

@@ -934,6 +934,32 @@ cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaS
   batch_pass_kernel<T><<<g, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
+size_t batch_fft_smem(int p_pad_max) { return fft_pass_smem<double>(p_pad_max); }
+const void* batch_fft_kernel_ptr() { return (const void*)batch_fft_kernel; }
+cudaError_t launch_batch_fft(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s) {
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  int g = (int)lmin((long long)grid, a.tiles_x);
+  if (g < 1) return cudaSuccess;
+  batch_fft_kernel<<<g, kThreads, batch_fft_smem(p_pad_max), s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_dspec(const BatchSeries* series, int count, cudaStream_t s) {
+  static int configured = 0;
+  const size_t smem = FftSmem<double>::bytes(0);
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_dspec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  if (count < 1) return cudaSuccess;
+  batch_dspec_kernel<<<count, kThreads, smem, s>>>(series);
+  return cudaGetLastError();
+}
 template cudaError_t launch_batch_pass<float>(const BatchArgs&, int, int, cudaStream_t);
 template cudaError_t launch_batch_pass<double>(const BatchArgs&, int, int, cudaStream_t);
 const void* batch_kernel_ptr(int is_double) {

@@ -415,7 +415,7 @@ void fill_info(tols_info* info, const DevState& s, int prec) {
   info->sweeps = s.sweeps;
   info->precision_used = prec;
   info->precond_used = s.precond;
-  info->product_used = TOLS_PRODUCT_DIRECT;  // overwritten by the single-series path when it used the FFT
+  info->product_used = s.fft ? TOLS_PRODUCT_FFT : TOLS_PRODUCT_DIRECT;  // single series: set after the call
   info->ne_ratio = s.ne_ratio;
   info->rnorm = s.rnorm;
   info->bnorm = s.bnorm;

@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
     if (!arrive(w, local, ntiles, nlag, pg, sm.tacc, sm.scratch, &s_last)) continue;
     const double n2_all = sm.scratch[8];
     __syncthreads();
+    if (tid == 0) w.st->fft = 1;
     run_tail<T>(tail, w, gram, nlag, sm.tacc, n2_all, sm.scratch, nullptr, w.bnorm2);
     __syncthreads();
     if (tid == 0 && !gram && w.st->done && a.done_count) atomicAdd(a.done_count, 1u);

@@ -67,6 +67,7 @@ struct DevState {
   int compatible;    // a check found ||r|| <= tol ||b||
   int shifted;       // the Cholesky factor needed the diagonal shift
   int trusted;       // unshifted factor with kappa(R)^2 u <= 1/4 (semi-normal-equation start, float refinement)
+  int fft;           // a batched pass with overlap-save FFT products ran for this series
   int no_precond;    // set by the host: plain LSQR (minimum-norm repeat of a rank-deficient problem)
 };
 

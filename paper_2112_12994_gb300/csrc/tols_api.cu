@@ -42,6 +42,8 @@ struct StreamSeries {
 
 }  // namespace
 
+constexpr size_t kStateBytes = (sizeof(tols::DevState) + 255) / 256 * 256;   // pinned state, then phi
+
 struct tols_ctx {
   tols_config cfg{};
   int device = 0;
@@ -54,7 +56,8 @@ struct tols_ctx {
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
   size_t h_stage_cap = 0;
-  DevState* h_state = nullptr;  // pinned copy of the device state
+  DevState* h_state = nullptr;  // pinned copy of the device state, followed by a pinned phi (TOLS_MAX_P doubles)
+  double* h_phi = nullptr;
   std::string err;
   std::map<int, StreamSeries> streams;
   int next_handle = 1;
@@ -427,7 +430,9 @@ void fill_info(tols_info* info, const DevState& s, int prec) {
 // One complete solve of the series at d_y (device). phi0 (device, nullable) warm-starts. Leaves phi in w.phi
 // and the final state in *ctx->h_state.
 int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, bool mixed, const double* phi0,
-               Work& w, bool no_precond = false) {
+               Work& w, bool no_precond = false, double* d_phi_out = nullptr, bool* phi_out_done = nullptr,
+               double* h_phi_out = nullptr) {
+  if (phi_out_done) *phi_out_done = false;
   int rc = prepare_work(ctx, d_y, n, p, mixed, true, w);
   if (rc) return rc;
   const int max_iter = ctx->cfg.max_iter > 0 ? ctx->cfg.max_iter : 4 * p + 200;
@@ -481,7 +486,8 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   const int gf = mixed ? pass_grid_for(ctx, 0, af.p_pad, af.fft) : 0;
   const long long max_launch = (long long)(max_iter + 4) * (max_sweeps + 2) * 2 + 16;
   long long launched = 0;
-  int burst = 4;
+  // a float64 solve from a trusted factor usually ends with its first (check) pass: start with a burst of one
+  int burst = mixed ? 4 : 1;
   while (true) {
     if (mixed) {
       for (int k = 0; k < burst; ++k) RUN(run_pass<float>(ctx, af, gf));
@@ -491,12 +497,19 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
       for (int k = 0; k < burst; ++k) RUN(run_pass<double>(ctx, ad, gd));
       launched += burst;
     }
+    // phi goes out with every state read, so a converged solve needs no further round trip
+    if (d_phi_out) CK(cudaMemcpyAsync(d_phi_out, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (h_phi_out) CK(cudaMemcpyAsync(h_phi_out, w.phi, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     RUN(flush_profile(ctx));
     if (ctx->h_state->done || ctx->h_state->phase == PH_DONE) break;
     if (launched > max_launch) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "solver did not reach a final state");
-    burst = std::min(burst * 2, 16);
+    burst = burst == 1 ? 4 : std::min(burst * 2, 16);
+  }
+  if (ctx->h_state->status == TOLS_OK) {
+    if (phi_out_done) *phi_out_done = d_phi_out != nullptr;
+    return TOLS_OK;                              // nothing for the finishing kernel to do
   }
   RUN(run_small(ctx, 12, [&] { return launch_finish(w, ctx->stream); }));
   CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -507,17 +520,21 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
 
 // Solve with precision fallback; phi (device) receives the result.
 int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, double tol, double* d_phi,
-                      double* rnorm, tols_info* info, const double* phi0, int force_prec = -1) {
+                      double* rnorm, tols_info* info, const double* phi0, int force_prec = -1,
+                      double* h_phi = nullptr, bool* h_phi_done = nullptr) {
   if (tol <= 0) tol = 1e-12;
   bool mixed = force_prec >= 0 ? force_prec == TOLS_MIXED : ctx->cfg.precision == TOLS_MIXED;
   Work w;
-  int rc = solve_core(ctx, d_y, n, p, tol, mixed, phi0, w);
+  bool phi_done = false;
+  if (h_phi_done) *h_phi_done = false;
+  int rc = solve_core(ctx, d_y, n, p, tol, mixed, phi0, w, false, d_phi, &phi_done, h_phi);
   if (rc) return rc;
   if (mixed && (ctx->h_state->mixed_ok == 0 || ctx->h_state->precond == 0) &&
       ctx->h_state->status != TOLS_ERR_NONFINITE && ctx->h_state->status != TOLS_OK) {
     // float products cannot refine this problem (kappa(X)^2 * u32 too large): redo it in float64,
     // warm-started from the best mixed iterate when that one is usable, else from zero
     const bool warm = ctx->h_state->ne_best < 1e-3;
+    phi_done = false;
     if (warm) CK(cudaMemcpyAsync(d_phi, w.best, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
     mixed = false;
     const int saved_iter = ctx->h_state->total_iter;
@@ -528,6 +545,7 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
   if (ctx->h_state->singular && ctx->h_state->compatible && ctx->h_state->status >= 0) {
     // X is exactly rank deficient (singular Gram matrix, zero residual): the shifted preconditioner does not
     // give the minimum-norm solution, plain LSQR from zero does. Keep the first result if the repeat fails.
+    phi_done = false;
     CK(cudaMemcpyAsync(d_phi, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
     const DevState first = *ctx->h_state;
     rc = solve_core(ctx, d_y, n, p, tol, false, nullptr, w, true);
@@ -543,8 +561,12 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
   }
   const DevState& s = *ctx->h_state;
   if (s.status == TOLS_ERR_NONFINITE) return fail(ctx, TOLS_ERR_NONFINITE, "y holds NaN or Inf");
-  CK(cudaMemcpyAsync(d_phi, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  if (!phi_done) {   // (a converged first solve already delivered phi with its last state read)
+    CK(cudaMemcpyAsync(d_phi, w.phi, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else if (h_phi_done) {
+    *h_phi_done = h_phi != nullptr;
+  }
   if (rnorm) *rnorm = s.rnorm;
   fill_info(info, s, mixed ? TOLS_MIXED : TOLS_FP64);
   if (info && ctx->last_fft) info->product_used = TOLS_PRODUCT_FFT;
@@ -569,8 +591,14 @@ int host_solve(tols_ctx* ctx, const double* y, long long n, int p, double tol, d
     d_phi0 = d_phi + p;
     CK(cudaMemcpyAsync(d_phi0, phi0_host, sizeof(double) * p, cudaMemcpyHostToDevice, ctx->stream));
   }
-  rc = solve_device_impl(ctx, (const double*)ctx->y64.p, n, p, tol, d_phi, rnorm, info, d_phi0);
+  bool h_done = false;
+  rc = solve_device_impl(ctx, (const double*)ctx->y64.p, n, p, tol, d_phi, rnorm, info, d_phi0, -1, ctx->h_phi,
+                         &h_done);
   if (rc < 0) return rc;
+  if (h_done) {      // phi came back with the last state read
+    memcpy(phi, ctx->h_phi, sizeof(double) * p);
+    return rc;
+  }
   cudaError_t e = cudaMemcpyAsync(phi, d_phi, sizeof(double) * p, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "copy phi to host", e);
@@ -1411,11 +1439,12 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
       return TOLS_ERR_OOM;
     }
   }
-  if (cudaMallocHost(&ctx->h_state, sizeof(DevState)) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->h_state, kStateBytes + sizeof(double) * TOLS_MAX_P) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TOLS_ERR_OOM;
   }
+  ctx->h_phi = (double*)((char*)ctx->h_state + kStateBytes);
   *out = ctx;
   return TOLS_OK;
 }

@@ -141,10 +141,21 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
 int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
                                       const int* p, double tol, double* d_phi, double* rnorm, tols_info* info);
 
+/* Order sweep and PACF (Def. "Partial Autocorrelation Function", Section 3, with the order rule of the LSAR
+ * algorithm's last step taken on the full data): fits AR(h) for h = 1 .. h_max to the one series y, as one batch;
+ * tau[h-1] = the last coefficient of the AR(h) fit, the PACF estimate at lag h; *order = the largest h with
+ * |tau[h-1]| >= 1.96 / sqrt(n - h) (n - h: the rows of that fit), 0 if there is none.
+ * y: host, n doubles (copied in). tau: host, h_max doubles (caller-owned). order, info (h_max entries): host,
+ * nullable. Requires 1 <= h_max <= TOLS_MAX_P and n > h_max (else TOLS_ERR_ARG). Returns, like the batched solve,
+ * the worst per-fit code; a fit that failed contributes no lag to the order. */
+int toeplitz_ols_pacf(tols_ctx* ctx, const double* y, long long n, int h_max, double tol, double* tau, int* order,
+                      tols_info* info);
+
 /* ---- serving: continuous batching of fit requests ----------------------------------------------------
  * A server owns a context and one device arena. Submitted requests (series copied in at submit) wait in FIFO
  * order; each toeplitz_ols_server_step admits waiting requests while fewer than max_active are active and the
- * request's device footprint (about 24 n bytes in mixed precision, 40 n in float64, plus O(p^2)) fits in the
+ * request's device footprint (about 24 n bytes in mixed precision, 40 n in float64 or 49 n with the FFT window
+ * spectra of a float64 request with p >= 16, plus O(p^2)) fits in the
  * arena, sets the newcomers up, runs one burst of batched iterations over every active request, and retires the
  * finished ones (their memory is free for the next admission at once). A request's arithmetic depends only on
  * its own data, so its result is the same alone or among any other requests. */

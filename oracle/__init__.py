@@ -4,4 +4,4 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference leg
 library never imports it and shares no code with it.
 """
 from .tols import (OracleSolution, exact_leverage, gram, lag_matrix, leverage_p1, leverage_step, matvec,
-                   ols_qr, residual_check, rmatvec, row_norms)
+                   ols_qr, pacf, residual_check, rmatvec, row_norms)

@@ -217,3 +217,18 @@ def leverage_step(y, p: int, phi_hat, lev_prev):
     s = math.fsum((r * r).tolist())
     lev = np.asarray(lev_prev, dtype=np.float64) + r * r / s
     return lev, lev / p, s
+
+
+def pacf(y, h_max):
+    """PACF estimates tau_h, h = 1 .. h_max (Def. "Partial Autocorrelation Function", Section 3): tau_h is the last
+    coefficient of the AR(h) least-squares fit (ols_qr), and the order estimate is the largest h with
+    |tau_h| >= 1.96 / sqrt(n - h), n - h the rows of that fit (0 if none).
+    """
+    y = np.asarray(y, dtype=np.float64)
+    n = y.size
+    tau = np.array([ols_qr(y, h).phi[h - 1] for h in range(1, h_max + 1)])
+    order = 0
+    for h in range(1, h_max + 1):
+        if abs(tau[h - 1]) >= 1.96 / np.sqrt(n - h):
+            order = h
+    return tau, order

@@ -106,6 +106,7 @@ SIGNATURES = {
     "toeplitz_ols_solve_device": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, _D, ctypes.POINTER(tols_info)]),
     "toeplitz_ols_solve_batched": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P]),
     "toeplitz_ols_solve_batched_device": (_I, [_P, _I, _P, _P, _P, ctypes.c_double, _P, _P, _P]),
+    "toeplitz_ols_pacf": (_I, [_P, _P, _LL, _I, ctypes.c_double, _P, ctypes.POINTER(_I), _P]),
     "toeplitz_ols_stream_open": (_I, [_P, _I, ctypes.c_double, ctypes.POINTER(_I)]),
     "toeplitz_ols_stream_push": (_I, [_P, _I, _P, _LL]),
     "toeplitz_ols_stream_solve": (_I, [_P, _I, _P, _D, ctypes.POINTER(tols_info)]),
@@ -260,6 +261,19 @@ def toeplitz_ols_solve_batched_device(ctx: Context, d_ys, ps, d_phi, tol: float 
                                                ctypes.cast(infos, _P))
     ctx.check(rc, "toeplitz_ols_solve_batched_device")
     return rn, [i.as_dict() for i in infos], rc
+
+
+def toeplitz_ols_pacf(ctx: Context, y, h_max: int, tol: float = 0.0):
+    """Host series, largest lag -> (tau array of h_max PACF estimates, estimated order, list of info dicts, worst
+    status). tau[h-1] is the last coefficient of the AR(h) fit."""
+    y = _host_f64(y)
+    tau = np.zeros(int(h_max), dtype=np.float64)
+    order = ctypes.c_int(0)
+    infos = (tols_info * int(h_max))()
+    rc = lib.toeplitz_ols_pacf(ctx.handle, y.ctypes.data, y.size, int(h_max), tol, tau.ctypes.data,
+                               ctypes.byref(order), ctypes.cast(infos, _P))
+    ctx.check(rc, "toeplitz_ols_pacf")
+    return tau, order.value, [i.as_dict() for i in infos], rc
 
 
 def toeplitz_ols_stream_open(ctx: Context, p: int, tol: float = 0.0) -> int:

@@ -1548,6 +1548,49 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
   return worst;
 }
 
+int toeplitz_ols_pacf(tols_ctx* ctx, const double* y, long long n, int h_max, double tol, double* tau, int* order,
+                      tols_info* info) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (!y || !tau || h_max < 1 || h_max > TOLS_MAX_P || n <= h_max)
+    return fail(ctx, TOLS_ERR_ARG, "need y, tau, 1 <= h_max <= TOLS_MAX_P and n > h_max");
+  cudaSetDevice(ctx->device);
+  if (tol <= 0) tol = 1e-12;
+  int rc = stage_y(ctx, y, n);
+  if (rc) return rc;
+  // the fits of order 1 .. h_max, one batch over the one staged series
+  std::vector<long long> nn((size_t)h_max, n);
+  std::vector<int> pp((size_t)h_max);
+  for (int k = 0; k < h_max; ++k) pp[k] = k + 1;
+  std::vector<int> status((size_t)h_max, TOLS_OK);
+  const bool mixed = ctx->cfg.precision == TOLS_MIXED;
+  BatchPlan B;
+  plan_batch(B, h_max, nn.data(), pp.data(), status, mixed, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
+  for (size_t j = 0; j < B.idx.size(); ++j) B.y_dev.push_back((const double*)ctx->y64.p);
+  std::vector<DevState> states;
+  std::vector<int> prec_used;
+  std::vector<double> phis;
+  if ((rc = batch_solve_all(ctx, B, tol, mixed, states, phis, prec_used))) return rc;
+  int worst = TOLS_OK;
+  for (size_t j = 0; j < B.idx.size(); ++j) {
+    const int k = B.idx[j];
+    tau[k] = phis[B.off_phi[j] + (size_t)B.p[j] - 1];   // tau_h: the last coefficient of the AR(h) fit
+    status[k] = states[j].status;
+    if (info) fill_info(&info[k], states[j], prec_used[j]);
+  }
+  for (int k = 0; k < h_max; ++k) {
+    if (info) info[k].status = status[k];
+    if (status[k] < 0) worst = worst < 0 ? std::min(worst, status[k]) : status[k];
+    else if (worst >= 0 && status[k] > worst) worst = status[k];
+  }
+  if (order) {
+    int o = 0;
+    for (int h = 1; h <= h_max; ++h)
+      if (status[h - 1] >= 0 && fabs(tau[h - 1]) >= 1.96 / sqrt((double)(n - h))) o = h;
+    *order = o;
+  }
+  return worst;
+}
+
 int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
                                       const int* p, double tol, double* d_phi, double* rnorm, tols_info* info) {
   if (!ctx || count < 0 || (count > 0 && (!d_y || !n || !p || !d_phi))) return TOLS_ERR_ARG;

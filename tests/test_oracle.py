@@ -268,3 +268,21 @@ def test_planted_mistakes_are_caught(monkeypatch):
     yy, v = rng.standard_normal(50), rng.standard_normal(45)
     wrong = np.convolve(yy[:-1], v, mode="valid")
     assert not np.allclose(wrong, oracle.rmatvec(yy, 5, v))
+
+
+def test_pacf_pins():
+    # lag 1 is the p = 1 closed form (in rationals); a noise-free AR(2) recursion with dyadic coefficients is fitted
+    # exactly at lag 2, so tau_2 = phi_2
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal(400)
+    tau, _ = oracle.pacf(y, 3)
+    num = sum(Fraction(a) * Fraction(b) for a, b in zip(y[:-1], y[1:]))
+    den = sum(Fraction(a) * Fraction(a) for a in y[:-1])
+    assert tau[0] == pytest.approx(float(num / den), rel=1e-13)
+    z = np.zeros(60)
+    z[0], z[1] = 1.0, 0.5
+    for t in range(2, z.size):
+        z[t] = 0.75 * z[t - 1] - 0.25 * z[t - 2]
+    tau2, _ = oracle.pacf(z, 2)
+    assert tau2[1] == pytest.approx(-0.25, abs=1e-12)

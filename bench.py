@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
     ap.add_argument("--batch-series", type=int, default=1024,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
+    ap.add_argument("--pacf-lags", type=int, default=120,
+                    help="order sweep: PACF lags fitted on the bench series (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
     return ap.parse_args()
@@ -70,7 +72,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms while the timed region runs."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -86,7 +88,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(self.gpu_index)],
+                                          "-lms", "20", "-i", str(self.gpu_index)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -321,6 +323,7 @@ def run_ours(args, wl):
                                     tols.TOLS_MIXED)
     if serve_in:
         serving = run_serving(tols, serve_in, args)
+    order_sweep = run_order_sweep(tols, torch, s.y, args) if args.pacf_lags > 0 else None
 
     hbm_peak, hbm_src = peaks()
     r64, rmx = results["fp64"], results["mixed"]
@@ -400,6 +403,7 @@ def run_ours(args, wl):
            "batched": batched,
            "batched_mixed": batched_mixed,
            "serving": serving,
+           "order_sweep": order_sweep,
            "gpu_launches": int(r64["launches"] + rmx["launches"]),
            "clocks": r64["clocks"],
            "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r64["prof"].items() if v[0]}}
@@ -477,6 +481,23 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
     out["cpu_baseline"] = {"value": rows / t_or, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                            "sample": f"{rows} series of the batch"}
     return out
+
+
+def run_order_sweep(tols, torch, y, args):
+    """PACF of the bench series: the fits of order 1 .. h_max as one batch (toeplitz_ols_pacf, host series)."""
+    import numpy as np
+    h = args.pacf_lags
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        tols.toeplitz_ols_pacf(ctx, y, h, 1e-10)                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tau, order, infos, rc = tols.toeplitz_ols_pacf(ctx, y, h, 1e-10)
+        dt = time.perf_counter() - t0
+    return {"lags": h, "fits_per_s": h / dt, "ms_per_sweep": dt * 1e3, "order_estimate": order,
+            "statuses_ok": int(sum(1 for i in infos if i["status"] == 0)),
+            "max_iters": int(max(i["iters"] for i in infos)),
+            "workload": "AR(h), h = 1 .. lags, fitted to the bench series (n = 2^22), float64, tol 1e-10, "
+                        "end to end from host memory"}
 
 
 def run_serving(tols, serve_in, args):

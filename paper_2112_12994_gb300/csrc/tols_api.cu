@@ -627,9 +627,10 @@ struct BatchPlan {
   int p_pad_max = 16, p_pad_max_x = 16;
 };
 
-// Partial-sum slots (and arrival units) of a batched series: one per tile of the product kernel it uses.
+// Partial-sum slots (and arrival units) of a batched series: one per tile of the direct kernel, or one per unit of
+// kBatchFftUnit tiles of the FFT kernel.
 long long batch_units(long long m, int p, bool fx) {
-  return fx ? batch_fft_tiles(m, p) : (m + kTileD - 1) / kTileD;
+  return fx ? batch_fft_units(m, p) : (m + kTileD - 1) / kTileD;
 }
 
 void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status, bool mixed,
@@ -648,7 +649,7 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
     B.u_elems += align_up((size_t)mm, 64);
     const bool fx = allow_fft && batch_fft_series(p[k], mixed);
     const long long ntd = fx ? 0 : (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
-    const long long ntx = fx ? batch_fft_tiles(mm, p[k]) : 0;
+    const long long ntx = fx ? batch_fft_units(mm, p[k]) : 0;
     const long long nun = batch_units(mm, p[k], fx);
     const long long ngr = (nun + kGroup - 1) / kGroup;
     B.fft.push_back(fx ? 1 : 0);
@@ -1154,7 +1155,7 @@ int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, i
     hs[k].tile0_d = td;
     hs[k].tile0_x = tx;
     tf += (w.m + kTileF - 1) / kTileF;
-    if (w.dspec64) tx += batch_fft_tiles(w.m, w.p);
+    if (w.dspec64) tx += batch_fft_units(w.m, w.p);
     else td += (w.m + kTileD - 1) / kTileD;
     p_pad_max = std::max(p_pad_max, pad_p(w.p + 1));
   }
@@ -1163,7 +1164,7 @@ int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, i
     const Work& w = hs[k].w;
     const long long ntf = (w.m + kTileF - 1) / kTileF;
     const long long ntd = w.dspec64 ? 0 : (w.m + kTileD - 1) / kTileD;
-    const long long ntx = w.dspec64 ? batch_fft_tiles(w.m, w.p) : 0;
+    const long long ntx = w.dspec64 ? batch_fft_units(w.m, w.p) : 0;
     for (long long t = 0; t < ntf; ++t) tiles[(size_t)(hs[k].tile0_f + t)] = k;
     for (long long t = 0; t < ntd; ++t) tiles[(size_t)(tf + hs[k].tile0_d + t)] = k;
     for (long long t = 0; t < ntx; ++t) tiles[(size_t)(tf + td + hs[k].tile0_x + t)] = k;

@@ -482,11 +482,12 @@ __global__ void __launch_bounds__(kThreads) spectrum_kernel(const T* __restrict_
   }
 }
 
-// Batched float64 overlap-save pass: the CTAs stride over one list of the FFT tiles of every series that takes the
-// FFT products (tiles of L = N - pad_p(p + 1) rows; window spectra formed by the batch's Gram pass; the spectrum of
-// the series' d formed before the pass by batch_dspec_kernel). Each tile transforms its X^T u lags back itself
-// (three transforms per tile rather than two), so that a series' partials, and so its result, do not depend on
-// the rest of the batch; the tiles of a series then arrive and its last CTA runs the series' scalar step.
+// Batched float64 overlap-save pass: the CTAs stride over one list of work units, each up to kBatchFftUnit
+// consecutive FFT tiles of one series (tiles of L = N - pad_p(p + 1) rows; window spectra formed by the batch's
+// Gram pass; the spectrum of the series' d formed before the pass by batch_dspec_kernel). A unit sums its tiles'
+// X^T u spectra and transforms back once; the grouping depends only on the series, so a series' partials, and so
+// its result, do not depend on the rest of the batch. The units of a series then arrive and its last CTA runs
+// the series' scalar step.
 __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
   using T = double;
   using V = double2;
@@ -494,49 +495,47 @@ __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
   constexpr int M = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
-  __shared__ int s_skip;
   const int tid = threadIdx.x;
   for (long long g = blockIdx.x; g < a.tiles_x; g += gridDim.x) {
     const int sidx = a.tile_series_x[g];
     const BatchSeries& S = a.series[sidx];
     const Work& w = S.w;
     const int p = w.p, pg = pad_p(p + 1), L = N - pg;
-    const long long local = g - S.tile0_x, ntiles = (w.m + L - 1) / L;
+    const long long unit = g - S.tile0_x, ntiles = (w.m + L - 1) / L;
+    const long long nunits = (ntiles + kBatchFftUnit - 1) / kBatchFftUnit;
     int tail = TAIL_GRAM;
     const T* u_old = nullptr;
     T* u_new = nullptr;
     double coef = 0.0;
     const int gram = a.gram;
     const int nlag = gram ? p + 1 : p;
-    if (tid == 0) s_skip = gram ? 0 : !select_phase<T>(w.st, w.y64, p, w, tail, u_old, u_new, coef);
-    __syncthreads();
-    const int skip = s_skip;
-    __syncthreads();
-    if (skip) continue;
-    if (!gram) select_phase<T>(w.st, w.y64, p, w, tail, u_old, u_new, coef);
+    // every thread reads the series state itself: it cannot change while a unit of the series is pending
+    if (!gram && !select_phase<T>(w.st, w.y64, p, w, tail, u_old, u_new, coef)) continue;
+    __syncthreads();                                   // the previous unit is done with shared memory
     FftSmem<T> sm(smem_raw, pg);
     const V* tw = reinterpret_cast<const V*>(w.tw64);
-    V* wt = reinterpret_cast<V*>(w.wspec64) + (size_t)local * (M + 1);
     for (int k = tid; k < pg + 16; k += kThreads) sm.tacc[k] = 0.0;
     for (int f = tid; f <= M; f += kThreads) sm.S[f] = make_double2(0.0, 0.0);
     if (!gram) {
       const V* dsp = reinterpret_cast<const V*>(w.dspec64);
       for (int f = tid; f <= M; f += kThreads) sm.D[f] = dsp[f];
     }
-    __syncthreads();
+    const bool corr = (long long)pg * nlag <= GramCfg<T>::kDirectMax;
     double n2 = 0.0;
-    if (gram)
-      fft_gram_tile<T>(sm, w.y64, w.n, w.m, L, pg, nlag, local * L, tw, wt,
-                       (long long)pg * nlag <= GramCfg<T>::kDirectMax);
-    else
-      n2 = fft_tile<T>(sm, w.m, L, u_old, u_new, coef, local * L, tw, wt);
+    const long long t1 = lmin((unit + 1) * kBatchFftUnit, ntiles);
+    for (long long t = unit * kBatchFftUnit; t < t1; ++t) {
+      __syncthreads();
+      V* wt = reinterpret_cast<V*>(w.wspec64) + (size_t)t * (M + 1);
+      if (gram) fft_gram_tile<T>(sm, w.y64, w.n, w.m, L, pg, nlag, t * L, tw, wt, corr);
+      else n2 += fft_tile<T>(sm, w.m, L, u_old, u_new, coef, t * L, tw, wt);
+    }
     __syncthreads();
     fft_finish_lags<T>(sm, nlag, tw);
     __syncthreads();
-    for (int k = tid; k < nlag; k += kThreads) w.part_t[(size_t)local * pg + k] = sm.tacc[k];
-    const double n2_tile = block_sum(n2, sm.scratch);
-    if (tid == 0) w.part_n2[local] = n2_tile;
-    if (!arrive(w, local, ntiles, nlag, pg, sm.tacc, sm.scratch, &s_last)) continue;
+    for (int k = tid; k < nlag; k += kThreads) w.part_t[(size_t)unit * pg + k] = sm.tacc[k];
+    const double n2_unit = block_sum(n2, sm.scratch);
+    if (tid == 0) w.part_n2[unit] = n2_unit;
+    if (!arrive(w, unit, nunits, nlag, pg, sm.tacc, sm.scratch, &s_last)) continue;
     const double n2_all = sm.scratch[8];
     __syncthreads();
     if (tid == 0) w.st->fft = 1;

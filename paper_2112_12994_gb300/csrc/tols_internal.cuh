@@ -129,7 +129,7 @@ struct PassArgs {
 struct BatchSeries {
   Work w;
   long long tile0_f, tile0_d;   // first index of this series in the float / double tile lists
-  long long tile0_x;            // first index in the float64 FFT tile list (series with w.dspec64 set)
+  long long tile0_x;            // first index in the float64 FFT unit list (series with w.dspec64 set)
 };
 
 // Arguments of a batched pass launch.
@@ -138,8 +138,8 @@ struct BatchArgs {
   const int* tile_series_f;     // float tile list: tile -> series
   const int* tile_series_d;     // double tile list: tile -> series
   long long tiles_f, tiles_d;
-  const int* tile_series_x;     // float64 FFT tile list: tile -> series
-  long long tiles_x;
+  const int* tile_series_x;     // float64 FFT unit list (kBatchFftUnit tiles each): unit -> series
+  long long tiles_x;            // units in that list
   int gram;                     // 1: Gram lag-sum pass (TAIL_GRAM) instead of a solver pass
   unsigned int* done_count;     // incremented once per series that reaches PH_DONE
 };
@@ -152,6 +152,12 @@ __host__ __device__ constexpr bool batch_fft_series(int p, bool mixed) {
 }
 __host__ __device__ constexpr long long batch_fft_tiles(long long m, int p) {
   return (m + (kBatchFftN - pad_p(p + 1)) - 1) / (kBatchFftN - pad_p(p + 1));
+}
+// Work unit of the batched FFT pass: up to kBatchFftUnit consecutive tiles of one series, whose X^T u spectra are
+// summed and transformed back once (a fixed grouping per series, so results do not depend on the batch).
+constexpr int kBatchFftUnit = 4;
+__host__ __device__ constexpr long long batch_fft_units(long long m, int p) {
+  return (batch_fft_tiles(m, p) + kBatchFftUnit - 1) / kBatchFftUnit;
 }
 __host__ __device__ constexpr size_t batch_fft_spectra_doubles(long long m, int p) {
   return (size_t)batch_fft_tiles(m, p) * (kBatchFftN / 2 + 1) * 2;

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
     ap.add_argument("--batch-series", type=int, default=1024,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="solve the batch of --batch-series series once in float64 and print its timing (profiling)")
     ap.add_argument("--pacf-lags", type=int, default=120,
                     help="order sweep: PACF lags fitted on the bench series (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=400,
@@ -536,6 +538,32 @@ def run_serving(tols, serve_in, args):
     return res
 
 
+def run_batch_only(args):
+    """One float64 batched solve of the batch workload (after one warm-up solve), timed on the host."""
+    import numpy as np
+    import torch
+
+    import paper_2112_12994_gb300 as tols
+    from synthetic import batch_shapes
+    bn, bp = batch_shapes(args.batch_series, config_id=4, n_lo=1e4, n_hi=1e6, p_lo=5, p_hi=200)
+    ys = gen_many(list(zip(bn, bp)), 4)
+    ps = [int(x) for x in bp]
+    dev = torch.device("cuda", 0)
+    d_ys = [torch.tensor(y, dtype=torch.float64, device=dev) for y in ys]
+    d_phi = torch.empty(sum(ps), dtype=torch.float64, device=dev)
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rn, infos, rc = tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    it = np.array([i["iters"] for i in infos])
+    print(json.dumps({"batch_only": True, "series": len(ys), "sum_n": int(sum(y.size for y in ys)), "seconds": dt,
+                      "solves_per_s": len(ys) / dt, "mean_iters": float(it.mean()), "max_iters": int(it.max()),
+                      "sampled_qr": int(sum(1 for i in infos if i["precond_used"] == 2))}), flush=True)
+
+
 def run_kernel_only(args, wl):
     """The fused pass u_new = X v - c u_old, ||u_new||^2, X^T u_new alone, in both precisions."""
     import numpy as np
@@ -596,6 +624,8 @@ def main():
         run_reference(args, wl)
     elif args.kernel_only:
         run_kernel_only(args, wl)
+    elif args.batch_only:
+        run_batch_only(args)
     else:
         run_ours(args, wl)
 

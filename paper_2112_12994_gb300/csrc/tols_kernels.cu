@@ -1052,9 +1052,17 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       for (int t = threadIdx.x; t < ncol * nsplit; t += kPcThreads) {
         const int r0 = t / ncol, jj = t - r0 * ncol;      // t < kPcThreads: one division per thread
         const int j = k + 1 + jj;
-        double acc = 0.0;
-        for (int i = k + r0; i < c; i += nsplit) acc = fma(qv[i], A[(size_t)i * p + j], acc);
-        qpart[t] = acc;
+        // four independent accumulators: the loads of A (L2-resident) overlap instead of waiting one by one
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int i = k + r0;
+        for (; i + 3 * nsplit < c; i += 4 * nsplit) {
+          a0 = fma(qv[i], A[(size_t)i * p + j], a0);
+          a1 = fma(qv[i + nsplit], A[(size_t)(i + nsplit) * p + j], a1);
+          a2 = fma(qv[i + 2 * nsplit], A[(size_t)(i + 2 * nsplit) * p + j], a2);
+          a3 = fma(qv[i + 3 * nsplit], A[(size_t)(i + 3 * nsplit) * p + j], a3);
+        }
+        for (; i < c; i += nsplit) a0 = fma(qv[i], A[(size_t)i * p + j], a0);
+        qpart[t] = (a0 + a1) + (a2 + a3);
       }
       __syncthreads();
       for (int jj = threadIdx.x; jj < ncol; jj += kPcThreads) {
@@ -1066,10 +1074,24 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
       // A[i][j] -= v_i qw_j over the trailing block ((c - k) ncol < 4 p^2 entries: q ncol < 2^32)
       const int tot = (c - k) * ncol;
       const unsigned nmag = div_magic((unsigned)ncol);
-      for (int q = threadIdx.x; q < tot; q += kPcThreads) {
-        const int r = small_div(q, nmag), jj = q - r * ncol;
-        const size_t idx = (size_t)(k + r) * p + (k + 1 + jj);
-        A[idx] = fma(-qv[k + r], qw[jj], A[idx]);
+      // four entries per thread at a time: all four loads issue before the stores (the entries are distinct)
+      for (int q0 = threadIdx.x; q0 < tot; q0 += 4 * kPcThreads) {
+        size_t idx[4];
+        double va[4], wb[4], av[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int q = q0 + s * kPcThreads;
+          const int qq = q < tot ? q : q0;                  // out of range: a harmless duplicate of q0
+          const int r = small_div(qq, nmag), jj = qq - r * ncol;
+          idx[s] = (size_t)(k + r) * p + (k + 1 + jj);
+          va[s] = qv[k + r];
+          wb[s] = qw[jj];
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) av[s] = A[idx[s]];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (q0 + s * kPcThreads < tot) A[idx[s]] = fma(-va[s], wb[s], av[s]);
       }
       __syncthreads();
     }

@@ -1009,11 +1009,12 @@ __device__ __forceinline__ int small_div(int s, unsigned magic) {
 // dependent shared-memory and FP64 operations better than 8.
 constexpr int kPcThreads = 512;
 
-__device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, double* qpart, double* scratch) {
+__device__ bool sampled_qr(const Work& w, double* R, double* qw, double* qpart, double* scratch) {
   const int p = w.p;
   const long long m = w.m;
   const int c = kQrRowsPerP * p;
   double* A = w.qr;
+  double* qv = w.qr + (size_t)c * p;                   // the Householder vector (global scratch, L1-cached reads)
   const double* y = w.y64;
   // gather: one row per warp at a time, its lanes along the row (one 64-bit division per row, not per entry)
   for (int i = threadIdx.x >> 5; i < c; i += kPcThreads / 32) {
@@ -1071,7 +1072,7 @@ __device__ bool sampled_qr(const Work& w, double* R, double* qv, double* qw, dou
         qw[jj] = beta * acc;
       }
       __syncthreads();
-      // A[i][j] -= v_i qw_j over the trailing block ((c - k) ncol < 4 p^2 entries: q ncol < 2^32)
+      // A[i][j] -= v_i qw_j over the trailing block ((c - k) ncol < 6 p^2 entries: q ncol < 2^32)
       const int tot = (c - k) * ncol;
       const unsigned nmag = div_magic((unsigned)ncol);
       // four entries per thread at a time: all four loads issue before the stores (the entries are distinct)
@@ -1114,7 +1115,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   __shared__ float red2[2 * (kPcThreads / 32)];
   __shared__ unsigned s_mag[TOLS_MAX_P + 2];       // div_magic(d), d = 0 .. p + 1, formed once (a division each)
   for (int d = threadIdx.x; d <= p + 1; d += kPcThreads) s_mag[d] = d > 0 ? div_magic((unsigned)d) : 0u;
-  __shared__ double qv[kQrRowsPerP * kQrMaxP], qw[kQrMaxP], qpart[kPcThreads];
+  __shared__ double qw[kQrMaxP], qpart[kPcThreads];
   const bool in_smem = smem && p <= kPrecondSmemP;
   double* G = in_smem ? smem : w.G;
   double* Mm = in_smem ? smem + (size_t)p * p : w.M;
@@ -1445,7 +1446,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   bool qr_used = false;
   if (want_precond && !st->no_precond && !st->mixed && (want_precond == 2 || !trusted) && w.qr &&
       p <= kQrMaxP && w.m >= (long long)kQrRowsPerP * p) {
-    if (sampled_qr(w, G, qv, qw, qpart, scratch)) {
+    if (sampled_qr(w, G, qw, qpart, scratch)) {
       cond = invert_and_estimate();
       store();
       qr_used = true;

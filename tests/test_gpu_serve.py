@@ -43,13 +43,16 @@ def test_served_results_match_oracle(tols, prec):
         assert r["info"]["rnorm"] == pytest.approx(sol.rnorm, rel=1e-11)
 
 
-def test_result_is_the_same_alone_and_in_the_mix(tols):
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_result_is_the_same_alone_and_in_the_mix(tols, prec):
+    # the probe's order (>= 16) takes the FFT products in float64, whose work units are fixed per request
     reqs = _requests(24, 81)
-    probe = reqs[5]
-    with tols.Server(precision=tols.TOLS_MIXED, arena_bytes=2 << 30) as srv:
+    probe = next(r for r in reqs if r[2] >= 16)
+    P = tols.TOLS_MIXED if prec == "mixed" else tols.TOLS_FP64
+    with tols.Server(precision=P, arena_bytes=2 << 30) as srv:
         srv.submit(1000, probe[1], probe[2], 1e-12)
         alone = srv.run_until_idle()[0]["phi"]
-    with tols.Server(precision=tols.TOLS_MIXED, arena_bytes=2 << 30, max_active=8) as srv:
+    with tols.Server(precision=P, arena_bytes=2 << 30, max_active=8) as srv:
         # requests arrive while others are on the GPU: submit in waves between steps
         for i, (rid, y, p) in enumerate(reqs):
             srv.submit(rid, y, p, 1e-12)

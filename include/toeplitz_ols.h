@@ -53,10 +53,10 @@ typedef enum {
   TOLS_PRECOND_NONE = 0,      /* plain LSQR on X                                                           */
   TOLS_PRECOND_GRAM_CHOL = 1, /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X. A float64
                                  solve whose factor is not trustworthy (kappa(R)^2 u > 1/4) switches to
-                                 TOLS_PRECOND_SAMPLED_QR by itself (p <= 256, n - p >= 6p)                      */
-  TOLS_PRECOND_SAMPLED_QR = 2 /* LSQR on X R^{-1}, R from a float64 Householder QR of 6p rows of X sampled
+                                 TOLS_PRECOND_SAMPLED_QR by itself (p <= 256, n - p >= 8p)                      */
+  TOLS_PRECOND_SAMPLED_QR = 2 /* LSQR on X R^{-1}, R from a float64 Householder QR of 8p rows of X sampled
                                  evenly (the row-sampling idea of Section 3.1 used as a preconditioner; errors
-                                 of order kappa u instead of kappa^2 u). float64 solves, p <= 256, n - p >= 6p;
+                                 of order kappa u instead of kappa^2 u). float64 solves, p <= 256, n - p >= 8p;
                                  otherwise the Gram factor is used                                             */
 } tols_precond;
 

@@ -24,7 +24,7 @@ __host__ __device__ constexpr int pad_p(int p) { return (p + 15) & ~15; }
 
 // Sampled-row QR preconditioner: orders it serves and rows sampled per coefficient; its scratch (doubles).
 constexpr int kQrMaxP = 256;
-constexpr int kQrRowsPerP = 6;
+constexpr int kQrRowsPerP = 8;
 __host__ __device__ constexpr size_t qr_scratch_doubles(int p) {
   return p <= kQrMaxP ? (size_t)kQrRowsPerP * p * (p + 1) : 0;   // the sampled rows, then a Householder vector
 }

@@ -162,7 +162,7 @@ def test_ill_conditioned_reaches_the_float64_floor(tols, ctx, prec, p, idx, grad
 
 @pytest.mark.parametrize("n,p,lo,hi", [(10_000, 10, 1.2, 3.0), (20_000, 57, 1.2, 3.0), (50_000, 200, 2.0, 4.0)])
 def test_sampled_qr_preconditioner(tols, n, p, lo, hi):
-    # TOLS_PRECOND_SAMPLED_QR asked for: R from the QR of 6p evenly sampled rows, LSQR from zero on X R^{-1}
+    # TOLS_PRECOND_SAMPLED_QR asked for: R from the QR of 8p evenly sampled rows, LSQR from zero on X R^{-1}
     s = ar_series(n, p, config_id=71, series_index=p, root_lo=lo, root_hi=hi, max_log10_bound=6.0)
     sol = oracle.ols_qr(s.y, p)
     with tols.Context(precision=tols.TOLS_FP64, precond=tols.TOLS_PRECOND_SAMPLED_QR) as c:

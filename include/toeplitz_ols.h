@@ -130,7 +130,11 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
                               double* rnorm, tols_info* info);
 
 /* Solve count independent problems (host series y[k][0..n[k]-1], orders p[k]) in one batched launch
- * sequence. phi[k] (host, p[k] doubles), rnorm (host, count, nullable), info (host, count, nullable).
+ * sequence (each problem is eq. (xphi) for its own series, Section 3). Every pass kernel covers all
+ * series at once; float64 series with pad16(p[k] + 1) >= 32 take the overlap-save FFT products, the others (and
+ * every series of a mixed batch) the direct products, unless the context's product setting says otherwise
+ * (TOLS_PRODUCT_DIRECT forces the direct products). A series' result does not depend on the rest of the batch.
+ * phi[k] (host, p[k] doubles), rnorm (host, count, nullable), info (host, count, nullable).
  * Returns the worst status over the batch; info[k].status holds each series' own code. */
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
                                const int* p, double tol, double* const* phi, double* rnorm, tols_info* info);

@@ -91,7 +91,8 @@ struct Work {
   float* M32;             // float copies for the mixed path
   float* Mt32;
   double* bnorm2;         // device scalar ||b||^2 written by the Gram pass
-  double* qr;             // (nullable) 4p x p float64 scratch for the sampled-row QR preconditioner (p <= 256)
+  double* qr;             // (nullable) float64 scratch of the sampled-row QR preconditioner (p <= 256): the sampled
+                          // rows (kQrRowsPerP p x p) and a Householder vector
   DevState* st;
   const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)

@@ -361,8 +361,8 @@ def run_ours(args, wl):
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
     byts_fp64 = 8.0 * n + 16.0 * m
     # DRAM traffic of the FFT check/LSQR pass from an ncu capture of the same kernel (n = 2^26, p = 100: 1.106 GB
-    # read + 0.507 GB written per launch, 24.04 B per row of y), scaled to this launch's rows
-    traffic = 24.04 * n if (fft_used and not dom.endswith("gram") and p == 100) else None
+    # read + 0.508 GB written per launch, 24.05 B per row of y), scaled to this launch's rows
+    traffic = 24.05 * n if (fft_used and not dom.endswith("gram") and p == 100) else None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "traffic_source": "ncu dram__bytes_read+write of fft_pass_kernel<double> at "

@@ -3,5 +3,5 @@
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference leg may import it. The CUDA
 library never imports it and shares no code with it.
 """
-from .tols import (OracleSolution, exact_leverage, gram, lag_matrix, leverage_p1, leverage_step, matvec,
-                   ols_qr, pacf, residual_check, rmatvec, row_norms)
+from .tols import (LsarResult, OracleSolution, compressed_ols, exact_leverage, gram, lag_matrix, leverage_p1,
+                   leverage_sample, leverage_step, lsar, matvec, ols_qr, pacf, residual_check, rmatvec, row_norms)

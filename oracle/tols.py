@@ -28,6 +28,14 @@ Functions and the passage each follows:
                       l_{n,1}(i) = y_i^2 / sum_{t=1}^{n-1} y_t^2.
   leverage_step       eqs. (FALS), (FAR), (FASD), Section 3.1: l_{n,p} = l_{n-1,p-1} + r^2/||r||^2 with
                       r = X_{n-1,p-1} phi_hat - y_{n-1,p-1}, and pi = l / p.
+  leverage_sample     the sampling step of Algorithm "LSAR" (Section 3.1): c rows drawn with replacement from the
+                      distribution pi of eq. (FASD), by inverse CDF on the given uniforms.
+  compressed_ols      the compressed OLS problem of Algorithm "LSAR": min ||S X phi - S b|| with S picking the
+                      sampled rows of eq. (xphi), each scaled by 1 / sqrt(c pi_i); its minimiser by LAPACK lstsq.
+  lsar                Algorithm "LSAR" (Section 3.1): for lags p = 1 .. p_bar on the same m = n - p_bar rows,
+                      approximate leverage scores (Def. "Approximate Leverage Scores"), sampling, compressed
+                      solve, PACF estimate tau_p = last coefficient, and the order estimate: the largest p with
+                      |tau_p| >= 1.96 / sqrt(c).
 """
 from __future__ import annotations
 
@@ -232,3 +240,71 @@ def pacf(y, h_max):
         if abs(tau[h - 1]) >= 1.96 / np.sqrt(n - h):
             order = h
     return tau, order
+
+
+def leverage_sample(lev, u) -> np.ndarray:
+    """Rows drawn with replacement from pi(i) = lev(i) / p, eq. (FASD) (sum lev = p in exact arithmetic, so pi is
+    lev normalised by its sum): draw k is the smallest row i with lev[0] + ... + lev[i] > u[k] * sum(lev), or the
+    last row if rounding leaves no such i. u: uniforms in [0, 1)."""
+    lev = np.asarray(lev, dtype=np.float64)
+    cdf = np.cumsum(lev)
+    t = np.asarray(u, dtype=np.float64) * cdf[-1]
+    return np.minimum(np.searchsorted(cdf, t, side="right"), lev.size - 1).astype(np.int64)
+
+
+def compressed_ols(y, p: int, rows, pi_rows, c: int) -> np.ndarray:
+    """Minimiser of ||S X phi - S b|| (Algorithm "LSAR", Section 3.1): S takes row rows[k] of X and b of
+    eq. (xphi) and scales it by 1 / sqrt(c pi_rows[k])."""
+    y = _series(y, p)
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.arange(p)
+    Xs = y[p + rows[:, None] - cols[None, :] - 1]
+    bs = y[p + rows]
+    s = 1.0 / np.sqrt(c * np.asarray(pi_rows, dtype=np.float64))
+    phi, *_ = np.linalg.lstsq(Xs * s[:, None], bs * s, rcond=None)
+    return phi
+
+
+@dataclass
+class LsarResult:
+    tau: np.ndarray          # PACF estimates tau_p, p = 1 .. p_bar
+    order: int               # largest p with |tau_p| >= 1.96 / sqrt(c), 0 if none
+    phi: list                # phi_hat at each lag (p coefficients at lag p)
+    rows: np.ndarray         # (p_bar, c) sampled rows
+    lev_sum: np.ndarray      # sum of the approximate leverage scores at each lag (p in exact arithmetic)
+    rr: np.ndarray           # ||r||^2 of eq. (FAR) feeding lag p (nan at lag 1)
+
+
+def lsar(y, p_bar: int, c: int, unif) -> LsarResult:
+    """Algorithm "LSAR" (Section 3.1) with the c rows per lag drawn by leverage_sample from unif[p - 1].
+
+    Every lag uses the same m = n - p_bar rows: at lag p the data are y[0 .. m + p) and its order-p matrix of
+    eq. (xphi) has m rows. Lag 1 samples by the exact scores l_{.,1}; lag p >= 2 by l_p = l_{p-1} + r^2/||r||^2,
+    eq. (FALS), with r the full-data residual of lag p-1's compressed estimate, eq. (FAR)."""
+    y = _series(y, p_bar)
+    unif = np.asarray(unif, dtype=np.float64)
+    if unif.shape != (p_bar, c):
+        raise ValueError("unif must have shape (p_bar, c)")
+    m = y.size - p_bar
+    tau = np.empty(p_bar)
+    rows_all = np.empty((p_bar, c), dtype=np.int64)
+    lev_sum = np.empty(p_bar)
+    rr = np.full(p_bar, np.nan)
+    phis = []
+    lev = phi = None
+    for p in range(1, p_bar + 1):
+        yp = y[:m + p]
+        if p == 1:
+            lev = leverage_p1(yp)
+        else:
+            lev, _, rr[p - 1] = leverage_step(yp, p, phi, lev)
+        pi = lev / p
+        rows = leverage_sample(lev, unif[p - 1])
+        phi = compressed_ols(yp, p, rows, pi[rows], c)
+        tau[p - 1] = phi[p - 1]
+        rows_all[p - 1] = rows
+        lev_sum[p - 1] = math.fsum(lev.tolist())
+        phis.append(phi)
+    thr = 1.96 / math.sqrt(c)
+    order = max([h for h in range(1, p_bar + 1) if abs(tau[h - 1]) >= thr], default=0)
+    return LsarResult(tau=tau, order=order, phi=phis, rows=rows_all, lev_sum=lev_sum, rr=rr)

@@ -164,3 +164,11 @@ def batch_shapes(count: int, *, config_id: int, n_lo: float, n_hi: float, p_lo: 
         p = rng.integers(p_lo, p_hi + 1, size=count).astype(np.int64)
     n = np.maximum(n, p + 2)
     return n, p
+
+
+def lsar_uniforms(p_bar: int, c: int, *, config_id: int, series_index: int = 0,
+                  base_seed: int = BASE_SEED) -> np.ndarray:
+    """The random draws of a leverage-sampling sweep over lags 1..p_bar: row h-1 holds the c uniforms in [0, 1)
+    that pick the sampled rows at lag h (inverse-CDF sampling with replacement). Passed to the sampler as input."""
+    rng = rng_for(config_id, 2 * 10**9 + series_index, base_seed)
+    return np.ascontiguousarray(rng.random((p_bar, c)))

@@ -286,3 +286,96 @@ def test_pacf_pins():
         z[t] = 0.75 * z[t - 1] - 0.25 * z[t - 2]
     tau2, _ = oracle.pacf(z, 2)
     assert tau2[1] == pytest.approx(-0.25, abs=1e-12)
+
+
+# ---- Algorithm "LSAR" (Section 3.1) -------------------------------------------------------------------------
+def test_leverage_sample_pins():
+    # a linear scan over the running sum (brute force) on tiny inputs, with zero-score rows that can never be drawn
+    rng = np.random.default_rng(11)
+    lev = np.array([0.0, 0.5, 0.0, 1.25, 0.25, 0.0, 2.0])
+    u = np.concatenate([[0.0, 0.999999], rng.random(500)])
+    got = oracle.leverage_sample(lev, u)
+    total = sum(lev)
+    for uk, g in zip(u, got):
+        run, want = 0.0, len(lev) - 1
+        for i, v in enumerate(lev):
+            run += v
+            if run > uk * total:
+                want = i
+                break
+        assert g == want
+    assert not np.isin(got, [0, 2, 5]).any()
+    # frequencies follow lev / sum(lev) (4 sigma over 200,000 draws)
+    u = rng.random(200_000)
+    counts = np.bincount(oracle.leverage_sample(lev, u), minlength=lev.size)
+    prob = lev / total
+    assert np.all(np.abs(counts - u.size * prob) <= 4 * np.sqrt(u.size * prob * (1 - prob)) + 1e-9)
+
+
+def test_compressed_ols_pins():
+    # hand-written rows of eq. (xphi) (golden n = 5, p = 2): rows 0 and 2 with equal pi give the plain LS fit of
+    # those two rows, here an exactly determined 2x2 system
+    g = _golden("xphi_n5_p2.json")
+    y = np.array(g["y"], dtype=np.float64)
+    X = np.array(g["X"], dtype=np.float64)[[0, 2]]
+    b = np.array(g["b"], dtype=np.float64)[[0, 2]]
+    phi = oracle.compressed_ols(y, 2, [0, 2], [0.5, 0.5], 2)
+    assert phi == pytest.approx(np.linalg.solve(X, b), abs=1e-12)
+    # the 1 / sqrt(c pi) rescale: row i drawn k_i times with pi_i = k_i / c makes S^T S = I, so the compressed
+    # problem is the full one and its minimiser is the exact OLS fit (the QR oracle)
+    s = ar_series(300, 3, config_id=5)
+    m = s.y.size - 3
+    k = np.random.default_rng(2).integers(1, 5, size=m)
+    rows = np.repeat(np.arange(m), k)
+    c = int(k.sum())
+    phi = oracle.compressed_ols(s.y, 3, rows, k[rows] / c, c)
+    assert phi == pytest.approx(oracle.ols_qr(s.y, 3).phi, rel=1e-10, abs=1e-12)
+    # without the rescale the same rows give a different fit (the pin above depends on it)
+    phi_unscaled = oracle.compressed_ols(s.y, 3, rows, np.full(rows.size, 1.0 / c), c)
+    assert np.max(np.abs(phi_unscaled - phi)) > 1e-6
+
+
+def test_lsar_pins():
+    from synthetic import lsar_uniforms
+    s = ar_series(20_000, 3, config_id=7, series_index=2, root_lo=1.1, root_hi=1.6)
+    p_bar, c = 10, 2000
+    u = lsar_uniforms(p_bar, c, config_id=7, series_index=2)
+    r = oracle.lsar(s.y, p_bar, c, u)
+    m = s.y.size - p_bar
+    # eq. (FALS) adds r^2 / ||r||^2 (sum 1) per lag to the exact p = 1 scores (sum 1): the scores sum to p
+    assert r.lev_sum == pytest.approx(np.arange(1, p_bar + 1), rel=1e-12)
+    # lag 1 in closed form: with pi_i = y_i^2 / sum y^2 every weighted row has w^2 x^2 = sum y^2 / c, so
+    # phi_1 = mean over the draws of y[i + 1] / y[i]
+    rows = r.rows[0]
+    assert r.tau[0] == pytest.approx(np.mean(s.y[rows + 1] / s.y[rows]), rel=1e-11)
+    assert np.all((r.rows >= 0) & (r.rows < m))
+    # the compressed fits track the exact PACF (oracle.pacf on the same series) within a few 1/sqrt(c)
+    tau_exact, _ = oracle.pacf(s.y, p_bar)
+    assert np.max(np.abs(r.tau - tau_exact)) <= 3.0 / math.sqrt(c)
+    # the true order's coefficient is far above the threshold 1.96 / sqrt(c)
+    assert abs(r.tau[2]) > 5 * 1.96 / math.sqrt(c) and r.order >= 3
+
+
+def test_lsar_planted_mistakes_are_caught(monkeypatch):
+    """Plant mistakes in the LSAR oracle (CPU only) and check the pins of test_lsar_pins notice them."""
+    from synthetic import lsar_uniforms
+    s = ar_series(5000, 2, config_id=7, series_index=3, root_lo=1.1, root_hi=1.6)
+    u = lsar_uniforms(4, 500, config_id=7, series_index=3)
+    real_ols, real_step = tols.compressed_ols, tols.leverage_step
+
+    def shifted_ols(y, p, rows, pi_rows, c):           # sampled responses one row late
+        phi_ = real_ols(y[1:], p, rows, pi_rows, c)
+        return phi_
+
+    monkeypatch.setattr(tols, "compressed_ols", shifted_ols)
+    r = tols.lsar(s.y, 4, 500, u)
+    assert abs(r.tau[0] - np.mean(s.y[r.rows[0] + 1] / s.y[r.rows[0]])) > 1e-6
+    monkeypatch.setattr(tols, "compressed_ols", real_ols)
+
+    def unnormalised_step(y, p, phi_hat, lev_prev):   # r^2 added without dividing by ||r||^2
+        lev, pi, rr = real_step(y, p, phi_hat, lev_prev)
+        return lev + (lev - lev_prev) * (rr - 1.0), pi, rr
+
+    monkeypatch.setattr(tols, "leverage_step", unnormalised_step)
+    r = tols.lsar(s.y, 4, 500, u)
+    assert not np.allclose(r.lev_sum, np.arange(1, 5), rtol=1e-6)

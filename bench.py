@@ -55,10 +55,15 @@ def parse():
     ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
     ap.add_argument("--batch-series", type=int, default=1024,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
+    ap.add_argument("--lsar-only", action="store_true",
+                    help="time only Algorithm LSAR on the bench series (--lsar-lags, --lsar-c)")
     ap.add_argument("--batch-only", action="store_true",
                     help="solve the batch of --batch-series series once in float64 and print its timing (profiling)")
     ap.add_argument("--pacf-lags", type=int, default=120,
                     help="order sweep: PACF lags fitted on the bench series (0 = skip)")
+    ap.add_argument("--lsar-lags", type=int, default=120,
+                    help="Algorithm LSAR on the bench series: lags 1 .. p_bar (0 = skip)")
+    ap.add_argument("--lsar-c", type=int, default=2000, help="Algorithm LSAR: rows sampled per lag")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
     return ap.parse_args()
@@ -326,6 +331,8 @@ def run_ours(args, wl):
     if serve_in:
         serving = run_serving(tols, serve_in, args)
     order_sweep = run_order_sweep(tols, torch, s.y, args) if args.pacf_lags > 0 else None
+    lsar = (run_lsar(tols, torch, s.y, args, order_sweep["ms_per_sweep"] if order_sweep and
+                     order_sweep["lags"] == args.lsar_lags else None) if args.lsar_lags > 0 else None)
 
     hbm_peak, hbm_src = peaks()
     r64, rmx = results["fp64"], results["mixed"]
@@ -406,6 +413,7 @@ def run_ours(args, wl):
            "batched_mixed": batched_mixed,
            "serving": serving,
            "order_sweep": order_sweep,
+           "lsar": lsar,
            "gpu_launches": int(r64["launches"] + rmx["launches"]),
            "clocks": r64["clocks"],
            "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r64["prof"].items() if v[0]}}
@@ -500,6 +508,33 @@ def run_order_sweep(tols, torch, y, args):
             "max_iters": int(max(i["iters"] for i in infos)),
             "workload": "AR(h), h = 1 .. lags, fitted to the bench series (n = 2^22), float64, tol 1e-10, "
                         "end to end from host memory"}
+
+
+def run_lsar(tols, torch, y, args, exact_ms):
+    """Algorithm LSAR on the bench series: compressed fits of lags 1 .. p_bar with c sampled rows each, series and
+    uniforms resident on the device (toeplitz_ols_lsar); timed with CUDA events after one warm-up sweep."""
+    from synthetic import lsar_uniforms
+    p_bar, c = args.lsar_lags, args.lsar_c
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_u = torch.tensor(lsar_uniforms(p_bar, c, config_id=2), dtype=torch.float64, device="cuda")
+    times = []
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        tau, order, _, rc = tols.toeplitz_ols_lsar(ctx, d_y, y.size, p_bar, c, d_u)     # warm-up
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tau, order, _, rc = tols.toeplitz_ols_lsar(ctx, d_y, y.size, p_bar, c, d_u)
+            times.append(time.perf_counter() - t0)
+    ms = min(times) * 1e3
+    res = {"lags": p_bar, "c": c, "ms_per_sweep": ms, "lags_per_s": p_bar / (ms * 1e-3), "order_estimate": order,
+           "status": rc, "tau_finite": bool(all(math.isfinite(t) for t in tau)),
+           "workload": "Algorithm LSAR on the bench series (n = 2^22): lags 1 .. p_bar on n - p_bar rows, c rows "
+                       "sampled per lag, series and uniforms in HBM, best of 3 sweeps (host clock around the call, "
+                       "which returns after the device finishes)"}
+    if exact_ms:
+        res["exact_sweep_ms"] = exact_ms
+        res["speedup_vs_exact_sweep"] = exact_ms / ms
+    return res
 
 
 def run_serving(tols, serve_in, args):
@@ -626,6 +661,11 @@ def main():
         run_kernel_only(args, wl)
     elif args.batch_only:
         run_batch_only(args)
+    elif args.lsar_only:
+        import torch
+
+        import paper_2112_12994_gb300 as tols
+        print(json.dumps({"lsar_only": True, **run_lsar(tols, torch, make_series(wl).y, args, None)}), flush=True)
     else:
         run_ours(args, wl)
 

@@ -271,6 +271,26 @@ int toeplitz_ols_leverage_p1(tols_ctx* ctx, const double* d_y, long long n, doub
 int toeplitz_ols_leverage_step(tols_ctx* ctx, const double* d_y, long long n, int p, const double* d_phi_hat,
                                const double* d_lev_prev, double* d_lev, double* d_pi, double* rnorm2);
 
+/* Algorithm "LSAR" (Section 3.1): PACF estimates from compressed fits, lags p = 1 .. p_bar, on the device.
+ * Every lag uses the same m = n - p_bar rows: lag p fits the order-p problem of eq. (xphi) on y[0 .. m + p).
+ *   scores   lag 1: the exact l_1(i) = y[i]^2 / sum_{t<m} y[t]^2; lag p >= 2: eq. (FALS),
+ *            l_p = l_{p-1} + r^2 / ||r||^2 with r the full-data residual of lag p-1's estimate, eq. (FAR);
+ *   sampling c rows with replacement from pi = l_p / p, eq. (FASD): draw k takes the first row whose running sum of
+ *            l_p exceeds d_unif[(p-1) c + k] * sum(l_p) (the last row with a positive score if rounding leaves
+ *            none), and scales it by 1 / sqrt(c pi_i);
+ *   solve    phi_hat_p = the minimiser of the compressed problem, by Cholesky of the sampled X^T W X and one
+ *            corrected semi-normal-equation step; tau[p-1] = phi_hat_p[p-1], the PACF estimate at lag p.
+ * The order estimate is the largest p with |tau[p-1]| >= 1.96 / sqrt(c) (0 if none).
+ * d_y: n doubles (device). d_unif: p_bar x c uniforms in [0, 1) (device, row p-1 for lag p): the random draws are
+ * inputs. tau: p_bar doubles (host). order: host, nullable. phi: host, nullable, p_bar doubles: phi_hat at the
+ * order estimate, zero-padded (all zero if the order is 0). d_rows: device, nullable, p_bar x c sampled rows
+ * (int64, row p-1 for lag p). d_phi_all: device, nullable, p_bar x p_bar: row p-1 holds phi_hat_p, zero-padded.
+ * Needs 1 <= p_bar <= 256, c >= p_bar, n > p_bar. Returns TOLS_NOT_CONVERGED if a sampled X^T W X is not positive
+ * definite (tau is NaN from that lag on; the message names the lag). Runs on the context's stream and returns
+ * after it finishes. */
+int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, int c, const double* d_unif,
+                      double* tau, int* order, double* phi, long long* d_rows, double* d_phi_all);
+
 /* ---- instrumentation (no counterpart in the paper: measurement of this library's own kernels) ----------
  * toeplitz_ols_profile(ctx, 1) clears the counters and starts timing every kernel the context launches with
  * a pair of CUDA events on the context's stream; 0 stops timing (counters are kept).

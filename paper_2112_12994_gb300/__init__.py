@@ -118,6 +118,7 @@ SIGNATURES = {
     "toeplitz_ols_residual": (_I, [_P, _P, _LL, _I, _P, _P, _D]),
     "toeplitz_ols_leverage_p1": (_I, [_P, _P, _LL, _P]),
     "toeplitz_ols_leverage_step": (_I, [_P, _P, _LL, _I, _P, _P, _P, _P, _D]),
+    "toeplitz_ols_lsar": (_I, [_P, _P, _LL, _I, _I, _P, _P, ctypes.POINTER(_I), _P, _P, _P]),
     "toeplitz_ols_server_config_default": (None, [ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_destroy": (_I, [_P]),
@@ -347,6 +348,18 @@ def toeplitz_ols_leverage_step(ctx: Context, d_y, n: int, p: int, d_phi_hat, d_l
     ctx.check(lib.toeplitz_ols_leverage_step(ctx.handle, _ptr(d_y), n, p, _ptr(d_phi_hat), _ptr(d_lev_prev),
                                              _ptr(d_lev), _ptr(d_pi), ctypes.byref(rr)), "toeplitz_ols_leverage_step")
     return rr.value
+
+
+def toeplitz_ols_lsar(ctx: Context, d_y, n: int, p_bar: int, c: int, d_unif, d_rows=None, d_phi_all=None):
+    """Algorithm LSAR on a device series with device uniforms (p_bar x c) -> (tau array of p_bar PACF estimates,
+    estimated order, phi_hat at that order (p_bar doubles, zero-padded), status)."""
+    tau = np.zeros(int(p_bar), dtype=np.float64)
+    phi = np.zeros(int(p_bar), dtype=np.float64)
+    order = ctypes.c_int(0)
+    rc = lib.toeplitz_ols_lsar(ctx.handle, _ptr(d_y), int(n), int(p_bar), int(c), _ptr(d_unif), tau.ctypes.data,
+                               ctypes.byref(order), phi.ctypes.data, _ptr(d_rows), _ptr(d_phi_all))
+    ctx.check(rc, "toeplitz_ols_lsar")
+    return tau, order.value, phi, rc
 
 
 def toeplitz_ols_profile(ctx: Context, enable: bool):

@@ -51,7 +51,7 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec, lsar;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -1462,7 +1462,7 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
                     &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
-                    &ctx->spec64, &ctx->b_spec};
+                    &ctx->spec64, &ctx->b_spec, &ctx->lsar};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -1594,6 +1594,120 @@ int toeplitz_ols_pacf(tols_ctx* ctx, const double* y, long long n, int h_max, do
     *order = o;
   }
   return worst;
+}
+
+int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, int c, const double* d_unif,
+                      double* tau, int* order, double* phi, long long* d_rows, double* d_phi_all) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (!d_y || !d_unif || !tau) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  if (p_bar < 1 || p_bar > kLsarMaxP) return fail(ctx, TOLS_ERR_ARG, "p_bar out of range [1, 256]");
+  if (c < p_bar) return fail(ctx, TOLS_ERR_ARG, "need c >= p_bar");
+  const long long m = n - p_bar;   // rows at every lag
+  if (m < 1) return fail(ctx, TOLS_ERR_ARG, "need n > p_bar");
+  cudaSetDevice(ctx->device);
+  const long long nb = (m + kLsarBlock - 1) / kLsarBlock;
+  const long long tri_max = lsar_tri(p_bar);
+  const int ng = std::max(1, std::min(ctx->sms, (c + 7) / 8));
+  const size_t p2 = (size_t)p_bar * p_bar;
+  // one buffer: lev, bsum, bpre, w2, rw, Gram partials, G, the global Cholesky scratch, tau, phi per lag,
+  // ||r||^2, the leverage-p1 scratch, then the sampled rows (int64) and the status word
+  const size_t lev_scr = (size_t)((m + 4095) / 4096) + 64;
+  const size_t nd = (size_t)m + nb + (nb + 1) + 2 * (size_t)c + ng * (size_t)tri_max + tri_max +
+                    (p_bar > kLsarSmemP ? p2 : 0) + p_bar + (d_phi_all ? 0 : p2) + 8 + lev_scr;
+  const size_t bytes = sizeof(double) * nd + sizeof(long long) * (d_rows ? 0 : (size_t)c) + 256;
+  int rc;
+  if ((rc = ensure(ctx, ctx->lsar, bytes))) return rc;
+  if ((rc = ensure(ctx, ctx->rbuf, sizeof(double) * (size_t)m))) return rc;
+  double* q = (double*)ctx->lsar.p;
+  double* lev = q; q += m;
+  double* bsum = q; q += nb;
+  double* bpre = q; q += nb + 1;
+  double* w2 = q; q += c;
+  double* rw = q; q += c;
+  double* part = q; q += ng * (size_t)tri_max;
+  double* G = q; q += tri_max;
+  double* Lg = nullptr;
+  if (p_bar > kLsarSmemP) { Lg = q; q += p2; }
+  double* tau_dev = q; q += p_bar;
+  double* phi_all = d_phi_all;
+  if (!phi_all) { phi_all = q; q += p2; }
+  double* rr = q; q += 8;
+  double* lscr = q; q += lev_scr;
+  long long* rows_tmp = (long long*)q;
+  int* status = (int*)(rows_tmp + (d_rows ? 0 : c));
+  double* r = (double*)ctx->rbuf.p;
+  // buffers for the residual passes, sized for the largest order
+  Work w;
+  if ((rc = prepare_work(ctx, d_y, n, p_bar, false, false, w))) return rc;
+  const bool use_fft = p_bar - 1 >= kLsarFftMinOrder && m >= (1LL << 16);
+  const int pp_fft = pad_p(p_bar);
+  if (use_fft) RUN(fft_spectra(ctx, w, 1, d_y, n, m, pp_fft, true));
+  void* spec = ctx->spec64.p;
+  CK(cudaMemsetAsync(phi_all, 0, sizeof(double) * p2, ctx->stream));
+  CK(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
+  for (int p = 1; p <= p_bar; ++p) {
+    // eq. (FALS): exact scores at lag 1, else add the full-data residual of lag p-1's estimate, eq. (FAR)
+    if (p == 1) {
+      RUN(run_small(ctx, 12, [&] { return launch_leverage_p1(d_y, m + 1, lev, lscr, ctx->stream); }));
+    } else {
+      const int qo = p - 1;   // the order-(p-1) problem on y[0 .. m + p - 1): m rows
+      if ((rc = prepare_work(ctx, d_y, m + qo, qo, false, false, w))) return rc;
+      const bool fft = use_fft && qo >= kLsarFftMinOrder;
+      const int pp = fft ? pp_fft : pad_p(qo);
+      PassArgs<double> a = base_args<double>(w, d_y, m + qo, qo, pp);
+      a.d = phi_all + (size_t)(p - 2) * p_bar;
+      a.u_old = d_y + qo;
+      a.coef_host = 1.0;
+      a.u_new = r;
+      a.nlag = 0;
+      a.tail = TAIL_STORE;
+      a.out_t = nullptr;
+      a.out_n2 = rr;
+      if (fft) {
+        a.fft = 1;
+        a.w.wspec64 = spec;
+      }
+      RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, fft ? 1 : 0)));
+    }
+    long long* rows_p = d_rows ? d_rows + (size_t)(p - 1) * c : rows_tmp;
+    RUN(run_small(ctx, 12, [&] { return launch_lsar_lev(p == 1 ? nullptr : r, rr, lev, m, bsum, status, ctx->stream); }));
+    RUN(run_small(ctx, 12, [&] { return launch_lsar_prefix(bsum, nb, bpre, status, ctx->stream); }));
+    RUN(run_small(ctx, 12, [&] {
+      return launch_lsar_sample(lev, m, bsum, bpre, d_unif + (size_t)(p - 1) * c, c, p, rows_p, w2, status,
+                                ctx->stream);
+    }));
+    RUN(run_small(ctx, 12, [&] { return launch_lsar_gram(d_y, p, rows_p, w2, c, ng, part, G, status, ctx->stream); }));
+    RUN(run_small(ctx, 12, [&] {
+      return launch_lsar_solve(G, p, d_y, rows_p, w2, c, Lg, rw, phi_all + (size_t)(p - 1) * p_bar, tau_dev, p,
+                               status, ctx->stream);
+    }));
+  }
+  int h_status = 0;
+  CK(cudaMemcpyAsync(tau, tau_dev, sizeof(double) * p_bar, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // Algorithm "LSAR": the order estimate is the largest lag with |tau_p| >= 1.96 / sqrt(c)
+  int o = 0;
+  const double thr = 1.96 / sqrt((double)c);
+  for (int p = 1; p <= p_bar; ++p)
+    if (fabs(tau[p - 1]) >= thr) o = p;
+  if (order) *order = o;
+  if (phi) {
+    if (o > 0) {
+      CK(cudaMemcpyAsync(phi, phi_all + (size_t)(o - 1) * p_bar, sizeof(double) * p_bar, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      for (int j = 0; j < p_bar; ++j) phi[j] = 0.0;
+    }
+  }
+  if (h_status) {
+    char msg[96];
+    snprintf(msg, sizeof msg, "sampled Gram matrix not positive definite at lag %d", h_status);
+    ctx->err = msg;
+    return TOLS_NOT_CONVERGED;
+  }
+  return TOLS_OK;
 }
 
 int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,

@@ -274,7 +274,8 @@ __device__ __forceinline__ void acc_add(double2& s, V v) {
 // (M + 1 entries, global). Returns this thread's part of ||u||^2.
 template <typename T>
 __device__ double fft_tile(FftSmem<T>& sm, long long m, int L, const T* u_old, T* u_new, double coef, long long i0,
-                           const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wt) {
+                           const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wt,
+                           bool lags) {
   using V = typename FftCfg<T>::V;
   constexpr int M = FftCfg<T>::N / 2;
   const T sc = (T)(1.0 / (8.0 * M));
@@ -311,6 +312,7 @@ __device__ double fft_tile(FftSmem<T>& sm, long long m, int L, const T* u_old, T
     sm.B[pix(j)] = v;
   }
   __syncthreads();
+  if (!lags) return (double)nn;   // no X^T u wanted (nlag == 0): u and ||u||^2 only
   fft_complex<V, T, M>(sm.B, sm.A, tw, false);
   // S += W . conj(U)
   for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
@@ -438,10 +440,10 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
     __syncthreads();
     V* wt = wspec + (size_t)tile * (M + 1);
     if (a.gram) fft_gram_tile<T>(sm, a.y, a.n, a.m, L, p_pad, nlag, tile * L, tw, wt, corr);
-    else n2 += fft_tile<T>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt);
+    else n2 += fft_tile<T>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt, nlag > 0);
   }
   __syncthreads();
-  if (blockIdx.x < ntiles) fft_finish_lags<T>(sm, nlag, tw);
+  if (blockIdx.x < ntiles && nlag > 0) fft_finish_lags<T>(sm, nlag, tw);
   __syncthreads();
   const double n2_cta = block_sum(n2, sm.scratch);
   for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
       __syncthreads();
       V* wt = reinterpret_cast<V*>(w.wspec64) + (size_t)t * (M + 1);
       if (gram) fft_gram_tile<T>(sm, w.y64, w.n, w.m, L, pg, nlag, t * L, tw, wt, corr);
-      else n2 += fft_tile<T>(sm, w.m, L, u_old, u_new, coef, t * L, tw, wt);
+      else n2 += fft_tile<T>(sm, w.m, L, u_old, u_new, coef, t * L, tw, wt, true);
     }
     __syncthreads();
     fft_finish_lags<T>(sm, nlag, tw);

@@ -200,4 +200,26 @@ cudaError_t launch_leverage_step(const double* r, long long m, int p, const doub
                                  double* lev, double* pi, double* unused, cudaStream_t s);
 cudaError_t launch_check_finite(const double* y, long long n, int* flag, cudaStream_t s);
 
+// Algorithm "LSAR" (Section 3.1), tols_lsar.cu.
+constexpr int kLsarMaxP = 256;          // largest p_bar
+constexpr int kLsarBlock = 512;         // rows per sampling block (one warp scans it in 16 chunks of 32)
+constexpr int kLsarChunk = 16;          // sampled rows staged in shared memory at a time by the Gram kernel
+constexpr int kLsarSolveThreads = 512;  // threads of the one-CTA Cholesky solve
+constexpr int kLsarSmemP = 144;         // the solve keeps its Cholesky factor in shared memory up to this order
+constexpr int kLsarFftMinOrder = 32;    // full-data residual by the FFT pass from this order (and 2^16 rows) up
+__host__ __device__ constexpr long long lsar_tri(int p) { return (long long)(p + 1) * (p + 2) / 2; }
+size_t lsar_solve_smem(int p);
+size_t lsar_gram_smem(int p);
+cudaError_t launch_lsar_lev(const double* r, const double* rr, double* lev, long long m, double* bsum,
+                            const int* status, cudaStream_t s);
+cudaError_t launch_lsar_prefix(const double* bsum, long long nb, double* bpre, const int* status, cudaStream_t s);
+cudaError_t launch_lsar_sample(const double* lev, long long m, const double* bsum, const double* bpre,
+                               const double* unif, int c, int p, long long* rows, double* w2, const int* status,
+                               cudaStream_t s);
+cudaError_t launch_lsar_gram(const double* y, int p, const long long* rows, const double* w2, int c, int ng,
+                             double* part, double* G, const int* status, cudaStream_t s);
+cudaError_t launch_lsar_solve(const double* G, int p, const double* y, const long long* rows, const double* w2,
+                              int c, double* Lg, double* rw, double* phi, double* tau, int lag, int* status,
+                              cudaStream_t s);
+
 }  // namespace tols

@@ -74,3 +74,38 @@ def test_bench_size_fused_pass_sampled(tols, series):
         [np.dot(np.abs(u), np.abs(y[P - 1 - j: P - 1 - j + m])) for j in range(P)])
     assert np.all(np.abs(t - ref_t) <= bound)
     assert n2 == pytest.approx(float(u @ u), rel=64 * U64)
+
+
+def test_bench_workload_lsar(tols, series):
+    """Algorithm LSAR at the bench's size (p_bar = 120, c = 2000): lags 1 and 2 against the oracle on the full
+    data (their scores need only y and phi_hat_1), every lag against the exact PACF within the sampling error, and
+    a bitwise repeat."""
+    import torch
+    from synthetic import lsar_uniforms
+    p_bar, c = 120, 2000
+    y = series.y
+    m = y.size - p_bar
+    unif = lsar_uniforms(p_bar, c, config_id=2)
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_u = torch.tensor(unif, dtype=torch.float64, device="cuda")
+    outs = []
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        for _ in range(2):
+            d_rows = torch.empty((p_bar, c), dtype=torch.int64, device="cuda")
+            d_phi = torch.empty((p_bar, p_bar), dtype=torch.float64, device="cuda")
+            tau, order, phi, rc = tols.toeplitz_ols_lsar(ctx, d_y, y.size, p_bar, c, d_u, d_rows, d_phi)
+            assert rc == tols.TOLS_OK
+            outs.append((tau, d_rows.cpu().numpy(), d_phi.cpu().numpy()))
+        tau_exact, _, _, _ = tols.toeplitz_ols_pacf(ctx, y, p_bar, 1e-10)
+    tau, rows, phi_all = outs[0]
+    assert np.array_equal(outs[1][0], tau) and np.array_equal(outs[1][1], rows) and np.array_equal(outs[1][2], phi_all)
+    assert np.all((rows >= 0) & (rows < m))
+    lev1 = oracle.leverage_p1(y[:m + 1])
+    assert np.array_equal(rows[0], oracle.leverage_sample(lev1, unif[0]))
+    phi1 = oracle.compressed_ols(y[:m + 1], 1, rows[0], lev1[rows[0]], c)
+    assert phi_all[0, 0] == pytest.approx(phi1[0], rel=1e-11)
+    lev2, pi2, _ = oracle.leverage_step(y[:m + 2], 2, phi_all[0, :1], lev1)
+    assert np.array_equal(rows[1], oracle.leverage_sample(lev2, unif[1]))
+    phi2 = oracle.compressed_ols(y[:m + 2], 2, rows[1], pi2[rows[1]], c)
+    assert np.linalg.norm(phi_all[1, :2] - phi2) <= 1e-9 * np.linalg.norm(phi2)
+    assert np.max(np.abs(tau - tau_exact)) <= 8.0 / math.sqrt(c)

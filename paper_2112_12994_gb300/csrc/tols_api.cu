@@ -1609,11 +1609,12 @@ int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, 
   const long long tri_max = lsar_tri(p_bar);
   const int ng = std::max(1, std::min(ctx->sms, (c + 7) / 8));
   const size_t p2 = (size_t)p_bar * p_bar;
-  // one buffer: lev, bsum, bpre, w2, rw, Gram partials, G, the global Cholesky scratch, tau, phi per lag,
-  // ||r||^2, the leverage-p1 scratch, then the sampled rows (int64) and the status word
+  // one buffer: lev, bsum, bpre, w2, Gram partials, G, the Cholesky factor and its reciprocal diagonal, the
+  // refinement partials, tau, phi per lag, ||r||^2, the leverage-p1 scratch, then the sampled rows (int64) and
+  // the status word
   const size_t lev_scr = (size_t)((m + 4095) / 4096) + 64;
-  const size_t nd = (size_t)m + nb + (nb + 1) + 2 * (size_t)c + ng * (size_t)tri_max + tri_max +
-                    (p_bar > kLsarSmemP ? p2 : 0) + p_bar + (d_phi_all ? 0 : p2) + 8 + lev_scr;
+  const size_t nd = (size_t)m + nb + (nb + 1) + (size_t)c + ng * (size_t)tri_max + tri_max + p2 + p_bar +
+                    ng * (size_t)p_bar + p_bar + (d_phi_all ? 0 : p2) + 8 + lev_scr;
   const size_t bytes = sizeof(double) * nd + sizeof(long long) * (d_rows ? 0 : (size_t)c) + 256;
   int rc;
   if ((rc = ensure(ctx, ctx->lsar, bytes))) return rc;
@@ -1623,11 +1624,11 @@ int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, 
   double* bsum = q; q += nb;
   double* bpre = q; q += nb + 1;
   double* w2 = q; q += c;
-  double* rw = q; q += c;
   double* part = q; q += ng * (size_t)tri_max;
   double* G = q; q += tri_max;
-  double* Lg = nullptr;
-  if (p_bar > kLsarSmemP) { Lg = q; q += p2; }
+  double* Lg = q; q += p2;
+  double* rdg = q; q += p_bar;
+  double* gpart = q; q += ng * (size_t)p_bar;
   double* tau_dev = q; q += p_bar;
   double* phi_all = d_phi_all;
   if (!phi_all) { phi_all = q; q += p2; }
@@ -1678,8 +1679,8 @@ int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, 
     }));
     RUN(run_small(ctx, 12, [&] { return launch_lsar_gram(d_y, p, rows_p, w2, c, ng, part, G, status, ctx->stream); }));
     RUN(run_small(ctx, 12, [&] {
-      return launch_lsar_solve(G, p, d_y, rows_p, w2, c, Lg, rw, phi_all + (size_t)(p - 1) * p_bar, tau_dev, p,
-                               status, ctx->stream);
+      return launch_lsar_solve(G, p, d_y, rows_p, w2, c, ng, Lg, rdg, gpart, phi_all + (size_t)(p - 1) * p_bar,
+                               tau_dev, p, status, ctx->stream);
     }));
   }
   int h_status = 0;

@@ -19,6 +19,23 @@ constexpr int kGroup = 16;               // CTAs per first-level reduction group
 constexpr int kMaxGrid = 152 * 4;        // upper bound on pass grid size (partials buffer rows)
 constexpr int kMaxGroups = (kMaxGrid + kGroup - 1) / kGroup;
 
+// 1/sqrt(x) for x > 0 in float64 by Newton-Raphson for f(r) = 1/r^2 - x (r <- r (3 - x r^2) / 2), started from
+// the float reciprocal square root: two steps take the 24-bit start to full float64 accuracy (quadratic
+// convergence). A short chain of FP64 operations, where sqrt followed by a division is a long one.
+// x is first scaled by an even power of two into [1, 4) (exponent arithmetic on the bits), so the float start
+// never overflows or underflows.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return 1.0 / sqrt(x);         // zero, subnormal, inf, nan: the plain way
+  const int kk = (ef - 1023) >> 1;                           // x = xs 4^kk, xs in [1, 4)
+  const double xs = __longlong_as_double(bits - ((long long)(2 * kk) << 52));
+  double r = (double)rsqrtf((float)xs);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  r = r * fma(-0.5 * xs, r * r, 1.5);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)kk << 52));   // r 2^-kk
+}
+
 // Round p up to the lag-chunk granularity used by the direct kernels.
 __host__ __device__ constexpr int pad_p(int p) { return (p + 15) & ~15; }
 
@@ -208,7 +225,8 @@ constexpr int kLsarSolveThreads = 512;  // threads of the one-CTA Cholesky solve
 constexpr int kLsarSmemP = 144;         // the solve keeps its Cholesky factor in shared memory up to this order
 constexpr int kLsarFftMinOrder = 32;    // full-data residual by the FFT pass from this order (and 2^16 rows) up
 __host__ __device__ constexpr long long lsar_tri(int p) { return (long long)(p + 1) * (p + 2) / 2; }
-size_t lsar_solve_smem(int p);
+size_t lsar_chol_smem(int p);
+size_t lsar_correct_smem(int p);
 size_t lsar_gram_smem(int p);
 cudaError_t launch_lsar_lev(const double* r, const double* rr, double* lev, long long m, double* bsum,
                             const int* status, cudaStream_t s);
@@ -219,7 +237,7 @@ cudaError_t launch_lsar_sample(const double* lev, long long m, const double* bsu
 cudaError_t launch_lsar_gram(const double* y, int p, const long long* rows, const double* w2, int c, int ng,
                              double* part, double* G, const int* status, cudaStream_t s);
 cudaError_t launch_lsar_solve(const double* G, int p, const double* y, const long long* rows, const double* w2,
-                              int c, double* Lg, double* rw, double* phi, double* tau, int lag, int* status,
-                              cudaStream_t s);
+                              int c, int ng, double* Lg, double* rdg, double* gpart, double* phi, double* tau,
+                              int lag, int* status, cudaStream_t s);
 
 }  // namespace tols

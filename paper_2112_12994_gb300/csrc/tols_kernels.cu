@@ -975,27 +975,6 @@ __device__ __forceinline__ double* scratch_vec(const Work& w) { return w.t; }  /
 // substitutions are chains of dependent read-modify-writes, which would wait on L2 round trips in global memory.
 constexpr int kPrecondSmemP = 112;
 
-// Sampled-row QR (Section 3.1: a least-squares problem on sampled rows of X): c = kQrRowsPerP p rows of X,
-// evenly spaced (row i_k = floor((k + 1/2) m / c)), gathered into w.qr (c x p, row-major), then Householder QR
-// in float64. R (upper triangular, p x p, row-major) is written to R. Returns false when a column of the sample
-// is (numerically) dependent on the others, i.e. R would be singular.
-// 1/sqrt(x) for x > 0 in float64 by Newton-Raphson for f(r) = 1/r^2 - x (r <- r (3 - x r^2) / 2), started from
-// the float reciprocal square root: two steps take the 24-bit start to full float64 accuracy (quadratic
-// convergence). A short chain of FP64 operations, where sqrt followed by a division is a long one.
-// x is first scaled by an even power of two into [1, 4) (exponent arithmetic on the bits), so the float start
-// never overflows or underflows.
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  const long long bits = __double_as_longlong(x);
-  const int ef = (int)((bits >> 52) & 0x7ff);
-  if (ef == 0 || ef == 0x7ff) return 1.0 / sqrt(x);         // zero, subnormal, inf, nan: the plain way
-  const int kk = (ef - 1023) >> 1;                           // x = xs 4^kk, xs in [1, 4)
-  const double xs = __longlong_as_double(bits - ((long long)(2 * kk) << 52));
-  double r = (double)rsqrtf((float)xs);
-  r = r * fma(-0.5 * xs, r * r, 1.5);
-  r = r * fma(-0.5 * xs, r * r, 1.5);
-  return __longlong_as_double(__double_as_longlong(r) - ((long long)kk << 52));   // r 2^-kk
-}
-
 // s / d by multiplication with magic = ceil(2^32 / d) = (2^32 - 1) / d + 1 (division by an invariant integer,
 // Granlund & Montgomery 1994): exact while s d < 2^32, integer instructions only (the general division
 // sequence goes through float conversions, which are slow here).
@@ -1009,6 +988,10 @@ __device__ __forceinline__ int small_div(int s, unsigned magic) {
 // dependent shared-memory and FP64 operations better than 8.
 constexpr int kPcThreads = 512;
 
+// Sampled-row QR (Section 3.1: a least-squares problem on sampled rows of X): c = kQrRowsPerP p rows of X,
+// evenly spaced (row i_k = floor((k + 1/2) m / c)), gathered into w.qr (c x p, row-major), then Householder QR
+// in float64. R (upper triangular, p x p, row-major) is written to R. Returns false when a column of the sample
+// is (numerically) dependent on the others, i.e. R would be singular.
 __device__ bool sampled_qr(const Work& w, double* R, double* qw, double* qpart, double* scratch) {
   const int p = w.p;
   const long long m = w.m;

@@ -11,8 +11,9 @@
 //                       scan inside the block; the draw's weight p / (c lev_i) = 1 / (c pi_i);
 //   lsar_gram_kernel    per-CTA partial Gram of the weighted sampled rows [b | X] (augmented, upper triangle);
 //   lsar_reduce_kernel  the partials summed in CTA order;
-//   lsar_solve_kernel   one CTA: Cholesky of the sampled X^T W X, then phi = (X^T W X)^-1 X^T W b with one step
-//                       of the corrected semi-normal equations (residual of the sampled rows, second solve).
+//   lsar_chol_kernel    one CTA: Cholesky H = L L^T of the sampled H = X^T W X, phi0 = H^-1 X^T W b;
+//   lsar_refine_kernel  per-CTA partial of g = X^T W (b - X phi0) over the sampled rows;
+//   lsar_correct_kernel one CTA: phi = phi0 + H^-1 g (one step of the corrected semi-normal equations).
 // Every sum runs in a fixed order, so a sweep is bitwise reproducible. Rows with score 0 are never drawn.
 #include <math.h>
 
@@ -24,8 +25,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Inclusive warp scan in a fixed order. The block sums and the sampler both use it, so the running sum at a
-// block's last row equals the block's sum bit for bit.
+// Inclusive warp scan in a fixed order.
 __device__ __forceinline__ double warp_incl_scan(double v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -56,8 +56,9 @@ __device__ __forceinline__ void tri_unpack(long long e, int& q, int& q2) {
 
 }  // namespace
 
-// lev[i] += r[i]^2 / ||r||^2 (r == nullptr: lev unchanged), then bsum[b] = sum of block b's lev in the sampler's
-// order. One warp per block of kLsarBlock rows.
+// lev[i] += r[i]^2 / ||r||^2 (r == nullptr: lev unchanged), then bsum[b] = the sum of block b's lev (a warp sum:
+// the sampler's running sums inside a block may differ from it in the last bit, which its fallback covers).
+// One warp per block of kLsarBlock rows.
 __global__ void __launch_bounds__(256) lsar_lev_kernel(const double* __restrict__ r, const double* rr, double* lev,
                                                        long long m, long long nb, double* bsum, const int* status) {
   if (*status) return;
@@ -66,54 +67,61 @@ __global__ void __launch_bounds__(256) lsar_lev_kernel(const double* __restrict_
   const int lane = threadIdx.x & 31;
   const double inv = r ? 1.0 / *rr : 0.0;
   const long long i0 = b * kLsarBlock;
-  double carry = 0.0;
+  double s = 0.0;
+#pragma unroll 4
   for (int ch = 0; ch < kLsarBlock / 32; ++ch) {
     const long long i = i0 + ch * 32 + lane;
-    double v = 0.0;
     if (i < m) {
-      v = lev[i];
+      double v = lev[i];
       if (r) {
         v = fma(r[i] * r[i], inv, v);
         lev[i] = v;
       }
+      s += v;
     }
-    carry += __shfl_sync(kFull, warp_incl_scan(v), 31);
   }
-  if (lane == 0) bsum[b] = carry;
+  s = warp_sum(s);
+  if (lane == 0) bsum[b] = s;
 }
 
-// bpre[b] = bsum[0] + ... + bsum[b-1], b <= nb (bpre[nb] is the total). One CTA of 1024 threads.
+// bpre[b] = bsum[0] + ... + bsum[b-1], b <= nb (bpre[nb] is the total). One CTA of 1024 threads: thread t sums
+// its contiguous segment of the block sums, a block scan of the segment sums gives each segment's offset, then
+// each thread writes its segment's running sums.
 __global__ void __launch_bounds__(1024) lsar_prefix_kernel(const double* __restrict__ bsum, long long nb,
                                                            double* bpre, const int* status) {
   if (*status) return;
   __shared__ double s_warp[32];
   __shared__ double s_tot;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double carry = 0.0;   // the same value in every thread
-  for (long long base = 0; base < nb; base += 1024) {
-    const long long i = base + threadIdx.x;
-    const double v = i < nb ? bsum[i] : 0.0;
-    const double incl = warp_incl_scan(v);
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      const double wi = warp_incl_scan(s_warp[lane]);
-      const double ex = __shfl_up_sync(kFull, wi, 1);
-      if (lane == 31) s_tot = wi;
-      __syncwarp();
-      s_warp[lane] = lane ? ex : 0.0;
-    }
-    __syncthreads();
-    const double within = __shfl_up_sync(kFull, incl, 1);
-    if (i < nb) bpre[i] = carry + ((lane ? within : 0.0) + s_warp[wid]);
-    carry += s_tot;
-    __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long seg = (nb + 1023) / 1024;
+  const long long j0 = (long long)tid * seg;
+  const long long j1 = j0 + seg < nb ? j0 + seg : nb;
+  double s = 0.0;
+  for (long long j = j0; j < j1; ++j) s += bsum[j];
+  const double incl = warp_incl_scan(s);
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const double wi = warp_incl_scan(s_warp[lane]);
+    const double ex = __shfl_up_sync(kFull, wi, 1);
+    if (lane == 31) s_tot = wi;
+    __syncwarp();
+    s_warp[lane] = lane ? ex : 0.0;
   }
-  if (threadIdx.x == 0) bpre[nb] = carry;
+  __syncthreads();
+  const double within = __shfl_up_sync(kFull, incl, 1);
+  double run = (lane ? within : 0.0) + s_warp[wid];
+  for (long long j = j0; j < j1; ++j) {
+    bpre[j] = run;
+    run += bsum[j];
+  }
+  if (tid == 0) bpre[nb] = s_tot;
 }
 
 // Draw k (one warp): t = unif[k] * total; the row is the first i whose running sum exceeds t, or, if rounding
 // leaves none, the last row with a positive score. rows[k] = i, w2[k] = p / (c lev[i]) = 1 / (c pi_i).
+// The running sums are formed block prefix + lane-segment prefix + rows within the segment; they may differ
+// from a plain left-to-right sum in the last bits, which matters only for a t within rounding of a boundary.
 __global__ void __launch_bounds__(256) lsar_sample_kernel(const double* __restrict__ lev, long long m,
                                                           const double* __restrict__ bsum,
                                                           const double* __restrict__ bpre, long long nb,
@@ -136,19 +144,43 @@ __global__ void __launch_bounds__(256) lsar_sample_kernel(const double* __restri
   }
   const long long b = lo;
   const double base = bpre[b];
-  const long long i0 = b * kLsarBlock;
-  long long pick = -1, last_pos = -1;
-  double carry = 0.0;
-  for (int ch = 0; ch < kLsarBlock / 32 && pick < 0; ++ch) {
-    const long long i = i0 + ch * 32 + lane;
+  // inside block b: lane l holds rows [i0 + 16 l, i0 + 16 l + 16); the crossing lane is the first whose running
+  // sum exceeds t, and it walks its own rows
+  constexpr int kSeg = kLsarBlock / 32;
+  const long long s0 = b * kLsarBlock + (long long)lane * kSeg;
+  double seg = 0.0;
+  long long my_pos = -1;
+#pragma unroll
+  for (int r = 0; r < kSeg; ++r) {
+    const long long i = s0 + r;
     const double v = i < m ? lev[i] : 0.0;
-    const double incl = warp_incl_scan(v);
-    const unsigned hit = __ballot_sync(kFull, i < m && base + (carry + incl) > t);
-    const unsigned pos = __ballot_sync(kFull, i < m && v > 0.0);
-    if (hit) pick = i0 + ch * 32 + (__ffs((int)hit) - 1);
-    else if (pos) last_pos = i0 + ch * 32 + (31 - __clz((int)pos));
-    carry += __shfl_sync(kFull, incl, 31);
+    seg += v;
+    if (v > 0.0) my_pos = i;
   }
+  const double incl = warp_incl_scan(seg);
+  const double up = __shfl_up_sync(kFull, incl, 1);   // every lane takes part in the shuffle
+  const double excl = lane ? up : 0.0;
+  const unsigned hit = __ballot_sync(kFull, base + incl > t);
+  long long pick = -1, last_pos = -1;
+  if (hit) {
+    const int L = __ffs((int)hit) - 1;
+    if (lane == L) {
+      double run = excl;
+      for (int r = 0; r < kSeg && pick < 0; ++r) {
+        const long long i = s0 + r;
+        const double v = i < m ? lev[i] : 0.0;
+        run += v;
+        if (v > 0.0 && base + run > t) pick = i;
+      }
+      if (pick < 0) pick = my_pos;
+    }
+    pick = __shfl_sync(kFull, pick, L);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long other = __shfl_xor_sync(kFull, my_pos, o);
+    my_pos = other > my_pos ? other : my_pos;
+  }
+  last_pos = my_pos;
   if (pick < 0 && last_pos < 0) {
     // no positive score in block b (only past the last positive block): the last earlier block with a positive
     // sum, then its last positive row
@@ -167,6 +199,7 @@ __global__ void __launch_bounds__(256) lsar_sample_kernel(const double* __restri
     }
   }
   if (pick < 0) pick = last_pos >= 0 ? last_pos : m - 1;
+  if (pick >= m) pick = m - 1;   // cannot happen; keeps every later read of y and lev in bounds
   if (lane == 0) {
     rows[k] = pick;
     w2[k] = (double)p / ((double)c * lev[pick]);
@@ -211,89 +244,121 @@ __global__ void __launch_bounds__(256) lsar_gram_kernel(const double* __restrict
   }
 }
 
+// G[e] = the sum over the ng partials, in a fixed order: eight running sums over g = u mod 8, then combined
+// pairwise (independent accumulators keep eight loads in flight).
 __global__ void lsar_reduce_kernel(const double* __restrict__ part, int ng, long long tri, double* G,
                                    const int* status) {
   if (*status) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tri; e += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < ng; ++g) s += part[(size_t)g * tri + e];
-    G[e] = s;
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int g = 0;
+    for (; g + 8 <= ng; g += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += part[(size_t)(g + u) * tri + e];
+    }
+    for (int u = 0; g < ng; ++g, ++u) acc[u] += part[(size_t)g * tri + e];
+    G[e] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
   }
 }
 
 namespace {
 
-// z := L^-1 z (forward) then z := L^-T z (backward), L lower triangular row-major with leading dimension p and
-// reciprocal diagonal rdiag. One warp.
-__device__ void chol_solve_warp(const double* L, const double* rdiag, int p, double* z) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < p; ++k) {
-    const double zk = z[k] * rdiag[k];
-    __syncwarp();
-    if (lane == 0) z[k] = zk;
-    for (int i = k + 1 + lane; i < p; i += 32) z[i] = fma(-L[(size_t)i * p + k], zk, z[i]);
-    __syncwarp();
+// w := L^-1 h (h is overwritten), then x := L^-T w, for L lower triangular (row-major, leading dimension p) with
+// reciprocal diagonal rdiag. The first four warps (one per SM sub-partition) do the work with one named barrier
+// per step; the others wait at the closing __syncthreads. Callers have h, L, rdiag in place before it
+// (visible to the first four warps through a __syncthreads).
+__device__ void chol_solve_cta(const double* L, const double* rdiag, int p, double* h, double* w, double* x) {
+  const int tid = threadIdx.x;
+  if (tid < 128) {
+    for (int k = 0; k < p; ++k) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const double zk = h[k] * rdiag[k];
+      if (tid == 0) w[k] = zk;
+      for (int i = k + 1 + tid; i < p; i += 128) h[i] = fma(-L[(size_t)i * p + k], zk, h[i]);
+    }
+    for (int k = p - 1; k >= 0; --k) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const double xk = w[k] * rdiag[k];
+      if (tid == 0) x[k] = xk;
+      for (int i = tid; i < k; i += 128) w[i] = fma(-L[(size_t)k * p + i], xk, w[i]);
+    }
   }
-  for (int k = p - 1; k >= 0; --k) {
-    const double xk = z[k] * rdiag[k];
-    __syncwarp();
-    if (lane == 0) z[k] = xk;
-    for (int i = lane; i < k; i += 32) z[i] = fma(-L[(size_t)k * p + i], xk, z[i]);
-    __syncwarp();
-  }
+  __syncthreads();
 }
 
 }  // namespace
 
 // One CTA of kLsarSolveThreads. H[j][l] = G[e(1 + j, 1 + l)] (the sampled X^T W X), h[j] = G[e(0, 1 + j)]
-// (X^T W b). L: p x p scratch (shared memory when p <= kLsarSmemP, else Lg in global memory); rw: c doubles of
-// global scratch. Writes phi (p doubles) and tau[lag - 1]; on a pivot that is not positive and finite, phi and
-// tau are NaN and *status becomes lag (later lags are skipped).
-__global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_solve_kernel(
-    const double* __restrict__ G, int p, const double* __restrict__ y, const long long* __restrict__ rows,
-    const double* __restrict__ w2, int c, double* Lg, double* rw, double* phi, double* tau, int lag, int* status) {
+// (X^T W b). Right-looking Cholesky H = L L^T with one barrier per step k: warps 1.. update their rows
+// i >= k + 2 of the trailing triangle from a contiguous copy of column k (cur), write their rows of column k
+// scaled, and copy the updated column k + 1 to the other buffer (nxt); meanwhile thread 0 updates the next
+// pivot, entry (k + 1, k + 1), and forms its reciprocal square root. L works in shared memory when
+// p <= kLsarSmemP, else in place in Lg. Writes L and its reciprocal diagonal to Lg, rdg (for
+// lsar_correct_kernel) and phi0 = H^-1 h to phi. A pivot that is not positive and finite makes phi and
+// tau[lag - 1] NaN and sets *status = lag, which skips every later kernel of the sweep.
+__global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_chol_kernel(const double* __restrict__ G, int p,
+                                                                         double* Lg, double* rdg, double* phi,
+                                                                         double* tau, int lag, int* status) {
   if (*status) return;
   extern __shared__ double lsm[];
   __shared__ int s_fail;
+  __shared__ double s_piv[2][2];   // per step parity: 1/sqrt(d), 1/d
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int kWarps = kLsarSolveThreads / 32;
   const bool in_smem = p <= kLsarSmemP;
   double* L = in_smem ? lsm : Lg;
-  double* vec = lsm + (in_smem ? (size_t)p * p : 0);
-  double* z = vec;              // p
-  double* x = vec + p;          // p
-  double* rdiag = vec + 2 * p;  // p
-  double* wpart = vec + 3 * p;  // kWarps x p
-  if (tid == 0) s_fail = 0;
+  double* v = lsm + (in_smem ? (size_t)p * p : 0);
+  double* h = v + 2 * p;
+  double* w = v + 3 * p;
+  double* x = v + 4 * p;
+  double* rdiag = v + 5 * p;
   for (int idx = tid; idx < p * p; idx += kLsarSolveThreads) {
     const int i = idx / p, j = idx - i * p;
     L[idx] = j <= i ? G[tri_index(1 + j, 1 + i)] : 0.0;
   }
-  for (int j = tid; j < p; j += kLsarSolveThreads) z[j] = G[tri_index(0, 1 + j)];
-  __syncthreads();
-  // right-looking Cholesky H = L L^T
-  for (int k = 0; k < p; ++k) {
-    if (tid == 0) {
-      const double d = L[(size_t)k * p + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        s_fail = 1;
-      } else {
-        const double l = sqrt(d);
-        L[(size_t)k * p + k] = l;
-        rdiag[k] = 1.0 / l;
-      }
+  for (int j = tid; j < p; j += kLsarSolveThreads) {
+    h[j] = G[tri_index(0, 1 + j)];
+    v[j] = G[tri_index(1, 1 + j)];   // column 0 of H, the first column buffer
+  }
+  if (tid == 0) {
+    const double d = G[tri_index(1, 1)];
+    s_fail = !(d > 0.0) || !isfinite(d);
+    if (!s_fail) {
+      const double r = rsqrt_newton(d);
+      s_piv[0][0] = r;
+      s_piv[0][1] = r * r;
+      rdiag[0] = r;
     }
-    __syncthreads();
-    if (s_fail) break;
-    const double r = rdiag[k];
-    for (int i = k + 1 + tid; i < p; i += kLsarSolveThreads) L[(size_t)i * p + k] *= r;
-    __syncthreads();
-    const int t = p - k - 1;
-    for (int idx = tid; idx < t * t; idx += kLsarSolveThreads) {
-      const int ii = idx / t, jj = idx - ii * t;
-      if (jj <= ii) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        L[(size_t)i * p + j] = fma(-L[(size_t)i * p + k], L[(size_t)j * p + k], L[(size_t)i * p + j]);
+  }
+  __syncthreads();
+  if (tid == 0 && !s_fail) L[0] = G[tri_index(1, 1)] * s_piv[0][0];
+  for (int k = 0; k < p && !s_fail; ++k) {
+    const double r = s_piv[k & 1][0], r2 = s_piv[k & 1][1];
+    const double* cur = v + (k & 1) * p;   // column buffers: v[0, p) and v[p, 2p)
+    double* nxt = v + ((k + 1) & 1) * p;
+    if (wid == 0) {
+      if (tid == 0 && k + 1 < p) {
+        L[(size_t)(k + 1) * p + k] = cur[k + 1] * r;
+        const double d = fma(-cur[k + 1] * r2, cur[k + 1], L[(size_t)(k + 1) * p + k + 1]);
+        if (!(d > 0.0) || !isfinite(d)) {
+          s_fail = 1;
+        } else {
+          const double rn = rsqrt_newton(d);
+          s_piv[(k + 1) & 1][0] = rn;
+          s_piv[(k + 1) & 1][1] = rn * rn;
+          rdiag[k + 1] = rn;
+          L[(size_t)(k + 1) * p + k + 1] = d * rn;
+        }
+      }
+    } else {
+      for (int i = k + 2 + (wid - 1); i < p; i += kWarps - 1) {
+        const double ci = cur[i] * r2;
+        for (int j = k + 1 + lane; j <= i; j += 32) {
+          const double nv = fma(-ci, cur[j], L[(size_t)i * p + j]);
+          L[(size_t)i * p + j] = nv;
+          if (j == k + 1) nxt[i] = nv;
+        }
+        if (lane == 0) L[(size_t)i * p + k] = cur[i] * r;
       }
     }
     __syncthreads();
@@ -306,40 +371,94 @@ __global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_solve_kernel(
     }
     return;
   }
-  // phi = H^-1 h
-  if (wid == 0) chol_solve_warp(L, rdiag, p, z);
+  chol_solve_cta(L, rdiag, p, h, w, x);
+  for (int j = tid; j < p; j += kLsarSolveThreads) {
+    phi[j] = x[j];
+    rdg[j] = rdiag[j];
+  }
+  if (in_smem)
+    for (int idx = tid; idx < p * p; idx += kLsarSolveThreads) Lg[idx] = L[idx];
+}
+
+// CTA g and its draws k (one warp each): rho_k = b_k - x_k . phi0, gpart[g][j] = sum_k w2_k rho_k x_k[j]
+// (x_k[j] = y[p + rows[k] - 1 - j], b_k = y[p + rows[k]]).
+__global__ void __launch_bounds__(256) lsar_refine_kernel(const double* __restrict__ y, int p,
+                                                          const long long* __restrict__ rows,
+                                                          const double* __restrict__ w2, int c, int per_cta,
+                                                          const double* __restrict__ phi0, double* gpart,
+                                                          const int* status) {
+  if (*status) return;
+  extern __shared__ double lsm[];
+  double* ph = lsm;
+  double* gw = lsm + p;   // 8 x p, one row per warp
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int j = tid; j < p; j += 256) ph[j] = phi0[j];
+  for (int j = tid; j < 8 * p; j += 256) gw[j] = 0.0;
   __syncthreads();
-  for (int j = tid; j < p; j += kLsarSolveThreads) x[j] = z[j];
-  __syncthreads();
-  // corrected semi-normal equations: rw_k = w2_k (b_k - x_k . phi), g = sum_k rw_k x_k, phi += H^-1 g
-  for (int k = wid; k < c; k += kWarps) {
-    const long long i = rows[k];
+  const int k0 = blockIdx.x * per_cta;
+  const int k1 = min(c, k0 + per_cta);
+  for (int k = k0 + wid; k < k1; k += 8) {
+    const double* xr = y + p + rows[k] - 1;
     double s = 0.0;
-    for (int j = lane; j < p; j += 32) s = fma(y[p + i - 1 - j], x[j], s);
+    for (int j = lane; j < p; j += 32) s = fma(xr[-j], ph[j], s);
     s = warp_sum(s);
-    if (lane == 0) rw[k] = w2[k] * (y[p + i] - s);
+    const double rho = w2[k] * (xr[1] - s);
+    for (int j = lane; j < p; j += 32) gw[wid * p + j] = fma(rho, xr[-j], gw[wid * p + j]);
   }
   __syncthreads();
-  for (int j = lane; j < p; j += 32) {
+  for (int j = tid; j < p; j += 256) {
     double g = 0.0;
-    for (int k = wid; k < c; k += kWarps) g = fma(rw[k], y[p + rows[k] - 1 - j], g);
-    wpart[wid * p + j] = g;
+    for (int q = 0; q < 8; ++q) g += gw[q * p + j];
+    gpart[(size_t)blockIdx.x * p + j] = g;
+  }
+}
+
+// One CTA of kLsarSolveThreads: g = the sum of the ng partials in CTA order, then phi += H^-1 g with the factor of
+// lsar_chol_kernel (Lg, rdg); tau[lag - 1] = phi[p - 1].
+__global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_correct_kernel(const double* __restrict__ Lg,
+                                                                            const double* __restrict__ rdg, int p,
+                                                                            const double* __restrict__ gpart, int ng,
+                                                                            double* phi, double* tau, int lag,
+                                                                            const int* status) {
+  if (*status) return;
+  extern __shared__ double lsm[];
+  const int tid = threadIdx.x;
+  const bool in_smem = p <= kLsarSmemP;
+  double* Ls = lsm;
+  double* v = lsm + (in_smem ? (size_t)p * p : 0);
+  double* h = v;
+  double* w = v + p;
+  double* x = v + 2 * p;
+  double* rdiag = v + 3 * p;
+  double* red = v + 4 * p;   // kLsarSolveThreads
+  if (in_smem)
+    for (int idx = tid; idx < p * p; idx += kLsarSolveThreads) Ls[idx] = Lg[idx];
+  for (int j = tid; j < p; j += kLsarSolveThreads) rdiag[j] = rdg[j];
+  const int S = kLsarSolveThreads / p > 1 ? kLsarSolveThreads / p : 1;
+  for (int t = tid; t < S * p; t += kLsarSolveThreads) {
+    const int s = t / p, j = t - s * p;
+    double acc = 0.0;
+    for (int g = s; g < ng; g += S) acc += gpart[(size_t)g * p + j];
+    red[t] = acc;
   }
   __syncthreads();
   for (int j = tid; j < p; j += kLsarSolveThreads) {
-    double g = 0.0;
-    for (int w = 0; w < kWarps; ++w) g += wpart[w * p + j];
-    z[j] = g;
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) acc += red[s * p + j];
+    h[j] = acc;
   }
   __syncthreads();
-  if (wid == 0) chol_solve_warp(L, rdiag, p, z);
-  __syncthreads();
-  for (int j = tid; j < p; j += kLsarSolveThreads) phi[j] = x[j] + z[j];
-  if (tid == 0) tau[lag - 1] = x[p - 1] + z[p - 1];
+  chol_solve_cta(in_smem ? Ls : Lg, rdiag, p, h, w, x);
+  for (int j = tid; j < p; j += kLsarSolveThreads) {
+    const double v2 = phi[j] + x[j];
+    phi[j] = v2;
+    if (j == p - 1) tau[lag - 1] = v2;
+  }
 }
 
-size_t lsar_solve_smem(int p) {
-  return sizeof(double) * ((p <= kLsarSmemP ? (size_t)p * p : 0) + (size_t)(3 + kLsarSolveThreads / 32) * p);
+size_t lsar_chol_smem(int p) { return sizeof(double) * ((p <= kLsarSmemP ? (size_t)p * p : 0) + 6 * (size_t)p); }
+size_t lsar_correct_smem(int p) {
+  return sizeof(double) * ((p <= kLsarSmemP ? (size_t)p * p : 0) + 4 * (size_t)p + kLsarSolveThreads);
 }
 
 size_t lsar_gram_smem(int p) { return sizeof(double) * 2 * kLsarChunk * (size_t)(p + 1); }
@@ -372,18 +491,24 @@ cudaError_t launch_lsar_gram(const double* y, int p, const long long* rows, cons
   cudaError_t e = cudaFuncSetAttribute(lsar_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   lsar_gram_kernel<<<ng, 256, smem, s>>>(y, p, rows, w2, c, per_cta, part, tri, status);
-  const int rb = (int)((tri + 255) / 256);
-  lsar_reduce_kernel<<<rb < 1 ? 1 : rb, 256, 0, s>>>(part, ng, tri, G, status);
+  const int rb = (int)((tri + 63) / 64);
+  lsar_reduce_kernel<<<rb < 1 ? 1 : rb, 64, 0, s>>>(part, ng, tri, G, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lsar_solve(const double* G, int p, const double* y, const long long* rows, const double* w2,
-                              int c, double* Lg, double* rw, double* phi, double* tau, int lag, int* status,
-                              cudaStream_t s) {
-  const size_t smem = lsar_solve_smem(p);
-  cudaError_t e = cudaFuncSetAttribute(lsar_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                              int c, int ng, double* Lg, double* rdg, double* gpart, double* phi, double* tau,
+                              int lag, int* status, cudaStream_t s) {
+  size_t smem = lsar_chol_smem(p);
+  cudaError_t e = cudaFuncSetAttribute(lsar_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  lsar_solve_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, p, y, rows, w2, c, Lg, rw, phi, tau, lag, status);
+  lsar_chol_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, p, Lg, rdg, phi, tau, lag, status);
+  const int per_cta = (c + ng - 1) / ng;
+  lsar_refine_kernel<<<ng, 256, sizeof(double) * 9 * (size_t)p, s>>>(y, p, rows, w2, c, per_cta, phi, gpart, status);
+  smem = lsar_correct_smem(p);
+  e = cudaFuncSetAttribute(lsar_correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  lsar_correct_kernel<<<1, kLsarSolveThreads, smem, s>>>(Lg, rdg, p, gpart, ng, phi, tau, lag, status);
   return cudaGetLastError();
 }
 

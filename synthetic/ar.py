@@ -172,3 +172,14 @@ def lsar_uniforms(p_bar: int, c: int, *, config_id: int, series_index: int = 0,
     that pick the sampled rows at lag h (inverse-CDF sampling with replacement). Passed to the sampler as input."""
     rng = rng_for(config_id, 2 * 10**9 + series_index, base_seed)
     return np.ascontiguousarray(rng.random((p_bar, c)))
+
+
+def with_outliers(y: np.ndarray, count: int, *, config_id: int, series_index: int = 0,
+                  base_seed: int = BASE_SEED) -> np.ndarray:
+    """A copy of y with `count` distinct positions, drawn uniformly, replaced by y + U[-3, 3] + N(0, 100): the
+    outlier workload of the paper's Section 4.2 (1,000 such points in two million)."""
+    rng = rng_for(config_id, 3 * 10**9 + series_index, base_seed)
+    out = np.array(y, dtype=np.float64, copy=True)
+    pos = rng.choice(out.size, size=count, replace=False)
+    out[pos] += rng.uniform(-3.0, 3.0, size=count) + rng.normal(0.0, 10.0, size=count)
+    return out

@@ -87,3 +87,16 @@ def test_lsar_rejects_bad_arguments(tols):
             tols.toeplitz_ols_lsar(ctx, y, 100, 300, 400, u)    # p_bar > 256
         with pytest.raises(tols.TolsError):
             tols.toeplitz_ols_lsar(ctx, y, 10, 10, 10, u)       # n <= p_bar
+
+
+def test_lsar_with_outliers_matches_oracle(tols):
+    # the outlier workload of Section 4.2 (0.05 % of the points), where the outliers carry large leverage
+    from synthetic import with_outliers
+    s = ar_series(40_000, 5, config_id=91, root_lo=1.2, root_hi=3.0)
+    y = with_outliers(s.y, 20, config_id=91)
+    unif = lsar_uniforms(12, 2000, config_id=91)
+    ref = oracle.lsar(y, 12, 2000, unif)
+    tau, order, phi, rc, rows, phi_all = _run(tols, y, 12, 2000, unif)
+    assert rc == tols.TOLS_OK
+    assert np.array_equal(rows, ref.rows)
+    assert np.max(np.abs(tau - ref.tau)) <= 1e-9 * np.max(np.abs(ref.tau)) + 1e-12

@@ -193,3 +193,14 @@ def test_ill_conditioned_switches_to_sampled_qr(tols, k):
     rn, _, ne = oracle.residual_check(s.y, p, phi, norm2=sol.norm2)
     assert rn <= sol.rnorm * (1 + 1e-9), (rn, sol.rnorm, info)
     assert ne <= 10 * sol.ne_ratio, (ne, sol.ne_ratio, info)
+
+
+@pytest.mark.parametrize("n,p,count,cfg", [(200_000, 5, 100, 70), (100_000, 50, 50, 71)])
+def test_solve_with_outliers(tols, ctx, prec, n, p, count, cfg):
+    # the outlier workload of Section 4.2 (0.05 % of the points replaced by y + U[-3, 3] + N(0, 100))
+    from synthetic import with_outliers
+    y = with_outliers(ar_series(n, p, config_id=cfg, root_lo=1.2, root_hi=3.0).y, count, config_id=cfg)
+    sol = oracle.ols_qr(y, p)
+    phi, rnorm, info, rc = tols.toeplitz_ols_solve(ctx, y, p, 1e-12)
+    assert rc == tols.TOLS_OK, info
+    assert_solve_parity(y, p, phi, sol, COEF_TOL[prec])

@@ -379,3 +379,18 @@ def test_lsar_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(tols, "leverage_step", unnormalised_step)
     r = tols.lsar(s.y, 4, 500, u)
     assert not np.allclose(r.lev_sum, np.arange(1, 5), rtol=1e-6)
+
+
+def test_outlier_workload_generator():
+    # Section 4.2: `count` distinct points replaced by y + U[-3, 3] + N(0, 100)
+    from synthetic import with_outliers
+    y = ar_series(20_000, 3, config_id=7).y
+    z = with_outliers(y, 1000, config_id=7)
+    assert np.array_equal(z, with_outliers(y, 1000, config_id=7))
+    d = z - y
+    changed = np.flatnonzero(d)
+    assert changed.size == 1000
+    dv = d[changed]
+    assert abs(dv.mean()) < 4 * math.sqrt(103.0 / 1000)            # variance 100 + 36/12
+    assert abs(dv.var() - 103.0) < 4 * 103.0 * math.sqrt(2.0 / 1000)
+    assert np.all(z[np.setdiff1d(np.arange(y.size), changed)] == y[np.setdiff1d(np.arange(y.size), changed)])

@@ -36,6 +36,17 @@ Functions and the passage each follows:
                       approximate leverage scores (Def. "Approximate Leverage Scores"), sampling, compressed
                       solve, PACF estimate tau_p = last coefficient, and the order estimate: the largest p with
                       |tau_p| >= 1.96 / sqrt(c).
+  hadamard_transform  Def. "Hadamard Transform" (Section 2.1): H_m v by its recursion, normalised.
+  srht_ols            Algorithm "SRHT" (Section 2.1, eq. (SRHT)): min ||S H D (X phi - b)|| with D random signs,
+                      H the normalised Hadamard transform (rows zero-padded to a power of two) and S uniform
+                      sampling with replacement scaled by sqrt(n/c).
+  generalized_leverage  Def. "Generalised Leverage Score" (Section 3.2) and its Gaussian-sketch approximation,
+                      eq. (glev).
+  repeated_halving    Algorithm "Repeated Halving" (Section 3.2): halve uniformly down to a small level, then
+                      back up, sampling each level by its approximate generalised leverage scores with respect to
+                      the spectral approximation of the level below.
+  rh_lsar             the RH variant of LSAR (end of Section 3.2): Algorithm "LSAR" with the leverage scores
+                      replaced by those Repeated Halving gives for the lag-p_bar matrix [X | b].
 """
 from __future__ import annotations
 
@@ -308,3 +319,121 @@ def lsar(y, p_bar: int, c: int, unif) -> LsarResult:
     thr = 1.96 / math.sqrt(c)
     order = max([h for h in range(1, p_bar + 1) if abs(tau[h - 1]) >= thr], default=0)
     return LsarResult(tau=tau, order=order, phi=phis, rows=rows_all, lev_sum=lev_sum, rr=rr)
+
+
+def hadamard_transform(v) -> np.ndarray:
+    """H_m v, Def. "Hadamard Transform" (Section 2.1): H_0 = 1, H_m = [[H_{m-1}, H_{m-1}], [H_{m-1}, -H_{m-1}]] / sqrt(2),
+    applied by that recursion (stage h combines the halves of every block of 2h entries). len(v) = 2^m."""
+    v = np.array(v, dtype=np.float64, copy=True)
+    n = v.size
+    if n & (n - 1):
+        raise ValueError("length must be a power of two")
+    s = 1.0 / math.sqrt(2.0)
+    h = 1
+    while h < n:
+        blocks = v.reshape(-1, 2, h)
+        top = blocks[:, 0, :].copy()
+        bot = blocks[:, 1, :].copy()
+        blocks[:, 0, :] = (top + bot) * s
+        blocks[:, 1, :] = (top - bot) * s
+        h *= 2
+    return v
+
+
+def srht_ols(y, p: int, rows, signs) -> np.ndarray:
+    """Algorithm "SRHT" (Section 2.1): phi minimising ||S H D (X phi - b)||, eq. (SRHT). The m rows of [X | b] are
+    zero-padded to m2 = 2^ceil(log2 m); D = diag(signs) (m2 entries of +-1); H the normalised Hadamard transform
+    of size m2; S takes rows[t] (drawn uniformly with replacement, c = len(rows) of them) scaled by sqrt(m2 / c)."""
+    X, b = lag_matrix(y, p)
+    m = X.shape[0]
+    m2 = 1 << max(0, (m - 1).bit_length())
+    signs = np.asarray(signs, dtype=np.float64)
+    if signs.size != m2:
+        raise ValueError("need one sign per padded row")
+    Z = np.zeros((m2, p + 1))
+    Z[:m, :p] = X
+    Z[:m, p] = b
+    Z *= signs[:, None]
+    for j in range(p + 1):
+        Z[:, j] = hadamard_transform(Z[:, j])
+    rows = np.asarray(rows, dtype=np.int64)
+    sc = math.sqrt(m2 / rows.size)
+    phi, *_ = np.linalg.lstsq(sc * Z[rows, :p], sc * Z[rows, p], rcond=None)
+    return phi
+
+
+def generalized_leverage(C, B, G=None) -> np.ndarray:
+    """Def. "Generalised Leverage Score" (Section 3.2): l^B(i) = C(i,:) (B^T B)^{-1} C(i,:)^T; with a sketch G
+    (k x rows(B)), eq. (glev): ||G B (B^T B)^{-1} C(i,:)^T||^2."""
+    C = np.asarray(C, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    K = np.linalg.solve(B.T @ B, C.T)            # (B^T B)^{-1} C^T, one column per row of C
+    if G is None:
+        return np.einsum("ij,ji->i", C, K)
+    V = np.asarray(G, dtype=np.float64) @ (B @ K)   # G B (B^T B)^{-1} C(i,:)^T, one column per row
+    return np.sum(V * V, axis=0)
+
+
+@dataclass
+class RHResult:
+    scores: np.ndarray       # approximate generalised leverage scores of the rows of X (w.r.t. the level below)
+    rows: np.ndarray         # the c rows of X sampled at the top level
+    Xt: np.ndarray           # the spectral approximation: those rows, each scaled by 1 / sqrt(c p_i)
+    sizes: list              # rows at each halving level, top first
+
+
+def repeated_halving(X, c: int, min_rows: int, keys, gauss, unif) -> RHResult:
+    """Algorithm "Repeated Halving" (Section 3.2) with its random draws as inputs.
+
+    Level 0 is X; level j+1 keeps the floor(n_j / 2) rows of level j with the smallest keys[j] (a uniform sample
+    without replacement), while level j has more than min_rows rows. The deepest level is its own spectral
+    approximation. Going back up, level j's rows get the approximate generalised leverage scores of eq. (glev)
+    with respect to the approximation of level j+1 (sketch gauss[j], k x rows of that approximation), and c rows
+    are drawn with replacement by leverage_sample on unif[j], each scaled by 1 / sqrt(c p_i),
+    p_i = score_i / sum(scores)."""
+    X = np.asarray(X, dtype=np.float64)
+    levels = [X]
+    while levels[-1].shape[0] > min_rows:
+        j = len(levels) - 1
+        nj = levels[j].shape[0]
+        keep = np.sort(np.argsort(np.asarray(keys[j]), kind="stable")[: nj // 2])
+        levels.append(levels[j][keep])
+    Xt = levels[-1]
+    scores = rows = None
+    for j in range(len(levels) - 2, -1, -1):
+        scores = generalized_leverage(levels[j], Xt, gauss[j])
+        rows = leverage_sample(scores, unif[j])
+        prob = scores[rows] / math.fsum(scores.tolist())
+        Xt = levels[j][rows] / np.sqrt(c * prob)[:, None]
+    if scores is None:                         # X itself is small: its exact scores, all of its rows
+        scores = generalized_leverage(X, X)
+        rows = np.arange(X.shape[0])
+    return RHResult(scores=scores, rows=rows, Xt=Xt, sizes=[lv.shape[0] for lv in levels])
+
+
+def rh_lsar(y, p_bar: int, c: int, rh: RHResult, unif) -> LsarResult:
+    """The RH variant of Algorithm "LSAR" (end of Section 3.2): rh holds Repeated Halving run on [X | b] of order
+    p_bar (m = n - p_bar rows); at every lag p the c rows are drawn by leverage_sample from rh.scores with
+    unif[p - 1] and weighted by 1 / sqrt(c pi_i), pi = scores / sum(scores); the compressed fit, tau_p and the
+    order estimate are those of lsar."""
+    y = _series(y, p_bar)
+    unif = np.asarray(unif, dtype=np.float64)
+    if unif.shape != (p_bar, c):
+        raise ValueError("unif must have shape (p_bar, c)")
+    m = y.size - p_bar
+    if rh.scores.size != m:
+        raise ValueError("scores must cover the m = n - p_bar rows")
+    pi = rh.scores / math.fsum(rh.scores.tolist())
+    tau = np.empty(p_bar)
+    rows_all = np.empty((p_bar, c), dtype=np.int64)
+    phis = []
+    for p in range(1, p_bar + 1):
+        rows = leverage_sample(rh.scores, unif[p - 1])
+        phi = compressed_ols(y[:m + p], p, rows, pi[rows], c)
+        tau[p - 1] = phi[p - 1]
+        rows_all[p - 1] = rows
+        phis.append(phi)
+    thr = 1.96 / math.sqrt(c)
+    order = max([h for h in range(1, p_bar + 1) if abs(tau[h - 1]) >= thr], default=0)
+    return LsarResult(tau=tau, order=order, phi=phis, rows=rows_all, lev_sum=np.full(p_bar, np.nan),
+                      rr=np.full(p_bar, np.nan))

@@ -183,3 +183,30 @@ def with_outliers(y: np.ndarray, count: int, *, config_id: int, series_index: in
     pos = rng.choice(out.size, size=count, replace=False)
     out[pos] += rng.uniform(-3.0, 3.0, size=count) + rng.normal(0.0, 10.0, size=count)
     return out
+
+
+def srht_draws(m: int, c: int, *, config_id: int, series_index: int = 0, base_seed: int = BASE_SEED):
+    """The random draws of a sampled randomised Hadamard transform on m rows padded to m2 = 2^ceil(log2 m): m2
+    signs +-1 (the diagonal D) and c row indices uniform in [0, m2) with replacement (the sampling S)."""
+    rng = rng_for(config_id, 4 * 10**9 + series_index, base_seed)
+    m2 = 1 << max(0, (m - 1).bit_length())
+    signs = np.where(rng.random(m2) < 0.5, -1.0, 1.0)
+    rows = rng.integers(0, m2, size=c)
+    return signs, rows
+
+
+def rh_draws(n_rows: int, c: int, k: int, min_rows: int, *, config_id: int, series_index: int = 0,
+             base_seed: int = BASE_SEED):
+    """The random draws of a Repeated Halving run on n_rows rows: per halving level j (while the level has more
+    than min_rows rows; the next level keeps half of them) n_j uniform keys, a k x r_j Gaussian sketch with
+    N(0, 1/k) entries (r_j: rows of the approximation one level down, the deepest level's own rows or c), and c
+    uniforms for the leverage sampling. Returns (keys, gauss, unif), lists indexed by level."""
+    rng = rng_for(config_id, 5 * 10**9 + series_index, base_seed)
+    sizes = [n_rows]
+    while sizes[-1] > min_rows:
+        sizes.append(sizes[-1] // 2)
+    levels = len(sizes) - 1
+    keys = [rng.random(sizes[j]) for j in range(levels)]
+    gauss = [rng.standard_normal((k, sizes[-1] if j == levels - 1 else c)) / math.sqrt(k) for j in range(levels)]
+    unif = [rng.random(c) for _ in range(levels)]
+    return keys, gauss, unif

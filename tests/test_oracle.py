@@ -394,3 +394,111 @@ def test_outlier_workload_generator():
     assert abs(dv.mean()) < 4 * math.sqrt(103.0 / 1000)            # variance 100 + 36/12
     assert abs(dv.var() - 103.0) < 4 * 103.0 * math.sqrt(2.0 / 1000)
     assert np.all(z[np.setdiff1d(np.arange(y.size), changed)] == y[np.setdiff1d(np.arange(y.size), changed)])
+
+
+# ---- Algorithm "SRHT" (Section 2.1) and Algorithm "Repeated Halving" (Section 3.2) --------------------------
+@pytest.mark.parametrize("n", [1, 2, 8, 64, 1024])
+def test_hadamard_transform_pins(n):
+    # the normalised Sylvester matrix (scipy.linalg.hadamard / sqrt(n)); orthogonal and symmetric, so H H = I
+    v = np.random.default_rng(n).standard_normal(n)
+    Hv = oracle.hadamard_transform(v)
+    assert np.allclose(Hv, scipy.linalg.hadamard(n) @ v / math.sqrt(n), rtol=0, atol=1e-13 * max(1.0, math.sqrt(n)))
+    assert np.linalg.norm(Hv) == pytest.approx(np.linalg.norm(v), rel=1e-14)
+    assert np.allclose(oracle.hadamard_transform(Hv), v, rtol=0, atol=1e-13)
+
+
+def test_srht_pins():
+    from synthetic import srht_draws
+    s = ar_series(3000, 3, config_id=5)
+    m, m2 = 3000 - 3, 4096
+    exact = oracle.ols_qr(s.y, 3)
+    # S takes every padded row once (c = m2, scale 1): S H D is orthogonal, so the fit is the exact OLS fit
+    signs, _ = srht_draws(m, 1, config_id=5)
+    perm = np.random.default_rng(0).permutation(m2)
+    assert oracle.srht_ols(s.y, 3, perm, signs) == pytest.approx(exact.phi, rel=1e-11, abs=1e-13)
+    # c = 300 uniform draws: the residual is within a few percent of the optimum (Theorem "Number of Rows to
+    # Sample in SRHT Algorithm": (1 + eps) with probability >= 0.8)
+    signs, rows = srht_draws(m, 300, config_id=5)
+    phi = oracle.srht_ols(s.y, 3, rows, signs)
+    rn = oracle.residual_check(s.y, 3, phi)[0]
+    assert exact.rnorm <= rn <= 1.1 * exact.rnorm
+
+
+def test_generalized_leverage_pins():
+    rng = np.random.default_rng(4)
+    C = rng.standard_normal((400, 5)) * np.array([1.0, 3.0, 0.2, 1.0, 5.0])
+    Q, _ = np.linalg.qr(C)
+    hat = np.sum(Q * Q, axis=1)                            # leverage scores: squared row norms of an orthonormal basis
+    assert oracle.generalized_leverage(C, C) == pytest.approx(hat, rel=1e-10)
+    B = C[rng.choice(400, 200, replace=False)]
+    exact_B = oracle.generalized_leverage(C, B)
+    assert oracle.generalized_leverage(C, B, np.eye(200)) == pytest.approx(exact_B, rel=1e-10)
+    # Theorem "Leverage Score Approximation via Uniform Sampling": every generalised score w.r.t. an unscaled
+    # row subset is at least the true score, and their total is about n d / m = 10
+    assert np.all(exact_B >= hat * (1 - 1e-12))
+    assert exact_B.sum() <= 2 * 400 * 5 / 200
+    # the Gaussian sketch of eq. (glev) is unbiased: the mean over 400 sketches (N(0, 1/k) entries) is close
+    k = 16
+    est = np.mean([oracle.generalized_leverage(C, B, rng.standard_normal((k, 200)) / math.sqrt(k))
+                   for _ in range(400)], axis=0)
+    assert np.max(np.abs(est / exact_B - 1)) < 0.15
+
+
+def test_repeated_halving_pins():
+    from synthetic import rh_draws
+    y = ar_series(20_000, 3, config_id=6).y
+    X, b = oracle.lag_matrix(y, 8)
+    C = np.column_stack([X, b])
+    c = 400
+    keys, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=6)
+    rh = oracle.repeated_halving(C, c, c, keys, gauss, unif)
+    assert rh.sizes[0] == C.shape[0] and rh.sizes[-1] <= c < rh.sizes[-2]
+    assert all(b_ == a_ // 2 for a_, b_ in zip(rh.sizes, rh.sizes[1:]))
+    assert np.all(rh.scores > 0)
+    prob = rh.scores[rh.rows] / math.fsum(rh.scores.tolist())
+    assert np.allclose(rh.Xt, C[rh.rows] / np.sqrt(c * prob)[:, None], rtol=1e-14, atol=0)
+    # a spectral approximation (Def. "lambda-Spectral Approximation"): x^T Xt^T Xt x / x^T C^T C x stays within a
+    # small factor for every x
+    Lc = np.linalg.cholesky(C.T @ C)
+    M = np.linalg.solve(Lc, np.linalg.solve(Lc, rh.Xt.T @ rh.Xt).T)
+    w = np.linalg.eigvalsh((M + M.T) / 2)
+    assert 0.5 <= w.min() and w.max() <= 2.0
+    # the scores track the true leverage of C (normalised) within a small factor for almost every row
+    Q, _ = np.linalg.qr(C)
+    ex = np.sum(Q * Q, axis=1)
+    ratio = (rh.scores / rh.scores.sum()) / (ex / ex.sum())
+    assert np.percentile(ratio, 1) > 0.25 and np.percentile(ratio, 99) < 4.0
+
+
+def test_rh_lsar_pins():
+    from synthetic import lsar_uniforms, rh_draws
+    s = ar_series(20_000, 3, config_id=7, series_index=2, root_lo=1.1, root_hi=1.6)
+    p_bar, c = 10, 2000
+    X, b = oracle.lag_matrix(s.y, p_bar)
+    C = np.column_stack([X, b])
+    keys, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=7)
+    rh = oracle.repeated_halving(C, c, c, keys, gauss, unif)
+    r = oracle.rh_lsar(s.y, p_bar, c, rh, lsar_uniforms(p_bar, c, config_id=7, series_index=2))
+    tau_exact, _ = oracle.pacf(s.y, p_bar)
+    assert np.max(np.abs(r.tau - tau_exact)) <= 3.0 / math.sqrt(c)
+    assert abs(r.tau[2]) > 5 * 1.96 / math.sqrt(c) and r.order >= 3
+    assert np.all((r.rows >= 0) & (r.rows < C.shape[0]))
+
+
+def test_sketch_planted_mistakes_are_caught(monkeypatch):
+    """Plant mistakes in the SRHT / Repeated Halving oracle (CPU only) and check the pins above notice them."""
+    v = np.random.default_rng(1).standard_normal(64)
+    real_h = tols.hadamard_transform
+
+    def unnormalised(x):                                  # the 1/sqrt(2) of each stage dropped
+        return real_h(x) * math.sqrt(len(x))
+
+    monkeypatch.setattr(tols, "hadamard_transform", unnormalised)
+    assert not np.isclose(np.linalg.norm(tols.hadamard_transform(v)), np.linalg.norm(v))
+    monkeypatch.setattr(tols, "hadamard_transform", real_h)
+    # generalised scores with B^T B in place of its inverse
+    rng = np.random.default_rng(4)
+    C = rng.standard_normal((100, 4))
+    Q, _ = np.linalg.qr(C)
+    wrong = np.einsum("ij,jk,ik->i", C, C.T @ C, C)
+    assert not np.allclose(wrong, np.sum(Q * Q, axis=1))

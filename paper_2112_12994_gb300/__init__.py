@@ -154,6 +154,23 @@ def _host_f64(a):
     return a
 
 
+def _dev(x, count, itemsize, name):
+    """Check a device-buffer argument before its address reaches a kernel: a tensor must be contiguous, have
+    elements of itemsize bytes and hold at least count of them (raw integer addresses pass unchecked)."""
+    if x is None or isinstance(x, int):
+        return
+    if hasattr(x, "element_size") and x.element_size() != itemsize:
+        raise TolsError(TOLS_ERR_ARG, f"{name}: elements of {x.element_size()} bytes, expected {itemsize}")
+    if hasattr(x, "is_contiguous") and not x.is_contiguous():
+        raise TolsError(TOLS_ERR_ARG, f"{name}: not contiguous")
+    if hasattr(x, "numel") and x.numel() < count:
+        raise TolsError(TOLS_ERR_ARG, f"{name}: {x.numel()} elements, needs {count}")
+
+
+def _pass_itemsize(precision):
+    return 8 if precision == TOLS_FP64 else 4
+
+
 def strerror(code: int) -> str:
     return lib.toeplitz_ols_strerror(code).decode()
 
@@ -223,6 +240,8 @@ def toeplitz_ols_solve(ctx: Context, y, p: int, tol: float = 0.0):
 
 def toeplitz_ols_solve_device(ctx: Context, d_y, n: int, p: int, d_phi, tol: float = 0.0):
     """Device series d_y (n float64) -> d_phi (p float64, device); returns (rnorm, info dict, status)."""
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_phi, p, 8, "d_phi")
     rn = ctypes.c_double()
     info = tols_info()
     rc = lib.toeplitz_ols_solve_device(ctx.handle, _ptr(d_y), n, p, tol, _ptr(d_phi), ctypes.byref(rn),
@@ -252,6 +271,9 @@ def toeplitz_ols_solve_batched_device(ctx: Context, d_ys, ps, d_phi, tol: float 
     """Device series (list of CUDA tensors / addresses) -> coefficients packed in d_phi (device, sum(ps));
     returns (rnorm array, list of info dicts, worst status)."""
     count = len(d_ys)
+    for y in d_ys:
+        _dev(y, 0, 8, "d_ys[k]")
+    _dev(d_phi, int(sum(int(q) for q in ps)), 8, "d_phi")
     yp = (ctypes.c_void_p * count)(*[_ptr(y) for y in d_ys])
     ns = np.array([int(y.numel()) if hasattr(y, "numel") else 0 for y in d_ys], dtype=np.int64)
     pv = np.array(ps, dtype=np.int32)
@@ -302,8 +324,18 @@ def toeplitz_ols_stream_close(ctx: Context, handle: int):
     ctx.check(lib.toeplitz_ols_stream_close(ctx.handle, handle), "toeplitz_ols_stream_close")
 
 
+def _check_pass_args(precision, d_y, n, p, d_v, d_u_old, d_u_new, d_xtu):
+    es = _pass_itemsize(precision)
+    _dev(d_y, n, es, "d_y")
+    _dev(d_v, p, 8, "d_v")
+    _dev(d_u_old, n - p, es, "d_u_old")
+    _dev(d_u_new, n - p, es, "d_u_new")
+    _dev(d_xtu, p, 8, "d_xtu")
+
+
 def toeplitz_ols_gk_pass(ctx: Context, precision: int, d_y, n: int, p: int, d_v, d_u_old, c: float, d_u_new, d_xtu):
     """u_new = X v - c u_old, X^T u_new -> d_xtu; returns ||u_new||^2 (device buffers)."""
+    _check_pass_args(precision, d_y, n, p, d_v, d_u_old, d_u_new, d_xtu)
     n2 = ctypes.c_double()
     ctx.check(lib.toeplitz_ols_gk_pass(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_v), _ptr(d_u_old), c,
                                        _ptr(d_u_new), _ptr(d_xtu), ctypes.byref(n2)), "toeplitz_ols_gk_pass")
@@ -314,11 +346,16 @@ def toeplitz_ols_gk_pass_noalloc(precision: int, d_y, n: int, p: int, d_v, d_u_o
                                  d_unorm2, stream=None) -> int:
     """The allocation-free fused pass (no context): enqueues on `stream` (a cudaStream_t handle or None) and
     returns the status code without waiting; ||u_new||^2 goes to the device scalar d_unorm2."""
+    _check_pass_args(precision, d_y, n, p, d_v, d_u_old, d_u_new, d_xtu)
+    _dev(d_unorm2, 1, 8, "d_unorm2")
     return lib.toeplitz_ols_gk_pass_noalloc(precision, _ptr(d_y), n, p, _ptr(d_v), _ptr(d_u_old), c, _ptr(d_u_new),
                                             _ptr(d_xtu), _ptr(d_unorm2), stream)
 
 
 def toeplitz_ols_gram(ctx: Context, precision: int, d_y, n: int, p: int, d_G, d_h):
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_G, p * p, 8, "d_G")
+    _dev(d_h, p, 8, "d_h")
     b2 = ctypes.c_double()
     ctx.check(lib.toeplitz_ols_gram(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_G), _ptr(d_h), ctypes.byref(b2)),
               "toeplitz_ols_gram")
@@ -326,6 +363,8 @@ def toeplitz_ols_gram(ctx: Context, precision: int, d_y, n: int, p: int, d_G, d_
 
 
 def toeplitz_ols_row_norms(ctx: Context, d_y, n: int, p: int, d_rn2=None):
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_rn2, n - p, 8, "d_rn2")
     f = ctypes.c_double()
     ctx.check(lib.toeplitz_ols_row_norms(ctx.handle, _ptr(d_y), n, p, _ptr(d_rn2), ctypes.byref(f)),
               "toeplitz_ols_row_norms")
@@ -333,6 +372,9 @@ def toeplitz_ols_row_norms(ctx: Context, d_y, n: int, p: int, d_rn2=None):
 
 
 def toeplitz_ols_residual(ctx: Context, d_y, n: int, p: int, d_phi, d_g):
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_phi, p, 8, "d_phi")
+    _dev(d_g, p, 8, "d_g")
     rn = ctypes.c_double()
     ctx.check(lib.toeplitz_ols_residual(ctx.handle, _ptr(d_y), n, p, _ptr(d_phi), _ptr(d_g), ctypes.byref(rn)),
               "toeplitz_ols_residual")
@@ -340,10 +382,16 @@ def toeplitz_ols_residual(ctx: Context, d_y, n: int, p: int, d_phi, d_g):
 
 
 def toeplitz_ols_leverage_p1(ctx: Context, d_y, n: int, d_lev):
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_lev, n - 1, 8, "d_lev")
     ctx.check(lib.toeplitz_ols_leverage_p1(ctx.handle, _ptr(d_y), n, _ptr(d_lev)), "toeplitz_ols_leverage_p1")
 
 
 def toeplitz_ols_leverage_step(ctx: Context, d_y, n: int, p: int, d_phi_hat, d_lev_prev, d_lev, d_pi=None):
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_phi_hat, p - 1, 8, "d_phi_hat")
+    for name, buf in (("d_lev_prev", d_lev_prev), ("d_lev", d_lev), ("d_pi", d_pi)):
+        _dev(buf, n - p, 8, name)
     rr = ctypes.c_double()
     ctx.check(lib.toeplitz_ols_leverage_step(ctx.handle, _ptr(d_y), n, p, _ptr(d_phi_hat), _ptr(d_lev_prev),
                                              _ptr(d_lev), _ptr(d_pi), ctypes.byref(rr)), "toeplitz_ols_leverage_step")
@@ -353,6 +401,10 @@ def toeplitz_ols_leverage_step(ctx: Context, d_y, n: int, p: int, d_phi_hat, d_l
 def toeplitz_ols_lsar(ctx: Context, d_y, n: int, p_bar: int, c: int, d_unif, d_rows=None, d_phi_all=None):
     """Algorithm LSAR on a device series with device uniforms (p_bar x c) -> (tau array of p_bar PACF estimates,
     estimated order, phi_hat at that order (p_bar doubles, zero-padded), status)."""
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_unif, p_bar * c, 8, "d_unif")
+    _dev(d_rows, p_bar * c, 8, "d_rows")
+    _dev(d_phi_all, p_bar * p_bar, 8, "d_phi_all")
     tau = np.zeros(int(p_bar), dtype=np.float64)
     phi = np.zeros(int(p_bar), dtype=np.float64)
     order = ctypes.c_int(0)

@@ -60,3 +60,26 @@ def test_host_side_contract_without_gpu(lib):
     if not has_gpu:
         h = ctypes.c_void_p()
         assert t.lib.toeplitz_ols_create(ctypes.byref(h), ctypes.byref(cfg)) == t.TOLS_ERR_NO_DEVICE
+
+
+def test_binding_checks_device_buffers(lib):
+    # the binding refuses a tensor that is too small, of the wrong element size or not contiguous before any
+    # address reaches the library (CPU tensors stand in: the check needs no device)
+    torch = pytest.importorskip("torch")
+    import paper_2112_12994_gb300 as t
+    y = torch.zeros(100, dtype=torch.float64)
+    with pytest.raises(t.TolsError, match="d_unif"):
+        t.toeplitz_ols_lsar(None, y, 100, 10, 20, torch.zeros(150, dtype=torch.float64))
+    with pytest.raises(t.TolsError, match="d_unif"):
+        t.toeplitz_ols_lsar(None, y, 100, 10, 20, torch.zeros(200, dtype=torch.float32))
+    with pytest.raises(t.TolsError, match="d_rows"):
+        t.toeplitz_ols_lsar(None, y, 100, 10, 20, torch.zeros(200, dtype=torch.float64),
+                            torch.zeros(200, dtype=torch.int32))
+    with pytest.raises(t.TolsError, match="d_y"):
+        t.toeplitz_ols_gk_pass(None, t.TOLS_MIXED, y, 100, 5, torch.zeros(5, dtype=torch.float64), None, 0.0,
+                               torch.zeros(95, dtype=torch.float32), torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(t.TolsError, match="d_u_new"):
+        t.toeplitz_ols_gk_pass(None, t.TOLS_FP64, y, 100, 5, torch.zeros(5, dtype=torch.float64), None, 0.0,
+                               torch.zeros(190, dtype=torch.float64)[::2], torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(t.TolsError, match="d_phi"):
+        t.toeplitz_ols_solve_device(None, y, 100, 20, torch.zeros(19, dtype=torch.float64))

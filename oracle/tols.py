@@ -382,12 +382,12 @@ class RHResult:
     sizes: list              # rows at each halving level, top first
 
 
-def repeated_halving(X, c: int, min_rows: int, keys, gauss, unif) -> RHResult:
+def repeated_halving(X, c: int, min_rows: int, keep, gauss, unif) -> RHResult:
     """Algorithm "Repeated Halving" (Section 3.2) with its random draws as inputs.
 
-    Level 0 is X; level j+1 keeps the floor(n_j / 2) rows of level j with the smallest keys[j] (a uniform sample
-    without replacement), while level j has more than min_rows rows. The deepest level is its own spectral
-    approximation. Going back up, level j's rows get the approximate generalised leverage scores of eq. (glev)
+    Level 0 is X; while level j has more than min_rows rows, level j+1 is its rows keep[j] (floor(n_j / 2)
+    distinct positions within level j, increasing: a uniform sample without replacement). The deepest level is
+    its own spectral approximation. Going back up, level j's rows get the approximate generalised leverage scores of eq. (glev)
     with respect to the approximation of level j+1 (sketch gauss[j], k x rows of that approximation), and c rows
     are drawn with replacement by leverage_sample on unif[j], each scaled by 1 / sqrt(c p_i),
     p_i = score_i / sum(scores)."""
@@ -395,9 +395,10 @@ def repeated_halving(X, c: int, min_rows: int, keys, gauss, unif) -> RHResult:
     levels = [X]
     while levels[-1].shape[0] > min_rows:
         j = len(levels) - 1
-        nj = levels[j].shape[0]
-        keep = np.sort(np.argsort(np.asarray(keys[j]), kind="stable")[: nj // 2])
-        levels.append(levels[j][keep])
+        kj = np.asarray(keep[j], dtype=np.int64)
+        if kj.size != levels[j].shape[0] // 2:
+            raise ValueError("keep[j] must hold floor(n_j / 2) positions")
+        levels.append(levels[j][kj])
     Xt = levels[-1]
     scores = rows = None
     for j in range(len(levels) - 2, -1, -1):

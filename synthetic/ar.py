@@ -198,15 +198,17 @@ def srht_draws(m: int, c: int, *, config_id: int, series_index: int = 0, base_se
 def rh_draws(n_rows: int, c: int, k: int, min_rows: int, *, config_id: int, series_index: int = 0,
              base_seed: int = BASE_SEED):
     """The random draws of a Repeated Halving run on n_rows rows: per halving level j (while the level has more
-    than min_rows rows; the next level keeps half of them) n_j uniform keys, a k x r_j Gaussian sketch with
-    N(0, 1/k) entries (r_j: rows of the approximation one level down, the deepest level's own rows or c), and c
-    uniforms for the leverage sampling. Returns (keys, gauss, unif), lists indexed by level."""
+    than min_rows rows) the floor(n_j / 2) positions the next level keeps (a uniform subset, increasing), a
+    k x r_j Gaussian sketch with N(0, 1/k) entries (r_j: rows of the approximation one level down, the deepest
+    level's own rows or c), and c uniforms for the leverage sampling. Returns (keep, gauss, unif), lists
+    indexed by level."""
     rng = rng_for(config_id, 5 * 10**9 + series_index, base_seed)
     sizes = [n_rows]
     while sizes[-1] > min_rows:
         sizes.append(sizes[-1] // 2)
     levels = len(sizes) - 1
-    keys = [rng.random(sizes[j]) for j in range(levels)]
+    keep = [np.sort(rng.choice(sizes[j], size=sizes[j + 1], replace=False)).astype(np.int64)
+            for j in range(levels)]
     gauss = [rng.standard_normal((k, sizes[-1] if j == levels - 1 else c)) / math.sqrt(k) for j in range(levels)]
     unif = [rng.random(c) for _ in range(levels)]
-    return keys, gauss, unif
+    return keep, gauss, unif

@@ -450,8 +450,8 @@ def test_repeated_halving_pins():
     X, b = oracle.lag_matrix(y, 8)
     C = np.column_stack([X, b])
     c = 400
-    keys, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=6)
-    rh = oracle.repeated_halving(C, c, c, keys, gauss, unif)
+    keep, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=6)
+    rh = oracle.repeated_halving(C, c, c, keep, gauss, unif)
     assert rh.sizes[0] == C.shape[0] and rh.sizes[-1] <= c < rh.sizes[-2]
     assert all(b_ == a_ // 2 for a_, b_ in zip(rh.sizes, rh.sizes[1:]))
     assert np.all(rh.scores > 0)
@@ -476,8 +476,8 @@ def test_rh_lsar_pins():
     p_bar, c = 10, 2000
     X, b = oracle.lag_matrix(s.y, p_bar)
     C = np.column_stack([X, b])
-    keys, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=7)
-    rh = oracle.repeated_halving(C, c, c, keys, gauss, unif)
+    keep, gauss, unif = rh_draws(C.shape[0], c, 16, c, config_id=7)
+    rh = oracle.repeated_halving(C, c, c, keep, gauss, unif)
     r = oracle.rh_lsar(s.y, p_bar, c, rh, lsar_uniforms(p_bar, c, config_id=7, series_index=2))
     tau_exact, _ = oracle.pacf(s.y, p_bar)
     assert np.max(np.abs(r.tau - tau_exact)) <= 3.0 / math.sqrt(c)

@@ -291,6 +291,31 @@ int toeplitz_ols_leverage_step(tols_ctx* ctx, const double* d_y, long long n, in
 int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, int c, const double* d_unif,
                       double* tau, int* order, double* phi, long long* d_rows, double* d_phi_all);
 
+/* The Repeated Halving variant of Algorithm "LSAR" (end of Section 3.2): Algorithm "Repeated Halving" (Section 3.2)
+ * runs once on C = [X | b] of order p_bar (m = n - p_bar rows: C(i,:) holds y[i .. i + p_bar]); its top-level
+ * scores then replace eq. (FALS) at every lag of LSAR (same lags, sampling, compressed fits and order estimate as
+ * toeplitz_ols_lsar; the draws at each lag are weighted by 1 / sqrt(c pi_i), pi = scores / sum(scores)).
+ *   halving  levels >= 1 halvings: h_sizes[0] = m, h_sizes[j+1] = h_sizes[j] / 2 (host, levels + 1 entries);
+ *            h_keep (host) holds, level after level, the h_sizes[j+1] increasing positions within level j that
+ *            level j+1 keeps (the uniform subsets are inputs). The deepest level is its own approximation.
+ *   upward   for j = levels-1 .. 0: B = the approximation of level j+1 (the deepest level's rows, unscaled, or c
+ *            rows drawn from level j+1, each scaled by 1 / sqrt(c p_r)); the scores of level j's rows are
+ *            ||S_j B (B^T B)^-1 C(i,:)^T||^2, eq. (glev), with the sketch S_j (k x rows(B), row-major; d_sketch
+ *            holds S_0, S_1, ... in turn, rows(B) = h_sizes[levels] for the deepest level's sketch, else c);
+ *            for j >= 1, c rows of level j are drawn from its scores with d_rh_unif[j c .. j c + c) (inverse CDF
+ *            as in toeplitz_ols_lsar) to form level j's approximation. Level 0's scores are the result.
+ * d_y: n doubles (device). d_unif: p_bar x c uniforms for the lags (device). tau (host, p_bar), order (host,
+ * nullable), phi (host, nullable, p_bar doubles) as in toeplitz_ols_lsar. d_scores: device, nullable, m doubles
+ * (level 0's scores). d_rows: device, nullable, p_bar x c sampled rows of the lags (int64).
+ * Needs 1 <= p_bar <= 256, 1 <= k <= 64, c >= p_bar + 1, h_sizes[levels] >= p_bar + 1. Returns TOLS_ERR_ARG on
+ * malformed sizes or keep lists (checked before any device work), TOLS_NOT_CONVERGED if a B^T B or a sampled
+ * Gram matrix is not positive definite (the message names the level or lag). Runs on the context's stream
+ * and returns after it finishes. */
+int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, int c, int k, int levels,
+                         const long long* h_sizes, const long long* h_keep, const double* d_sketch,
+                         const double* d_rh_unif, const double* d_unif, double* tau, int* order, double* phi,
+                         double* d_scores, long long* d_rows);
+
 /* ---- instrumentation (no counterpart in the paper: measurement of this library's own kernels) ----------
  * toeplitz_ols_profile(ctx, 1) clears the counters and starts timing every kernel the context launches with
  * a pair of CUDA events on the context's stream; 0 stops timing (counters are kept).

@@ -119,6 +119,8 @@ SIGNATURES = {
     "toeplitz_ols_leverage_p1": (_I, [_P, _P, _LL, _P]),
     "toeplitz_ols_leverage_step": (_I, [_P, _P, _LL, _I, _P, _P, _P, _P, _D]),
     "toeplitz_ols_lsar": (_I, [_P, _P, _LL, _I, _I, _P, _P, ctypes.POINTER(_I), _P, _P, _P]),
+    "toeplitz_ols_rh_lsar": (_I, [_P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I), _P, _P,
+                                  _P]),
     "toeplitz_ols_server_config_default": (None, [ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_destroy": (_I, [_P]),
@@ -411,6 +413,38 @@ def toeplitz_ols_lsar(ctx: Context, d_y, n: int, p_bar: int, c: int, d_unif, d_r
     rc = lib.toeplitz_ols_lsar(ctx.handle, _ptr(d_y), int(n), int(p_bar), int(c), _ptr(d_unif), tau.ctypes.data,
                                ctypes.byref(order), phi.ctypes.data, _ptr(d_rows), _ptr(d_phi_all))
     ctx.check(rc, "toeplitz_ols_lsar")
+    return tau, order.value, phi, rc
+
+
+def toeplitz_ols_rh_lsar(ctx: Context, d_y, n: int, p_bar: int, c: int, k: int, keep, d_sketch, d_rh_unif, d_unif,
+                         d_scores=None, d_rows=None):
+    """The Repeated Halving variant of LSAR. keep: list of host integer arrays, level j's kept positions (the
+    halvings, from m = n - p_bar rows); d_sketch: one device array holding the k x rows sketches of every level
+    in turn (row-major); d_rh_unif: device, levels x c; d_unif: device, p_bar x c. Returns (tau, order, phi,
+    status)."""
+    levels = len(keep)
+    m = int(n) - int(p_bar)
+    sizes = np.empty(levels + 1, dtype=np.int64)
+    sizes[0] = m
+    for j, kj in enumerate(keep):
+        sizes[j + 1] = len(kj)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(kj, dtype=np.int64) for kj in keep]) if levels else
+                                np.zeros(0, dtype=np.int64))
+    deep = int(sizes[-1])
+    rows_b = [deep if j == levels - 1 else int(c) for j in range(levels)]
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_sketch, k * sum(rows_b), 8, "d_sketch")
+    _dev(d_rh_unif, levels * c, 8, "d_rh_unif")
+    _dev(d_unif, p_bar * c, 8, "d_unif")
+    _dev(d_scores, m, 8, "d_scores")
+    _dev(d_rows, p_bar * c, 8, "d_rows")
+    tau = np.zeros(int(p_bar), dtype=np.float64)
+    phi = np.zeros(int(p_bar), dtype=np.float64)
+    order = ctypes.c_int(0)
+    rc = lib.toeplitz_ols_rh_lsar(ctx.handle, _ptr(d_y), int(n), int(p_bar), int(c), int(k), int(levels),
+                                  sizes.ctypes.data, flat.ctypes.data, _ptr(d_sketch), _ptr(d_rh_unif), _ptr(d_unif),
+                                  tau.ctypes.data, ctypes.byref(order), phi.ctypes.data, _ptr(d_scores), _ptr(d_rows))
+    ctx.check(rc, "toeplitz_ols_rh_lsar")
     return tau, order.value, phi, rc
 
 

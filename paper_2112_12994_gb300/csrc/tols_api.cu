@@ -1711,6 +1711,171 @@ int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, 
   return TOLS_OK;
 }
 
+int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, int c, int k, int levels,
+                         const long long* h_sizes, const long long* h_keep, const double* d_sketch,
+                         const double* d_rh_unif, const double* d_unif, double* tau, int* order, double* phi,
+                         double* d_scores, long long* d_rows) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (!d_y || !h_sizes || !h_keep || !d_sketch || !d_rh_unif || !d_unif || !tau)
+    return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  if (p_bar < 1 || p_bar > kLsarMaxP) return fail(ctx, TOLS_ERR_ARG, "p_bar out of range [1, 256]");
+  if (k < 1 || k > kRhMaxSketch) return fail(ctx, TOLS_ERR_ARG, "sketch rows k out of range [1, 64]");
+  const long long m = n - p_bar;
+  const int P1 = p_bar + 1;
+  if (m < 1 || levels < 1 || h_sizes[0] != m) return fail(ctx, TOLS_ERR_ARG, "need n > p_bar, levels >= 1, sizes[0] = n - p_bar");
+  if (c < P1) return fail(ctx, TOLS_ERR_ARG, "need c >= p_bar + 1");
+  size_t keep_total = 0, orig_total = 0;
+  for (int j = 0; j < levels; ++j) {
+    if (h_sizes[j + 1] != h_sizes[j] / 2) return fail(ctx, TOLS_ERR_ARG, "sizes must halve");
+    keep_total += (size_t)h_sizes[j + 1];
+  }
+  orig_total = keep_total;
+  const long long deep = h_sizes[levels];
+  if (deep < P1) return fail(ctx, TOLS_ERR_ARG, "the deepest level needs at least p_bar + 1 rows");
+  {
+    // each level's kept positions: increasing, inside the level above
+    size_t off = 0;
+    for (int j = 0; j < levels; ++j) {
+      for (long long e = 0; e < h_sizes[j + 1]; ++e) {
+        const long long v = h_keep[off + e];
+        if (v < 0 || v >= h_sizes[j] || (e > 0 && v <= h_keep[off + e - 1]))
+          return fail(ctx, TOLS_ERR_ARG, "keep lists must be increasing positions inside their level");
+      }
+      off += (size_t)h_sizes[j + 1];
+    }
+  }
+  cudaSetDevice(ctx->device);
+  const long long nb = (m + kLsarBlock - 1) / kLsarBlock;
+  const long long tri_max = lsar_tri(p_bar);
+  const long long bmax = std::max<long long>(c, deep);
+  const int ng = std::max(1, std::min(ctx->sms, (int)((bmax + 7) / 8)));
+  const size_t p2 = (size_t)p_bar * p_bar;
+  // doubles: scores of level 0 and of the current level, block sums and prefix, the weights of B and of a lag's
+  // draws, Gram partials, G, the Cholesky factor (order p_bar + 1) and its reciprocal diagonal, refinement
+  // partials, M, tau, phi per lag; then int64: the original rows of levels 1.., the kept positions, the drawn
+  // positions, B's rows, a lag's rows; then the status word
+  const size_t nd = (size_t)m + (size_t)h_sizes[1] + nb + (nb + 1) + bmax + c + ng * (size_t)tri_max + tri_max +
+                    (size_t)P1 * P1 + P1 + ng * (size_t)p_bar + (size_t)k * P1 + p_bar + p2;
+  const size_t ni = orig_total + keep_total + 2 * (size_t)c + (size_t)bmax;
+  int rc;
+  if ((rc = ensure(ctx, ctx->lsar, sizeof(double) * nd + sizeof(long long) * ni + 256))) return rc;
+  double* q = (double*)ctx->lsar.p;
+  double* scores0 = q; q += m;
+  double* scoresj = q; q += h_sizes[1];
+  double* bsum = q; q += nb;
+  double* bpre = q; q += nb + 1;
+  double* bw2 = q; q += bmax;
+  double* w2 = q; q += c;
+  double* part = q; q += ng * (size_t)tri_max;
+  double* G = q; q += tri_max;
+  double* Lg = q; q += (size_t)P1 * P1;
+  double* rdg = q; q += P1;
+  double* gpart = q; q += ng * (size_t)p_bar;
+  double* M = q; q += (size_t)k * P1;
+  double* tau_dev = q; q += p_bar;
+  double* phi_all = q; q += p2;
+  long long* orig = (long long*)q;
+  long long* keep = orig + orig_total;
+  long long* drawn = keep + keep_total;
+  long long* brows = drawn + c;
+  long long* rows_tmp = brows + bmax;
+  int* status = (int*)(rows_tmp + c);
+  CK(cudaMemsetAsync(phi_all, 0, sizeof(double) * p2, ctx->stream));
+  CK(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
+  CK(cudaMemcpyAsync(keep, h_keep, sizeof(long long) * keep_total, cudaMemcpyHostToDevice, ctx->stream));
+  // original rows of every level below the top: orig_{j+1} = orig_j[keep_j] (orig_0 the identity)
+  std::vector<size_t> orig_off((size_t)levels + 1, 0);
+  for (int j = 1; j <= levels; ++j) orig_off[j] = (j == 1 ? 0 : orig_off[j - 1] + (size_t)h_sizes[j - 1]);
+  {
+    size_t koff = 0;
+    for (int j = 0; j < levels; ++j) {
+      const long long* in = j == 0 ? nullptr : orig + orig_off[j];
+      RUN(run_small(ctx, 12, [&] {
+        return launch_rh_map(in, keep + koff, h_sizes[j + 1], orig + orig_off[j + 1], ctx->stream);
+      }));
+      koff += (size_t)h_sizes[j + 1];
+    }
+  }
+  // the deepest level is its own spectral approximation: its rows, weight 1
+  const long long* b_rows = orig + orig_off[levels];
+  long long b_cnt = deep;
+  RUN(run_small(ctx, 12, [&] { return launch_rh_fill(bw2, deep, 1.0, ctx->stream); }));
+  std::vector<size_t> sk_off((size_t)levels, 0);
+  for (int j = 1; j < levels; ++j) sk_off[j] = sk_off[j - 1] + (size_t)k * (size_t)(j - 1 == levels - 1 ? deep : c);
+  for (int j = levels - 1; j >= 0; --j) {
+    const int gj = std::max(1, std::min(ctx->sms, (int)((b_cnt + 7) / 8)));
+    const long long* list = j == 0 ? nullptr : orig + orig_off[j];
+    double* sc = j == 0 ? scores0 : scoresj;
+    RUN(run_small(ctx, 12, [&] {
+      return launch_lsar_gram(d_y, p_bar, b_rows, bw2, (int)b_cnt, gj, part, G, status, ctx->stream);
+    }));
+    RUN(run_small(ctx, 12, [&] { return launch_rh_factor(G, P1, Lg, rdg, 10000 + j, status, ctx->stream); }));
+    RUN(run_small(ctx, 12, [&] {
+      return launch_rh_sketch(d_y, P1, b_rows, bw2, (int)b_cnt, d_sketch + sk_off[j], k, Lg, rdg, M, status,
+                              ctx->stream);
+    }));
+    RUN(run_small(ctx, 12, [&] { return launch_rh_score(d_y, P1, M, k, list, h_sizes[j], sc, status, ctx->stream); }));
+    if (j > 0) {
+      // draw the c rows of this level's approximation (weights sum / (c score)), as original rows
+      RUN(run_small(ctx, 12, [&] { return launch_lsar_lev(nullptr, nullptr, sc, h_sizes[j], bsum, status, ctx->stream); }));
+      const long long nbj = (h_sizes[j] + kLsarBlock - 1) / kLsarBlock;
+      RUN(run_small(ctx, 12, [&] { return launch_lsar_prefix(bsum, nbj, bpre, status, ctx->stream); }));
+      RUN(run_small(ctx, 12, [&] {
+        return launch_lsar_sample(sc, h_sizes[j], bsum, bpre, d_rh_unif + (size_t)j * c, c, 0, drawn, bw2, status,
+                                  ctx->stream);
+      }));
+      RUN(run_small(ctx, 12, [&] { return launch_rh_map(list, drawn, c, brows, ctx->stream); }));
+      b_rows = brows;
+      b_cnt = c;
+    }
+  }
+  if (d_scores) CK(cudaMemcpyAsync(d_scores, scores0, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, ctx->stream));
+  // the LSAR lags with the level-0 scores in place of eq. (FALS)
+  RUN(run_small(ctx, 12, [&] { return launch_lsar_lev(nullptr, nullptr, scores0, m, bsum, status, ctx->stream); }));
+  RUN(run_small(ctx, 12, [&] { return launch_lsar_prefix(bsum, nb, bpre, status, ctx->stream); }));
+  const int ngl = std::max(1, std::min(ctx->sms, (c + 7) / 8));
+  for (int p = 1; p <= p_bar; ++p) {
+    long long* rows_p = d_rows ? d_rows + (size_t)(p - 1) * c : rows_tmp;
+    RUN(run_small(ctx, 12, [&] {
+      return launch_lsar_sample(scores0, m, bsum, bpre, d_unif + (size_t)(p - 1) * c, c, 0, rows_p, w2, status,
+                                ctx->stream);
+    }));
+    RUN(run_small(ctx, 12, [&] { return launch_lsar_gram(d_y, p, rows_p, w2, c, ngl, part, G, status, ctx->stream); }));
+    RUN(run_small(ctx, 12, [&] {
+      return launch_lsar_solve(G, p, d_y, rows_p, w2, c, ngl, Lg, rdg, gpart, phi_all + (size_t)(p - 1) * p_bar,
+                               tau_dev, p, status, ctx->stream);
+    }));
+  }
+  int h_status = 0;
+  CK(cudaMemcpyAsync(tau, tau_dev, sizeof(double) * p_bar, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int o = 0;
+  const double thr = 1.96 / sqrt((double)c);
+  for (int p = 1; p <= p_bar; ++p)
+    if (fabs(tau[p - 1]) >= thr) o = p;
+  if (order) *order = o;
+  if (phi) {
+    if (o > 0) {
+      CK(cudaMemcpyAsync(phi, phi_all + (size_t)(o - 1) * p_bar, sizeof(double) * p_bar, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      for (int j = 0; j < p_bar; ++j) phi[j] = 0.0;
+    }
+  }
+  if (h_status) {
+    char msg[112];
+    if (h_status >= 10000)
+      snprintf(msg, sizeof msg, "Repeated Halving: B^T B not positive definite at level %d", h_status - 10000);
+    else
+      snprintf(msg, sizeof msg, "sampled Gram matrix not positive definite at lag %d", h_status);
+    ctx->err = msg;
+    return TOLS_NOT_CONVERGED;
+  }
+  return TOLS_OK;
+}
+
 int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
                                       const int* p, double tol, double* d_phi, double* rnorm, tols_info* info) {
   if (!ctx || count < 0 || (count > 0 && (!d_y || !n || !p || !d_phi))) return TOLS_ERR_ARG;

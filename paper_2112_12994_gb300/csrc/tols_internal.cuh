@@ -239,5 +239,17 @@ cudaError_t launch_lsar_gram(const double* y, int p, const long long* rows, cons
 cudaError_t launch_lsar_solve(const double* G, int p, const double* y, const long long* rows, const double* w2,
                               int c, int ng, double* Lg, double* rdg, double* gpart, double* phi, double* tau,
                               int lag, int* status, cudaStream_t s);
+// Algorithm "Repeated Halving" (Section 3.2), tols_lsar.cu.
+constexpr int kRhMaxSketch = 64;        // largest sketch height k
+size_t rh_sketch_smem(int P1);
+cudaError_t launch_rh_map(const long long* in, const long long* keep, long long cnt, long long* out, cudaStream_t s);
+cudaError_t launch_rh_fill(double* x, long long cnt, double v, cudaStream_t s);
+cudaError_t launch_rh_factor(const double* G, int P1, double* Lg, double* rdg, int code, int* status,
+                             cudaStream_t s);
+cudaError_t launch_rh_sketch(const double* y, int P1, const long long* rows, const double* w2, int cnt,
+                             const double* S, int k, const double* Lg, const double* rdg, double* M, int* status,
+                             cudaStream_t s);
+cudaError_t launch_rh_score(const double* y, int P1, const double* M, int k, const long long* list, long long cnt,
+                            double* score, const int* status, cudaStream_t s);
 
 }  // namespace tols

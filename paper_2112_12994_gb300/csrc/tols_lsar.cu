@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(1024) lsar_prefix_kernel(const double* __restr
 }
 
 // Draw k (one warp): t = unif[k] * total; the row is the first i whose running sum exceeds t, or, if rounding
-// leaves none, the last row with a positive score. rows[k] = i, w2[k] = p / (c lev[i]) = 1 / (c pi_i).
+// leaves none, the last row with a positive score. rows[k] = i, w2[k] = p / (c lev[i]) = 1 / (c pi_i); with
+// p = 0 the scores are normalised by their sum instead, w2[k] = sum(lev) / (c lev[i]).
 // The running sums are formed block prefix + lane-segment prefix + rows within the segment; they may differ
 // from a plain left-to-right sum in the last bits, which matters only for a t within rounding of a boundary.
 __global__ void __launch_bounds__(256) lsar_sample_kernel(const double* __restrict__ lev, long long m,
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) lsar_sample_kernel(const double* __restri
   if (pick >= m) pick = m - 1;   // cannot happen; keeps every later read of y and lev in bounds
   if (lane == 0) {
     rows[k] = pick;
-    w2[k] = (double)p / ((double)c * lev[pick]);
+    w2[k] = (p > 0 ? (double)p : bpre[nb]) / ((double)c * lev[pick]);
   }
 }
 
@@ -294,11 +295,14 @@ __device__ void chol_solve_cta(const double* L, const double* rdiag, int p, doub
 // scaled, and copy the updated column k + 1 to the other buffer (nxt); meanwhile thread 0 updates the next
 // pivot, entry (k + 1, k + 1), and forms its reciprocal square root. L works in shared memory when
 // p <= kLsarSmemP, else in place in Lg. Writes L and its reciprocal diagonal to Lg, rdg (for
-// lsar_correct_kernel) and phi0 = H^-1 h to phi. A pivot that is not positive and finite makes phi and
-// tau[lag - 1] NaN and sets *status = lag, which skips every later kernel of the sweep.
+// lsar_correct_kernel) and, when phi is given, phi0 = H^-1 h to phi. off = 0 factors the whole augmented
+// matrix instead (H[j][l] = G[e(j, l)], p = its order; Repeated Halving's B^T B). A pivot that is not positive
+// and finite makes phi and tau[lag - 1] NaN (when given) and sets *status = lag, which skips every later
+// kernel of the sweep.
 __global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_chol_kernel(const double* __restrict__ G, int p,
-                                                                         double* Lg, double* rdg, double* phi,
-                                                                         double* tau, int lag, int* status) {
+                                                                         int off, double* Lg, double* rdg,
+                                                                         double* phi, double* tau, int lag,
+                                                                         int* status) {
   if (*status) return;
   extern __shared__ double lsm[];
   __shared__ int s_fail;
@@ -314,14 +318,14 @@ __global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_chol_kernel(const d
   double* rdiag = v + 5 * p;
   for (int idx = tid; idx < p * p; idx += kLsarSolveThreads) {
     const int i = idx / p, j = idx - i * p;
-    L[idx] = j <= i ? G[tri_index(1 + j, 1 + i)] : 0.0;
+    L[idx] = j <= i ? G[tri_index(off + j, off + i)] : 0.0;
   }
   for (int j = tid; j < p; j += kLsarSolveThreads) {
-    h[j] = G[tri_index(0, 1 + j)];
-    v[j] = G[tri_index(1, 1 + j)];   // column 0 of H, the first column buffer
+    if (phi) h[j] = G[tri_index(0, 1 + j)];
+    v[j] = G[tri_index(off, off + j)];   // column 0 of H, the first column buffer
   }
   if (tid == 0) {
-    const double d = G[tri_index(1, 1)];
+    const double d = G[tri_index(off, off)];
     s_fail = !(d > 0.0) || !isfinite(d);
     if (!s_fail) {
       const double r = rsqrt_newton(d);
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_chol_kernel(const d
     }
   }
   __syncthreads();
-  if (tid == 0 && !s_fail) L[0] = G[tri_index(1, 1)] * s_piv[0][0];
+  if (tid == 0 && !s_fail) L[0] = G[tri_index(off, off)] * s_piv[0][0];
   for (int k = 0; k < p && !s_fail; ++k) {
     const double r = s_piv[k & 1][0], r2 = s_piv[k & 1][1];
     const double* cur = v + (k & 1) * p;   // column buffers: v[0, p) and v[p, 2p)
@@ -364,18 +368,19 @@ __global__ void __launch_bounds__(kLsarSolveThreads, 1) lsar_chol_kernel(const d
     __syncthreads();
   }
   if (s_fail) {
-    for (int j = tid; j < p; j += kLsarSolveThreads) phi[j] = nan("");
+    if (phi)
+      for (int j = tid; j < p; j += kLsarSolveThreads) phi[j] = nan("");
     if (tid == 0) {
-      tau[lag - 1] = nan("");
+      if (tau) tau[lag - 1] = nan("");
       *status = lag;
     }
     return;
   }
-  chol_solve_cta(L, rdiag, p, h, w, x);
-  for (int j = tid; j < p; j += kLsarSolveThreads) {
-    phi[j] = x[j];
-    rdg[j] = rdiag[j];
+  if (phi) {
+    chol_solve_cta(L, rdiag, p, h, w, x);
+    for (int j = tid; j < p; j += kLsarSolveThreads) phi[j] = x[j];
   }
+  for (int j = tid; j < p; j += kLsarSolveThreads) rdg[j] = rdiag[j];
   if (in_smem)
     for (int idx = tid; idx < p * p; idx += kLsarSolveThreads) Lg[idx] = L[idx];
 }
@@ -502,13 +507,141 @@ cudaError_t launch_lsar_solve(const double* G, int p, const double* y, const lon
   size_t smem = lsar_chol_smem(p);
   cudaError_t e = cudaFuncSetAttribute(lsar_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  lsar_chol_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, p, Lg, rdg, phi, tau, lag, status);
+  lsar_chol_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, p, 1, Lg, rdg, phi, tau, lag, status);
   const int per_cta = (c + ng - 1) / ng;
   lsar_refine_kernel<<<ng, 256, sizeof(double) * 9 * (size_t)p, s>>>(y, p, rows, w2, c, per_cta, phi, gpart, status);
   smem = lsar_correct_smem(p);
   e = cudaFuncSetAttribute(lsar_correct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   lsar_correct_kernel<<<1, kLsarSolveThreads, smem, s>>>(Lg, rdg, p, gpart, ng, phi, tau, lag, status);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Algorithm "Repeated Halving" (Section 3.2) on [X | b] of order pb (rows a_i[q] = y[pb + i - q], q <= pb, the
+// augmented row order of the Gram kernel above; a column permutation changes no leverage score).
+
+// out[e] = (in ? in[keep[e]] : keep[e]), e < cnt: the original rows of the next halving level.
+__global__ void rh_map_kernel(const long long* __restrict__ in, const long long* __restrict__ keep, long long cnt,
+                              long long* out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    out[e] = in ? in[keep[e]] : keep[e];
+}
+
+__global__ void rh_fill_kernel(double* x, long long cnt, double v) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+
+// CTA t: row t of M = S B (B^T B)^-1, eq. (glev), with B's rows sqrt(w2_r) a_{rows[r]} (r < cnt), S the k x cnt
+// sketch (row-major) and B^T B = L L^T from lsar_chol_kernel (Lg, rdg; order P1 = pb + 1): first
+// h = B^T S(t,:)^T, then M(t,:) = (L L^T)^-1 h.
+__global__ void __launch_bounds__(kLsarSolveThreads, 1) rh_sketch_kernel(
+    const double* __restrict__ y, int P1, const long long* __restrict__ rows, const double* __restrict__ w2, int cnt,
+    const double* __restrict__ S, const double* __restrict__ Lg, const double* __restrict__ rdg, double* M,
+    const int* status) {
+  if (*status) return;
+  extern __shared__ double lsm[];
+  const int tid = threadIdx.x, t = blockIdx.x, pb = P1 - 1;
+  const bool in_smem = P1 <= kLsarSmemP;
+  double* Ls = lsm;
+  double* v = lsm + (in_smem ? (size_t)P1 * P1 : 0);
+  double* h = v;
+  double* w = v + P1;
+  double* x = v + 2 * P1;
+  double* rdiag = v + 3 * P1;
+  double* coef = v + 4 * P1;                                   // kLsarSolveThreads
+  long long* rr = reinterpret_cast<long long*>(coef + kLsarSolveThreads);   // kLsarSolveThreads
+  double acc = 0.0;                                            // h[q] for q = tid (tid < P1)
+  for (int r0 = 0; r0 < cnt; r0 += kLsarSolveThreads) {
+    const int nr = min(kLsarSolveThreads, cnt - r0);
+    __syncthreads();
+    if (tid < nr) {
+      coef[tid] = S[(size_t)t * cnt + r0 + tid] * sqrt(w2[r0 + tid]);
+      rr[tid] = rows[r0 + tid];
+    }
+    __syncthreads();
+    if (tid < P1)
+      for (int r = 0; r < nr; ++r) acc = fma(coef[r], y[pb + rr[r] - tid], acc);
+  }
+  if (tid < P1) h[tid] = acc;
+  if (in_smem)
+    for (int idx = tid; idx < P1 * P1; idx += kLsarSolveThreads) Ls[idx] = Lg[idx];
+  for (int j = tid; j < P1; j += kLsarSolveThreads) rdiag[j] = rdg[j];
+  __syncthreads();
+  chol_solve_cta(in_smem ? Ls : Lg, rdiag, P1, h, w, x);
+  for (int j = tid; j < P1; j += kLsarSolveThreads) M[(size_t)t * P1 + j] = x[j];
+}
+
+// score[e] = ||M a_i||^2, eq. (glev), for the row i = (list ? list[e] : e) of a halving level, e < cnt
+// (M: k x P1 in shared memory).
+__global__ void __launch_bounds__(256) rh_score_kernel(const double* __restrict__ y, int P1,
+                                                       const double* __restrict__ M, int k,
+                                                       const long long* __restrict__ list, long long cnt,
+                                                       double* score, const int* status) {
+  if (*status) return;
+  extern __shared__ double lsm[];
+  for (int idx = threadIdx.x; idx < k * P1; idx += blockDim.x) lsm[idx] = M[idx];
+  __syncthreads();
+  const int pb = P1 - 1;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x) {
+    const long long i = list ? list[e] : e;
+    const double* base = y + pb + i;
+    double sc = 0.0;
+    for (int t = 0; t < k; ++t) {
+      const double* mt = lsm + t * P1;
+      double s = 0.0;
+      for (int q = 0; q < P1; ++q) s = fma(mt[q], base[-q], s);
+      sc = fma(s, s, sc);
+    }
+    score[e] = sc;
+  }
+}
+
+size_t rh_sketch_smem(int P1) {
+  return sizeof(double) * ((P1 <= kLsarSmemP ? (size_t)P1 * P1 : 0) + 4 * (size_t)P1 + 2 * kLsarSolveThreads);
+}
+
+cudaError_t launch_rh_map(const long long* in, const long long* keep, long long cnt, long long* out,
+                          cudaStream_t s) {
+  const long long b = (cnt + 255) / 256;
+  rh_map_kernel<<<(unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b)), 256, 0, s>>>(in, keep, cnt, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rh_fill(double* x, long long cnt, double v, cudaStream_t s) {
+  const long long b = (cnt + 255) / 256;
+  rh_fill_kernel<<<(unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b)), 256, 0, s>>>(x, cnt, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rh_factor(const double* G, int P1, double* Lg, double* rdg, int code, int* status,
+                             cudaStream_t s) {
+  const size_t smem = lsar_chol_smem(P1);
+  cudaError_t e = cudaFuncSetAttribute(lsar_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  lsar_chol_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, P1, 0, Lg, rdg, nullptr, nullptr, code, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rh_sketch(const double* y, int P1, const long long* rows, const double* w2, int cnt,
+                             const double* S, int k, const double* Lg, const double* rdg, double* M, int* status,
+                             cudaStream_t s) {
+  const size_t smem = rh_sketch_smem(P1);
+  cudaError_t e = cudaFuncSetAttribute(rh_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  rh_sketch_kernel<<<k, kLsarSolveThreads, smem, s>>>(y, P1, rows, w2, cnt, S, Lg, rdg, M, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rh_score(const double* y, int P1, const double* M, int k, const long long* list, long long cnt,
+                            double* score, const int* status, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)k * P1;
+  cudaError_t e = cudaFuncSetAttribute(rh_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long b = (cnt + 255) / 256;
+  rh_score_kernel<<<(unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b)), 256, smem, s>>>(y, P1, M, k, list, cnt,
+                                                                                         score, status);
   return cudaGetLastError();
 }
 

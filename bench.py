@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--lsar-lags", type=int, default=120,
                     help="Algorithm LSAR on the bench series: lags 1 .. p_bar (0 = skip)")
     ap.add_argument("--lsar-c", type=int, default=2000, help="Algorithm LSAR: rows sampled per lag")
+    ap.add_argument("--rh-sketch", type=int, default=16, help="Repeated Halving: rows of the Gaussian sketch")
+    ap.add_argument("--rh-only", action="store_true",
+                    help="time only the Repeated Halving variant of LSAR on the bench series")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
     return ap.parse_args()
@@ -537,6 +540,34 @@ def run_lsar(tols, torch, y, args, exact_ms):
     return res
 
 
+def run_rh(tols, torch, y, args):
+    """The Repeated Halving variant of LSAR on the bench series (toeplitz_ols_rh_lsar): halvings down to c rows,
+    a k-row sketch per level, then lags 1 .. p_bar; draws and series resident on the device; best of 3."""
+    import numpy as np
+    from synthetic import lsar_uniforms, rh_draws
+    p_bar, c, k = args.lsar_lags, args.lsar_c, args.rh_sketch
+    m = y.size - p_bar
+    keep, gauss, rh_unif = rh_draws(m, c, k, c, config_id=2)
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_sk = torch.tensor(np.concatenate([g.reshape(-1) for g in gauss]), dtype=torch.float64, device="cuda")
+    d_rh = torch.tensor(np.stack(rh_unif), dtype=torch.float64, device="cuda")
+    d_u = torch.tensor(lsar_uniforms(p_bar, c, config_id=2), dtype=torch.float64, device="cuda")
+    times = []
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        tau, order, _, rc = tols.toeplitz_ols_rh_lsar(ctx, d_y, y.size, p_bar, c, k, keep, d_sk, d_rh, d_u)
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tau, order, _, rc = tols.toeplitz_ols_rh_lsar(ctx, d_y, y.size, p_bar, c, k, keep, d_sk, d_rh, d_u)
+            times.append(time.perf_counter() - t0)
+    ms = min(times) * 1e3
+    return {"lags": p_bar, "c": c, "k": k, "levels": len(keep), "ms_per_sweep": ms, "lags_per_s": p_bar / (ms * 1e-3),
+            "order_estimate": order, "status": rc, "tau_finite": bool(all(math.isfinite(t) for t in tau)),
+            "workload": "Repeated Halving variant of LSAR on the bench series (n = 2^22): halvings to c rows, "
+                        "k-row Gaussian sketches, lags 1 .. p_bar with c rows each; inputs in HBM, best of 3 "
+                        "(host clock around the call; the halving lists are copied to the device inside it)"}
+
+
 def run_serving(tols, serve_in, args):
     """Continuous batching: saturation throughput, then Poisson arrivals at half of it; p50/p99 latency."""
     import numpy as np
@@ -661,6 +692,11 @@ def main():
         run_kernel_only(args, wl)
     elif args.batch_only:
         run_batch_only(args)
+    elif args.rh_only:
+        import torch
+
+        import paper_2112_12994_gb300 as tols
+        print(json.dumps({"rh_only": True, **run_rh(tols, torch, make_series(wl).y, args)}), flush=True)
     elif args.lsar_only:
         import torch
 

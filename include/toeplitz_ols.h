@@ -316,6 +316,18 @@ int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_ba
                          const double* d_rh_unif, const double* d_unif, double* tau, int* order, double* phi,
                          double* d_scores, long long* d_rows);
 
+/* Algorithm "SRHT" (Section 2.1): phi minimising ||S H D (X phi - b)||, eq. (SRHT), for the order-p problem of
+ * eq. (xphi). The m = n - p rows of [X | b] are zero-padded to m2 = 2^ceil(log2 m); D = diag(d_signs) (m2 doubles,
+ * +-1, device); H is the normalised Hadamard transform of Def. "Hadamard Transform" (m2 x m2), applied to every
+ * column by its recursion; S takes the c rows d_rows[0 .. c) (int64 in [0, m2), device; drawn uniformly with
+ * replacement by the caller) scaled by sqrt(m2 / c). The compressed problem is solved through its normal
+ * equations (Cholesky). d_phi: p doubles (device). Needs 1 <= p <= 256, c >= p, n > p; holds (p + 1) m2
+ * doubles of device memory while it runs. Returns TOLS_ERR_ARG for a row index outside [0, m2) (found on the
+ * device; phi is then not written), TOLS_NOT_CONVERGED if the normal matrix is not positive definite. Returns
+ * after the context's stream finishes. */
+int toeplitz_ols_srht(tols_ctx* ctx, const double* d_y, long long n, int p, int c, const double* d_signs,
+                      const long long* d_rows, double* d_phi);
+
 /* ---- instrumentation (no counterpart in the paper: measurement of this library's own kernels) ----------
  * toeplitz_ols_profile(ctx, 1) clears the counters and starts timing every kernel the context launches with
  * a pair of CUDA events on the context's stream; 0 stops timing (counters are kept).

@@ -121,6 +121,7 @@ SIGNATURES = {
     "toeplitz_ols_lsar": (_I, [_P, _P, _LL, _I, _I, _P, _P, ctypes.POINTER(_I), _P, _P, _P]),
     "toeplitz_ols_rh_lsar": (_I, [_P, _P, _LL, _I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I), _P, _P,
                                   _P]),
+    "toeplitz_ols_srht": (_I, [_P, _P, _LL, _I, _I, _P, _P, _P]),
     "toeplitz_ols_server_config_default": (None, [ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tols_server_config)]),
     "toeplitz_ols_server_destroy": (_I, [_P]),
@@ -446,6 +447,21 @@ def toeplitz_ols_rh_lsar(ctx: Context, d_y, n: int, p_bar: int, c: int, k: int, 
                                   tau.ctypes.data, ctypes.byref(order), phi.ctypes.data, _ptr(d_scores), _ptr(d_rows))
     ctx.check(rc, "toeplitz_ols_rh_lsar")
     return tau, order.value, phi, rc
+
+
+def toeplitz_ols_srht(ctx: Context, d_y, n: int, p: int, d_signs, d_rows, d_phi):
+    """Algorithm SRHT for the order-p problem: device series, signs (m2 = next power of two >= n - p of them),
+    c = len(d_rows) sampled row indices (int64) -> d_phi (p doubles, device); returns the status."""
+    m = int(n) - int(p)
+    m2 = 1 << max(0, (m - 1).bit_length())
+    c = int(d_rows.numel()) if hasattr(d_rows, "numel") else 0
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_signs, m2, 8, "d_signs")
+    _dev(d_rows, c, 8, "d_rows")
+    _dev(d_phi, p, 8, "d_phi")
+    rc = lib.toeplitz_ols_srht(ctx.handle, _ptr(d_y), int(n), int(p), c, _ptr(d_signs), _ptr(d_rows), _ptr(d_phi))
+    ctx.check(rc, "toeplitz_ols_srht")
+    return rc
 
 
 def toeplitz_ols_profile(ctx: Context, enable: bool):

@@ -1876,6 +1876,45 @@ int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_ba
   return TOLS_OK;
 }
 
+int toeplitz_ols_srht(tols_ctx* ctx, const double* d_y, long long n, int p, int c, const double* d_signs,
+                      const long long* d_rows, double* d_phi) {
+  if (!ctx) return TOLS_ERR_ARG;
+  if (!d_y || !d_signs || !d_rows || !d_phi) return fail(ctx, TOLS_ERR_ARG, "null pointer");
+  if (p < 1 || p > kLsarMaxP) return fail(ctx, TOLS_ERR_ARG, "p out of range [1, 256]");
+  if (n <= p) return fail(ctx, TOLS_ERR_ARG, "need n > p");
+  if (c < p) return fail(ctx, TOLS_ERR_ARG, "need c >= p");
+  cudaSetDevice(ctx->device);
+  const long long m = n - p;
+  long long m2 = 1;
+  while (m2 < m) m2 <<= 1;
+  const long long tri = lsar_tri(p);
+  const int ng = std::max(1, std::min(ctx->sms, (c + 7) / 8));
+  const size_t nd = (size_t)(p + 1) * m2 + ng * (size_t)tri + tri + (size_t)p * p + p;
+  int rc;
+  if ((rc = ensure(ctx, ctx->lsar, sizeof(double) * nd + 256))) return rc;
+  double* q = (double*)ctx->lsar.p;
+  double* Z = q; q += (size_t)(p + 1) * m2;
+  double* part = q; q += ng * (size_t)tri;
+  double* G = q; q += tri;
+  double* Lg = q; q += (size_t)p * p;
+  double* rdg = q; q += p;
+  int* status = (int*)q;
+  CK(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
+  RUN(run_small(ctx, 12, [&] { return launch_srht_transform(d_y, p, m, m2, d_signs, Z, ctx->stream); }));
+  const double sc = sqrt((double)m2 / (double)c);
+  RUN(run_small(ctx, 12, [&] { return launch_srht_gram(Z, m2, p, d_rows, c, sc, ng, part, G, status, ctx->stream); }));
+  RUN(run_small(ctx, 12, [&] { return launch_srht_solve(G, p, Lg, rdg, d_phi, status, ctx->stream); }));
+  int h_status = 0;
+  CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h_status < 0) return fail(ctx, TOLS_ERR_ARG, "a sampled row index is outside [0, m2)");
+  if (h_status > 0) {
+    ctx->err = "the sampled, transformed Gram matrix is not positive definite";
+    return TOLS_NOT_CONVERGED;
+  }
+  return TOLS_OK;
+}
+
 int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* const* d_y, const long long* n,
                                       const int* p, double tol, double* d_phi, double* rnorm, tols_info* info) {
   if (!ctx || count < 0 || (count > 0 && (!d_y || !n || !p || !d_phi))) return TOLS_ERR_ARG;

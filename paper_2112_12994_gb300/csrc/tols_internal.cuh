@@ -251,5 +251,12 @@ cudaError_t launch_rh_sketch(const double* y, int P1, const long long* rows, con
                              cudaStream_t s);
 cudaError_t launch_rh_score(const double* y, int P1, const double* M, int k, const long long* list, long long cnt,
                             double* score, const int* status, cudaStream_t s);
+// Algorithm "SRHT" (Section 2.1), tols_lsar.cu.
+cudaError_t launch_srht_transform(const double* y, int p, long long m, long long m2, const double* signs, double* Z,
+                                  cudaStream_t s);
+cudaError_t launch_srht_gram(const double* Z, long long m2, int p, const long long* rows, int c, double sc, int ng,
+                             double* part, double* G, int* status, cudaStream_t s);
+cudaError_t launch_srht_solve(const double* G, int p, double* Lg, double* rdg, double* phi, int* status,
+                              cudaStream_t s);
 
 }  // namespace tols

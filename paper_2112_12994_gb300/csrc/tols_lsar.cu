@@ -645,4 +645,137 @@ cudaError_t launch_rh_score(const double* y, int P1, const double* M, int k, con
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Algorithm "SRHT" (Section 2.1, eq. (SRHT)) for the order-p problem: Z = H D [X | b] with the m rows zero-padded to
+// m2 = 2^k (column-major, column j < p holds X(:, j), column p holds b), then the c sampled rows scaled by
+// sqrt(m2 / c) go through the Gram kernel's layout (augmented order: b first) to lsar_chol_kernel.
+
+// Z[j m2 + i] = signs[i] * (i < m ? C(i, j) : 0).
+__global__ void srht_form_kernel(const double* __restrict__ y, int p, long long m, long long m2,
+                                 const double* __restrict__ signs, double* Z) {
+  const long long total = (long long)(p + 1) * m2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / m2, i = e - j * m2;
+    double v = 0.0;
+    if (i < m) v = j < p ? y[p - 1 + i - j] : y[p + i];
+    Z[e] = signs[i] * v;
+  }
+}
+
+// The Hadamard stages h = 1 .. blk/2 of Def. "Hadamard Transform" on chunks of blk entries (a power of two
+// dividing m2), in shared memory: (a, b) -> ((a + b) / sqrt 2, (a - b) / sqrt 2) for the pairs (i, i + h) of
+// every 2h-block.
+__global__ void __launch_bounds__(256) fwht_block_kernel(double* Z, int lblk) {
+  extern __shared__ double lsm[];
+  const int blk = 1 << lblk;
+  double* z = Z + (size_t)blockIdx.x * blk;
+  for (int i = threadIdx.x; i < blk; i += blockDim.x) lsm[i] = z[i];
+  const double s = 1.0 / sqrt(2.0);   // square root and quotient each rounded to double
+  for (int lh = 0; lh < lblk; ++lh) {
+    __syncthreads();
+    const int h = 1 << lh;
+    for (int t = threadIdx.x; t < blk / 2; t += blockDim.x) {
+      const int i = ((t >> lh) << (lh + 1)) + (t & (h - 1));
+      const double a = lsm[i], b = lsm[i + h];
+      lsm[i] = (a + b) * s;
+      lsm[i + h] = (a - b) * s;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < blk; i += blockDim.x) z[i] = lsm[i];
+}
+
+// One Hadamard stage with pair distance h = 2^lh over every column of length m2.
+__global__ void fwht_stage_kernel(double* Z, int cols, long long m2, int lh) {
+  const long long half = m2 / 2, total = (long long)cols * half, h = 1LL << lh;
+  const double s = 1.0 / sqrt(2.0);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long col = t / half, tt = t - col * half;
+    const long long i = col * m2 + ((tt >> lh) << (lh + 1)) + (tt & (h - 1));
+    const double a = Z[i], b = Z[i + h];
+    Z[i] = (a + b) * s;
+    Z[i + h] = (a - b) * s;
+  }
+}
+
+// CTA g: part[g][e(q, q2)] = sum over its draws k of a_k[q] a_k[q2], a_k = sc (Z(rows[k], p), Z(rows[k], 0 .. p-1)).
+// A row index outside [0, m2) sets *status = -1 and reads row 0 instead.
+__global__ void __launch_bounds__(256) srht_gram_kernel(const double* __restrict__ Z, long long m2, int p,
+                                                        const long long* __restrict__ rows, int c, double sc,
+                                                        int per_cta, double* part, long long tri, int* status) {
+  extern __shared__ double lsm[];
+  const int P1 = p + 1;
+  const int k0 = blockIdx.x * per_cta;
+  const int k1 = min(c, k0 + per_cta);
+  double* out = part + (size_t)blockIdx.x * tri;
+  if (k0 >= k1) {
+    for (long long e = threadIdx.x; e < tri; e += blockDim.x) out[e] = 0.0;
+    return;
+  }
+  for (int kc = k0; kc < k1; kc += kLsarChunk) {
+    const int cnt = min(kLsarChunk, k1 - kc);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt * P1; e += blockDim.x) {
+      const int kk = e / P1, q = e - kk * P1;
+      long long r = rows[kc + kk];
+      if (r < 0 || r >= m2) {
+        *status = -1;
+        r = 0;
+      }
+      const int col = q == 0 ? p : q - 1;
+      lsm[kk * P1 + q] = sc * Z[(size_t)col * m2 + r];
+    }
+    __syncthreads();
+    for (long long e = threadIdx.x; e < tri; e += blockDim.x) {
+      int q, q2;
+      tri_unpack(e, q, q2);
+      double acc = kc == k0 ? 0.0 : out[e];
+      for (int kk = 0; kk < cnt; ++kk) acc = fma(lsm[kk * P1 + q], lsm[kk * P1 + q2], acc);
+      out[e] = acc;
+    }
+  }
+}
+
+cudaError_t launch_srht_transform(const double* y, int p, long long m, long long m2, const double* signs, double* Z,
+                                  cudaStream_t s) {
+  const long long total = (long long)(p + 1) * m2;
+  const long long b = (total + 255) / 256;
+  srht_form_kernel<<<(unsigned)(b > 152 * 32 ? 152 * 32 : b), 256, 0, s>>>(y, p, m, m2, signs, Z);
+  int lm2 = 0;
+  while ((1LL << lm2) < m2) ++lm2;
+  const int lblk = lm2 < 12 ? lm2 : 12;   // chunks of up to 4,096 entries in shared memory
+  if (lblk > 0) {
+    const size_t smem = sizeof(double) * ((size_t)1 << lblk);
+    cudaError_t e = cudaFuncSetAttribute(fwht_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fwht_block_kernel<<<(unsigned)(total >> lblk), 256, smem, s>>>(Z, lblk);
+  }
+  for (int lh = lblk; lh < lm2; ++lh) {
+    const long long half = total / 2;
+    const long long bb = (half + 255) / 256;
+    fwht_stage_kernel<<<(unsigned)(bb > 152 * 32 ? 152 * 32 : bb), 256, 0, s>>>(Z, p + 1, m2, lh);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_srht_gram(const double* Z, long long m2, int p, const long long* rows, int c, double sc, int ng,
+                             double* part, double* G, int* status, cudaStream_t s) {
+  const long long tri = lsar_tri(p);
+  const int per_cta = (c + ng - 1) / ng;
+  const size_t smem = sizeof(double) * kLsarChunk * (size_t)(p + 1);
+  srht_gram_kernel<<<ng, 256, smem, s>>>(Z, m2, p, rows, c, sc, per_cta, part, tri, status);
+  const int rb = (int)((tri + 63) / 64);
+  lsar_reduce_kernel<<<rb < 1 ? 1 : rb, 64, 0, s>>>(part, ng, tri, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_srht_solve(const double* G, int p, double* Lg, double* rdg, double* phi, int* status,
+                              cudaStream_t s) {
+  const size_t smem = lsar_chol_smem(p);
+  cudaError_t e = cudaFuncSetAttribute(lsar_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  lsar_chol_kernel<<<1, kLsarSolveThreads, smem, s>>>(G, p, 1, Lg, rdg, phi, nullptr, 1, status);
+  return cudaGetLastError();
+}
+
 }  // namespace tols

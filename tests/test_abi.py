@@ -4,6 +4,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -83,3 +84,19 @@ def test_binding_checks_device_buffers(lib):
                                torch.zeros(190, dtype=torch.float64)[::2], torch.zeros(5, dtype=torch.float64))
     with pytest.raises(t.TolsError, match="d_phi"):
         t.toeplitz_ols_solve_device(None, y, 100, 20, torch.zeros(19, dtype=torch.float64))
+
+
+def test_binding_checks_sketch_buffers(lib):
+    torch = pytest.importorskip("torch")
+    import paper_2112_12994_gb300 as t
+    y = torch.zeros(3000, dtype=torch.float64)
+    with pytest.raises(t.TolsError, match="d_signs"):          # m2 = 4096 signs needed for m = 2997
+        t.toeplitz_ols_srht(None, y, 3000, 3, torch.zeros(2997, dtype=torch.float64),
+                            torch.zeros(10, dtype=torch.int64), torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(t.TolsError, match="d_rows"):
+        t.toeplitz_ols_srht(None, y, 3000, 3, torch.zeros(4096, dtype=torch.float64),
+                            torch.zeros(10, dtype=torch.int32), torch.zeros(3, dtype=torch.float64))
+    keep = [np.arange(1498), np.arange(749)]
+    with pytest.raises(t.TolsError, match="d_rh_unif"):
+        t.toeplitz_ols_rh_lsar(None, y, 3000, 4, 100, 4, keep, torch.zeros(4 * (100 + 749), dtype=torch.float64),
+                               torch.zeros(100, dtype=torch.float64), torch.zeros(400, dtype=torch.float64))

@@ -1732,6 +1732,7 @@ int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_ba
   orig_total = keep_total;
   const long long deep = h_sizes[levels];
   if (deep < P1) return fail(ctx, TOLS_ERR_ARG, "the deepest level needs at least p_bar + 1 rows");
+  if (deep > (1LL << 30)) return fail(ctx, TOLS_ERR_ARG, "the deepest level may hold at most 2^30 rows");
   {
     // each level's kept positions: increasing, inside the level above
     size_t off = 0;

@@ -307,7 +307,7 @@ int toeplitz_ols_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_bar, 
  * d_y: n doubles (device). d_unif: p_bar x c uniforms for the lags (device). tau (host, p_bar), order (host,
  * nullable), phi (host, nullable, p_bar doubles) as in toeplitz_ols_lsar. d_scores: device, nullable, m doubles
  * (level 0's scores). d_rows: device, nullable, p_bar x c sampled rows of the lags (int64).
- * Needs 1 <= p_bar <= 256, 1 <= k <= 64, c >= p_bar + 1, h_sizes[levels] >= p_bar + 1. Returns TOLS_ERR_ARG on
+ * Needs 1 <= p_bar <= 256, 1 <= k <= 64, c >= p_bar + 1, p_bar + 1 <= h_sizes[levels] <= 2^30. Returns TOLS_ERR_ARG on
  * malformed sizes or keep lists (checked before any device work), TOLS_NOT_CONVERGED if a B^T B or a sampled
  * Gram matrix is not positive definite (the message names the level or lag). Runs on the context's stream
  * and returns after it finishes. */

@@ -15,6 +15,10 @@
 //   lsar_refine_kernel  per-CTA partial of g = X^T W (b - X phi0) over the sampled rows;
 //   lsar_correct_kernel one CTA: phi = phi0 + H^-1 g (one step of the corrected semi-normal equations).
 // Every sum runs in a fixed order, so a sweep is bitwise reproducible. Rows with score 0 are never drawn.
+//
+// The same file holds Algorithm "Repeated Halving" (Section 3.2: rh_* kernels, which reuse the sampler, the Gram
+// kernel and the Cholesky kernel above on the augmented matrix [b | X] of order p_bar) and Algorithm "SRHT"
+// (Section 2.1: srht_* and fwht_* kernels, whose sampled rows go through the same Gram layout and Cholesky).
 #include <math.h>
 
 #include "tols_internal.cuh"

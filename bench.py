@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--rh-sketch", type=int, default=16, help="Repeated Halving: rows of the Gaussian sketch")
     ap.add_argument("--rh-only", action="store_true",
                     help="time only the Repeated Halving variant of LSAR on the bench series")
+    ap.add_argument("--srht-only", action="store_true",
+                    help="time only Algorithm SRHT for the order-p fit of the bench series (c = --lsar-c rows)")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
     return ap.parse_args()
@@ -568,6 +570,31 @@ def run_rh(tols, torch, y, args):
                         "(host clock around the call; the halving lists are copied to the device inside it)"}
 
 
+def run_srht(tols, torch, y, p, args):
+    """Algorithm SRHT (toeplitz_ols_srht) for the order-p fit of the bench series: random signs, the normalised
+    Hadamard transform of the p+1 padded columns, c sampled rows, the compressed fit; best of 3."""
+    import numpy as np
+    from synthetic import srht_draws
+    c = args.lsar_c
+    signs, rows = srht_draws(y.size - p, c, config_id=2)
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_s = torch.tensor(signs, dtype=torch.float64, device="cuda")
+    d_r = torch.tensor(rows.astype(np.int64), device="cuda")
+    d_phi = torch.empty(p, dtype=torch.float64, device="cuda")
+    times = []
+    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+        rc = tols.toeplitz_ols_srht(ctx, d_y, y.size, p, d_s, d_r, d_phi)
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = tols.toeplitz_ols_srht(ctx, d_y, y.size, p, d_s, d_r, d_phi)
+            times.append(time.perf_counter() - t0)
+    ms = min(times) * 1e3
+    return {"p": p, "c": c, "m2": int(signs.size), "ms_per_fit": ms, "fits_per_s": 1e3 / ms, "status": rc,
+            "workload": "Algorithm SRHT for the AR(p) fit of the bench series (n = 2^22): (p+1) columns of "
+                        "2^22 padded rows through the Hadamard transform, c rows sampled; best of 3 (host clock)"}
+
+
 def run_serving(tols, serve_in, args):
     """Continuous batching: saturation throughput, then Poisson arrivals at half of it; p50/p99 latency."""
     import numpy as np
@@ -692,6 +719,11 @@ def main():
         run_kernel_only(args, wl)
     elif args.batch_only:
         run_batch_only(args)
+    elif args.srht_only:
+        import torch
+
+        import paper_2112_12994_gb300 as tols
+        print(json.dumps({"srht_only": True, **run_srht(tols, torch, make_series(wl).y, wl["p"], args)}), flush=True)
     elif args.rh_only:
         import torch
 

@@ -9,8 +9,8 @@
  *     phi* = argmin_phi || X phi - b ||_2     (minimum-norm when X is rank deficient, Thm. "Solution to OLS
  *                                              problem").
  *
- * X is never formed: the Toeplitz structure means only the n numbers of y are needed (Section 3, "there are
- * only n+p-1 distinct numbers").
+ * X is never formed: a Toeplitz matrix is fixed by its first row and column (Section 3), here by y[0 .. n-2],
+ * and b by y[p .. n-1].
  *
  * Conventions for every function below:
  *   - Return 0 (TOLS_OK) on success, TOLS_NOT_CONVERGED (> 0, a warning) or a negative TOLS_ERR_* code.

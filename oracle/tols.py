@@ -42,6 +42,8 @@ Functions and the passage each follows:
                       sampling with replacement scaled by sqrt(n/c).
   generalized_leverage  Def. "Generalised Leverage Score" (Section 3.2) and its Gaussian-sketch approximation,
                       eq. (glev).
+  spectral_approximation  the sampling step of Algorithm "Repeated Halving" (Section 3.2): c rows drawn by their
+                      scores, each scaled by 1 / sqrt(c p_i).
   repeated_halving    Algorithm "Repeated Halving" (Section 3.2): halve uniformly down to a small level, then
                       back up, sampling each level by its approximate generalised leverage scores with respect to
                       the spectral approximation of the level below.
@@ -382,6 +384,15 @@ class RHResult:
     sizes: list              # rows at each halving level, top first
 
 
+def spectral_approximation(A, scores, u, c: int):
+    """The sampling step of Algorithm "Repeated Halving" (Section 3.2): c rows of A drawn with replacement from
+    p_i = scores_i / sum(scores) by leverage_sample on the uniforms u, each scaled by 1 / sqrt(c p_i). Returns the
+    drawn row indices and the scaled rows (the approximation that the level above is scored against)."""
+    rows = leverage_sample(scores, u)
+    prob = scores[rows] / math.fsum(np.asarray(scores, dtype=np.float64).tolist())
+    return rows, np.asarray(A, dtype=np.float64)[rows] / np.sqrt(c * prob)[:, None]
+
+
 def repeated_halving(X, c: int, min_rows: int, keep, gauss, unif) -> RHResult:
     """Algorithm "Repeated Halving" (Section 3.2) with its random draws as inputs.
 
@@ -403,9 +414,7 @@ def repeated_halving(X, c: int, min_rows: int, keep, gauss, unif) -> RHResult:
     scores = rows = None
     for j in range(len(levels) - 2, -1, -1):
         scores = generalized_leverage(levels[j], Xt, gauss[j])
-        rows = leverage_sample(scores, unif[j])
-        prob = scores[rows] / math.fsum(scores.tolist())
-        Xt = levels[j][rows] / np.sqrt(c * prob)[:, None]
+        rows, Xt = spectral_approximation(levels[j], scores, unif[j], c)
     if scores is None:                         # X itself is small: its exact scores, all of its rows
         scores = generalized_leverage(X, X)
         rows = np.arange(X.shape[0])

@@ -502,3 +502,52 @@ def test_sketch_planted_mistakes_are_caught(monkeypatch):
     Q, _ = np.linalg.qr(C)
     wrong = np.einsum("ij,jk,ik->i", C, C.T @ C, C)
     assert not np.allclose(wrong, np.sum(Q * Q, axis=1))
+
+
+def _rh_upsweep_expected():
+    """Level-0 scores of Algorithm "Repeated Halving" (Section 3.2) on a hand-built 8 x 2 matrix, written out
+    with explicit 2 x 2 Gram matrices (no oracle call). Halving keeps rows 0, 2, 5, 7 (level 1) and then level
+    1's rows 1, 2 (level 2, the deepest: its own approximation, unscaled). Sketches are identities, so eq. (glev)
+    gives the exact generalised scores x^T (B^T B)^{-1} x of Def. "Generalised Leverage Score"."""
+    C = np.array([[1, 0], [0, 1], [1, 1], [2, -1], [1, 3], [-1, 2], [3, 1], [0, 2]], dtype=np.float64)
+    lvl1 = C[[0, 2, 5, 7]]
+    lvl2 = lvl1[[1, 2]]
+    G2 = sum(np.outer(r, r) for r in lvl2)                  # [[2, -1], [-1, 5]], det 9
+    s1 = np.array([r @ np.linalg.inv(G2) @ r for r in lvl1])
+    assert np.allclose(s1 * 9, [5, 9, 9, 8])
+    # three draws from level 1 by inverse CDF at u = 0.1, 0.5, 0.9 of the running sums 5, 14, 23, 31 (/ 9)
+    picks = [0, 2, 3]
+    pi = s1[picks] / s1.sum()                              # 5/31, 9/31, 8/31
+    G1 = sum(np.outer(lvl1[k], lvl1[k]) / (3 * q) for k, q in zip(picks, pi))
+    s0 = np.array([r @ np.linalg.inv(G1) @ r for r in C])
+    return C, G1, s0
+
+
+def test_repeated_halving_upsweep_pinned():
+    """Level j is scored against the rescaled sample of level j+1 (its spectral approximation), not against the
+    raw level j+1."""
+    C, G1, s0 = _rh_upsweep_expected()
+    keep = [np.array([0, 2, 5, 7]), np.array([1, 2])]
+    gauss = [np.eye(3), np.eye(2)]
+    unif = [np.array([0.3, 0.6, 0.95]), np.array([0.1, 0.5, 0.9])]
+    rh = oracle.repeated_halving(C, 3, 2, keep, gauss, unif)
+    assert rh.sizes == [8, 4, 2]
+    assert np.allclose(rh.scores, s0, rtol=1e-13, atol=0)
+    # scored against the raw level 1 instead, the scores differ by far more than rounding
+    G_raw = C[[0, 2, 5, 7]].T @ C[[0, 2, 5, 7]]
+    s_raw = np.array([r @ np.linalg.inv(G_raw) @ r for r in C])
+    assert np.max(np.abs(s_raw - s0) / s0) > 0.1
+
+
+def test_repeated_halving_raw_level_mistake_is_caught(monkeypatch):
+    """Plant the raw-level mistake in the oracle (CPU only): the approximation step returns level j+1 itself."""
+    C, _, s0 = _rh_upsweep_expected()
+
+    def raw_level(A, scores, u, c):
+        A = np.asarray(A, dtype=np.float64)
+        return np.arange(A.shape[0]), A
+
+    monkeypatch.setattr(tols, "spectral_approximation", raw_level)
+    rh = oracle.repeated_halving(C, 3, 2, [np.array([0, 2, 5, 7]), np.array([1, 2])], [np.eye(4), np.eye(2)],
+                                 [np.array([0.3, 0.6, 0.95]), np.array([0.1, 0.5, 0.9])])
+    assert not np.allclose(rh.scores, s0, rtol=1e-6, atol=0)

@@ -236,7 +236,9 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
  *     every GPU that loads the library until the process exits. Its size limits p to TOLS_NOALLOC_MAX_P; larger
  *     p returns TOLS_ERR_ARG, as do n <= p, a bad precision and null d_y, d_v, d_xtu or d_unorm2.
  *   - The first call on a device looks up that array's device address (cudaGetSymbolAddress) with that device
- *     current; make this first call before any stream capture on that device.
+ *     current; make this first call before any stream capture on that device. The address is kept for the life
+ *     of the process and belongs to the device's primary context: do not call this entry point from another
+ *     context on that device, nor after cudaDeviceReset.
  *   - Every call on a device shares the one array: calls whose work overlaps on the GPU (different streams, or
  *     different host threads) race and give wrong results. Serialise them (one stream, or events). Each call
  *     clears the arrival counters it relies on before its kernel runs.

@@ -216,7 +216,7 @@ int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
     int nb = 0;
     const void* fn = fft ? fft_kernel_ptr(is_double) : pass_kernel_ptr(is_double);
     const size_t smem = pass_smem_bytes(is_double, p_pad, fft);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    smem_opt_in(fn, 200 * 1024);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
     // A float64 FFT pass keeps the FP64 pipe busy with two CTAs per SM already; a third adds one more closing
     // inverse transform per SM without raising the pipe's throughput (4M rows, p = 100: 0.471 ms at 2 per SM,
@@ -683,7 +683,7 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
 
 int batch_grid(tols_ctx* ctx, int is_double, int p_pad) {
   int nb = 0;
-  cudaFuncSetAttribute(batch_kernel_ptr(is_double), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  smem_opt_in(batch_kernel_ptr(is_double), 200 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(is_double), kThreads,
                                                     pass_smem_bytes(is_double, p_pad)) != cudaSuccess || nb < 1)
     nb = 1;
@@ -692,7 +692,7 @@ int batch_grid(tols_ctx* ctx, int is_double, int p_pad) {
 
 int batch_fft_grid(tols_ctx* ctx, int p_pad) {
   int nb = 0;
-  cudaFuncSetAttribute(batch_fft_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  smem_opt_in(batch_fft_kernel_ptr(), 200 * 1024);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fft_kernel_ptr(), kThreads, batch_fft_smem(p_pad)) !=
           cudaSuccess || nb < 1)
     nb = 1;
@@ -1801,8 +1801,9 @@ int toeplitz_ols_rh_lsar(tols_ctx* ctx, const double* d_y, long long n, int p_ba
   const long long* b_rows = orig + orig_off[levels];
   long long b_cnt = deep;
   RUN(run_small(ctx, 12, [&] { return launch_rh_fill(bw2, deep, 1.0, ctx->stream); }));
+  // S_0 .. S_{levels-2} are k x c each; the deepest level's k x deep sketch S_{levels-1} comes last
   std::vector<size_t> sk_off((size_t)levels, 0);
-  for (int j = 1; j < levels; ++j) sk_off[j] = sk_off[j - 1] + (size_t)k * (size_t)(j - 1 == levels - 1 ? deep : c);
+  for (int j = 1; j < levels; ++j) sk_off[j] = (size_t)k * (size_t)c * (size_t)j;
   for (int j = levels - 1; j >= 0; --j) {
     const int gj = std::max(1, std::min(ctx->sms, (int)((b_cnt + 7) / 8)));
     const long long* list = j == 0 ? nullptr : orig + orig_off[j];

@@ -182,6 +182,7 @@ __host__ __device__ constexpr size_t batch_fft_spectra_doubles(long long m, int 
 }
 
 // Launch helpers (tols_kernels.cu).
+cudaError_t smem_opt_in(const void* fn, int bytes);   // per-device dynamic shared-memory opt-in, set once
 size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
 const void* fft_kernel_ptr(int is_double);
 int fft_size(int is_double);              // N of the real FFT per tile (float 4096, double 2048)

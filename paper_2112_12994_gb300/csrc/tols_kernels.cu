@@ -15,11 +15,31 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "tols_internal.cuh"
 
 namespace tols {
 
 __host__ __device__ inline long long lmin(long long a, long long b) { return a < b ? a : b; }
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device. The attribute belongs to the
+// device, so the record of what was set is kept per (device, kernel, bytes); several host threads may call this.
+cudaError_t smem_opt_in(const void* fn, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  const auto key = std::make_tuple(dev, fn, bytes);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
 
 // ------------------------------------------------------------------------------------------------------
 // shared-memory layout of the y window: 4 pad elements after every 16, so that 16-B vector loads by lanes
@@ -851,14 +871,8 @@ static size_t pass_smem(int p_pad) {
 
 template <typename T>
 cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
-  static int configured[4] = {0, 0, 0, 0};
-  const int which = (sizeof(T) == 8) + 2 * (a.fft != 0);
-  if (!configured[which]) {
-    cudaError_t e = cudaFuncSetAttribute(a.fft ? (const void*)fft_pass_kernel<T> : (const void*)pass_kernel<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured[which] = 1;
-  }
+  cudaError_t e = smem_opt_in(a.fft ? (const void*)fft_pass_kernel<T> : (const void*)pass_kernel<T>, 200 * 1024);
+  if (e != cudaSuccess) return e;
   const long long rows_per_tile = a.fft ? (long long)(FftCfg<T>::N - a.p_pad) : (long long)TileCfg<T>::TILE;
   const long long ntiles = (a.m + rows_per_tile - 1) / rows_per_tile;
   int g = (int)lmin((long long)grid, ntiles);
@@ -895,12 +909,8 @@ static cudaError_t launch_spectra_t(const T* y, long long n, long long m, int p_
                                     int grid, cudaStream_t s) {
   using V = typename FftCfg<T>::V;
   const size_t smem = round16(sizeof(V) * 2 * (size_t)FftCfg2<T>::PADDED);   // the work arrays A, B only
-  static int configured = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(spectrum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = 1;
-  }
+  cudaError_t e = smem_opt_in((const void*)spectrum_kernel<T>, 200 * 1024);
+  if (e != cudaSuccess) return e;
   const int L = FftCfg<T>::N - p_pad;
   const long long ntiles = (m + L - 1) / L;
   const int g = (int)lmin((long long)grid, ntiles);
@@ -920,14 +930,8 @@ const void* pass_kernel_ptr(int is_double) {
 template <typename T>
 cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s) {
   const size_t smem = pass_smem<T>(p_pad_max);
-  static int configured[2] = {0, 0};
-  const int which = sizeof(T) == 8;
-  if (!configured[which]) {
-    cudaError_t e =
-        cudaFuncSetAttribute(batch_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured[which] = 1;
-  }
+  cudaError_t e = smem_opt_in((const void*)batch_pass_kernel<T>, 200 * 1024);
+  if (e != cudaSuccess) return e;
   const long long total = sizeof(T) == 8 ? a.tiles_d : a.tiles_f;
   int g = (int)lmin((long long)grid, total);
   if (g < 1) g = 1;
@@ -937,25 +941,17 @@ cudaError_t launch_batch_pass(const BatchArgs& a, int grid, int p_pad_max, cudaS
 size_t batch_fft_smem(int p_pad_max) { return fft_pass_smem<double>(p_pad_max); }
 const void* batch_fft_kernel_ptr() { return (const void*)batch_fft_kernel; }
 cudaError_t launch_batch_fft(const BatchArgs& a, int grid, int p_pad_max, cudaStream_t s) {
-  static int configured = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = 1;
-  }
+  cudaError_t e = smem_opt_in((const void*)batch_fft_kernel, 200 * 1024);
+  if (e != cudaSuccess) return e;
   int g = (int)lmin((long long)grid, a.tiles_x);
   if (g < 1) return cudaSuccess;
   batch_fft_kernel<<<g, kThreads, batch_fft_smem(p_pad_max), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_batch_dspec(const BatchSeries* series, int count, cudaStream_t s) {
-  static int configured = 0;
   const size_t smem = FftSmem<double>::bytes(0);
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(batch_dspec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = 1;
-  }
+  cudaError_t e = smem_opt_in((const void*)batch_dspec_kernel, (int)smem);
+  if (e != cudaSuccess) return e;
   if (count < 1) return cudaSuccess;
   batch_dspec_kernel<<<count, kThreads, smem, s>>>(series);
   return cudaGetLastError();
@@ -1466,14 +1462,10 @@ static size_t precond_smem(int p_max) {
   return sizeof(double) * 2 * (size_t)q * q;
 }
 static cudaError_t precond_config() {
-  static int done = 0;
-  if (done) return cudaSuccess;
   // dynamic plus static shared memory must stay within the per-CTA limit: ask for exactly the largest need
   const int bytes = (int)precond_smem(kPrecondSmemP);
-  cudaError_t e = cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(precond_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done = 1;
+  cudaError_t e = smem_opt_in((const void*)precond_kernel, bytes);
+  if (e == cudaSuccess) e = smem_opt_in((const void*)precond_batch_kernel, bytes);
   return e;
 }
 

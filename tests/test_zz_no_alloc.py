@@ -76,3 +76,40 @@ def test_noalloc_rejects_orders_beyond_its_array():
     d_n2 = torch.zeros(1, dtype=torch.float64, device="cuda")
     rc = t.toeplitz_ols_gk_pass_noalloc(t.TOLS_FP64, d_y, n, p, d_v, None, 0.0, None, d_t, d_n2, None)
     assert rc == t.TOLS_ERR_ARG
+
+
+def test_noalloc_second_stream_ordered_by_event():
+    """Calls on two streams share the one array; ordered by an event (the documented way to serialise them),
+    the second call on another stream gives the first call's outputs bit for bit."""
+    import torch
+
+    import paper_2112_12994_gb300 as t
+    from synthetic import ar_series
+
+    p, n = 64, 5 * 4096 + 123
+    m = n - p
+    y = ar_series(n, 3, config_id=71).y
+    rng = np.random.default_rng(7)
+    d_y = torch.tensor(y, dtype=torch.float64, device="cuda")
+    d_v = torch.tensor(rng.standard_normal(p), dtype=torch.float64, device="cuda")
+    d_uo = torch.tensor(rng.standard_normal(m), dtype=torch.float64, device="cuda")
+    s1 = torch.cuda.Stream()
+    s2 = torch.cuda.Stream()
+    outs = []
+    done = torch.cuda.Event()
+    for k, s in enumerate((s1, s2)):
+        out_u = torch.empty(m, dtype=torch.float64, device="cuda")
+        out_t = torch.empty(p, dtype=torch.float64, device="cuda")
+        out_n2 = torch.empty(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()            # the outputs exist before either stream touches them
+        if k == 1:
+            s.wait_event(done)              # the second call waits for the first one's kernel
+        rc = t.toeplitz_ols_gk_pass_noalloc(t.TOLS_FP64, d_y, n, p, d_v, d_uo, 0.25, out_u, out_t, out_n2,
+                                            s.cuda_stream)
+        assert rc == t.TOLS_OK
+        if k == 0:
+            done.record(s)
+        outs.append((out_u, out_t, out_n2))
+    torch.cuda.synchronize()
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)

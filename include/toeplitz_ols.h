@@ -253,6 +253,21 @@ int toeplitz_ols_gk_pass_noalloc(int precision, const void* d_y, long long n, in
 int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, double* d_G,
                       double* d_h, double* bnorm2);
 
+/* The preconditioner of a solve (the factor R of LSQR on X R^{-1}; the row-sampling idea of Section 3.1 supplies
+ * the sampled-row variant): from a Gram pass over d_y (n doubles, device) in the given precision,
+ *   kind = TOLS_PRECOND_GRAM_CHOL : R = the Cholesky factor of G = X^T X (shifted by 10 p u max_j G_jj when a pivot
+ *                                   falls to rounding level);
+ *   kind = TOLS_PRECOND_SAMPLED_QR: float64 only: if the Gram factor is not trusted (kappa(R)^2 u > 1/4) or always
+ *                                   when asked, R from shifted Cholesky QR of c rows of X sampled evenly (row
+ *                                   floor((2k + 1) m / (2c)), k < c), c = 32p if m >= 256 p^2, 16p if m >= 128 p^2,
+ *                                   else 8p; needs m >= 8p; the Gram factor if that fails.
+ * From p = 64 up this runs on every SM (32 x 32 tiles); below, in one CTA (sampled-row Householder QR, p <= 256).
+ * d_M (device, p x p doubles, row-major) receives M = R^{-1}, upper triangular. info (host, nullable): precond_used,
+ * cond_est (kappa estimate: ||X||_2 ||R^{-1}||_2, or that of the sample for the QR), anorm_2, anorm_f, bnorm.
+ * Returns TOLS_NOT_CONVERGED when no factor could be formed (d_M untouched). */
+int toeplitz_ols_preconditioner(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, int kind,
+                                double* d_M, tols_info* info);
+
 /* Row norms of X: d_rn2[i] = ||X(i,:)||^2 = sum_{t=i}^{i+p-1} y[t]^2 (m doubles, device, nullable) and
  * *fro2 = ||X||_F^2 (host), from a float64 prefix scan of y^2. */
 int toeplitz_ols_row_norms(tols_ctx* ctx, const double* d_y, long long n, int p, double* d_rn2, double* fro2);

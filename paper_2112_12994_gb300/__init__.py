@@ -114,6 +114,7 @@ SIGNATURES = {
     "toeplitz_ols_gk_pass": (_I, [_P, _I, _P, _LL, _I, _P, _P, ctypes.c_double, _P, _P, _D]),
     "toeplitz_ols_gk_pass_noalloc": (_I, [_I, _P, _LL, _I, _P, _P, ctypes.c_double, _P, _P, _P, _P]),
     "toeplitz_ols_gram": (_I, [_P, _I, _P, _LL, _I, _P, _P, _D]),
+    "toeplitz_ols_preconditioner": (_I, [_P, _I, _P, _LL, _I, _I, _P, ctypes.POINTER(tols_info)]),
     "toeplitz_ols_row_norms": (_I, [_P, _P, _LL, _I, _P, _D]),
     "toeplitz_ols_residual": (_I, [_P, _P, _LL, _I, _P, _P, _D]),
     "toeplitz_ols_leverage_p1": (_I, [_P, _P, _LL, _P]),
@@ -363,6 +364,16 @@ def toeplitz_ols_gram(ctx: Context, precision: int, d_y, n: int, p: int, d_G, d_
     ctx.check(lib.toeplitz_ols_gram(ctx.handle, precision, _ptr(d_y), n, p, _ptr(d_G), _ptr(d_h), ctypes.byref(b2)),
               "toeplitz_ols_gram")
     return b2.value
+
+
+def toeplitz_ols_preconditioner(ctx: Context, precision: int, d_y, n: int, p: int, kind: int, d_M):
+    """M = R^{-1} (p x p, row-major, device) of the solver's preconditioner; returns (info dict, status)."""
+    _dev(d_y, n, 8, "d_y")
+    _dev(d_M, p * p, 8, "d_M")
+    info = tols_info()
+    rc = lib.toeplitz_ols_preconditioner(ctx.handle, precision, _ptr(d_y), n, p, kind, _ptr(d_M), ctypes.byref(info))
+    ctx.check(rc, "toeplitz_ols_preconditioner")
+    return info.as_dict(), rc
 
 
 def toeplitz_ols_row_norms(ctx: Context, d_y, n: int, p: int, d_rn2=None):

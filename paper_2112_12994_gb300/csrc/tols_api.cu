@@ -51,13 +51,14 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec, lsar;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec, lsar, pcl;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
   size_t h_stage_cap = 0;
   DevState* h_state = nullptr;  // pinned copy of the device state, followed by a pinned phi (TOLS_MAX_P doubles)
   double* h_phi = nullptr;
+  PclInfo* h_pcl = nullptr;     // pinned copy of the multi-CTA preconditioner's report (after h_phi)
   std::string err;
   std::map<int, StreamSeries> streams;
   int next_handle = 1;
@@ -387,9 +388,135 @@ int validate(tols_ctx* ctx, long long n, int p) {
   return TOLS_OK;
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Multi-CTA preconditioner of single-series solves (tols_precond.cu), for orders from kPclMinP up.
+constexpr int kPclMinP = 64;
+
+// Rows of X sampled for the QR preconditioner: c = r p with r = 8, 16 or 32. More rows lower kappa(X R^{-1})
+// (about 2.1, 1.6, 1.4 on the AR(500) bench series), which saves LSQR iterations, each a pass over all m rows;
+// the sample's QR costs O(c p^2). r grows with m / (8 p^2), the ratio of the two.
+long long pcl_sample_rows(long long m, int p) {
+  const long long q = m / (8LL * p * p);
+  const long long r = q >= 32 ? 32 : q >= 16 ? 16 : 8;
+  return r * p;
+}
+
+int pcl_sync(tols_ctx* ctx, const PclInfo* d_info) {
+  CK(cudaMemcpyAsync(ctx->h_pcl, d_info, sizeof(PclInfo), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TOLS_OK;
+}
+
+// Every tile step of the blocked Cholesky of Gp (P x P).
+int pcl_factor(tols_ctx* ctx, double* Gp, int P, int p, double tiny_dmax, double tiny_shift, PclInfo* d_info) {
+  const int nt = P / kPclTile;
+  for (int k = 0; k < nt; ++k) {
+    RUN(run_small(ctx, 10, [&] { return pcl_chol_panel(Gp, P, p, k, tiny_dmax, tiny_shift, d_info, ctx->stream); }));
+    if (k + 1 < nt) RUN(run_small(ctx, 10, [&] { return pcl_chol_update(Gp, P, k, d_info, ctx->stream); }));
+  }
+  return TOLS_OK;
+}
+
+// The preconditioner of one solve, with the state precond_kernel leaves: norms of X from G (trace, power
+// iteration), the Cholesky factor of G (refactored with the shift 10 p u max_j G_jj if a pivot falls to rounding
+// level, which flags G as singular), M = R^{-1}, kappa(R) and the trust test kappa(R)^2 u <= 1/4 (u of the
+// precision G was formed in). A float64 solve whose factor is not trusted (or that asks for it) is preconditioned
+// instead by the R of c sampled rows of X from shifted Cholesky QR (two shifted stages, shift
+// 11 (c p + p (p + 1)) u lambda_max, then one plain stage; R = R3 R2 R1). The host reads a small report after
+// each factorisation.
+int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
+  const int p = w.p, P = pcl_pad_p(p), nt = P / kPclTile;
+  const size_t PP = (size_t)P * P;
+  const double ueps = mixed ? 5.96e-8 : 1.11e-16;
+  const bool qr_ok = !mixed && want != 0 && w.m >= 8LL * p;
+  const long long c = qr_ok ? pcl_sample_rows(w.m, p) : 0;
+  const int slices = c ? pcl_gram_slices(c, P) : 0;
+  const size_t ntiles = (size_t)nt * (nt + 1) / 2;
+  const size_t head = 256;                                   // PclInfo
+  const size_t fb_bytes = (sizeof(float) * (size_t)p * p + 255) / 256 * 256;
+  size_t bytes = head + fb_bytes + sizeof(double) * PP;      // report, float copy, Gp
+  if (c) bytes += sizeof(double) * (3 * PP + (size_t)c * p + (size_t)slices * ntiles * 1024);
+  RUN(ensure(ctx, ctx->pcl, bytes));
+  char* base = (char*)ctx->pcl.p;
+  PclInfo* d_info = (PclInfo*)base;
+  float* fb = (float*)(base + head);
+  double* Gp = (double*)(base + head + fb_bytes);
+  double* Rq[3] = {Gp + PP, Gp + 2 * PP, Gp + 3 * PP};
+  double* A = Gp + 4 * PP;
+  double* part = A + (size_t)c * p;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(d_info, 0, sizeof(PclInfo), st));
+  RUN(run_small(ctx, 10, [&] { return pcl_lambda(w.G, p, p, 0.0, 0, fb, d_info, st); }));
+  bool ok = false, shifted = false, singular = false;
+  double cond = 0.0;
+  if (want) {
+    RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, 0.0, nullptr, st); }));
+    RUN(pcl_factor(ctx, Gp, P, p, (double)p * ueps, 0.0, d_info));
+    RUN(pcl_sync(ctx, d_info));
+    if (!ctx->h_pcl->nonfinite) {
+      if (ctx->h_pcl->fail) {
+        singular = true;
+        const double lambda = 10.0 * (double)p * ueps * ctx->h_pcl->dmax;
+        CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
+        RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, lambda, nullptr, st); }));
+        RUN(pcl_factor(ctx, Gp, P, p, 1e-3 * 10.0 * (double)p * ueps, 0.0, d_info));
+        RUN(pcl_sync(ctx, d_info));
+        shifted = !ctx->h_pcl->fail;
+      }
+      if (!ctx->h_pcl->fail) {
+        RUN(run_small(ctx, 10, [&] { return pcl_inverse(Gp, P, p, w.M, d_info, st); }));
+        RUN(run_small(ctx, 10, [&] { return pcl_estimate(w.M, p, 0, fb, d_info, st); }));
+        RUN(pcl_sync(ctx, d_info));
+        cond = ctx->h_pcl->cond;
+        ok = true;
+      }
+    }
+  }
+  const bool nonfinite = ctx->h_pcl->nonfinite != 0 && want;
+  bool trusted = ok && !shifted && cond * cond * ueps <= 0.25;
+  int precond = ok ? 1 : 0;
+  double kappa_est = cond;
+  if (qr_ok && !nonfinite && (want == 2 || !trusted)) {
+    CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
+    RUN(run_small(ctx, 10, [&] { return pcl_gather(w.y64, w.m, p, c, A, st); }));
+    for (int s = 0; s < 3; ++s) {
+      const double shift_rel = s < 2 ? 11.0 * ((double)c * p + (double)p * (p + 1)) * 1.11e-16 : 0.0;
+      RUN(run_small(ctx, 10, [&] { return pcl_tall_gram(A, c, p, P, slices, part, st); }));
+      RUN(run_small(ctx, 10, [&] { return pcl_gram_reduce(part, P, slices, p, Gp, st); }));
+      RUN(run_small(ctx, 10, [&] { return pcl_lambda(Gp, P, p, shift_rel, s == 0 ? 1 : -1, fb, d_info, st); }));
+      RUN(pcl_factor(ctx, Gp, P, p, s < 2 ? 0.0 : (double)p * 1.11e-16, s < 2 ? 1e-3 : 0.0, d_info));
+      if (s < 2) {
+        CK(cudaMemcpyAsync(Rq[s], Gp, sizeof(double) * PP, cudaMemcpyDeviceToDevice, st));
+        RUN(run_small(ctx, 10, [&] { return pcl_trsm(A, c, p, Gp, P, st); }));
+      }
+    }
+    RUN(pcl_sync(ctx, d_info));
+    if (!ctx->h_pcl->fail && !ctx->h_pcl->nonfinite) {
+      RUN(run_small(ctx, 10, [&] { return pcl_trmm(Rq[1], Rq[0], Rq[2], P, st); }));   // R2 R1
+      RUN(run_small(ctx, 10, [&] { return pcl_trmm(Gp, Rq[2], Rq[0], P, st); }));      // R3 R2 R1
+      RUN(run_small(ctx, 10, [&] { return pcl_inverse(Rq[0], P, p, w.M, d_info, st); }));
+      RUN(run_small(ctx, 10, [&] { return pcl_estimate(w.M, p, 1, fb, d_info, st); }));
+      RUN(pcl_sync(ctx, d_info));
+      cond = ctx->h_pcl->cond;
+      // the sampled R is about sqrt(c / m) times the full one: ||A||_2 ||R^{-1}||_2 is kappa of the sample
+      kappa_est = cond;
+      precond = 2;
+      trusted = false;
+      shifted = false;
+    }
+    CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
+  }
+  if (precond) RUN(run_small(ctx, 10, [&] { return pcl_store(w, mixed ? 1 : 0, d_info, st); }));
+  RUN(run_small(ctx, 10, [&] {
+    return pcl_state(w, d_info, precond, shifted ? 1 : 0, trusted ? 1 : 0, singular ? 1 : 0, cond, kappa_est, st);
+  }));
+  return TOLS_OK;
+}
+
 // Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path). fft: the Gram pass uses the FFT
 // kernel and writes the window spectra of its precision (room made by fft_spectra).
-int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, bool converted = false) {
+int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, bool converted = false,
+              int want_override = -1) {
   const int pg = pad_p(w.p + 1);
   if (mixed) {
     if (!converted)
@@ -410,7 +537,8 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, 
     a.fft = fft;
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   }
-  const int want = no_precond ? 0 : ctx->cfg.precond;
+  const int want = no_precond ? 0 : want_override >= 0 ? want_override : ctx->cfg.precond;
+  if (w.p >= kPclMinP) return precond_large(ctx, w, want, mixed);
   RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
   return TOLS_OK;
 }
@@ -1444,12 +1572,13 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
       return TOLS_ERR_OOM;
     }
   }
-  if (cudaMallocHost(&ctx->h_state, kStateBytes + sizeof(double) * TOLS_MAX_P) != cudaSuccess) {
+  if (cudaMallocHost(&ctx->h_state, kStateBytes + sizeof(double) * TOLS_MAX_P + sizeof(PclInfo)) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TOLS_ERR_OOM;
   }
   ctx->h_phi = (double*)((char*)ctx->h_state + kStateBytes);
+  ctx->h_pcl = (PclInfo*)(ctx->h_phi + TOLS_MAX_P);
   *out = ctx;
   return TOLS_OK;
 }
@@ -1462,7 +1591,7 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
                     &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
-                    &ctx->spec64, &ctx->b_spec, &ctx->lsar};
+                    &ctx->spec64, &ctx->b_spec, &ctx->lsar, &ctx->pcl};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -2096,6 +2225,43 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
   CK(cudaStreamSynchronize(ctx->stream));
   if (bnorm2) *bnorm2 = h;
   return TOLS_OK;
+}
+
+int toeplitz_ols_preconditioner(tols_ctx* ctx, int precision, const double* d_y, long long n, int p, int kind,
+                                double* d_M, tols_info* info) {
+  int rc = validate(ctx, n, p);
+  if (rc) return rc;
+  if (!d_y || !d_M || (precision != TOLS_FP64 && precision != TOLS_MIXED) ||
+      (kind != TOLS_PRECOND_GRAM_CHOL && kind != TOLS_PRECOND_SAMPLED_QR))
+    return fail(ctx, TOLS_ERR_ARG, "bad argument");
+  cudaSetDevice(ctx->device);
+  const bool mixed = precision == TOLS_MIXED;
+  Work w;
+  if ((rc = prepare_work(ctx, d_y, n, p, mixed, false, w))) return rc;
+  DevState hs;
+  memset(&hs, 0, sizeof hs);
+  hs.mixed = mixed ? 1 : 0;
+  *ctx->h_state = hs;
+  CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
+  const int pg = pad_p(p + 1);
+  if (mixed) RUN(run_small(ctx, 11, [&] { return launch_convert_f32(d_y, w.y32, n, ctx->stream); }));
+  const int fft = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pg, p + 1, 1)
+                        : choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
+  if (fft) RUN(fft_spectra(ctx, w, mixed ? 0 : 1, nullptr, n, n - p, pg, false));
+  RUN(run_setup(ctx, w, mixed, false, fft, mixed, kind));
+  CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const DevState& s = *ctx->h_state;
+  if (s.status == TOLS_ERR_NONFINITE) return fail(ctx, TOLS_ERR_NONFINITE, "y holds NaN or Inf");
+  if (s.precond) CK(cudaMemcpyAsync(d_M, w.M, sizeof(double) * (size_t)p * p, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (info) {
+    memset(info, 0, sizeof *info);
+    fill_info(info, s, mixed ? TOLS_MIXED : TOLS_FP64);
+    info->status = s.precond ? TOLS_OK : TOLS_NOT_CONVERGED;
+    info->cond_est = s.kappa_est;
+  }
+  return s.precond ? TOLS_OK : TOLS_NOT_CONVERGED;
 }
 
 int toeplitz_ols_row_norms(tols_ctx* ctx, const double* d_y, long long n, int p, double* d_rn2, double* fro2) {

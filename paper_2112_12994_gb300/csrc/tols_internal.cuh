@@ -218,6 +218,34 @@ cudaError_t launch_leverage_step(const double* r, long long m, int p, const doub
                                  double* lev, double* pi, double* unused, cudaStream_t s);
 cudaError_t launch_check_finite(const double* y, long long n, int* flag, cudaStream_t s);
 
+// Multi-CTA preconditioner of single-series solves (tols_precond.cu); the host runs its steps (tols_api.cu).
+struct PclInfo {
+  int fail;             // a pivot of the running factorisation fell to its floor
+  int nonfinite;        // a trace or lambda_max was not finite
+  double lam, dmax, trace, shift;   // the last power iteration: lambda_max, largest diagonal entry, trace, shift
+  double lam_keep[2];   // lambda_max of G (||X||_2^2) and of the sample's Gram matrix (QR path)
+  double trace_g;       // trace of G (||X||_F^2)
+  double cond;          // the last kappa(R) estimate
+};
+constexpr int kPclTile = 32;
+__host__ __device__ constexpr int pcl_pad_p(int p) { return (p + kPclTile - 1) / kPclTile * kPclTile; }
+cudaError_t pcl_lambda(double* S, int ld, int p, double shift_rel, int keep, float* fb, PclInfo* info, cudaStream_t s);
+cudaError_t pcl_pad(const double* G, int p, double* Gp, int P, double shift, double* Gsave, cudaStream_t s);
+cudaError_t pcl_chol_panel(double* Gp, int P, int p, int k, double tiny_dmax, double tiny_shift, PclInfo* info,
+                           cudaStream_t s);
+cudaError_t pcl_chol_update(double* Gp, int P, int k, const PclInfo* info, cudaStream_t s);
+cudaError_t pcl_inverse(const double* Rp, int P, int p, double* M, const PclInfo* info, cudaStream_t s);
+cudaError_t pcl_estimate(const double* M, int p, int slot, float* fb, PclInfo* info, cudaStream_t s);
+cudaError_t pcl_store(const Work& w, int mixed, const PclInfo* info, cudaStream_t s);
+cudaError_t pcl_state(const Work& w, const PclInfo* info, int precond, int shifted, int trusted, int singular,
+                      double cond, double kappa_est, cudaStream_t s);
+cudaError_t pcl_gather(const double* y, long long m, int p, long long c, double* A, cudaStream_t s);
+int pcl_gram_slices(long long c, int P);
+cudaError_t pcl_tall_gram(const double* A, long long c, int p, int P, int slices, double* part, cudaStream_t s);
+cudaError_t pcl_gram_reduce(const double* part, int P, int slices, int p, double* Gp, cudaStream_t s);
+cudaError_t pcl_trsm(double* A, long long c, int p, const double* Rp, int P, cudaStream_t s);
+cudaError_t pcl_trmm(const double* X, const double* Y, double* Z, int P, cudaStream_t s);
+
 // Algorithm "LSAR" (Section 3.1), tols_lsar.cu.
 constexpr int kLsarMaxP = 256;          // largest p_bar
 constexpr int kLsarBlock = 512;         // rows per sampling block (one warp scans it in 16 chunks of 32)

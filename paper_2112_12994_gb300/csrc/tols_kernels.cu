@@ -15,9 +15,9 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
+#include <utility>
 
 #include "tols_internal.cuh"
 
@@ -25,19 +25,28 @@ namespace tols {
 
 __host__ __device__ inline long long lmin(long long a, long long b) { return a < b ? a : b; }
 
-// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device. The attribute belongs to the
-// device, so the record of what was set is kept per (device, kernel, bytes); several host threads may call this.
+// Let a kernel launch with `bytes` of dynamic shared memory on the current device: its limit (at first the
+// default, 48 KB less its static shared memory) is raised when needed, never lowered, since a launch is valid for
+// any size up to the limit. The attribute belongs to the device, so the limit is recorded per (device, kernel);
+// several host threads may call this.
 cudaError_t smem_opt_in(const void* fn, int bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   static std::mutex mu;
-  static std::set<std::tuple<int, const void*, int>> done;
-  const auto key = std::make_tuple(dev, fn, bytes);
+  static std::map<std::pair<int, const void*>, int> limit;
   std::lock_guard<std::mutex> lock(mu);
-  if (done.count(key)) return cudaSuccess;
+  auto it = limit.find(std::make_pair(dev, fn));
+  if (it == limit.end()) {
+    cudaFuncAttributes attr;
+    e = cudaFuncGetAttributes(&attr, fn);
+    if (e != cudaSuccess) return e;
+    it = limit.emplace(std::make_pair(dev, fn), attr.maxDynamicSharedSizeBytes).first;
+  }
+  int& cur = it->second;
+  if (cur >= bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert(key);
+  if (e == cudaSuccess) cur = bytes;
   return e;
 }
 

@@ -46,17 +46,19 @@ extern "C" {
 /* ---- configuration ------------------------------------------------------------------------------- */
 typedef enum {
   TOLS_FP64 = 0,   /* every product of X in float64 on the GPU                                               */
-  TOLS_MIXED = 1   /* float32 products, float64 recurrence scalars, float64 residual-correction passes       */
+  TOLS_MIXED = 1   /* the float64 route (float64 Gram pass, factor and checks) with float32 products in the
+                      correction sweeps that follow a check, when kappa(X) u32 <= 1e-2 lets them contract the
+                      error; float64 recurrence scalars throughout                                             */
 } tols_precision;
 
 typedef enum {
   TOLS_PRECOND_NONE = 0,      /* plain LSQR on X                                                           */
-  TOLS_PRECOND_GRAM_CHOL = 1, /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X. A float64
+  TOLS_PRECOND_GRAM_CHOL = 1, /* LSQR on X R^{-1}, R the Cholesky factor of the Gram matrix X^T X. A       
                                  solve whose factor is not trustworthy (kappa(R)^2 u > 1/4) switches to
-                                 TOLS_PRECOND_SAMPLED_QR by itself (p <= 256, n - p >= 8p)                      */
-  TOLS_PRECOND_SAMPLED_QR = 2 /* LSQR on X R^{-1}, R from a float64 Householder QR of 8p rows of X sampled
-                                 evenly (the row-sampling idea of Section 3.1 used as a preconditioner; errors
-                                 of order kappa u instead of kappa^2 u). float64 solves, p <= 256, n - p >= 8p;
+                                 TOLS_PRECOND_SAMPLED_QR by itself (n - p >= 8p)                                */
+  TOLS_PRECOND_SAMPLED_QR = 2 /* LSQR on X R^{-1}, R from a float64 QR of 8p to 32p rows of X sampled evenly
+                                 (the row-sampling idea of Section 3.1 used as a preconditioner; errors of order
+                                 kappa u instead of kappa^2 u; see toeplitz_ols_preconditioner). n - p >= 8p;
                                  otherwise the Gram factor is used                                             */
 } tols_precond;
 
@@ -82,7 +84,7 @@ typedef struct {
   int status;             /* same code the call returned (per series in batched calls)                      */
   int iters;              /* LSQR iterations (FP64) or inner iterations over all sweeps (mixed)             */
   int sweeps;             /* float64 residual passes made                                                   */
-  int precision_used;     /* tols_precision actually used (mixed falls back to FP64 when kappa is too big)  */
+  int precision_used;     /* TOLS_MIXED when float32 products did part of the work, else TOLS_FP64          */
   int precond_used;       /* tols_precond actually used (SAMPLED_QR for an ill-conditioned float64 solve,
                              NONE if no factor could be formed)                                               */
   int product_used;       /* tols_product actually used                                                     */
@@ -131,9 +133,9 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
 
 /* Solve count independent problems (host series y[k][0..n[k]-1], orders p[k]) in one batched launch
  * sequence (each problem is eq. (xphi) for its own series, Section 3). Every pass kernel covers all
- * series at once; float64 series with pad16(p[k] + 1) >= 32 take the overlap-save FFT products, the others (and
- * every series of a mixed batch) the direct products, unless the context's product setting says otherwise
- * (TOLS_PRODUCT_DIRECT forces the direct products). A series' result does not depend on the rest of the batch.
+ * series at once; series with pad16(p[k] + 1) >= 32 take the overlap-save float64 FFT products, the others the
+ * direct products, unless the context's product setting says otherwise (TOLS_PRODUCT_DIRECT forces the direct
+ * products); the float correction sweeps of a mixed batch use the direct float products. A series' result does not depend on the rest of the batch.
  * phi[k] (host, p[k] doubles), rnorm (host, count, nullable), info (host, count, nullable).
  * Returns the worst status over the batch; info[k].status holds each series' own code. */
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
@@ -158,8 +160,8 @@ int toeplitz_ols_pacf(tols_ctx* ctx, const double* y, long long n, int h_max, do
 /* ---- serving: continuous batching of fit requests ----------------------------------------------------
  * A server owns a context and one device arena. Submitted requests (series copied in at submit) wait in FIFO
  * order; each toeplitz_ols_server_step admits waiting requests while fewer than max_active are active and the
- * request's device footprint (about 24 n bytes in mixed precision, 40 n in float64 or 49 n with the FFT window
- * spectra of a float64 request with p >= 16, plus O(p^2)) fits in the
+ * request's device footprint (about 28 n bytes for a mixed request, 24 n for a float64 one, plus about 8.5 n
+ * for the float64 FFT window spectra of a request with p >= 16, plus O(p^2)) fits in the
  * arena, sets the newcomers up, runs one burst of batched iterations over every active request, and retires the
  * finished ones (their memory is free for the next admission at once). A request's arithmetic depends only on
  * its own data, so its result is the same alone or among any other requests. */
@@ -254,10 +256,11 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
                       double* d_h, double* bnorm2);
 
 /* The preconditioner of a solve (the factor R of LSQR on X R^{-1}; the row-sampling idea of Section 3.1 supplies
- * the sampled-row variant): from a Gram pass over d_y (n doubles, device) in the given precision,
+ * the sampled-row variant): from a float64 Gram pass over d_y (n doubles, device); precision TOLS_MIXED gives the
+ * same factor (a mixed solve also keeps float copies of it),
  *   kind = TOLS_PRECOND_GRAM_CHOL : R = the Cholesky factor of G = X^T X (shifted by 10 p u max_j G_jj when a pivot
  *                                   falls to rounding level);
- *   kind = TOLS_PRECOND_SAMPLED_QR: float64 only: if the Gram factor is not trusted (kappa(R)^2 u > 1/4) or always
+ *   kind = TOLS_PRECOND_SAMPLED_QR: if the Gram factor is not trusted (kappa(R)^2 u > 1/4) or always
  *                                   when asked, R from shifted Cholesky QR of c rows of X sampled evenly (row
  *                                   floor((2k + 1) m / (2c)), k < c), c = 32p if m >= 256 p^2, 16p if m >= 128 p^2,
  *                                   else 8p; needs m >= 8p; the Gram factor if that fails.

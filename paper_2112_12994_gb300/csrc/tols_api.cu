@@ -312,10 +312,12 @@ int prepare_work(tols_ctx* ctx, const double* y64, long long n, int p, bool mixe
   int rc;
   if (mixed) {
     if ((rc = ensure(ctx, ctx->y32, sizeof(float) * (size_t)n))) return rc;
-    w.y32 = (float*)ctx->y32.p;
+    w.y32 = (float*)ctx->y32.p;   // filled when the first float pass is due
   }
   if (need_u) {
-    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    // float64 even for a mixed solve: it runs float64 iterations when float products cannot refine it (the float
+    // passes use the first half)
+    const size_t es = sizeof(double);
     if ((rc = ensure(ctx, ctx->u0, es * m))) return rc;
     if ((rc = ensure(ctx, ctx->u1, es * m))) return rc;
     w.U[0] = ctx->u0.p;
@@ -419,16 +421,16 @@ int pcl_factor(tols_ctx* ctx, double* Gp, int P, int p, double tiny_dmax, double
 
 // The preconditioner of one solve, with the state precond_kernel leaves: norms of X from G (trace, power
 // iteration), the Cholesky factor of G (refactored with the shift 10 p u max_j G_jj if a pivot falls to rounding
-// level, which flags G as singular), M = R^{-1}, kappa(R) and the trust test kappa(R)^2 u <= 1/4 (u of the
-// precision G was formed in). A float64 solve whose factor is not trusted (or that asks for it) is preconditioned
+// level, which flags G as singular), M = R^{-1}, kappa(R) and the trust test kappa(R)^2 u <= 1/4 (u of float64: G
+// is formed from float64 products). A solve whose factor is not trusted (or that asks for it) is preconditioned
 // instead by the R of c sampled rows of X from shifted Cholesky QR (two shifted stages, shift
 // 11 (c p + p (p + 1)) u lambda_max, then one plain stage; R = R3 R2 R1). The host reads a small report after
 // each factorisation.
 int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
   const int p = w.p, P = pcl_pad_p(p), nt = P / kPclTile;
   const size_t PP = (size_t)P * P;
-  const double ueps = mixed ? 5.96e-8 : 1.11e-16;
-  const bool qr_ok = !mixed && want != 0 && w.m >= 8LL * p;
+  const double ueps = 1.11e-16;                              // G comes from float64 products in every precision
+  const bool qr_ok = want != 0 && w.m >= 8LL * p;
   const long long c = qr_ok ? pcl_sample_rows(w.m, p) : 0;
   const int slices = c ? pcl_gram_slices(c, P) : 0;
   const size_t ntiles = (size_t)nt * (nt + 1) / 2;
@@ -513,30 +515,18 @@ int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
   return TOLS_OK;
 }
 
-// Gram pass + preconditioner for series w.y64 (and w.y32 in the mixed path). fft: the Gram pass uses the FFT
-// kernel and writes the window spectra of its precision (room made by fft_spectra).
-int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, bool converted = false,
-              int want_override = -1) {
+// Gram pass (float64 products, in every precision) + preconditioner for series w.y64. fft: the Gram pass uses the
+// FFT kernel and writes the float64 window spectra (room made by fft_spectra). The float copy y32 of a mixed solve
+// is made when its first float pass is due.
+int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, int want_override = -1) {
   const int pg = pad_p(w.p + 1);
-  if (mixed) {
-    if (!converted)
-      RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
-    PassArgs<float> a = base_args<float>(w, w.y32, w.n, w.p, pg);
-    a.gram = 1;
-    a.nlag = w.p + 1;
-    a.tail = TAIL_GRAM;
-    a.out_n2 = w.bnorm2;
-    a.fft = fft;
-    RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pg, a.fft)));
-  } else {
-    PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
-    a.gram = 1;
-    a.nlag = w.p + 1;
-    a.tail = TAIL_GRAM;
-    a.out_n2 = w.bnorm2;
-    a.fft = fft;
-    RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
-  }
+  PassArgs<double> a = base_args<double>(w, w.y64, w.n, w.p, pg);
+  a.gram = 1;
+  a.nlag = w.p + 1;
+  a.tail = TAIL_GRAM;
+  a.out_n2 = w.bnorm2;
+  a.fft = fft;
+  RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   const int want = no_precond ? 0 : want_override >= 0 ? want_override : ctx->cfg.precond;
   if (w.p >= kPclMinP) return precond_large(ctx, w, want, mixed);
   RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
@@ -575,7 +565,7 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   hs.tol_inner = 1e-5;
   hs.est_ratio = tol;
   hs.max_iter = max_iter;
-  // float inner solves that need more than ~100 preconditioned iterations mean kappa(X) is too large for
+  // float correction solves that need more than ~100 preconditioned iterations mean kappa(X) is too large for
   // float products; they stop early and the stall test hands the problem to the float64 path
   hs.iter_cap = mixed ? std::min(max_iter, 100) : max_iter;
   hs.max_sweeps = max_sweeps;
@@ -589,16 +579,13 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   *ctx->h_state = hs;
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
   // products: the direct or FFT kernel per precision. FFT passes use tiles of N - pad_p(p + 1) rows and read
-  // the tile window spectra: the Gram pass of the same precision forms them; the float64 spectra of a mixed
-  // solve come from spectrum_kernel.
+  // the tile window spectra: the float64 Gram pass forms the float64 ones; the float ones (mixed solves that run
+  // float correction sweeps) come from spectrum_kernel when first needed.
   const int pp = pad_p(p);
   const int pg = pad_p(p + 1);
-  if (mixed) RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, n, ctx->stream); }));
   const int fft64 = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
-  const int fft32 = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0) : 0;
-  if (fft64) RUN(fft_spectra(ctx, w, 1, w.y64, n, n - p, pg, mixed));
-  if (fft32) RUN(fft_spectra(ctx, w, 0, w.y32, n, n - p, pg, false));
-  if ((rc = run_setup(ctx, w, mixed, no_precond, mixed ? fft32 : fft64, true))) return rc;
+  if (fft64) RUN(fft_spectra(ctx, w, 1, w.y64, n, n - p, pg, false));
+  if ((rc = run_setup(ctx, w, mixed, no_precond, fft64))) return rc;
   if (phi0) {
     CK(cudaMemcpyAsync(w.phi, phi0, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
     RUN(run_small(ctx, 12, [&] { return launch_init_lsqr(w, 1, ctx->stream); }));
@@ -609,19 +596,19 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   ad.check_done = 1;
   ad.d = w.d;
   ad.fft = fft64;
-  PassArgs<float> af = base_args<float>(w, w.y32, n, p, fft32 ? pg : pp);
+  PassArgs<float> af = base_args<float>(w, w.y32, n, p, pp);
   af.check_done = 1;
   af.d = w.d;
-  af.fft = fft32;
-  ctx->last_fft = mixed ? af.fft : ad.fft;
+  ctx->last_fft = ad.fft;
   const int gd = pass_grid_for(ctx, 1, ad.p_pad, ad.fft);
-  const int gf = mixed ? pass_grid_for(ctx, 0, af.p_pad, af.fft) : 0;
+  int gf = 0;
+  bool f32_ready = false, f32_mode = false;
   const long long max_launch = (long long)(max_iter + 4) * (max_sweeps + 2) * 2 + 16;
   long long launched = 0;
-  // a float64 solve from a trusted factor usually ends with its first (check) pass: start with a burst of one
-  int burst = mixed ? 4 : 1;
+  // a solve from a trusted factor usually ends with its first (check) pass: start with a burst of one
+  int burst = 1;
   while (true) {
-    if (mixed) {
+    if (f32_mode) {
       for (int k = 0; k < burst; ++k) RUN(run_pass<float>(ctx, af, gf));
       RUN(run_pass<double>(ctx, ad, gd));
       launched += burst + 1;
@@ -635,9 +622,27 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     RUN(flush_profile(ctx));
-    if (ctx->h_state->done || ctx->h_state->phase == PH_DONE) break;
+    const DevState& cur = *ctx->h_state;
+    if (cur.done || cur.phase == PH_DONE) break;
     if (launched > max_launch) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "solver did not reach a final state");
-    burst = burst == 1 ? 4 : std::min(burst * 2, 16);
+    // float passes are due while a mixed solve runs a correction sweep
+    const bool want32 = mixed && cur.mixed && (cur.phase == PH_NECORR || cur.phase == PH_LSQR);
+    if (want32 && !f32_ready) {
+      RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, n, ctx->stream); }));
+      const int fft32 = choose_fft<float>(ctx, w, w.y32, n, p, pp, p, 0);
+      if (fft32) RUN(fft_spectra(ctx, w, 0, w.y32, n, n - p, pg, true));
+      af.fft = fft32;
+      af.p_pad = fft32 ? pg : pp;
+      af.w = w;
+      gf = pass_grid_for(ctx, 0, af.p_pad, af.fft);
+      f32_ready = true;
+    }
+    if (want32 != f32_mode) {
+      f32_mode = want32;
+      burst = 4;
+    } else {
+      burst = burst == 1 ? 4 : std::min(burst * 2, 16);
+    }
   }
   if (ctx->h_state->status == TOLS_OK) {
     if (phi_out_done) *phi_out_done = d_phi_out != nullptr;
@@ -661,10 +666,10 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
   if (h_phi_done) *h_phi_done = false;
   int rc = solve_core(ctx, d_y, n, p, tol, mixed, phi0, w, false, d_phi, &phi_done, h_phi);
   if (rc) return rc;
-  if (mixed && (ctx->h_state->mixed_ok == 0 || ctx->h_state->precond == 0) &&
-      ctx->h_state->status != TOLS_ERR_NONFINITE && ctx->h_state->status != TOLS_OK) {
-    // float products cannot refine this problem (kappa(X)^2 * u32 too large): redo it in float64,
-    // warm-started from the best mixed iterate when that one is usable, else from zero
+  if (mixed && ctx->h_state->mixed_ok == 0 && ctx->h_state->status != TOLS_ERR_NONFINITE &&
+      ctx->h_state->status != TOLS_OK) {
+    // the float correction sweeps stopped contracting: redo it in float64, warm-started from the best iterate
+    // when that one is usable, else from zero
     const bool warm = ctx->h_state->ne_best < 1e-3;
     phi_done = false;
     if (warm) CK(cudaMemcpyAsync(d_phi, w.best, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -700,7 +705,8 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
     *h_phi_done = h_phi != nullptr;
   }
   if (rnorm) *rnorm = s.rnorm;
-  fill_info(info, s, mixed ? TOLS_MIXED : TOLS_FP64);
+  // a mixed request is reported as mixed only when float products did part of the work
+  fill_info(info, s, mixed && s.f32_iter > 0 ? TOLS_MIXED : TOLS_FP64);
   if (info && ctx->last_fft) info->product_used = TOLS_PRODUCT_FFT;
   return s.status;
 }
@@ -779,7 +785,7 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
     B.y_elems += align_up((size_t)nn, 64);
     B.off_u.push_back((long long)B.u_elems);
     B.u_elems += align_up((size_t)mm, 64);
-    const bool fx = allow_fft && batch_fft_series(p[k], mixed);
+    const bool fx = allow_fft && batch_fft_series(p[k]);
     const long long ntd = fx ? 0 : (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
     const long long ntx = fx ? batch_fft_units(mm, p[k]) : 0;
     const long long nun = batch_units(mm, p[k], fx);
@@ -834,7 +840,8 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   if (cnt == 0) return TOLS_OK;
   int rc;
   if (mixed && (rc = ensure(ctx, ctx->b_y32, sizeof(float) * B.y_elems))) return rc;
-  const size_t ues = mixed ? sizeof(float) : sizeof(double);
+  // float64 for mixed series too: they run float64 iterations when float products cannot refine them
+  const size_t ues = sizeof(double);
   if ((rc = ensure(ctx, ctx->b_u0, ues * B.u_elems)) || (rc = ensure(ctx, ctx->b_u1, ues * B.u_elems))) return rc;
   if ((rc = ensure(ctx, ctx->b_part, sizeof(double) * B.part_doubles))) return rc;
   const bool fresh_cnt = ctx->b_cnt.cap < sizeof(unsigned) * (B.cnt_uints + 4);
@@ -955,39 +962,29 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   BatchArgs ag = a;
   ag.gram = 1;
   const int gx = B.tiles_x ? batch_fft_grid(ctx, B.p_pad_max_x) : 0;
-  // launches per solver pass: float (mixed) or the FFT pair (d spectra, FFT pass) and/or the direct float64 pass
-  const int per_pass = mixed ? 1 : (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0);
-  ctx->launch_total += mixed ? 1 : (B.tiles_x ? 1 : 0) + (B.tiles_d ? 1 : 0);
-  if (mixed) {
-    CK(launch_batch_pass<float>(ag, gf, B.p_pad_max, ctx->stream));
-  } else {
-    // the FFT series' Gram pass also forms their window spectra
-    if (B.tiles_x) CK(launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream));
-    if (B.tiles_d) CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
-  }
+  // launches per float64 solver pass: the FFT pair (d spectra, FFT pass) and/or the direct float64 pass; a mixed
+  // batch adds the float pass of its correction sweeps
+  const int per_pass = (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0) + (mixed ? 1 : 0);
+  // the Gram pass (float64 products for every series); the FFT series' one also forms their window spectra
+  ctx->launch_total += (B.tiles_x ? 1 : 0) + (B.tiles_d ? 1 : 0);
+  if (B.tiles_x) CK(launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream));
+  if (B.tiles_d) CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
   const int want = no_precond ? 0 : ctx->cfg.precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream, B.p_pad_max); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
 
   // iterations: a burst of batched passes captured once into a CUDA graph, replayed until all series are done
-  const int burst = mixed ? 6 : 4;
+  const int burst = 4;
   cudaGraphExec_t exec = nullptr;
   auto enqueue_burst = [&]() -> int {
     for (int k = 0; k < burst; ++k) {
       ctx->launch_total += per_pass;
-      if (mixed) {
-        CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
-      } else {
-        if (B.tiles_x) {
-          CK(launch_batch_dspec(d_series, cnt, ctx->stream));
-          CK(launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream));
-        }
-        if (B.tiles_d) CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+      if (mixed) CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
+      if (B.tiles_x) {
+        CK(launch_batch_dspec(d_series, cnt, ctx->stream));
+        CK(launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream));
       }
-    }
-    if (mixed) {
-      ctx->launch_total++;
-      CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+      if (B.tiles_d) CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
     }
     return TOLS_OK;
   };
@@ -1011,7 +1008,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   int out = TOLS_OK;
   for (long long round = 0;; ++round) {
     if (exec) {
-      ctx->launch_total += burst * per_pass + (mixed ? 1 : 0);
+      ctx->launch_total += burst * per_pass;
       cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
       if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "cudaGraphLaunch", e); break; }
     } else if ((out = enqueue_burst())) {
@@ -1049,24 +1046,26 @@ BatchPlan sub_plan(tols_ctx* ctx, const BatchPlan& B, const std::vector<int>& wh
   return S;
 }
 
-// Run the batch, then, together as float64 sub-batches: the series the mixed path handed back (float products
-// cannot refine them: kappa(X)^2 u32 too large), and the exactly rank-deficient ones (plain LSQR from zero gives
-// the minimum norm). phi_host: coefficients packed at B.off_phi.
+// Run the batch, then, together as float64 sub-batches: the series whose float correction sweeps stopped
+// contracting, and the exactly rank-deficient ones (plain LSQR from zero gives the minimum norm). phi_host:
+// coefficients packed at B.off_phi.
 int batch_solve_all(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<DevState>& states,
                     std::vector<double>& phi_host, std::vector<int>& prec_used) {
   const int cnt = (int)B.idx.size();
-  prec_used.assign(cnt, mixed ? TOLS_MIXED : TOLS_FP64);
+  prec_used.assign(cnt, TOLS_FP64);
   phi_host.assign(B.phi_doubles, 0.0);
   if (cnt == 0) return TOLS_OK;
   int rc;
   if ((rc = batch_core(ctx, B, tol, mixed, states))) return rc;
   CK(cudaMemcpy(phi_host.data(), ctx->b_phi.p, sizeof(double) * B.phi_doubles, cudaMemcpyDeviceToHost));
+  // a mixed series counts as mixed when float products did part of its work
+  for (int k = 0; k < cnt; ++k)
+    if (mixed && states[k].f32_iter > 0) prec_used[k] = TOLS_MIXED;
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<int> which;
     for (int k = 0; k < cnt; ++k) {
       const DevState& s = states[k];
-      if (pass == 0 && mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
-          (s.mixed_ok == 0 || s.precond == 0))
+      if (pass == 0 && mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE && s.mixed_ok == 0)
         which.push_back(k);
       if (pass == 1 && s.singular && s.compatible && s.status >= 0) which.push_back(k);
     }
@@ -1142,9 +1141,9 @@ class ArenaAlloc {
 size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
   const long long m = n - p;
   const size_t pp1 = (size_t)pad_p(p + 1);
-  const bool fx = batch_fft_series(p, mixed);
+  const bool fx = batch_fft_series(p);
   const long long ntd = batch_units(m, p, fx), ngr = (ntd + kGroup - 1) / kGroup;
-  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  const size_t es = sizeof(double);   // float64 even for mixed requests (float64 iterations when float cannot refine)
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -1160,7 +1159,7 @@ size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
   char* part = take(sizeof(double) * (size_t)(ntd * pp1 + ntd + ngr * pp1 + ngr));
   char* vec = take(sizeof(double) * (9 * pp1 + (size_t)p));
   char* mat = take(sizeof(double) * (3 * (size_t)p * p + qr_scratch_doubles(p)) + sizeof(float) * 2 * (size_t)p * p);
-  // window spectra of the FFT tiles and the spectrum of d (float64 requests with FFT products)
+  // window spectra of the FFT tiles and the spectrum of d (requests with float64 FFT products)
   char* spec = fx ? take(sizeof(double) * (batch_fft_spectra_doubles(m, p) + 2 * (kBatchFftN / 2 + 1))) : nullptr;
   if (base && w) {
     memset(w, 0, sizeof *w);
@@ -1346,33 +1345,23 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
   BatchArgs a;
   int pmax = 16;
   RUN(upload_table(srv, fresh, a, pmax));
-  bool any_mixed = false, any_fp64 = false;
   for (int k : fresh) {
     const SrvActive& A = srv->active[k];
     if (A.req.mixed) {
-      any_mixed = true;
       const Work& w = A.w;
       RUN(run_small(ctx, 11, [&] { return launch_convert_f32(w.y64, w.y32, w.n, ctx->stream); }));
-    } else {
-      any_fp64 = true;
     }
   }
   BatchArgs ag = a;
   ag.gram = 1;
-  if (any_mixed) {
+  // the Gram pass from float64 products for every request; the FFT requests' one also forms their window spectra
+  if (a.tiles_x) {
     ctx->launch_total++;
-    CK(launch_batch_pass<float>(ag, batch_grid(ctx, 0, pmax), pmax, ctx->stream));
+    CK(launch_batch_fft(ag, batch_fft_grid(ctx, pmax), pmax, ctx->stream));
   }
-  if (any_fp64) {
-    // the FFT requests' Gram pass also forms their window spectra
-    if (a.tiles_x) {
-      ctx->launch_total++;
-      CK(launch_batch_fft(ag, batch_fft_grid(ctx, pmax), pmax, ctx->stream));
-    }
-    if (a.tiles_d) {
-      ctx->launch_total++;
-      CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
-    }
+  if (a.tiles_d) {
+    ctx->launch_total++;
+    CK(launch_batch_pass<double>(ag, batch_grid(ctx, 1, pmax), pmax, ctx->stream));
   }
   const int want = ctx->cfg.precond;
   const int cnt = (int)fresh.size();
@@ -1444,8 +1433,7 @@ int server_round(tols_server* srv) {
       continue;
     }
     const double* phi = srv->h_phi.data() + (size_t)k * TOLS_MAX_P;
-    const bool hopeless = A.req.mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE &&
-                          (s.mixed_ok == 0 || s.precond == 0);
+    const bool hopeless = A.req.mixed && s.status != TOLS_OK && s.status != TOLS_ERR_NONFINITE && s.mixed_ok == 0;
     const bool rankdef = s.singular && s.compatible && s.status >= 0 && !A.req.no_precond;
     if (hopeless || rankdef) {
       // back to the head of the queue as a float64 request (plain LSQR for the minimum norm when X is exactly
@@ -1461,7 +1449,7 @@ int server_round(tols_server* srv) {
     }
     s.total_iter += A.req.prior_iters;
     s.sweeps += A.req.prior_sweeps;
-    const int prec = A.req.mixed ? TOLS_MIXED : TOLS_FP64;
+    const int prec = A.req.mixed && s.f32_iter > 0 ? TOLS_MIXED : TOLS_FP64;
     tols_result res;
     memset(&res, 0, sizeof res);
     res.id = A.req.id;
@@ -2244,11 +2232,9 @@ int toeplitz_ols_preconditioner(tols_ctx* ctx, int precision, const double* d_y,
   *ctx->h_state = hs;
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
   const int pg = pad_p(p + 1);
-  if (mixed) RUN(run_small(ctx, 11, [&] { return launch_convert_f32(d_y, w.y32, n, ctx->stream); }));
-  const int fft = mixed ? choose_fft<float>(ctx, w, w.y32, n, p, pg, p + 1, 1)
-                        : choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
-  if (fft) RUN(fft_spectra(ctx, w, mixed ? 0 : 1, nullptr, n, n - p, pg, false));
-  RUN(run_setup(ctx, w, mixed, false, fft, mixed, kind));
+  const int fft = choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
+  if (fft) RUN(fft_spectra(ctx, w, 1, nullptr, n, n - p, pg, false));
+  RUN(run_setup(ctx, w, mixed, false, fft, kind));
   CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   const DevState& s = *ctx->h_state;

@@ -86,6 +86,7 @@ struct DevState {
   int trusted;       // unshifted factor with kappa(R)^2 u <= 1/4 (semi-normal-equation start, float refinement)
   int fft;           // a batched pass with overlap-save FFT products ran for this series
   int no_precond;    // set by the host: plain LSQR (minimum-norm repeat of a rank-deficient problem)
+  int f32_iter;      // inner iterations run with float products (a mixed solve that needed correction sweeps)
 };
 
 // Device pointers of one solve's workspace.
@@ -162,11 +163,12 @@ struct BatchArgs {
   unsigned int* done_count;     // incremented once per series that reaches PH_DONE
 };
 
-// Batched float64 series with p_pad(p + 1) in [32, 1024) take the overlap-save FFT products (N = 2,048, tiles of
-// 2,048 - pad_p(p + 1) rows); the others, and every series of a mixed batch, the direct products.
+// Batched series with p_pad(p + 1) in [32, 1024) take the overlap-save float64 FFT products (N = 2,048, tiles of
+// 2,048 - pad_p(p + 1) rows) for their Gram pass, checks and float64 iterations; the others the direct products.
+// The float correction sweeps of mixed series use the direct float products.
 constexpr int kBatchFftN = 2048;
-__host__ __device__ constexpr bool batch_fft_series(int p, bool mixed) {
-  return !mixed && pad_p(p + 1) >= 32 && pad_p(p + 1) < kBatchFftN / 2;
+__host__ __device__ constexpr bool batch_fft_series(int p) {
+  return pad_p(p + 1) >= 32 && pad_p(p + 1) < kBatchFftN / 2;
 }
 __host__ __device__ constexpr long long batch_fft_tiles(long long m, int p) {
   return (m + (kBatchFftN - pad_p(p + 1)) - 1) / (kBatchFftN - pad_p(p + 1));

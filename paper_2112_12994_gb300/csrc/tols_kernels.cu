@@ -361,6 +361,7 @@ __device__ void tail_lsqr(const Work& w, DevState* st, const double* tk, double 
     st->iter_best = iter_best;
     if (progress) st->phibar_mark = new_phibar;
     st->total_iter += 1;
+    if (mixed) st->f32_iter += 1;
     st->coef = beta > 0 ? alpha / beta : 0.0;
   }
   if (stop) {
@@ -423,6 +424,7 @@ __device__ void tail_necorr(const Work& w, DevState* st, const double* tk, doubl
     st->est_best = est_best;
     st->iter_best = iter_best;
     st->total_iter += 1;
+    st->f32_iter += 1;
     st->coef = rho > 0 ? theta_next / rho : 0.0;
   }
   __syncthreads();
@@ -474,8 +476,6 @@ __device__ void tail_check(const Work& w, DevState* st, const double* tk, double
   else if (sweeps >= st->max_sweeps || st->total_iter >= 64 * st->max_iter) next = 1;  // give up
   else if (sweeps >= 2 && ne > 0.7 * prev && !r_progress) {              // no progress since the last check
     next = (st->mixed && ne > 10.0 * floor64) ? 2 : 1;                   // mixed: float cannot refine it
-  } else if (st->mixed && sweeps == 1 && ne > 1e-2) {
-    next = 2;                                                             // float LSQR gained < 2 digits
   } else next = 3;                                                        // refine again
   if (next == 0 || next == 1 || next == 2) {
     if (threadIdx.x == 0) {
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) batch_pass_kernel(
     const int nlag = gram ? p + 1 : p;
     if (tid == 0) {
       int skip = 0;
-      if (gram) skip = (w.st->mixed ? 0 : 1) != is_double;   // Gram lag sums in the series' own precision
+      if (gram) skip = !is_double;                            // Gram lag sums from float64 products
       else skip = !select_phase<T>(w.st, y, p, w, tail, u_old, u_new, coef);
       s_skip = skip;
     }
@@ -1222,7 +1222,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   // (Thm. "Solution to OLS problem"). kappa(R) = ||X||_2 ||R^{-1}||_2 is estimated by power iteration; a factor
   // with kappa(R)^2 u > 1/4 still preconditions LSQR (better than a shifted one) but is not trusted for the
   // semi-normal-equation start, nor for refinement with float products.
-  const double ueps = st->mixed ? 5.96e-8 : 1.11e-16;
+  const double ueps = 1.11e-16;   // G is formed from float64 products in every precision
   if (want_precond && !in_smem) {
     for (size_t q = threadIdx.x; q < (size_t)p * p; q += kPcThreads) w.Mt[q] = G[q];
     __syncthreads();
@@ -1432,7 +1432,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   // preconditioner. R from QR carries errors of order kappa u, not kappa^2 u, so LSQR on X R^{-1} converges in
   // a few tens of iterations up to kappa(X) ~ 1/u. The Gram factor stays if the sample is rank deficient.
   bool qr_used = false;
-  if (want_precond && !st->no_precond && !st->mixed && (want_precond == 2 || !trusted) && w.qr &&
+  if (want_precond && !st->no_precond && (want_precond == 2 || !trusted) && w.qr &&
       p <= kQrMaxP && w.m >= (long long)kQrRowsPerP * p) {
     if (sampled_qr(w, G, qw, qpart, scratch)) {
       cond = invert_and_estimate();
@@ -1494,29 +1494,27 @@ cudaError_t launch_precond_batch(const BatchSeries* series, int count, int want_
   return cudaGetLastError();
 }
 
-// LSQR start on rhs = b with X^T b = h and ||b|| = bnorm (already in state).
-// A mixed solve whose float Gram factor is not trusted (kappa(R)^2 u32 > 1/4, shifted or singular) cannot be
-// refined with float products: it is handed back to the float64 path at once.
-__device__ bool mixed_hopeless(DevState* st) {
-  if (!(st->mixed && ((st->precond && !st->trusted) || st->singular))) return false;
-  if (threadIdx.x == 0) {
-    st->mixed_ok = 0;
-    st->status = TOLS_NOT_CONVERGED;
-    st->phase = PH_DONE;
-    st->done = 1;
-  }
-  __syncthreads();
-  return true;
-}
-
-// Start of a solve. Float64 with a trusted (unshifted, kappa(R)^2 u <= 1/4) Cholesky factor: start from the semi-normal-equation solution
-// phi0 = R^{-1} R^{-T} X^T b (O(p^2)) and let a float64 check pass decide whether LSQR on the residual is needed.
-// Otherwise (mixed precision, or no factor): LSQR from zero on b.
+// Start of a solve. With a trusted (unshifted, kappa(R)^2 u <= 1/4) Cholesky factor of the float64 Gram matrix:
+// start from the semi-normal-equation solution phi0 = R^{-1} R^{-T} X^T b (O(p^2)) and let a float64 check pass
+// decide whether more is needed. Otherwise LSQR from zero on b with float64 products.
+// A mixed solve takes the same route. Its float products serve only the correction sweeps that may follow a
+// check (Bidiag 2 on (X^T X) delta = g), and only when they can contract the error: a trusted factor and
+// kappa(X) u32 <= 1e-2 (a sweep then gains about -log10(kappa(X) u32) digits). Otherwise the state drops its
+// mixed flag and every later pass is a float64 one.
 __device__ void start_solve(const Work& w, DevState* st, double* scratch) {
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
   if (st->precond == 2 && threadIdx.x == 0) st->iter_cap = min(st->iter_cap, kQrIterCap);
-  if (!st->mixed && st->precond && st->trusted) {
+  if (st->mixed) {
+    const bool float_ok = st->precond && st->trusted && !st->singular && st->kappa_est * 5.96e-8 <= 1e-2;
+    __syncthreads();
+    if (!float_ok && threadIdx.x == 0) {
+      st->mixed = 0;
+      st->iter_cap = st->max_iter;
+    }
+    __syncthreads();
+  }
+  if (st->precond && st->trusted) {
     apply_Mt(w, 1, 0, w.h, w.t);
     __syncthreads();
     apply_M_exact(w, 1, 0, w.t, w.phi);
@@ -1532,7 +1530,7 @@ __global__ void __launch_bounds__(kThreads) init_lsqr_kernel(Work w) {
   DevState* st = w.st;
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
-  if (mixed_hopeless(st)) return;
+  if (st->done) return;   // e.g. non-finite input found by the preconditioner
   start_solve(w, st, scratch);
 }
 
@@ -1552,10 +1550,6 @@ __global__ void __launch_bounds__(kThreads) init_lsqr_batch_kernel(const BatchSe
   }
   for (int j = threadIdx.x; j < w.p; j += kThreads) w.phi[j] = 0.0;
   __syncthreads();
-  if (mixed_hopeless(st)) {
-    if (threadIdx.x == 0 && done) atomicAdd(done, 1u);
-    return;
-  }
   start_solve(w, st, scratch);
 }
 cudaError_t launch_init_lsqr_batch(const BatchSeries* series, int count, unsigned int* done, cudaStream_t s) {

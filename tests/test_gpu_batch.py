@@ -120,13 +120,10 @@ def test_batched_device_equals_host_batched(tols, ctx):
 
 
 def test_batch_products_by_order(tols, ctx, prec):
-    # float64 batches give series with pad16(p + 1) >= 32 the overlap-save FFT products and the others the direct
-    # ones; mixed batches use the direct products (a series handed to float64 is re-solved as float64)
+    # series with pad16(p + 1) >= 32 take the overlap-save float64 FFT products and the others the direct ones, in
+    # both precisions (a mixed series runs its Gram pass and checks in float64 too)
     ys, ps = _batch(12, 43, 5_000, 40_000, 2, 60)
     phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(ctx, ys, ps, 1e-12)
     for p, info in zip(ps, infos):
-        if prec == "fp64" or info["precision_used"] == tols.TOLS_FP64:
-            want = tols.TOLS_PRODUCT_FFT if ((p + 1 + 15) // 16) * 16 >= 32 else tols.TOLS_PRODUCT_DIRECT
-        else:
-            want = tols.TOLS_PRODUCT_DIRECT
+        want = tols.TOLS_PRODUCT_FFT if ((p + 1 + 15) // 16) * 16 >= 32 else tols.TOLS_PRODUCT_DIRECT
         assert info["product_used"] == want, (p, info)

@@ -68,8 +68,8 @@ def test_result_is_the_same_alone_and_in_the_mix(tols, prec):
 def test_admission_by_memory(tols):
     # an arena that holds about two of these requests at a time: the rest wait, all complete
     reqs = [(k, ar_series(100_000, 8, config_id=82, series_index=k).y, 8) for k in range(6)]
-    # each request needs about 2.0 MB (float64 + float32 series, two float32 work vectors): 5 MiB holds two
-    with tols.Server(precision=tols.TOLS_MIXED, arena_bytes=5 << 20) as srv:
+    # each request needs about 2.8 MB (float64 + float32 series, two float64 work vectors): 6.5 MiB holds two
+    with tols.Server(precision=tols.TOLS_MIXED, arena_bytes=13 << 19) as srv:
         for rid, y, p in reqs:
             assert srv.submit(rid, y, p, 1e-12) == tols.TOLS_OK
         active, queued = srv.step()

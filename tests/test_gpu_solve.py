@@ -204,3 +204,29 @@ def test_solve_with_outliers(tols, ctx, prec, n, p, count, cfg):
     phi, rnorm, info, rc = tols.toeplitz_ols_solve(ctx, y, p, 1e-12)
     assert rc == tols.TOLS_OK, info
     assert_solve_parity(y, p, phi, sol, COEF_TOL[prec])
+
+
+@pytest.mark.parametrize("idx,lo,hi,p,float_sweeps", [
+    (6, 1.05, 1.3, 20, True),     # kappa(X) 2.9e4: kappa u32 = 1.7e-3, float correction sweeps contract the error
+    (5, 1.02, 1.2, 12, True),     # kappa(X) 1.3e4
+    (6, 1.1, 1.5, 30, False),     # kappa(X) 6.6e6: kappa u32 = 0.4, the mixed request stays on the float64 route
+])
+def test_mixed_route(tols, idx, lo, hi, p, float_sweeps):
+    """A mixed request follows the float64 route (float64 Gram factor, semi-normal start, float64 checks) and runs
+    float-product correction sweeps only when kappa(X) u32 <= 1e-2. Asked for more than the semi-normal start gives
+    (tol 1e-14), the moderately conditioned series need such sweeps; the result meets the mixed gate and its ratio,
+    recomputed by the oracle, is within 10x of the float64 solve's."""
+    s = ar_series(50_000, p, config_id=90, series_index=idx, root_lo=lo, root_hi=hi)
+    sol = oracle.ols_qr(s.y, p)
+    with tols.Context(precision=tols.TOLS_MIXED) as c:
+        phi, rnorm, info, rc = tols.toeplitz_ols_solve(c, s.y, p, 1e-14)
+    with tols.Context(precision=tols.TOLS_FP64) as c:
+        phi64, _, info64, rc64 = tols.toeplitz_ols_solve(c, s.y, p, 1e-14)
+    assert rc in (tols.TOLS_OK, tols.TOLS_NOT_CONVERGED)
+    assert (info["precision_used"] == tols.TOLS_MIXED) == float_sweeps, info
+    if not float_sweeps:
+        assert np.array_equal(phi, phi64)       # the same float64 route, the same arithmetic
+    assert_solve_parity(s.y, p, phi, sol, 1e-6, backward_tol=1e-11)
+    _, _, ne = oracle.residual_check(s.y, p, phi, norm2=sol.norm2)
+    _, _, ne64 = oracle.residual_check(s.y, p, phi64, norm2=sol.norm2)
+    assert ne <= 10 * max(ne64, 1e-16), (ne, ne64, info, info64)

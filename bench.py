@@ -1,17 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark: AR(p) Toeplitz-LSQR solves/s, FP64 and mixed precision, on one GB300 per rank.
+"""Benchmark: AR(p) Toeplitz-LSQR solves/s (mixed vs FP64), matvec HBM GB/s and p99 latency on one GB300 per rank.
 
-Workload (default): one stationary AR(100) series, n = 2^22, roots of modulus U[1.05, 2], Student-t(5)
-innovations scaled to unit variance, FP64 throughout, solved to a normal-equation ratio of 1e-10. A step is
-one complete solve (Gram pass, Cholesky preconditioner, LSQR passes, float64 check pass) of that series with
-the series already resident in HBM. The same series is also solved in mixed precision, and end to end from
-pinned host memory through the C ABI (toeplitz_ols_solve).
+Headline workload: one stationary AR(500) series, n = 2^26, roots of modulus U[1.05, 2], N(0,1) innovations, solved
+to the float64 floor (tol 1e-10 is below what float64 can reach on it: kappa(X) is about 6e12), requested in mixed
+precision and in FP64. A step is one complete solve (Gram pass, preconditioner, LSQR passes, float64 checks) with
+the series resident in HBM; the L2 is flushed between steps outside the timed events. Beside it: the matvec pass
+alone in both precisions at that size, the order sweep p in {50, 100, 200, 500} on the same series, end to end from
+pinned host memory through toeplitz_ols_solve, and sub-lines for the other configurations: AR(10), n = 10^4
+(plain LSQR, median of 1,000); AR(100), n = 2^22 over 8 seeds; 4,096 batched series; Poisson-arrival serving.
+
+A solve counts toward a rate only if it meets the parity gate, checked with the oracle where a bench run can afford
+it (sampled series of the batch and of the served requests; every seed of the AR(100) line); the others are
+reported beside it.
 
 Under torchrun every rank solves its own replica (weak scaling, no collective on the data path); value is the
-whole-job solves/s with the max time over ranks.
+whole-job rate with the max time over ranks.
 
---impl reference times the CPU oracle (float64 Householder QR, NumPy/LAPACK on the host cores) on a bounded
-sample of the same workload and prints the same JSON line with "impl": "reference".
+--impl reference times the CPU oracle (float64 Householder QR, NumPy/LAPACK on the host cores) on a bounded sample
+of the headline workload (its first rows) and prints the same JSON line with "impl": "reference".
 """
 import argparse
 import json
@@ -28,6 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "AR(p) Toeplitz-LSQR solves/s & matvec HBM GB/s, mixed vs FP64; p99 latency"
 WORKLOADS = {
+    "ar500_n64M": dict(n=1 << 26, p=500, root_lo=1.05, root_hi=2.0, noise="normal", tol=1e-10, config_id=3,
+                       desc="AR(500), n=2^26, roots |r| in U[1.05,2], N(0,1) innovations, mixed vs FP64, "
+                            "to the float64 floor (tol 1e-10)"),
     "ar100_n4M": dict(n=1 << 22, p=100, root_lo=1.05, root_hi=2.0, noise="t5", tol=1e-10, config_id=2,
                       desc="AR(100), n=2^22, roots |r| in U[1.05,2], Student-t(5) innovations, FP64, ne-ratio 1e-10"),
     "ar100_n64M": dict(n=1 << 26, p=100, root_lo=1.05, root_hi=2.0, noise="normal", tol=1e-10, config_id=3,
@@ -35,42 +44,49 @@ WORKLOADS = {
     "ar10_n10k": dict(n=10_000, p=10, root_lo=1.2, root_hi=3.0, noise="normal", tol=1e-12, config_id=1,
                       desc="AR(10), n=10,000, roots |r| in U[1.2,3], N(0,1) innovations, FP64, ne-ratio 1e-12"),
 }
+SWEEP_ORDERS = (50, 100, 200, 500)
 L2_FLUSH_BYTES = 512 << 20
-BATCH_TOL = 1e-10   # normal-equation ratio for the batched and served fits (as for the AR(100) fit)
+GATE_TOL = 1e-12    # normal-equation ratio of the gated lines: the parity gate asks for ratios at 1e-12
+BATCH_TOL = GATE_TOL
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA (4 flop)/clk/SM x 2.07 GHz max clock
+COEF_TOL = {"fp64": 1e-8, "mixed": 1e-6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ar100_n4M")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ar500_n64M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sublines", action="store_true", help="headline only (no cfg 1/2/4/5 lines, sweep, PACF)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused product pass (toeplitz_ols_gk_pass), float64 then float32")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--only", default="", help="kernel-only: comma list of direct_fp64,direct_fp32,fft_fp64,fft_fp32")
     ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
-    ap.add_argument("--batch-series", type=int, default=1024,
+    ap.add_argument("--batch-series", type=int, default=4096,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
+    ap.add_argument("--gate-sample", type=int, default=64,
+                    help="batched / served fits checked against the oracle (the parity gate) per run")
     ap.add_argument("--lsar-only", action="store_true",
-                    help="time only Algorithm LSAR on the bench series (--lsar-lags, --lsar-c)")
+                    help="time only Algorithm LSAR on the AR(100) series (--lsar-lags, --lsar-c)")
     ap.add_argument("--batch-only", action="store_true",
-                    help="solve the batch of --batch-series series once in float64 and print its timing (profiling)")
+                    help="one float64 batched solve of the batch workload (--batch-series), host-timed")
     ap.add_argument("--pacf-lags", type=int, default=120,
-                    help="order sweep: PACF lags fitted on the bench series (0 = skip)")
+                    help="order sweep / PACF on the AR(100) series: lags 1 .. h_max; 0 = skip")
     ap.add_argument("--lsar-lags", type=int, default=120,
-                    help="Algorithm LSAR on the bench series: lags 1 .. p_bar (0 = skip)")
+                    help="Algorithm LSAR on the AR(100) series: lags 1 .. p_bar; 0 = skip")
     ap.add_argument("--lsar-c", type=int, default=2000, help="Algorithm LSAR: rows sampled per lag")
     ap.add_argument("--rh-sketch", type=int, default=16, help="Repeated Halving: rows of the Gaussian sketch")
     ap.add_argument("--rh-only", action="store_true",
-                    help="time only the Repeated Halving variant of LSAR on the bench series")
+                    help="time only the Repeated Halving variant of LSAR on the AR(100) series")
     ap.add_argument("--srht-only", action="store_true",
-                    help="time only Algorithm SRHT for the order-p fit of the bench series (c = --lsar-c rows)")
+                    help="time only Algorithm SRHT for the AR(100) fit")
     ap.add_argument("--serve-requests", type=int, default=400,
-                    help="requests in the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); 0 = skip")
+                    help="requests of the serving run (n log-uniform in [1e3, 1e7], p log-uniform in [1, 300]); "
+                         "0 = skip")
     return ap.parse_args()
 
 
@@ -81,8 +97,6 @@ def peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
-
-
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 20 ms while the timed region runs."""
 
@@ -203,39 +217,68 @@ def gen_many(shapes, cfg, lo=1.2, hi=3.0):
         return pool.map(_gen_one, jobs, chunksize=4)
 
 
-def make_series(wl):
+def make_series(wl, n=None):
+    """The workload's series (its first n samples when n is given: the generator is causal, so a prefix of the
+    full series)."""
     from synthetic import ar_series
-    return ar_series(wl["n"], wl["p"], config_id=wl["config_id"], root_lo=wl["root_lo"], root_hi=wl["root_hi"],
-                     noise=wl["noise"])
+    return ar_series(wl["n"] if n is None else n, wl["p"], config_id=wl["config_id"], root_lo=wl["root_lo"],
+                     root_hi=wl["root_hi"], noise=wl["noise"])
+
+
+def headline_config(wl, world=1):
+    """The config block of the headline line, the same in both arms."""
+    return {"workload": wl["desc"], "n": wl["n"], "p": wl["p"], "tol": wl["tol"], "series_per_rank": 1,
+            "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, not timed)",
+            "parallelism": "replicas" if world > 1 else "single",
+            "request": "mixed precision (value) and FP64 on the same series"}
+
+
+def gate(y, p, phi, coef_tol, sol=None):
+    """The parity gate of one fit against the oracle (float64 QR of the explicit X): coefficients within coef_tol
+    where the oracle's own forward-error bound 10 u (kappa + kappa^2 eta) is at most coef_tol / 10; always a
+    residual no larger than the oracle's (relative 1e-9) and a normal-equation ratio within 10x of the oracle's
+    (or 1e-12), both recomputed by the oracle in float64. Returns (passed, details)."""
+    import numpy as np
+    import oracle
+    sol = sol or oracle.ols_qr(y, p)
+    rn, _, ne = oracle.residual_check(y, p, phi, norm2=sol.norm2)
+    B = sol.forward_error_bound()
+    rel = float(np.linalg.norm(np.asarray(phi) - sol.phi) / max(np.linalg.norm(sol.phi), 1e-300))
+    ok = (B > coef_tol / 10 or rel <= coef_tol) and rn <= sol.rnorm * (1 + 1e-9) + 1e-300 and \
+        ne <= max(1e-12, 10 * sol.ne_ratio)
+    return bool(ok), {"coef_rel_err": rel, "bound": B, "rnorm_rel": (rn - sol.rnorm) / max(sol.rnorm, 1e-300),
+                      "ne": ne, "ne_oracle": sol.ne_ratio}
 
 
 # ---------------------------------------------------------------------------------------------------------
+REF_ROWS = 1 << 16
+
+
 def run_reference(args, wl):
-    """The oracle on the host cores, each step a bounded sample of the workload: the first rows of the series."""
+    """The oracle on the host cores on the headline workload's configuration, each step a bounded sample: the QR of
+    its first REF_ROWS rows (the series' prefix). Dense QR costs a fixed amount per row, so a step does
+    REF_ROWS / m of one solve; value = that fraction / the measured step time."""
     world, rank, _ = dist()
     if rank != 0:
         return
-    import numpy as np
     import oracle
-    s = make_series(wl)
     p = wl["p"]
     m_full = wl["n"] - p
-    m_s = min(m_full, 1 << 19)
-    ys = s.y[: m_s + p]
+    rows = min(m_full, REF_ROWS)
+    y = make_series(wl, rows + p).y
     for _ in range(args.warmup):
-        oracle.ols_qr(ys, p)
+        oracle.ols_qr(y, p)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.ols_qr(ys, p)
+        oracle.ols_qr(y, p)
     dt = (time.perf_counter() - t0) / args.steps
-    per_solve = dt * (m_full / m_s)      # dense QR cost is linear in the row count
-    value = 1.0 / per_solve
-    sample = f"oracle (blocked Householder QR, float64) on the first {m_s} of {m_full} rows per step; " \
-             f"solves/s scaled by {m_full / m_s:.3g}"
+    value = (rows / m_full) / dt
+    sample = (f"oracle (blocked Householder QR, float64) on the first {rows} of the {m_full} rows each step "
+              f"(the series' prefix); a step is {rows / m_full:.3g} of a solve")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": wl["n"], "p": p},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded stationary AR series",
+            "config": headline_config(wl, world),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -243,217 +286,173 @@ def run_reference(args, wl):
 
 
 # ---------------------------------------------------------------------------------------------------------
-def run_ours(args, wl):
+def timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, tol, steps, host_y=None, phi_host=None):
+    """steps solves, each timed with CUDA events on the solver's stream, the L2 flushed before each (not timed)."""
+    times, infos = [], []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if host_y is None:
+            _, info, rc = tols.toeplitz_ols_solve_device(ctx, d_y, n, p, d_phi, tol)
+        else:
+            phi, _, info, rc = tols.toeplitz_ols_solve(ctx, host_y, p, tol)
+            phi_host[:] = phi
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+    return times, infos
+
+
+def profile_dict(tols, ctx):
+    return {tols.PROFILE_CLASS_NAMES[k]: tols.toeplitz_ols_profile_read(ctx, k) for k in range(tols.TOLS_PROFILE_CLASSES)}
+
+
+def run_matvec(tols, torch, dev, stream, y, p_list, reps):
+    """The fused pass u_new = X v - c u_old, ||u_new||^2, X^T u_new alone (toeplitz_ols_gk_pass), float64 and
+    float32, direct and overlap-save FFT products, on the headline series: device time of the pass kernel itself
+    (in-library CUDA events; the window spectra an FFT pass reads are formed beforehand by another kernel, not
+    counted), algorithmic bytes n s_y + 2 m s_u, and the fraction of the measured HBM copy rate."""
     import numpy as np
-    import torch
+    hbm, src = peaks()
+    n = y.size
+    rng = np.random.default_rng(1)
+    out = {"hbm_peak_gbs": hbm, "hbm_peak_source": src, "n": n}
+    for name, dt, prec, cls, es in (("fp64", torch.float64, tols.TOLS_FP64, 5, 8),
+                                    ("fp32", torch.float32, tols.TOLS_MIXED, 0, 4)):
+        d_y = torch.tensor(y, dtype=dt, device=dev)
+        for p in p_list:
+            m = n - p
+            v = torch.tensor(rng.standard_normal(p), dtype=torch.float64, device=dev)
+            t = torch.empty(p, dtype=torch.float64, device=dev)
+            u0 = torch.tensor(rng.standard_normal(m), dtype=dt, device=dev)
+            u1 = torch.empty(m, dtype=dt, device=dev)
+            for prod_name, prod in (("direct", tols.TOLS_PRODUCT_DIRECT), ("fft", tols.TOLS_PRODUCT_FFT)):
+                with tols.Context(precision=tols.TOLS_FP64, product=prod, device=dev.index,
+                                  cuda_stream=stream.cuda_stream) as ctx:
+                    tols.toeplitz_ols_gk_pass(ctx, prec, d_y, n, p, v, u0, 0.5, u1, t)     # warm-up
+                    tols.toeplitz_ols_profile(ctx, True)
+                    for _ in range(reps):
+                        tols.toeplitz_ols_gk_pass(ctx, prec, d_y, n, p, v, u0, 0.5, u1, t)
+                    cnt, ms = tols.toeplitz_ols_profile_read(ctx, cls)
+                    tols.toeplitz_ols_profile(ctx, False)
+                byts = float(es) * n + 2.0 * es * m
+                avg = ms / max(cnt, 1)
+                gbs = byts / (avg * 1e-3) / 1e9
+                out[f"p{p}_{name}_{prod_name}"] = {"ms": avg, "gbs": gbs, "frac_hbm": gbs / hbm, "bytes": byts,
+                                                   "launches": cnt}
+            del u0, u1, v, t
+        del d_y
+    return out
 
-    import paper_2112_12994_gb300 as tols
 
-    world, rank, local = dist()
-    from synthetic import batch_shapes
-    batch_in = serve_in = None
-    if args.batch_series > 0:
-        bn, bp = batch_shapes(args.batch_series, config_id=4, n_lo=1e4, n_hi=1e6, p_lo=5, p_hi=200)
-        batch_in = (gen_many(list(zip(bn, bp)), 4), [int(x) for x in bp])
-    if args.serve_requests > 0:
-        sn, sp = batch_shapes(args.serve_requests, config_id=5, n_lo=1e3, n_hi=1e7, p_lo=1, p_hi=300,
-                              p_log_uniform=True)
-        serve_in = (gen_many(list(zip(sn, sp)), 5), [int(x) for x in sp])
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    ranks = Ranks(world, rank, dev)
-    barrier, max_over_ranks = ranks.barrier, ranks.max
+def run_sweep(tols, torch, dev, stream, flush, d_y, n, steps):
+    """The order sweep of the headline configuration: AR(p) fits for p in SWEEP_ORDERS to the same series (each an
+    independent problem on m = n - p rows), mixed and FP64 requests."""
+    import numpy as np
+    out = {}
+    for p in SWEEP_ORDERS:
+        d_phi = torch.empty(p, dtype=torch.float64, device=dev)
+        for name, prec in (("fp64", tols.TOLS_FP64), ("mixed", tols.TOLS_MIXED)):
+            with tols.Context(precision=prec, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
+                timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, 1e-10, 1)
+                times, infos = timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, 1e-10, steps)
+            i = infos[-1]
+            out[f"p{p}_{name}"] = {"ms_median": float(np.median(times)), "solves_per_s": 1e3 / float(np.median(times)),
+                                   "status": i["status"], "iters": i["iters"], "sweeps": i["sweeps"],
+                                   "ne_ratio": i["ne_ratio"], "precision_used": i["precision_used"],
+                                   "precond_used": i["precond_used"], "cond_est": i["cond_est"]}
+        del d_phi
+    return out
 
+
+def run_cfg1(tols, torch, dev, stream, reps=1000):
+    """AR(10), n = 10,000 (roots |r| in U[1.2, 3], N(0,1)): plain LSQR, no preconditioner, FP64, tol 1e-12; the
+    median of `reps` solves of the series resident in HBM (CUDA events around each solve), and the iterations
+    with and without the preconditioner."""
+    import numpy as np
+    wl = WORKLOADS["ar10_n10k"]
     s = make_series(wl)
     n, p, tol = wl["n"], wl["p"], wl["tol"]
-    m = n - p
-    stream = torch.cuda.Stream(dev)
     d_y = torch.tensor(s.y, dtype=torch.float64, device=dev)
     d_phi = torch.empty(p, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {"workload": wl["desc"] + "; plain LSQR (no preconditioner)", "reps": reps}
+    for name, pre in (("plain", tols.TOLS_PRECOND_NONE), ("preconditioned", tols.TOLS_PRECOND_GRAM_CHOL)):
+        with tols.Context(precision=tols.TOLS_FP64, precond=pre, device=dev.index, cuda_stream=stream.cuda_stream) as c:
+            for _ in range(10):
+                tols.toeplitz_ols_solve_device(c, d_y, n, p, d_phi, tol)
+            times = []
+            for _ in range(reps if name == "plain" else 50):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, info, rc = tols.toeplitz_ols_solve_device(c, d_y, n, p, d_phi, tol)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        ok, det = gate(s.y, p, d_phi.cpu().numpy(), COEF_TOL["fp64"])
+        out[name] = {"ms_median": float(np.median(times)), "solves_per_s": 1e3 / float(np.median(times)),
+                     "p99_ms": float(np.percentile(times, 99)), "iters": info["iters"], "sweeps": info["sweeps"],
+                     "status": info["status"], "ne_ratio": info["ne_ratio"], "gate_passed": ok,
+                     "coef_rel_err": det["coef_rel_err"]}
+    out["value"] = out["plain"]["solves_per_s"] if out["plain"]["gate_passed"] else 0.0
+    out["unit"] = "solves/s"
+    return out
 
-    def timed_solves(ctx, steps, host_y=None, phi_host=None):
-        times, infos = [], []
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1)                       # evict y and the work vectors from L2 (not timed)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if host_y is None:
-                _, info, rc = tols.toeplitz_ols_solve_device(ctx, d_y, n, p, d_phi, tol)
-            else:
-                phi, _, info, rc = tols.toeplitz_ols_solve(ctx, host_y, p, tol)
-                phi_host[:] = phi
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            infos.append(info)
-        return times, infos
 
-    results = {}
-    for name, prec in (("fp64", tols.TOLS_FP64), ("mixed", tols.TOLS_MIXED)):
-        ctx = tols.Context(precision=prec, device=local, cuda_stream=stream.cuda_stream)
-        timed_solves(ctx, args.warmup)
-        tols.toeplitz_ols_profile(ctx, True)
-        clocks = ClockSampler(_smi_index(local)) if name == "fp64" else None
-        barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        times, infos = timed_solves(ctx, args.steps)
-        torch.cuda.synchronize()
-        barrier()
-        clk = clocks.stop() if clocks else None
-        prof = {tols.PROFILE_CLASS_NAMES[k]: tols.toeplitz_ols_profile_read(ctx, k)
-                for k in range(tols.TOLS_PROFILE_CLASSES)}
-        launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
-        tols.toeplitz_ols_profile(ctx, False)
-        phi = d_phi.cpu().numpy().copy()
-        total_ms = max_over_ranks(sum(times))
-        results[name] = dict(times=times, infos=infos, prof=prof, launches=launches, phi=phi, total_ms=total_ms,
-                             clocks=clk, ctx=ctx)
-
-    # end to end: pinned host series in, phi out, through toeplitz_ols_solve (FP64, the headline precision)
-    pinned = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    pinned.copy_(torch.from_numpy(s.y))
-    host_y = pinned.numpy()
-    phi_h = np.zeros(p)
-    ctx = results["fp64"]["ctx"]
-    timed_solves(ctx, 1, host_y, phi_h)
-    barrier()
-    torch.cuda.synchronize()
-    e2e_times, _ = timed_solves(ctx, args.steps, host_y, phi_h)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_ms = max_over_ranks(sum(e2e_times))
-
-    batched = batched_mixed = serving = None
-    if batch_in:
-        batched = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world, tols.TOLS_FP64)
-        batched_mixed = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world,
-                                    tols.TOLS_MIXED)
-    if serve_in:
-        serving = run_serving(tols, serve_in, args)
-    order_sweep = run_order_sweep(tols, torch, s.y, args) if args.pacf_lags > 0 else None
-    lsar = (run_lsar(tols, torch, s.y, args, order_sweep["ms_per_sweep"] if order_sweep and
-                     order_sweep["lags"] == args.lsar_lags else None) if args.lsar_lags > 0 else None)
-
-    hbm_peak, hbm_src = peaks()
-    r64, rmx = results["fp64"], results["mixed"]
-    K = args.steps
-    value = whole_job_rate(world, K, r64["total_ms"] / 1e3)
-    mixed_value = whole_job_rate(world, K, rmx["total_ms"] / 1e3)
-
-    def per_launch(prof, key):
-        cnt, ms = prof[key]
-        return (ms / cnt if cnt else float("nan")), cnt
-
-    # dominant kernel of the FP64 step and its roofline (float64 FMA units bound it; see the design notes).
-    # Flops per launch: direct products 4 m p (2 m p multiply-adds). Overlap-save FFT pass: per tile of
-    # L = N - pad16(p + 1) rows one inverse and one forward real N-point transform, 2 x 2.5 N log2 N (the window
-    # spectra are formed once per solve, the X^T u spectra are summed per CTA and transformed back once).
-    dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0 and k.startswith("pass_")),
-              key=lambda k: r64["prof"][k][1])
-    avg_ms, cnt = per_launch(r64["prof"], dom)
-    lags = p + 1 if dom.endswith("gram") else p
-    fft_used = r64["infos"][-1]["product_used"] == tols.TOLS_PRODUCT_FFT
-    if fft_used:
-        N = 2048
-        pg = ((p + 1 + 15) // 16) * 16
-        tiles = math.ceil(m / (N - pg))
-        if dom.endswith("gram"):    # one forward transform per tile plus the direct edge corrections
-            flops = tiles * (2.5 * N * math.log2(N) + 2.0 * pg * (p + 1))
-        else:
-            flops = tiles * 5.0 * N * math.log2(N)
-        kname = f"fft_pass_kernel<double> ({dom})"
-    else:
-        flops = (2.0 if dom.endswith("gram") else 4.0) * m * lags
-        kname = f"pass_kernel<double> ({dom})"
-    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
-    byts_fp64 = 8.0 * n + 16.0 * m
-    # DRAM traffic of the FFT check/LSQR pass from an ncu capture of the same kernel (n = 2^26, p = 100: 1.106 GB
-    # read + 0.508 GB written per launch, 24.05 B per row of y), scaled to this launch's rows
-    traffic = 24.05 * n if (fft_used and not dom.endswith("gram") and p == 100) else None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "traffic_source": "ncu dram__bytes_read+write of fft_pass_kernel<double> at "
-                                                      "n = 2^26, p = 100, scaled by rows" if traffic else None, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-                "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt,
-                "product": "fft" if fft_used else "direct"}
-    mx_dom = "pass_f32_lsqr" if rmx["prof"]["pass_f32_lsqr"][0] else "pass_f32_necorr"
-    mx_ms, mx_cnt = per_launch(rmx["prof"], mx_dom)
-    byts_mx = 4.0 * n + 8.0 * m
-    mx_gbs = byts_mx / (mx_ms * 1e-3) / 1e9 if mx_cnt else None
-    fp64_pass_ms, _ = per_launch(r64["prof"], "pass_f64_lsqr")
-
-    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
-           "warmup": args.warmup, "ms_per_step": r64["total_ms"] / K, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic: seeded stationary AR series (see config)",
-           "config": {"workload": wl["desc"], "n": n, "p": p, "tol": tol, "series_per_rank": 1,
-                      "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write, not timed)",
-                      "parallelism": "replicas" if world > 1 else "single"},
-           "roofline": roofline,
-           "matvec": {"fp64_pass_ms": fp64_pass_ms,
-                      "fp64_pass_gbs": byts_fp64 / (fp64_pass_ms * 1e-3) / 1e9 if fp64_pass_ms == fp64_pass_ms else None,
-                      "mixed_pass_kernel": mx_dom, "mixed_pass_ms": mx_ms, "mixed_pass_gbs": mx_gbs,
-                      "mixed_pass_frac_hbm": (mx_gbs / hbm_peak) if mx_gbs else None,
-                      "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
-                      "bytes_per_pass": {"fp64": byts_fp64, "mixed": byts_mx}},
-           "mixed": {"value": mixed_value, "unit": "solves/s", "ms_per_step": rmx["total_ms"] / K,
-                     "vs_fp64": mixed_value / value,
-                     "precision_used": rmx["infos"][-1]["precision_used"], "iters": rmx["infos"][-1]["iters"],
-                     "sweeps": rmx["infos"][-1]["sweeps"], "ne_ratio": rmx["infos"][-1]["ne_ratio"]},
-           "latency_ms": {"fp64_p50": float(np.percentile(r64["times"], 50)),
-                          "fp64_p99": float(np.percentile(r64["times"], 99)),
-                          "mixed_p50": float(np.percentile(rmx["times"], 50)),
-                          "mixed_p99": float(np.percentile(rmx["times"], 99))},
-           "solve": {"iters": r64["infos"][-1]["iters"], "sweeps": r64["infos"][-1]["sweeps"],
-                     "ne_ratio": r64["infos"][-1]["ne_ratio"], "cond_est": r64["infos"][-1]["cond_est"],
-                     "status": r64["infos"][-1]["status"]},
-           "e2e": {"value": whole_job_rate(world, K, e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
-                   "d2h_bytes_per_step": 8 * p},
-           "batched": batched,
-           "batched_mixed": batched_mixed,
-           "serving": serving,
-           "order_sweep": order_sweep,
-           "lsar": lsar,
-           "gpu_launches": int(r64["launches"] + rmx["launches"]),
-           "clocks": r64["clocks"],
-           "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r64["prof"].items() if v[0]}}
-
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        solves = 0
-        t0 = time.perf_counter()
-        while solves < 3 and (solves == 0 or time.perf_counter() - t0 < 10.0):   # about 10-15 s of CPU work
-            ref = oracle.ols_qr(s.y, p)
-            solves += 1
-        dt = (time.perf_counter() - t0) / solves
-        out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                               "sample": f"{solves} full solves of the same series (blocked Householder QR, float64)"}
-        out["accuracy"] = {"fp64_coef_rel_err": float(np.linalg.norm(r64["phi"] - ref.phi) / np.linalg.norm(ref.phi)),
-                           "mixed_coef_rel_err": float(np.linalg.norm(rmx["phi"] - ref.phi) / np.linalg.norm(ref.phi)),
-                           "oracle_kappa": ref.kappa, "oracle_forward_bound": ref.forward_error_bound(),
-                           "oracle_ne_ratio": ref.ne_ratio}
-    for r in results.values():
-        r["ctx"].close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    ranks.close()
+def run_cfg2(tols, torch, dev, stream, flush, series, steps=3):
+    """AR(100), n = 2^22 (roots |r| in U[1.05, 2], Student-t(5)) over several seeds, FP64 and mixed requests,
+    tol 1e-12 (the configuration's 1e-10 lets the semi-normal start stop short of the gate's 1e-12 ratio): per
+    seed the median solve time, iterations, sweeps, status and the parity gate."""
+    import numpy as np
+    wl = WORKLOADS["ar100_n4M"]
+    n, p, tol = wl["n"], wl["p"], GATE_TOL
+    d_phi = torch.empty(p, dtype=torch.float64, device=dev)
+    seeds = []
+    import oracle
+    for k, y in enumerate(series):
+        d_y = torch.tensor(y, dtype=torch.float64, device=dev)
+        sol = oracle.ols_qr(y, p)
+        rec = {"series_index": k, "oracle_kappa": sol.kappa, "oracle_bound": sol.forward_error_bound()}
+        for name, prec in (("fp64", tols.TOLS_FP64), ("mixed", tols.TOLS_MIXED)):
+            with tols.Context(precision=prec, device=dev.index, cuda_stream=stream.cuda_stream) as c:
+                timed_solves(tols, torch, c, stream, flush, d_y, n, p, d_phi, tol, 1)
+                times, infos = timed_solves(tols, torch, c, stream, flush, d_y, n, p, d_phi, tol, steps)
+            ok, det = gate(y, p, d_phi.cpu().numpy(), COEF_TOL[name], sol)
+            i = infos[-1]
+            rec[name] = {"ms_median": float(np.median(times)), "iters": i["iters"], "sweeps": i["sweeps"],
+                         "status": i["status"], "precond_used": i["precond_used"],
+                         "precision_used": i["precision_used"], "gate_passed": ok, **det}
+        seeds.append(rec)
+        del d_y
+    out = {"workload": wl["desc"].replace("ne-ratio 1e-10", "ne-ratio 1e-12 (the gate's)") +
+                       f"; {len(series)} seeds (series_index 0..{len(series) - 1})", "seeds": seeds}
+    for name in ("fp64", "mixed"):
+        ms = [r[name]["ms_median"] for r in seeds]
+        passed = [r[name]["gate_passed"] for r in seeds]
+        out[name] = {"ms_median_over_seeds": float(np.median(ms)),
+                     "solves_per_s": len(ms) / (sum(ms) * 1e-3),
+                     "solves_per_s_gated": sum(1 for x in passed if x) / (sum(ms) * 1e-3),
+                     "gate_passed": int(sum(passed)), "seeds": len(ms)}
+    return out
 
 
 def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks, world, prec):
-    """Many series of uneven length in one batched solve, series resident in HBM."""
+    """Many series of uneven length in one batched solve, series resident in HBM; the parity gate on an evenly
+    spaced sample of the series (oracle solves, also the CPU baseline of this workload)."""
     import numpy as np
+    import oracle
     ys, ps = batch_in
+    name = "fp64" if prec == tols.TOLS_FP64 else "mixed"
     d_ys = [torch.tensor(y, dtype=torch.float64, device=dev) for y in ys]
     d_phi = torch.empty(sum(ps), dtype=torch.float64, device=dev)
-    steps = max(2, min(args.steps, 5))
-    out = {"series": len(ys), "sum_n": int(sum(y.size for y in ys)),
-           "precision": "fp64" if prec == tols.TOLS_FP64 else "mixed",
-           "workload": "n log-uniform in [1e4, 1e6], p uniform in [5, 200], roots |r| in U[1.2, 3], N(0,1)"}
+    steps = max(2, min(args.steps, 3))
+    out = {"series": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": name,
+           "workload": "n log-uniform in [1e4, 1e6], p uniform in [5, 200], roots |r| in U[1.2, 3], N(0,1); "
+                       "unfiltered seeds"}
     with tols.Context(precision=prec, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
         tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)       # warm-up
         tols.toeplitz_ols_profile(ctx, True)
@@ -466,40 +465,96 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
         launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
-        f32 = tols.toeplitz_ols_profile_read(ctx, 1)
+        f32 = tols.toeplitz_ols_profile_read(ctx, 2)
         tols.toeplitz_ols_profile(ctx, False)
-        # end to end from host memory through toeplitz_ols_solve_batched
         t1 = time.perf_counter()
-        phis_h, _, _, _ = tols.toeplitz_ols_solve_batched(ctx, ys, ps, BATCH_TOL)
+        tols.toeplitz_ols_solve_batched(ctx, ys, ps, BATCH_TOL)                      # end to end from host memory
         e2e_dt = time.perf_counter() - t1
     status = [i["status"] for i in infos]
-    out.update({"value": whole_job_rate(world, len(ys) * steps, dt), "unit": "solves/s", "ms_per_batch": 1e3 * dt / steps,
-                "steps": steps, "tol": BATCH_TOL, "statuses_ok": int(sum(1 for x in status if x == 0)),
+    phi_all = d_phi.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(ps)])
+    sample = list(range(0, len(ys), max(1, len(ys) // args.gate_sample)))[: args.gate_sample]
+    passed, t_or, fails = 0, 0.0, []
+    for k in sample:
+        t2 = time.perf_counter()
+        sol = oracle.ols_qr(ys[k], ps[k])
+        t_or += time.perf_counter() - t2
+        ok, det = gate(ys[k], ps[k], phi_all[offs[k]:offs[k + 1]], COEF_TOL[name], sol)
+        passed += ok
+        if not ok:
+            fails.append({"series": k, "p": ps[k], "n": int(ys[k].size), "status": status[k], **det})
+    value = whole_job_rate(world, len(ys) * steps, dt)
+    out.update({"value": value, "unit": "solves/s", "ms_per_batch": 1e3 * dt / steps, "steps": steps,
+                "tol": BATCH_TOL, "statuses_ok": int(sum(1 for x in status if x == 0)),
                 "statuses_not_converged": int(sum(1 for x in status if x == 1)),
-                "fp64_fallbacks": int(sum(1 for i in infos if i["precision_used"] == 0)),
+                "gate_sample": {"checked": len(sample), "passed": int(passed), "failed": fails[:8]},
+                "value_gated_est": value * passed / max(len(sample), 1),
+                "float_sweep_series": int(sum(1 for i in infos if i["precision_used"] == tols.TOLS_MIXED)),
+                "sampled_qr_series": int(sum(1 for i in infos if i["precond_used"] == 2)),
                 "mean_iters": float(np.mean([i["iters"] for i in infos])),
                 "max_iters": int(max(i["iters"] for i in infos)),
                 "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches),
-                "f32_lsqr_pass_launches": f32[0], "f32_lsqr_pass_ms": f32[1]})
-    # accuracy on a few series against the oracle (timed as the CPU baseline of this workload)
-    import oracle
-    phi_all = d_phi.cpu().numpy()
-    offs = np.concatenate([[0], np.cumsum(ps)])
-    errs, t_or, rows = [], 0.0, 0
-    for k in range(0, len(ys), max(1, len(ys) // 4))[:4]:
-        t2 = time.perf_counter()
-        ref = oracle.ols_qr(ys[k], ps[k])
-        t_or += time.perf_counter() - t2
-        rows += 1
-        errs.append(float(np.linalg.norm(phi_all[offs[k]:offs[k + 1]] - ref.phi) / np.linalg.norm(ref.phi)))
-    out["max_coef_rel_err_sampled"] = max(errs)
-    out["cpu_baseline"] = {"value": rows / t_or, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                           "sample": f"{rows} series of the batch"}
+                "f32_necorr_pass_launches": f32[0], "f32_necorr_pass_ms": f32[1],
+                "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": cpu_cores(),
+                                 "kind": "oracle", "sample": f"{len(sample)} evenly spaced series of the batch"}})
+    del d_ys, d_phi
     return out
 
 
-def run_order_sweep(tols, torch, y, args):
-    """PACF of the bench series: the fits of order 1 .. h_max as one batch (toeplitz_ols_pacf, host series)."""
+def run_serving(tols, serve_in, args):
+    """Continuous batching of mixed-precision fit requests: saturation throughput (all requests submitted at
+    once), then Poisson arrivals at 0.25, 0.5, 0.75 and 1.0 times that rate; p50/p99 latency from submit to
+    retire; the parity gate on a sample of the saturation run's results."""
+    import numpy as np
+    import oracle
+    ys, ps = serve_in
+    res = {"requests": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "mixed",
+           "workload": "n log-uniform in [1e3, 1e7], p log-uniform in [1, 300], roots |r| in U[1.2, 3], N(0,1)"}
+
+    def run(rate):
+        rng = np.random.default_rng(5)
+        arrivals = np.zeros(len(ys)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, size=len(ys)))
+        with tols.Server(precision=tols.TOLS_MIXED, burst=4) as srv:
+            t0 = time.perf_counter()
+            nxt, done = 0, []
+            while len(done) < len(ys):
+                now = time.perf_counter() - t0
+                while nxt < len(ys) and arrivals[nxt] <= now:
+                    rc = srv.submit(nxt, ys[nxt], ps[nxt], BATCH_TOL)
+                    assert rc == 0, rc
+                    nxt += 1
+                active, queued = srv.step()
+                for r in srv.poll():
+                    done.append(r)
+                if active == 0 and queued == 0 and nxt < len(ys):
+                    time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+            makespan = time.perf_counter() - t0
+        lat = np.array([r["latency_s"] for r in done])
+        ok = sum(1 for r in done if r["status"] == 0)
+        return done, {"solves_per_s": len(done) / makespan, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "status_ok": ok,
+                      "status_not_converged": sum(1 for r in done if r["status"] == 1),
+                      "float_sweep_requests": sum(1 for r in done if r["info"]["precision_used"] == tols.TOLS_MIXED)}
+
+    done, sat = run(None)
+    by_id = {r["id"]: r for r in done}
+    k_gate = min(len(ys), max(1, args.gate_sample // 2))
+    sample = list(range(0, len(ys), max(1, len(ys) // k_gate)))[:k_gate]
+    passed, fails = 0, []
+    for k in sample:
+        ok, det = gate(ys[k], ps[k], by_id[k]["phi"], COEF_TOL["mixed"])
+        passed += ok
+        if not ok:
+            fails.append({"request": k, "p": ps[k], "n": int(ys[k].size), "status": by_id[k]["status"], **det})
+    sat["gate_sample"] = {"checked": len(sample), "passed": int(passed), "failed": fails[:8]}
+    sat["solves_per_s_gated_est"] = sat["solves_per_s"] * passed / max(len(sample), 1)
+    res["saturation"] = sat
+    for frac in (0.25, 0.5, 0.75, 1.0):
+        rate = frac * sat["solves_per_s"]
+        res[f"poisson_{frac:g}x"] = dict(run(rate)[1], rate_per_s=rate)
+    return res
+def run_pacf(tols, torch, y, args):
+    """PACF of the AR(100), n = 2^22 series: the fits of order 1 .. h_max as one batch (toeplitz_ols_pacf, host series)."""
     import numpy as np
     h = args.pacf_lags
     with tols.Context(precision=tols.TOLS_FP64) as ctx:
@@ -511,12 +566,12 @@ def run_order_sweep(tols, torch, y, args):
     return {"lags": h, "fits_per_s": h / dt, "ms_per_sweep": dt * 1e3, "order_estimate": order,
             "statuses_ok": int(sum(1 for i in infos if i["status"] == 0)),
             "max_iters": int(max(i["iters"] for i in infos)),
-            "workload": "AR(h), h = 1 .. lags, fitted to the bench series (n = 2^22), float64, tol 1e-10, "
+            "workload": "AR(h), h = 1 .. lags, fitted to the AR(100), n = 2^22 series, float64, tol 1e-10, "
                         "end to end from host memory"}
 
 
 def run_lsar(tols, torch, y, args, exact_ms):
-    """Algorithm LSAR on the bench series: compressed fits of lags 1 .. p_bar with c sampled rows each, series and
+    """Algorithm LSAR on the AR(100) series: compressed fits of lags 1 .. p_bar with c sampled rows each, series and
     uniforms resident on the device (toeplitz_ols_lsar); timed with CUDA events after one warm-up sweep."""
     from synthetic import lsar_uniforms
     p_bar, c = args.lsar_lags, args.lsar_c
@@ -533,7 +588,7 @@ def run_lsar(tols, torch, y, args, exact_ms):
     ms = min(times) * 1e3
     res = {"lags": p_bar, "c": c, "ms_per_sweep": ms, "lags_per_s": p_bar / (ms * 1e-3), "order_estimate": order,
            "status": rc, "tau_finite": bool(all(math.isfinite(t) for t in tau)),
-           "workload": "Algorithm LSAR on the bench series (n = 2^22): lags 1 .. p_bar on n - p_bar rows, c rows "
+           "workload": "Algorithm LSAR on the AR(100), n = 2^22 series: lags 1 .. p_bar on n - p_bar rows, c rows "
                        "sampled per lag, series and uniforms in HBM, best of 3 sweeps (host clock around the call, "
                        "which returns after the device finishes)"}
     if exact_ms:
@@ -543,7 +598,7 @@ def run_lsar(tols, torch, y, args, exact_ms):
 
 
 def run_rh(tols, torch, y, args):
-    """The Repeated Halving variant of LSAR on the bench series (toeplitz_ols_rh_lsar): halvings down to c rows,
+    """The Repeated Halving variant of LSAR on the AR(100) series (toeplitz_ols_rh_lsar): halvings down to c rows,
     a k-row sketch per level, then lags 1 .. p_bar; draws and series resident on the device; best of 3."""
     import numpy as np
     from synthetic import lsar_uniforms, rh_draws
@@ -565,13 +620,13 @@ def run_rh(tols, torch, y, args):
     ms = min(times) * 1e3
     return {"lags": p_bar, "c": c, "k": k, "levels": len(keep), "ms_per_sweep": ms, "lags_per_s": p_bar / (ms * 1e-3),
             "order_estimate": order, "status": rc, "tau_finite": bool(all(math.isfinite(t) for t in tau)),
-            "workload": "Repeated Halving variant of LSAR on the bench series (n = 2^22): halvings to c rows, "
+            "workload": "Repeated Halving variant of LSAR on the AR(100), n = 2^22 series: halvings to c rows, "
                         "k-row Gaussian sketches, lags 1 .. p_bar with c rows each; inputs in HBM, best of 3 "
                         "(host clock around the call; the halving lists are copied to the device inside it)"}
 
 
 def run_srht(tols, torch, y, p, args):
-    """Algorithm SRHT (toeplitz_ols_srht) for the order-p fit of the bench series: random signs, the normalised
+    """Algorithm SRHT (toeplitz_ols_srht) for the order-p fit of the AR(100) series: random signs, the normalised
     Hadamard transform of the p+1 padded columns, c sampled rows, the compressed fit; best of 3."""
     import numpy as np
     from synthetic import srht_draws
@@ -591,44 +646,8 @@ def run_srht(tols, torch, y, p, args):
             times.append(time.perf_counter() - t0)
     ms = min(times) * 1e3
     return {"p": p, "c": c, "m2": int(signs.size), "ms_per_fit": ms, "fits_per_s": 1e3 / ms, "status": rc,
-            "workload": "Algorithm SRHT for the AR(p) fit of the bench series (n = 2^22): (p+1) columns of "
+            "workload": "Algorithm SRHT for the AR(p) fit of the AR(100), n = 2^22 series: (p+1) columns of "
                         "2^22 padded rows through the Hadamard transform, c rows sampled; best of 3 (host clock)"}
-
-
-def run_serving(tols, serve_in, args):
-    """Continuous batching: saturation throughput, then Poisson arrivals at half of it; p50/p99 latency."""
-    import numpy as np
-    ys, ps = serve_in
-    res = {"requests": len(ys), "sum_n": int(sum(y.size for y in ys)), "precision": "fp64",
-           "workload": "n log-uniform in [1e3, 1e7], p log-uniform in [1, 300], roots |r| in U[1.2, 3], N(0,1)"}
-
-    def run(rate):
-        rng = np.random.default_rng(5)
-        arrivals = np.zeros(len(ys)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, size=len(ys)))
-        with tols.Server(precision=tols.TOLS_FP64, burst=4) as srv:
-            t0 = time.perf_counter()
-            nxt, done, lat = 0, [], []
-            while len(done) < len(ys):
-                now = time.perf_counter() - t0
-                while nxt < len(ys) and arrivals[nxt] <= now:
-                    rc = srv.submit(nxt, ys[nxt], ps[nxt], BATCH_TOL)
-                    assert rc == 0, rc
-                    nxt += 1
-                active, queued = srv.step()
-                for r in srv.poll():
-                    done.append(r)
-                if active == 0 and queued == 0 and nxt < len(ys):
-                    time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
-            makespan = time.perf_counter() - t0
-        lat = np.array([r["latency_s"] for r in done])
-        ok = sum(1 for r in done if r["status"] == 0)
-        return {"solves_per_s": len(done) / makespan, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "ok": ok}
-
-    sat = run(None)
-    res["saturation"] = sat
-    res["poisson_half_rate"] = dict(run(0.5 * sat["solves_per_s"]), rate_per_s=0.5 * sat["solves_per_s"])
-    return res
 
 
 def run_batch_only(args):
@@ -710,6 +729,227 @@ def _smi_index(local):
     return local
 
 
+
+
+def _gen_wl(job):
+    from synthetic import ar_series
+    name, idx = job
+    wl = WORKLOADS[name]
+    return ar_series(wl["n"], wl["p"], config_id=wl["config_id"], series_index=idx, root_lo=wl["root_lo"],
+                     root_hi=wl["root_hi"], noise=wl["noise"]).y
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+
+    import paper_2112_12994_gb300 as tols
+
+    world, rank, local = dist()
+    from synthetic import batch_shapes
+    sub = not args.no_sublines
+    # inputs of the sub-lines, generated in a spawn pool before any CUDA call
+    batch_in = serve_in = cfg2_in = None
+    if sub and args.batch_series > 0:
+        bn, bp = batch_shapes(args.batch_series, config_id=4, n_lo=1e4, n_hi=1e6, p_lo=5, p_hi=200)
+        batch_in = (gen_many(list(zip(bn, bp)), 4), [int(x) for x in bp])
+    if sub and args.serve_requests > 0:
+        sn, sp = batch_shapes(args.serve_requests, config_id=5, n_lo=1e3, n_hi=1e7, p_lo=1, p_hi=300,
+                              p_log_uniform=True)
+        serve_in = (gen_many(list(zip(sn, sp)), 5), [int(x) for x in sp])
+    if sub:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(8) as pool:
+            cfg2_in = pool.map(_gen_wl, [("ar100_n4M", k) for k in range(8)])
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ranks = Ranks(world, rank, dev)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
+
+    s = make_series(wl)
+    n, p, tol = wl["n"], wl["p"], wl["tol"]
+    m = n - p
+    stream = torch.cuda.Stream(dev)
+    d_y = torch.tensor(s.y, dtype=torch.float64, device=dev)
+    d_phi = torch.empty(p, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # headline: the same series requested in FP64 and in mixed precision, K timed solves each
+    results = {}
+    clocks = ClockSampler(_smi_index(local))
+    for name, prec in (("fp64", tols.TOLS_FP64), ("mixed", tols.TOLS_MIXED)):
+        ctx = tols.Context(precision=prec, device=local, cuda_stream=stream.cuda_stream)
+        timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, tol, args.warmup)
+        tols.toeplitz_ols_profile(ctx, True)
+        barrier()
+        torch.cuda.synchronize()
+        if name == "fp64":
+            clocks.start()
+        times, infos = timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, tol, args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if name == "mixed" else None
+        prof = profile_dict(tols, ctx)
+        launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
+        tols.toeplitz_ols_profile(ctx, False)
+        results[name] = dict(times=times, infos=infos, prof=prof, launches=launches, phi=d_phi.cpu().numpy().copy(),
+                             total_ms=max_over_ranks(sum(times)), clocks=clk, ctx=ctx)
+
+    # end to end: pinned host series in, phi out, through toeplitz_ols_solve (the mixed request)
+    pinned = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(s.y))
+    host_y = pinned.numpy()
+    phi_h = np.zeros(p)
+    ctx = results["mixed"]["ctx"]
+    timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, tol, 1, host_y, phi_h)
+    barrier()
+    torch.cuda.synchronize()
+    e2e_times, _ = timed_solves(tols, torch, ctx, stream, flush, d_y, n, p, d_phi, tol, args.steps, host_y, phi_h)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(sum(e2e_times))
+    for r in results.values():
+        r["ctx"].close()
+
+    matvec = run_matvec(tols, torch, dev, stream, s.y, (100, p), 5)
+    sweep = run_sweep(tols, torch, dev, stream, flush, d_y, n, 2) if sub else None
+    del d_y
+    subl = {}
+    if sub:
+        subl["cfg1_ar10_n10k"] = run_cfg1(tols, torch, dev, stream)
+        subl["cfg2_ar100_n4M"] = run_cfg2(tols, torch, dev, stream, flush, cfg2_in)
+        if batch_in:
+            subl["cfg4_batched_mixed"] = run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_ranks,
+                                                     world, tols.TOLS_MIXED)
+            subl["cfg4_batched_fp64"] = run_batched(tols, torch, dev, stream, batch_in, args, barrier,
+                                                    max_over_ranks, world, tols.TOLS_FP64)
+        if serve_in:
+            subl["cfg5_serving_mixed"] = run_serving(tols, serve_in, args)
+        if args.pacf_lags > 0:
+            subl["pacf_ar100_n4M"] = run_pacf(tols, torch, cfg2_in[0], args)
+        if args.lsar_lags > 0:
+            ex = subl.get("pacf_ar100_n4M")
+            subl["lsar_ar100_n4M"] = run_lsar(tols, torch, cfg2_in[0], args,
+                                             ex["ms_per_sweep"] if ex and ex["lags"] == args.lsar_lags else None)
+    return finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, rank, ranks)
+
+
+def fft_pass_flops(kind, m, p, gram=False):
+    """Counted flops of one overlap-save float64 pass (N = 2,048, tiles of N - pad16(p + 1) rows): a product pass
+    runs one inverse and one forward real transform per tile (2 x 2.5 N log2 N); a Gram pass one forward transform
+    plus pad16(p + 1) (p + 1) multiply-adds of edge corrections per tile when that is at most 24,576, else two
+    forward transforms (window and row block)."""
+    N = 2048
+    pg = ((p + 1 + 15) // 16) * 16
+    tiles = math.ceil(m / (N - pg))
+    t = 2.5 * N * math.log2(N)
+    if gram:
+        return tiles * (t + 2.0 * pg * (p + 1)) if pg * (p + 1) <= 24576 else tiles * 2 * t
+    return tiles * 2 * t
+
+
+def finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, rank, ranks):
+    import numpy as np
+    n, p, tol = wl["n"], wl["p"], wl["tol"]
+    m = n - p
+    K = args.steps
+    r64, rmx = results["fp64"], results["mixed"]
+    value = whole_job_rate(world, K, rmx["total_ms"] / 1e3)
+    fp64_value = whole_job_rate(world, K, r64["total_ms"] / 1e3)
+
+    def per_launch(prof, key):
+        cnt, ms = prof[key]
+        return (ms / cnt if cnt else float("nan")), cnt
+
+    # dominant kernel of the FP64 step and its roofline: float64 FMA units bound the float64 passes on GB300
+    dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0 and k.startswith("pass_")),
+              key=lambda k: r64["prof"][k][1])
+    avg_ms, cnt = per_launch(r64["prof"], dom)
+    fft_used = r64["infos"][-1]["product_used"] == tols.TOLS_PRODUCT_FFT
+    gram = dom.endswith("gram")
+    if fft_used:
+        flops = fft_pass_flops("fft", m, p, gram)
+        kname = f"fft_pass_kernel<double> ({dom})"
+    else:
+        flops = (2.0 if gram else 4.0) * m * (p + 1 if gram else p)
+        kname = f"pass_kernel<double> ({dom})"
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    traffic = TRAFFIC_PER_ROW.get((kname.split(" ")[0], p, gram))
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                "traffic": traffic * n if traffic else None,
+                "traffic_source": (f"ncu dram__bytes_read+write of {kname.split(' ')[0]} at p = {p}, smaller n, "
+                                   f"{traffic:.2f} B per row of y scaled to n") if traffic else None,
+                "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt,
+                "product": "fft" if fft_used else "direct"}
+
+    def line_of(r):
+        i = r["infos"]
+        return {"ms_median": float(np.median(r["times"])), "p50_ms": float(np.percentile(r["times"], 50)),
+                "p99_ms": float(np.percentile(r["times"], 99)), "status": [x["status"] for x in i][-1],
+                "statuses": {"ok": sum(1 for x in i if x["status"] == 0),
+                             "not_converged": sum(1 for x in i if x["status"] == 1)},
+                "iters": i[-1]["iters"], "sweeps": i[-1]["sweeps"], "ne_ratio": i[-1]["ne_ratio"],
+                "rnorm": i[-1]["rnorm"], "precond_used": i[-1]["precond_used"],
+                "precision_used": i[-1]["precision_used"], "cond_est": i[-1]["cond_est"],
+                "kernel_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in r["prof"].items() if v[0]}}
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": rmx["total_ms"] / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic: seeded stationary AR series (see config)",
+           "config": headline_config(wl, world),
+           "precision_note": "mixed requests take the float64 route and run float-product correction sweeps only "
+                             "when kappa(X) u32 <= 1e-2; on this series kappa(X) is about 6e12, so they compute in "
+                             "float64 (precision_used) and their arithmetic is the FP64 request's",
+           "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": r64["total_ms"] / K, **line_of(r64)},
+           "mixed": {"value": value, "unit": "solves/s", "vs_fp64": value / fp64_value, **line_of(rmx)},
+           "roofline": roofline,
+           "matvec": matvec,
+           "order_sweep": sweep,
+           "e2e": {"value": whole_job_rate(world, K, e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * p},
+           "gpu_launches": int(r64["launches"] + rmx["launches"]),
+           "clocks": rmx["clocks"],
+           "sublines": subl}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rows = min(m, REF_ROWS)
+        ys = s.y[: rows + p]
+        solves, t0 = 0, time.perf_counter()
+        while solves < 3 and (solves == 0 or time.perf_counter() - t0 < 8.0):
+            ref = oracle.ols_qr(ys, p)
+            solves += 1
+        dt = (time.perf_counter() - t0) / solves
+        out["cpu_baseline"] = {"value": (rows / m) / dt, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": f"{solves} oracle QR solves of the first {rows} of the {m} rows; a solve of "
+                                         f"all rows costs m / {rows} times as much (dense QR is linear in the rows)"}
+        # the oracle recomputes ||r|| and ||X^T r|| of the returned phi on all rows (||X||_2 estimated from the
+        # first rows' QR: sqrt(m / rows) sigma_max, a stationary series)
+        norm2 = float(ref.sigma[0]) * math.sqrt(m / rows)
+        acc = {}
+        for name, r in (("mixed", rmx), ("fp64", r64)):
+            if name == "fp64" and np.array_equal(r64["phi"], rmx["phi"]):
+                acc["fp64"] = "identical phi to the mixed request"
+                continue
+            rn, g, ne = oracle.residual_check(s.y, p, r["phi"], norm2=norm2)
+            acc[name] = {"rnorm_oracle": rn, "rnorm_device": r["infos"][-1]["rnorm"],
+                         "ne_ratio_oracle": ne, "ne_ratio_device": r["infos"][-1]["ne_ratio"]}
+        acc["gate"] = ("graded against the oracle's QR on the first 2^20 samples of this series in "
+                       "tests/test_gpu_fullsize.py (residual no larger than the oracle's, ratio within 10x); at "
+                       "kappa(X) ~ 6e12 the oracle's own coefficients are not determined beyond ~1e-3")
+        out["accuracy"] = acc
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ranks.close()
+
+
+# DRAM bytes per row of y of the dominant kernel, from ncu (see profiles/): (kernel, p, gram pass) -> bytes / row
+TRAFFIC_PER_ROW = {}
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -723,17 +963,19 @@ def main():
         import torch
 
         import paper_2112_12994_gb300 as tols
-        print(json.dumps({"srht_only": True, **run_srht(tols, torch, make_series(wl).y, wl["p"], args)}), flush=True)
+        y = _gen_wl(("ar100_n4M", 0))
+        print(json.dumps({"srht_only": True, **run_srht(tols, torch, y, 100, args)}), flush=True)
     elif args.rh_only:
         import torch
 
         import paper_2112_12994_gb300 as tols
-        print(json.dumps({"rh_only": True, **run_rh(tols, torch, make_series(wl).y, args)}), flush=True)
+        print(json.dumps({"rh_only": True, **run_rh(tols, torch, _gen_wl(("ar100_n4M", 0)), args)}), flush=True)
     elif args.lsar_only:
         import torch
 
         import paper_2112_12994_gb300 as tols
-        print(json.dumps({"lsar_only": True, **run_lsar(tols, torch, make_series(wl).y, args, None)}), flush=True)
+        print(json.dumps({"lsar_only": True, **run_lsar(tols, torch, _gen_wl(("ar100_n4M", 0)), args, None)}),
+              flush=True)
     else:
         run_ours(args, wl)
 

@@ -437,20 +437,20 @@ int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
   const size_t head = 256;                                   // PclInfo
   const size_t fb_bytes = (sizeof(float) * (size_t)p * p + 255) / 256 * 256;
   size_t bytes = head + fb_bytes + sizeof(double) * PP;      // report, float copy, Gp
-  if (c) bytes += sizeof(double) * (3 * PP + (size_t)c * p + (size_t)slices * ntiles * 1024);
+  if (c) bytes += sizeof(double) * (4 * PP + (size_t)c * p + (size_t)slices * ntiles * 1024);
   RUN(ensure(ctx, ctx->pcl, bytes));
   char* base = (char*)ctx->pcl.p;
   PclInfo* d_info = (PclInfo*)base;
   float* fb = (float*)(base + head);
   double* Gp = (double*)(base + head + fb_bytes);
-  double* Rq[3] = {Gp + PP, Gp + 2 * PP, Gp + 3 * PP};
-  double* A = Gp + 4 * PP;
+  double* Rq[4] = {Gp + PP, Gp + 2 * PP, Gp + 3 * PP, Gp + 4 * PP};
+  double* A = Gp + 5 * PP;
   double* part = A + (size_t)c * p;
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(d_info, 0, sizeof(PclInfo), st));
   RUN(run_small(ctx, 10, [&] { return pcl_lambda(w.G, p, p, 0.0, 0, fb, d_info, st); }));
   bool ok = false, shifted = false, singular = false;
-  double cond = 0.0;
+  double cond = 0.0, g_shift = 0.0, g_tiny = (double)p * ueps;
   if (want) {
     RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, 0.0, nullptr, st); }));
     RUN(pcl_factor(ctx, Gp, P, p, (double)p * ueps, 0.0, d_info));
@@ -458,10 +458,11 @@ int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
     if (!ctx->h_pcl->nonfinite) {
       if (ctx->h_pcl->fail) {
         singular = true;
-        const double lambda = 10.0 * (double)p * ueps * ctx->h_pcl->dmax;
+        g_shift = 10.0 * (double)p * ueps * ctx->h_pcl->dmax;
+        g_tiny = 1e-3 * 10.0 * (double)p * ueps;
         CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
-        RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, lambda, nullptr, st); }));
-        RUN(pcl_factor(ctx, Gp, P, p, 1e-3 * 10.0 * (double)p * ueps, 0.0, d_info));
+        RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, g_shift, nullptr, st); }));
+        RUN(pcl_factor(ctx, Gp, P, p, g_tiny, 0.0, d_info));
         RUN(pcl_sync(ctx, d_info));
         shifted = !ctx->h_pcl->fail;
       }
@@ -479,32 +480,63 @@ int precond_large(tols_ctx* ctx, Work& w, int want, bool mixed) {
   int precond = ok ? 1 : 0;
   double kappa_est = cond;
   if (qr_ok && !nonfinite && (want == 2 || !trusted)) {
+    const double shift_rel = 11.0 * ((double)c * p + (double)p * (p + 1)) * 1.11e-16;
     CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
     RUN(run_small(ctx, 10, [&] { return pcl_gather(w.y64, w.m, p, c, A, st); }));
-    for (int s = 0; s < 3; ++s) {
-      const double shift_rel = s < 2 ? 11.0 * ((double)c * p + (double)p * (p + 1)) * 1.11e-16 : 0.0;
+    // stage s: Gram matrix of the current A (the sample, then Q1, Q2), its factor; A <- A R^{-1} after stages 0, 1
+    auto stage = [&](int s, bool shift) -> int {
       RUN(run_small(ctx, 10, [&] { return pcl_tall_gram(A, c, p, P, slices, part, st); }));
       RUN(run_small(ctx, 10, [&] { return pcl_gram_reduce(part, P, slices, p, Gp, st); }));
-      RUN(run_small(ctx, 10, [&] { return pcl_lambda(Gp, P, p, shift_rel, s == 0 ? 1 : -1, fb, d_info, st); }));
-      RUN(pcl_factor(ctx, Gp, P, p, s < 2 ? 0.0 : (double)p * 1.11e-16, s < 2 ? 1e-3 : 0.0, d_info));
+      RUN(run_small(ctx, 10, [&] {
+        return pcl_lambda(Gp, P, p, shift ? shift_rel : 0.0, s == 0 ? 1 : -1, fb, d_info, st);
+      }));
+      RUN(pcl_factor(ctx, Gp, P, p, shift ? 0.0 : (double)p * 1.11e-16, shift ? 1e-3 : 0.0, d_info));
       if (s < 2) {
         CK(cudaMemcpyAsync(Rq[s], Gp, sizeof(double) * PP, cudaMemcpyDeviceToDevice, st));
         RUN(run_small(ctx, 10, [&] { return pcl_trsm(A, c, p, Gp, P, st); }));
       }
-    }
-    RUN(pcl_sync(ctx, d_info));
-    if (!ctx->h_pcl->fail && !ctx->h_pcl->nonfinite) {
+      return TOLS_OK;
+    };
+    // R = R3 R2 R1, M = R^{-1} and its kappa estimate
+    auto finish = [&]() -> int {
       RUN(run_small(ctx, 10, [&] { return pcl_trmm(Rq[1], Rq[0], Rq[2], P, st); }));   // R2 R1
-      RUN(run_small(ctx, 10, [&] { return pcl_trmm(Gp, Rq[2], Rq[0], P, st); }));      // R3 R2 R1
-      RUN(run_small(ctx, 10, [&] { return pcl_inverse(Rq[0], P, p, w.M, d_info, st); }));
+      RUN(run_small(ctx, 10, [&] { return pcl_trmm(Gp, Rq[2], Rq[3], P, st); }));      // R3 R2 R1
+      RUN(run_small(ctx, 10, [&] { return pcl_inverse(Rq[3], P, p, w.M, d_info, st); }));
       RUN(run_small(ctx, 10, [&] { return pcl_estimate(w.M, p, 1, fb, d_info, st); }));
+      return pcl_sync(ctx, d_info);
+    };
+    RUN(stage(0, true));
+    RUN(stage(1, true));
+    RUN(stage(2, false));
+    RUN(pcl_sync(ctx, d_info));
+    bool qr_done = false, m_replaced = false;
+    if (!ctx->h_pcl->fail && !ctx->h_pcl->nonfinite) {
+      RUN(finish());
+      qr_done = m_replaced = true;
+    }
+    // kappa(sample) beyond about 1e14: the plain last stage gives an R whose inverse float64 cannot apply (errors
+    // of order kappa u). Shift the last stage too: R is then regularised at about 1e-13 sigma_max, LSQR resolves
+    // the well-determined part fast and the near-null directions (no better determined in float64) slowly.
+    if (!ctx->h_pcl->nonfinite && (!qr_done || ctx->h_pcl->cond * 1.11e-16 > 1e-2)) {
+      CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
+      RUN(stage(2, true));
       RUN(pcl_sync(ctx, d_info));
+      qr_done = !ctx->h_pcl->fail && !ctx->h_pcl->nonfinite;
+      if (qr_done) RUN(finish());
+    }
+    if (qr_done) {
       cond = ctx->h_pcl->cond;
-      // the sampled R is about sqrt(c / m) times the full one: ||A||_2 ||R^{-1}||_2 is kappa of the sample
+      // ||A||_2 ||R^{-1}||_2 estimates kappa of the sample, which tracks kappa(X)
       kappa_est = cond;
       precond = 2;
       trusted = false;
       shifted = false;
+    } else if (ok && m_replaced) {
+      // the QR did not complete: the Gram factor stays; its inverse is formed again (the QR's overwrote it)
+      CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
+      RUN(run_small(ctx, 10, [&] { return pcl_pad(w.G, p, Gp, P, g_shift, nullptr, st); }));
+      RUN(pcl_factor(ctx, Gp, P, p, g_tiny, 0.0, d_info));
+      RUN(run_small(ctx, 10, [&] { return pcl_inverse(Gp, P, p, w.M, d_info, st); }));
     }
     CK(cudaMemsetAsync(&d_info->fail, 0, sizeof(int), st));
   }
@@ -765,10 +797,12 @@ struct BatchPlan {
   int p_pad_max = 16, p_pad_max_x = 16;
 };
 
-// Partial-sum slots (and arrival units) of a batched series: one per tile of the direct kernel, or one per unit of
-// kBatchFftUnit tiles of the FFT kernel.
+// Partial-sum slots (and arrival units) of a batched series, enough for every kernel that may run a pass over it:
+// one per tile of the direct float64 kernel, or one per unit of kBatchFftUnit tiles of the FFT kernel, and one per
+// tile of the direct float kernel (the correction sweeps of a mixed series; its tiles can outnumber the FFT units).
 long long batch_units(long long m, int p, bool fx) {
-  return fx ? batch_fft_units(m, p) : (m + kTileD - 1) / kTileD;
+  const long long d = fx ? batch_fft_units(m, p) : (m + kTileD - 1) / kTileD;
+  return std::max(d, (m + kTileF - 1) / kTileF);
 }
 
 void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status, bool mixed,
@@ -905,6 +939,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.M32 = (float*)(w.Mt + pq + qr_scratch_doubles(p));
     w.Mt32 = w.M32 + pq;
     w.st = (DevState*)ctx->b_state.p + k;
+    w.f32_active = mixed ? d_done + 1 : nullptr;   // the batch's count of series in a float correction sweep
     w.tw64 = ctx->tw64;
     w.tw32 = ctx->tw32;
     if (B.fft[k]) {
@@ -962,9 +997,9 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   BatchArgs ag = a;
   ag.gram = 1;
   const int gx = B.tiles_x ? batch_fft_grid(ctx, B.p_pad_max_x) : 0;
-  // launches per float64 solver pass: the FFT pair (d spectra, FFT pass) and/or the direct float64 pass; a mixed
-  // batch adds the float pass of its correction sweeps
-  const int per_pass = (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0) + (mixed ? 1 : 0);
+  // launches per float64 solver pass: the FFT pair (d spectra, FFT pass) and/or the direct float64 pass; while some
+  // series of a mixed batch run a float correction sweep, the float pass joins them
+  const int per_pass = (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0);
   // the Gram pass (float64 products for every series); the FFT series' one also forms their window spectra
   ctx->launch_total += (B.tiles_x ? 1 : 0) + (B.tiles_d ? 1 : 0);
   if (B.tiles_x) CK(launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream));
@@ -975,11 +1010,10 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
 
   // iterations: a burst of batched passes captured once into a CUDA graph, replayed until all series are done
   const int burst = 4;
-  cudaGraphExec_t exec = nullptr;
-  auto enqueue_burst = [&]() -> int {
+  auto enqueue_burst = [&](bool with_float) -> int {
     for (int k = 0; k < burst; ++k) {
-      ctx->launch_total += per_pass;
-      if (mixed) CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
+      ctx->launch_total += per_pass + (with_float ? 1 : 0);
+      if (with_float) CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
       if (B.tiles_x) {
         CK(launch_batch_dspec(d_series, cnt, ctx->stream));
         CK(launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream));
@@ -988,40 +1022,47 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     }
     return TOLS_OK;
   };
+  // two captured bursts: float64 passes only, and with the float pass (mixed batches)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
   if (!ctx->prof) {
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    const long long before = ctx->launch_total;
-    rc = enqueue_burst();
-    ctx->launch_total = before;
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-    if (rc) return rc;
-    if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "capture of the batched burst", e);
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "instantiate the batched burst", e);
+    for (int f = 0; f < (mixed ? 2 : 1); ++f) {
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      const long long before = ctx->launch_total;
+      rc = enqueue_burst(f == 1);
+      ctx->launch_total = before;
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (rc) return rc;
+      if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "capture of the batched burst", e);
+      e = cudaGraphInstantiate(&exec[f], graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(ctx, TOLS_ERR_CUDA, "instantiate the batched burst", e);
+    }
   }
-  unsigned int* h_done = (unsigned int*)ctx->h_worklog;  // pinned, reused as a 4-byte landing slot
+  unsigned int* h_done = (unsigned int*)ctx->h_worklog;  // pinned, reused as landing slots: done, in float sweeps
   int max_iter_all = 0;
   for (int k = 0; k < cnt; ++k) max_iter_all = std::max(max_iter_all, states[k].max_iter);
   const long long max_rounds = ((long long)(max_iter_all + 4) * (max_sweeps + 2) * 2) / burst + 16;
   int out = TOLS_OK;
+  bool with_float = false;
   for (long long round = 0;; ++round) {
-    if (exec) {
-      ctx->launch_total += burst * per_pass;
-      cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+    if (exec[with_float ? 1 : 0]) {
+      ctx->launch_total += burst * (per_pass + (with_float ? 1 : 0));
+      cudaError_t e = cudaGraphLaunch(exec[with_float ? 1 : 0], ctx->stream);
       if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "cudaGraphLaunch", e); break; }
-    } else if ((out = enqueue_burst())) {
+    } else if ((out = enqueue_burst(with_float))) {
       break;
     }
-    cudaError_t e = cudaMemcpyAsync(h_done, d_done, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(h_done, d_done, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "batched poll", e); break; }
     if ((out = flush_profile(ctx))) break;
-    if (*h_done >= (unsigned)cnt) break;
+    if (h_done[0] >= (unsigned)cnt) break;
     if (round > max_rounds) { out = fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "batched solve did not finish"); break; }
+    with_float = mixed && h_done[1] > 0;
   }
-  if (exec) cudaGraphExecDestroy(exec);
+  for (auto x : exec)
+    if (x) cudaGraphExecDestroy(x);
   if (out) return out;
   RUN(run_small(ctx, 12, [&] { return launch_finish_batch(d_series, cnt, ctx->stream); }));
   CK(cudaMemcpyAsync(states.data(), ctx->b_state.p, sizeof(DevState) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1084,6 +1125,27 @@ int batch_solve_all(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::ve
       memcpy(phi_host.data() + B.off_phi[k], sphi.data() + S.off_phi[j], sizeof(double) * B.p[k]);
       prec_used[k] = TOLS_FP64;
     }
+  }
+  // series whose sampled rows are numerically rank deficient in float64 (kappa of the sample beyond about 1e14):
+  // the one-CTA preconditioner has no regularised form, so they are solved one by one through the multi-CTA one
+  // (the last stage of its shifted Cholesky QR is shifted too). The order must be one that path serves.
+  for (int k = 0; k < cnt; ++k) {
+    const DevState s = states[k];
+    if (s.status == TOLS_OK || s.status == TOLS_ERR_NONFINITE || s.precond != 2 || s.kappa_est * 1.11e-16 <= 1e-2 ||
+        B.p[k] < kPclMinP)
+      continue;
+    const double* y = B.y_dev.empty() ? (const double*)ctx->b_y64.p + B.off_y[k] : B.y_dev[k];
+    if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)B.p[k] + 64)))) return rc;
+    double* d_phi = (double*)ctx->scratch.p;
+    double rn = 0.0;
+    rc = solve_device_impl(ctx, y, B.n[k], B.p[k], tol, d_phi, &rn, nullptr, nullptr, TOLS_FP64);
+    if (rc < 0) return rc;
+    DevState s2 = *ctx->h_state;
+    s2.total_iter += s.total_iter;
+    s2.sweeps += s.sweeps;
+    states[k] = s2;
+    CK(cudaMemcpy(phi_host.data() + B.off_phi[k], d_phi, sizeof(double) * B.p[k], cudaMemcpyDeviceToHost));
+    prec_used[k] = TOLS_FP64;
   }
   return TOLS_OK;
 }
@@ -1265,6 +1327,7 @@ struct tols_server {
   std::vector<double> h_phi;
   std::chrono::steady_clock::time_point t0;
   long long submitted = 0, completed = 0;
+  bool float_due = false;           // the last step left a mixed request in a float correction sweep
 };
 
 namespace {
@@ -1390,12 +1453,11 @@ int server_round(tols_server* srv) {
   RUN(upload_table(srv, all, a, pmax));
   const int gf = batch_grid(ctx, 0, pmax), gd = batch_grid(ctx, 1, pmax);
   const int gx = a.tiles_x ? batch_fft_grid(ctx, pmax) : 0;
-  bool any_mixed = false;
-  for (const SrvActive& A : srv->active) any_mixed |= A.req.mixed;
-  // float passes serve the mixed requests' iterations, double passes the float64 requests' iterations and every
-  // float64 check: interleaving them lets both kinds progress in every burst
+  // float passes serve the correction sweeps of mixed requests (launched while the last step left some request in
+  // one), double passes every float64 iteration and check: interleaving them lets both kinds progress in a burst
+  const bool any_float = srv->float_due;
   for (int k = 0; k < srv->burst; ++k) {
-    if (any_mixed) {
+    if (any_float) {
       ctx->launch_total++;
       CK(launch_batch_pass<float>(a, gf, pmax, ctx->stream));
     }
@@ -1422,7 +1484,12 @@ int server_round(tols_server* srv) {
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   RUN(flush_profile(ctx));
-  // retire the finished requests
+  // retire the finished requests; note whether a float correction sweep is under way
+  srv->float_due = false;
+  for (int k = 0; k < cnt; ++k) {
+    const DevState& s = srv->h_states[k];
+    if (!(s.done || s.phase == PH_DONE) && s.mixed && s.phase == PH_NECORR) srv->float_due = true;
+  }
   std::vector<SrvActive> keep;
   keep.reserve(cnt);
   for (int k = 0; k < cnt; ++k) {

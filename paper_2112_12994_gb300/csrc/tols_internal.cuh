@@ -117,6 +117,7 @@ struct Work {
   void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
   void* wspec64;          // the same for the float64 FFT tiles
   void* dspec64;          // (batched float64 FFT series) doubled spectrum of the lag-reversed d, N/2 + 1 entries
+  unsigned int* f32_active;  // (batches, nullable) count of the batch's series in a float correction sweep
 };
 
 // Arguments of a pass kernel (passed by value).

@@ -286,6 +286,7 @@ __device__ void start_necorr(const Work& w, DevState* st, double* scratch) {
     st->est_best = 1e300;
     st->iter_best = 0;
     st->phase = PH_NECORR;
+    if (w.f32_active) atomicAdd(w.f32_active, 1u);
   }
   __syncthreads();
 }
@@ -429,6 +430,7 @@ __device__ void tail_necorr(const Work& w, DevState* st, const double* tk, doubl
   }
   __syncthreads();
   if (stop) {
+    if (threadIdx.x == 0 && w.f32_active) atomicSub(w.f32_active, 1u);
     apply_M_exact(w, st->precond, 1, w.z, tmp);
     __syncthreads();
     for (int j = threadIdx.x; j < p; j += blockDim.x) w.phi[j] += tmp[j];

@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--only", default="", help="kernel-only: comma list of direct_fp64,direct_fp32,fft_fp64,fft_fp32")
     ap.add_argument("--p", type=int, default=0, help="kernel-only: override the order p")
+    ap.add_argument("--n", type=int, default=0, help="kernel-only: override the series length n")
     ap.add_argument("--batch-series", type=int, default=4096,
                     help="series in the batched run (n log-uniform in [1e4, 1e6], p uniform in [5, 200]); 0 = skip")
     ap.add_argument("--gate-sample", type=int, default=64,
@@ -684,6 +685,8 @@ def run_kernel_only(args, wl):
     import paper_2112_12994_gb300 as tols
     if args.p:
         wl = dict(wl, p=args.p)
+    if args.n:
+        wl = dict(wl, n=args.n)
     s = make_series(wl)
     n, p = wl["n"], wl["p"]
     m = n - p

@@ -570,3 +570,279 @@ __global__ void __launch_bounds__(kThreads) batch_dspec_kernel(const BatchSeries
   V* out = reinterpret_cast<V*>(w.dspec64);
   for (int f = threadIdx.x; f <= M; f += kThreads) out[f] = sm.D[f];
 }
+
+// ------------------------------------------------------------------------------------------------------------
+// Register-blocked float product pass (N = 4,096, M = 2,048; the float solver and step passes with lags or not,
+// not the Gram pass). The same arithmetic as fft_pass_kernel<float>, arranged so that every pointwise step works on
+// registers: thread j holds the points j + 256 r (r < 8) of a 2,048-point transform. The Stockham radix-8, 8, 8, 4
+// transform reads its first stage's input from, and leaves its last stage's output in, exactly that set, so the
+// spectral products before the inverse transform, the rows of u between the two transforms and the split after the
+// forward transform need no shared-memory pass; three exchanges per transform remain. The split and merge pair bin
+// f with bin M - f: lanes 0-15 of warp w take j = 16 w + l and lanes 16-31 the partners 256 - j (0 pairs with 128),
+// so the pair sits on lanes l and l ^ 16 of one warp (a shuffle). The CTA's spectral sum W . conj(U) is kept per
+// thread in float over at most kFft32Flush tiles and then added to the float64 sum in shared memory.
+constexpr int kFft32Flush = 16;
+
+__device__ __forceinline__ int fft32_j(int tid) {
+  const int w = tid >> 5, l = tid & 31;
+  const int a = 16 * w + (l & 15);
+  return l < 16 ? a : (a == 0 ? 128 : 256 - a);
+}
+
+// pv[q] = the value of bin M - f at this thread's bin f = j + 256 q (bin M itself, the partner of bin 0, is the
+// caller's business where it differs from bin 0).
+__device__ __forceinline__ void fft32_partner(const float2* v, float2* pv, int j) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    pv[q].x = __shfl_xor_sync(0xffffffffu, v[7 - q].x, 16);
+    pv[q].y = __shfl_xor_sync(0xffffffffu, v[7 - q].y, 16);
+  }
+  if (j == 128) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pv[q] = v[7 - q];
+  } else if (j == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pv[q] = v[(8 - q) & 7];
+  }
+}
+
+// One Stockham radix-8 stage between shared buffers for the thread's butterfly j (stride 256): in[j + 256 r],
+// twiddles tw[ts r k] (k = j mod Ls), out[g Ln + k + Ls q].
+template <bool INV, int Ls, int TS>
+__device__ __forceinline__ void fft32_stage8(float2* z, int j, const float2* in, float2* out, const float2* tw) {
+  constexpr int Ln = Ls * 8;
+  const int k = j & (Ls - 1), g = j / Ls;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) z[r] = in[pix(j + 256 * r)];
+  // twiddles w^r, r = 1..7, from three table entries (w, w^2, w^4) and four products: each is within a few ulp
+  float2 t[8];
+  t[1] = tw[TS * k];
+  t[2] = tw[2 * TS * k];
+  t[4] = tw[4 * TS * k];
+  if (INV) {
+    t[1].y = -t[1].y;
+    t[2].y = -t[2].y;
+    t[4].y = -t[4].y;
+  }
+  t[3] = cmul(t[1], t[2]);
+  t[5] = cmul(t[4], t[1]);
+  t[6] = cmul(t[4], t[2]);
+  t[7] = cmul(t[4], t[3]);
+#pragma unroll
+  for (int r = 1; r < 8; ++r) z[r] = cmul(z[r], t[r]);
+  dft_small<float2, float, 8>(z, INV);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[pix(g * Ln + k + Ls * q)] = z[q];
+}
+
+// 2,048-point complex transform of the thread-held points z[r] = x[j + 256 r]; on return z[r] = X[j + 256 r].
+// Stages radix 8 (Ls 1, from registers), 8 (Ls 8), 8 (Ls 64), 4 (Ls 512, into registers); bufA, bufB carry the
+// three exchanges. The caller separates a later write of bufA from this call's last reads by a barrier.
+template <bool INV>
+__device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float2* bufB, const float2* tw) {
+  dft_small<float2, float, 8>(z, INV);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) bufA[pix(8 * j + q)] = z[q];
+  __syncthreads();
+  fft32_stage8<INV, 8, 64>(z, j, bufA, bufB, tw);
+  __syncthreads();
+  fft32_stage8<INV, 64, 8>(z, j, bufB, bufA, tw);
+  __syncthreads();
+  float2 a[4], b[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    a[r] = bufA[pix(j + 512 * r)];
+    b[r] = bufA[pix(j + 256 + 512 * r)];
+  }
+  // twiddles of butterfly j + 256: those of j times exp(-+2 pi i r / 8)
+  const float h = 0.70710678118654752f;
+#pragma unroll
+  for (int r = 1; r < 4; ++r) {
+    float2 ta = tw[2 * r * j];
+    if (INV) ta.y = -ta.y;
+    const float2 e8 = r == 1 ? make_float2(h, INV ? h : -h) : r == 2 ? make_float2(0.f, INV ? 1.f : -1.f)
+                                                                     : make_float2(-h, INV ? h : -h);
+    a[r] = cmul(a[r], ta);
+    b[r] = cmul(b[r], cmul(ta, e8));
+  }
+  dft_small<float2, float, 4>(a, INV);
+  dft_small<float2, float, 4>(b, INV);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    z[2 * q] = a[q];
+    z[2 * q + 1] = b[q];
+  }
+}
+
+// w^f for f = j + 256 q (N = 4,096): w^j exp(-i pi q / 8), one table entry and a product with a constant.
+__device__ __forceinline__ float2 fft32_twf(float2 base, int q) {
+  const float cq[8] = {1.0f, 0.92387953251128676f, 0.70710678118654752f, 0.38268343236508977f,
+                       0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128676f};
+  const float sq[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128676f,
+                       1.0f, 0.92387953251128676f, 0.70710678118654752f, 0.38268343236508977f};
+  return q == 0 ? base : cmul(base, make_float2(cq[q], -sq[q]));
+}
+
+// 2Z[f] of the packed input of an inverse transform from the doubled half spectrum V at bins f and M - f (merge2).
+__device__ __forceinline__ float2 fft32_merge(float2 vf, float2 vmf, float2 twf) {
+  const float ax = vf.x + vmf.x, ay = vf.y - vmf.y;
+  const float bx = vf.x - vmf.x, by = vf.y + vmf.y;
+  const float cbx = twf.x * bx + twf.y * by;
+  const float cby = twf.x * by - twf.y * bx;
+  return make_float2(ax - cby, ay + cbx);
+}
+// 2X[f] (and, for f = 0, 2X[M] in xm) of a real sequence from its packed transform Z at bins f and M - f (split2).
+__device__ __forceinline__ float2 fft32_split(float2 zf, float2 zmf, float2 twf, float2* xm) {
+  const float ax = zf.x + zmf.x, ay = zf.y - zmf.y;
+  const float bx = zf.x - zmf.x, by = zf.y + zmf.y;
+  const float tbx = twf.x * bx - twf.y * by;
+  const float tby = twf.x * by + twf.y * bx;
+  if (xm) *xm = make_float2(ax - tby, -(ay + tbx));
+  return make_float2(ax + tby, ay - tbx);
+}
+
+__global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float> a) {
+  using V = float2;
+  constexpr int N = FftCfg<float>::N;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_last;
+  int tail = a.tail;
+  const float* u_old = a.u_old;
+  float* u_new = a.u_new;
+  double coef = a.coef_host;
+  if (a.check_done) {
+    if (!select_phase<float>(a.w.st, a.y, a.p, a.w, tail, u_old, u_new, coef)) return;
+  } else if (a.coef_dev) {
+    coef = *a.coef_dev;
+  }
+  const int p_pad = a.p_pad, nlag = a.nlag;
+  const int L = N - p_pad;
+  const V* tw = reinterpret_cast<const V*>(a.w.tw32);
+  const V* wspec = reinterpret_cast<const V*>(a.w.wspec32);
+  FftSmem<float> sm(smem_raw, p_pad);
+  const int tid = threadIdx.x;
+  const int j = fft32_j(tid);
+  for (int k = tid; k < p_pad + 16; k += kThreads) sm.tacc[k] = 0.0;
+  for (int f = tid; f <= M; f += kThreads) sm.S[f] = make_double2(0.0, 0.0);
+  const long long ntiles = (a.m + L - 1) / L;
+  const bool lags = nlag > 0;
+  double n2 = 0.0;
+  if (blockIdx.x < ntiles) {
+    fft_d_spectrum<float>(sm, a.d, a.d_scale, a.p, tw);      // sm.D, read per tile; ends with a barrier
+    V Sq[8], Sm = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Sq[q] = make_float2(0.f, 0.f);
+    const float sc = 1.0f / (8.0f * M);
+    const float c = (float)coef;
+    int pending = 0;
+    auto flush = [&]() {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        double2& s = sm.S[j + 256 * q];
+        s.x += (double)Sq[q].x;
+        s.y += (double)Sq[q].y;
+        Sq[q] = make_float2(0.f, 0.f);
+      }
+      if (j == 0) {
+        sm.S[M].x += (double)Sm.x;
+        sm.S[M].y += (double)Sm.y;
+        Sm = make_float2(0.f, 0.f);
+      }
+      pending = 0;
+    };
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const long long i0 = tile * L;
+      const int rows = (int)min((long long)L, a.m - i0);
+      const V* wt = wspec + (size_t)tile * (M + 1);
+      {
+        // ask L2 for the next tile's window spectrum and rows of u_old (one 128-byte line per thread) while this
+        // tile computes: their first use then waits on L2, not on HBM
+        const long long nt = tile + gridDim.x;
+        if (nt < ntiles) {
+          const char* pw = reinterpret_cast<const char*>(wspec + (size_t)nt * (M + 1));
+          const int wlines = (int)((sizeof(V) * (M + 1) + 127) / 128);
+          if (tid < wlines) asm volatile("prefetch.global.L2 [%0];" ::"l"(pw + 128 * tid));
+          if (u_old) {
+            const long long r0 = nt * L;
+            const int rn = (int)min((long long)L, a.m - r0);
+            const char* pu = reinterpret_cast<const char*>(u_old + r0);
+            const int ulines = (int)((sizeof(float) * rn + 127) / 128);
+            const int t2 = tid - wlines;
+            if (t2 >= 0 && t2 < ulines) asm volatile("prefetch.global.L2 [%0];" ::"l"(pu + 128 * t2));
+          }
+        }
+      }
+      // X d = IRFFT(W . conj(D)) on the tile's rows (W read again for the split: L2 holds it; fewer registers)
+      V z[8], pv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = cmulc(wt[j + 256 * q], sm.D[j + 256 * q]);
+      fft32_partner(z, pv, j);
+      if (j == 0) pv[0] = cmulc(wt[M], sm.D[M]);      // the partner of bin 0 is bin M
+      const V twj = tw[j];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
+      fft32_2048<true>(z, j, sm.A, sm.B, tw);
+      // rows 2i, 2i + 1 of u_old for the thread's points i = j + 256 r (tile offsets are even: L is)
+      V uo[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int r0 = 2 * (j + 256 * r);
+        uo[r] = make_float2(0.f, 0.f);
+        if (u_old) {
+          if (r0 + 1 < rows) uo[r] = *reinterpret_cast<const V*>(u_old + i0 + r0);
+          else if (r0 < rows) uo[r].x = u_old[i0 + r0];
+        }
+      }
+      // u = X d - c u_old on the tile's rows, zero elsewhere; u_new stored
+      float nn = 0.f;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int r0 = 2 * (j + 256 * r);
+        float u0 = 0.f, u1 = 0.f;
+        if (r0 < rows) u0 = u_old ? fmaf(-c, uo[r].x, z[r].x * sc) : z[r].x * sc;
+        if (r0 + 1 < rows) u1 = u_old ? fmaf(-c, uo[r].y, z[r].y * sc) : z[r].y * sc;
+        if (u_new) {
+          if (r0 + 1 < rows) *reinterpret_cast<V*>(u_new + i0 + r0) = make_float2(u0, u1);
+          else if (r0 < rows) u_new[i0 + r0] = u0;
+        }
+        nn = fmaf(u0, u0, fmaf(u1, u1, nn));
+        z[r] = make_float2(u0, u1);
+      }
+      n2 += (double)nn;
+      if (!lags) {
+        __syncthreads();        // the next tile's first stage rewrites sm.A, read by this tile's last stage
+        continue;
+      }
+      // S += W . conj(U), U the doubled half spectrum of u
+      fft32_2048<false>(z, j, sm.B, sm.A, tw);
+      fft32_partner(z, pv, j);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        V xm;
+        const V x = fft32_split(z[q], pv[q], fft32_twf(twj, q), (q == 0 && j == 0) ? &xm : nullptr);
+        const V t = cmulc(wt[j + 256 * q], x);
+        Sq[q].x += t.x;
+        Sq[q].y += t.y;
+        if (q == 0 && j == 0) {
+          const V tm = cmulc(wt[M], xm);
+          Sm.x += tm.x;
+          Sm.y += tm.y;
+        }
+      }
+      if (++pending == kFft32Flush) flush();
+    }
+    flush();
+  }
+  __syncthreads();
+  if (blockIdx.x < ntiles && lags) fft_finish_lags<float>(sm, nlag, tw);
+  __syncthreads();
+  const double n2_cta = block_sum(n2, sm.scratch);
+  for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
+  if (tid == 0) a.w.part_n2[blockIdx.x] = n2_cta;
+  if (!arrive(a.w, blockIdx.x, gridDim.x, nlag, p_pad, sm.tacc, sm.scratch, &s_last)) return;
+  const double n2_all = sm.scratch[8];
+  __syncthreads();
+  if (tid == 0 && a.worklog) a.worklog[a.work_slot] = 1 + tail;
+  run_tail<float>(tail, a.w, a.gram, nlag, sm.tacc, n2_all, sm.scratch, a.out_t, a.out_n2);
+}

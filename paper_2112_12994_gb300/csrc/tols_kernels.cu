@@ -888,6 +888,16 @@ cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
   const long long ntiles = (a.m + rows_per_tile - 1) / rows_per_tile;
   int g = (int)lmin((long long)grid, ntiles);
   if (g < 1) g = 1;
+  if constexpr (sizeof(T) == 4) {
+    // float product passes take the register-blocked kernel (it moves u two rows at a time: 8-byte aligned u)
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.u_old) | reinterpret_cast<uintptr_t>(a.u_new)) & 7) == 0;
+    if (a.fft && !a.gram && aligned) {
+      e = smem_opt_in((const void*)fft32_pass_kernel, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      fft32_pass_kernel<<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (a.fft) fft_pass_kernel<T><<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
   else pass_kernel<T><<<g, kThreads, pass_smem<T>(a.p_pad), s>>>(a);
   return cudaGetLastError();

@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ar500_n64M")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sublines", action="store_true", help="headline only (no cfg 1/2/4/5 lines, sweep, PACF)")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="the headline solves alone (no matvec, sweep, end-to-end, sub-lines, CPU baseline): the "
+                         "launch-list profiling command")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused product pass (toeplitz_ols_gk_pass), float64 then float32")
     ap.add_argument("--reps", type=int, default=5)
@@ -750,7 +753,7 @@ def run_ours(args, wl):
 
     world, rank, local = dist()
     from synthetic import batch_shapes
-    sub = not args.no_sublines
+    sub = not (args.no_sublines or args.only_headline)
     # inputs of the sub-lines, generated in a spawn pool before any CUDA call
     batch_in = serve_in = cfg2_in = None
     if sub and args.batch_series > 0:
@@ -798,6 +801,15 @@ def run_ours(args, wl):
         results[name] = dict(times=times, infos=infos, prof=prof, launches=launches, phi=d_phi.cpu().numpy().copy(),
                              total_ms=max_over_ranks(sum(times)), clocks=clk, ctx=ctx)
 
+    if args.only_headline:
+        for r in results.values():
+            r["ctx"].close()
+        if rank == 0:
+            print(json.dumps({"only_headline": True, "fp64_ms": results["fp64"]["times"],
+                              "mixed_ms": results["mixed"]["times"],
+                              "kernel_ms": {k: v for k, v in results["fp64"]["prof"].items() if v[0]}}), flush=True)
+        ranks.close()
+        return None
     # end to end: pinned host series in, phi out, through toeplitz_ols_solve (the mixed request)
     pinned = torch.empty(n, dtype=torch.float64, pin_memory=True)
     pinned.copy_(torch.from_numpy(s.y))
@@ -950,7 +962,7 @@ def finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, 
 
 
 # DRAM bytes per row of y of the dominant kernel, from ncu (see profiles/): (kernel, p, gram pass) -> bytes / row
-TRAFFIC_PER_ROW = {}
+TRAFFIC_PER_ROW = {("fft_pass_kernel<double>", 500, False): 25.15}
 
 
 def main():

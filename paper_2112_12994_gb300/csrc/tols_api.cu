@@ -51,7 +51,7 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, b_spec, lsar, pcl;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, sacc32, b_spec, lsar, pcl;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -234,8 +234,13 @@ int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
 int fft_spectra(tols_ctx* ctx, Work& w, int is_double, const void* y, long long n, long long m, int p_pad, bool form) {
   DevBuf& b = is_double ? ctx->spec64 : ctx->spec32;
   RUN(ensure(ctx, b, fft_spectra_bytes(is_double, m, p_pad)));
-  if (is_double) w.wspec64 = b.p;
-  else w.wspec32 = b.p;
+  if (is_double) {
+    w.wspec64 = b.p;
+  } else {
+    w.wspec32 = b.p;
+    RUN(ensure(ctx, ctx->sacc32, fft32_sum_bytes()));
+    w.sacc32 = ctx->sacc32.p;
+  }
   if (!form) return TOLS_OK;
   return run_small(ctx, 12, [&] {
     return launch_spectra(is_double, y, n, m, p_pad, b.p, is_double ? w.tw64 : w.tw32,
@@ -655,6 +660,7 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
     CK(cudaStreamSynchronize(ctx->stream));
     RUN(flush_profile(ctx));
     const DevState& cur = *ctx->h_state;
+    if (cur.dev_error) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "a kernel's wait on its bulk copies gave up");
     if (cur.done || cur.phase == PH_DONE) break;
     if (launched > max_launch) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "solver did not reach a final state");
     // float passes are due while a mixed solve runs a correction sweep
@@ -1646,7 +1652,7 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
                     &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
-                    &ctx->spec64, &ctx->b_spec, &ctx->lsar, &ctx->pcl};
+                    &ctx->spec64, &ctx->sacc32, &ctx->b_spec, &ctx->lsar, &ctx->pcl};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
@@ -2198,6 +2204,7 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
   if ((rc = ensure(ctx, ctx->scratch, sizeof(double) * (2 * (size_t)p + 64)))) return rc;
   double* d_n2 = (double*)ctx->scratch.p;
   const int pp = pad_p(p);
+  CK(cudaMemsetAsync(&w.st->dev_error, 0, sizeof(int), ctx->stream));
   if (precision == TOLS_FP64) {
     PassArgs<double> a = base_args<double>(w, (const double*)d_y, n, p, pp);
     a.d = d_v;
@@ -2226,12 +2233,16 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     if (a.fft) {
       RUN(fft_spectra(ctx, w, 0, d_y, n, n - p, pp, true));
       a.w.wspec32 = w.wspec32;
+      a.w.sacc32 = w.sacc32;
     }
     RUN(run_pass<float>(ctx, a, pass_grid_for(ctx, 0, pp, a.fft)));
   }
   double h = 0.0;
+  int derr = 0;
   CK(cudaMemcpyAsync(&h, d_n2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&derr, &w.st->dev_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (derr) return fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "a kernel's wait on its bulk copies gave up");
   if (unorm2) *unorm2 = h;
   return TOLS_OK;
 }

@@ -24,14 +24,18 @@ __device__ __forceinline__ int pix(int i) { return i + (i >> 3); }
 
 template <typename T>
 struct FftCfg;
+// N: real FFT length per tile. WS: entries per tile of the window-spectrum array (bins 0 .. N/2; the float
+// tiles are padded to N/2 + 2 entries so that every tile starts on a 16-byte boundary, as bulk copies require).
 template <>
 struct FftCfg<float> {
   static constexpr int N = 4096;
+  static constexpr int WS = N / 2 + 2;
   using V = float2;
 };
 template <>
 struct FftCfg<double> {
   static constexpr int N = 2048;
+  static constexpr int WS = N / 2 + 1;
   using V = double2;
 };
 
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   double n2 = 0.0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    V* wt = wspec + (size_t)tile * (M + 1);
+    V* wt = wspec + (size_t)tile * FftCfg<T>::WS;
     if (a.gram) fft_gram_tile<T>(sm, a.y, a.n, a.m, L, p_pad, nlag, tile * L, tw, wt, corr);
     else n2 += fft_tile<T>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt, nlag > 0);
   }
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) spectrum_kernel(const T* __restrict_
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
     fft_window<T>(sm, y, n, tile * L, tw);
-    V* wt = out + (size_t)tile * (M + 1);
+    V* wt = out + (size_t)tile * FftCfg<T>::WS;
     for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
       V xf, xm;
       split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
     const long long t1 = lmin((unit + 1) * kBatchFftUnit, ntiles);
     for (long long t = unit * kBatchFftUnit; t < t1; ++t) {
       __syncthreads();
-      V* wt = reinterpret_cast<V*>(w.wspec64) + (size_t)t * (M + 1);
+      V* wt = reinterpret_cast<V*>(w.wspec64) + (size_t)t * FftCfg<T>::WS;
       if (gram) fft_gram_tile<T>(sm, w.y64, w.n, w.m, L, pg, nlag, t * L, tw, wt, corr);
       else n2 += fft_tile<T>(sm, w.m, L, u_old, u_new, coef, t * L, tw, wt, true);
     }
@@ -572,15 +576,21 @@ __global__ void __launch_bounds__(kThreads) batch_dspec_kernel(const BatchSeries
 }
 
 // ------------------------------------------------------------------------------------------------------------
-// Register-blocked float product pass (N = 4,096, M = 2,048; the float solver and step passes with lags or not,
-// not the Gram pass). The same arithmetic as fft_pass_kernel<float>, arranged so that every pointwise step works on
+// Register-blocked float product pass (N = 4,096, M = 2,048; the float solver and step passes with X^T u, not the
+// Gram pass). The same arithmetic as fft_pass_kernel<float>, arranged so that every pointwise step works on
 // registers: thread j holds the points j + 256 r (r < 8) of a 2,048-point transform. The Stockham radix-8, 8, 8, 4
 // transform reads its first stage's input from, and leaves its last stage's output in, exactly that set, so the
 // spectral products before the inverse transform, the rows of u between the two transforms and the split after the
 // forward transform need no shared-memory pass; three exchanges per transform remain. The split and merge pair bin
 // f with bin M - f: lanes 0-15 of warp w take j = 16 w + l and lanes 16-31 the partners 256 - j (0 pairs with 128),
-// so the pair sits on lanes l and l ^ 16 of one warp (a shuffle). The CTA's spectral sum W . conj(U) is kept per
-// thread in float over at most kFft32Flush tiles and then added to the float64 sum in shared memory.
+// so the pair sits on lanes l and l ^ 16 of one warp (a shuffle).
+//
+// A tile's inputs from HBM — its window spectrum (16,400 bytes) and its rows of u_old — arrive by bulk copies
+// (cp.async.bulk, completion counted on an mbarrier) issued one tile ahead by thread 0: the spectrum into one of two
+// shared buffers while the previous tile still reads the other, u_old into one buffer as soon as the previous
+// tile's rows have been read. No thread waits on a global load of the main loop. The CTA's spectral sum
+// W . conj(U) is kept per thread in float over at most kFft32Flush tiles and then added to the CTA's float64 sum in
+// global memory (each thread owns its bins: no atomics); the CTA transforms its sum back once, at its end.
 constexpr int kFft32Flush = 16;
 
 __device__ __forceinline__ int fft32_j(int tid) {
@@ -638,12 +648,16 @@ __device__ __forceinline__ void fft32_stage8(float2* z, int j, const float2* in,
 // 2,048-point complex transform of the thread-held points z[r] = x[j + 256 r]; on return z[r] = X[j + 256 r].
 // Stages radix 8 (Ls 1, from registers), 8 (Ls 8), 8 (Ls 64), 4 (Ls 512, into registers); bufA, bufB carry the
 // three exchanges. The caller separates a later write of bufA from this call's last reads by a barrier.
-template <bool INV>
-__device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float2* bufB, const float2* tw) {
+// after_first_sync() runs in every thread right after the first barrier (every thread has then left the code
+// before this call).
+template <bool INV, typename F>
+__device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float2* bufB, const float2* tw,
+                                           F&& after_first_sync) {
   dft_small<float2, float, 8>(z, INV);
 #pragma unroll
   for (int q = 0; q < 8; ++q) bufA[pix(8 * j + q)] = z[q];
   __syncthreads();
+  after_first_sync();
   fft32_stage8<INV, 8, 64>(z, j, bufA, bufB, tw);
   __syncthreads();
   fft32_stage8<INV, 64, 8>(z, j, bufB, bufA, tw);
@@ -701,10 +715,72 @@ __device__ __forceinline__ float2 fft32_split(float2 zf, float2 zmf, float2 twf,
   return make_float2(ax + tby, ay - tbx);
 }
 
+// mbarrier and bulk-copy primitives (PTX ISA: mbarrier, cp.async.bulk; sm_90 and later).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// One arrival on bar announcing `bytes` of transfer, then the copy global -> shared that completes them. dst, src
+// 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Wait for the phase of parity `parity` of bar to complete, polling at most kMbarPolls times (each poll suspends
+// for up to about a microsecond); false if it gave up.
+constexpr int kMbarPolls = 1 << 21;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int i = 0; i < kMbarPolls; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, 1000;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Shared memory of fft32_pass_kernel: exchange buffers A, B (padded), the spectrum D of the lag-reversed d, two
+// staged window spectra, the staged u_old rows of a tile, three mbarriers, tacc, scratch.
+struct Fft32Smem {
+  static constexpr int M = FftCfg<float>::N / 2;
+  static constexpr int PADDED = FftCfg2<float>::PADDED;
+  static constexpr int WS = FftCfg<float>::WS;
+  static constexpr int UROWS = FftCfg<float>::N;     // more than any tile's rows
+  float2 *A, *B, *D, *W;     // W: the two spectrum buffers, WS entries apart
+  float* U;
+  unsigned long long* bar;   // [0], [1]: the spectrum buffers; [2]: the u_old buffer
+  double *tacc, *scratch;
+  __host__ __device__ static size_t bytes(int p_pad) {
+    return sizeof(float2) * (2 * (size_t)PADDED + 3 * (size_t)WS) + sizeof(float) * UROWS + 32 +
+           sizeof(double) * ((size_t)p_pad + 16 + 16);
+  }
+  __device__ Fft32Smem(unsigned char* raw) {
+    A = reinterpret_cast<float2*>(raw);
+    B = A + PADDED;
+    D = B + PADDED;
+    W = D + WS;
+    U = reinterpret_cast<float*>(W + 2 * WS);
+    bar = reinterpret_cast<unsigned long long*>(U + UROWS);
+    tacc = reinterpret_cast<double*>(bar + 4);
+    scratch = nullptr;   // set by the kernel (after tacc's p_pad + 16 entries)
+  }
+};
+static_assert((sizeof(float2) * 2 * FftCfg2<float>::PADDED) % 16 == 0, "D, W, U must start 16-byte aligned");
+static_assert((sizeof(float2) * FftCfg<float>::WS) % 16 == 0, "a spectrum tile must be a multiple of 16 bytes");
+
 __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float> a) {
   using V = float2;
   constexpr int N = FftCfg<float>::N;
   constexpr int M = N / 2;
+  constexpr int WS = FftCfg<float>::WS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
   int tail = a.tail;
@@ -720,78 +796,128 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
   const int L = N - p_pad;
   const V* tw = reinterpret_cast<const V*>(a.w.tw32);
   const V* wspec = reinterpret_cast<const V*>(a.w.wspec32);
-  FftSmem<float> sm(smem_raw, p_pad);
+  Fft32Smem sm(smem_raw);
+  sm.scratch = sm.tacc + p_pad + 16;
   const int tid = threadIdx.x;
   const int j = fft32_j(tid);
   for (int k = tid; k < p_pad + 16; k += kThreads) sm.tacc[k] = 0.0;
-  for (int f = tid; f <= M; f += kThreads) sm.S[f] = make_double2(0.0, 0.0);
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    mbar_init(&sm.bar[2], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
   const long long ntiles = (a.m + L - 1) / L;
-  const bool lags = nlag > 0;
   double n2 = 0.0;
+  bool failed = false;              // a wait gave up (this thread)
+  unsigned iss_w0 = 0u, iss_w1 = 0u, iss_u = 0u;   // thread 0: copies issued on bar[0], bar[1], bar[2]
+  // u_old rows of a tile that arrive by the bulk copy (a multiple of 4 rows; the rest are read directly)
+  auto u_bytes = [&](long long t) -> unsigned {
+    if (!u_old) return 0u;
+    const long long rows = lmin((long long)L, a.m - t * L);
+    return (unsigned)(rows * (long long)sizeof(float)) & ~15u;
+  };
+  auto issue_w = [&](long long t, int b) {
+    bulk_load(sm.W + b * WS, wspec + (size_t)t * WS, (unsigned)(sizeof(V) * WS), &sm.bar[b]);
+    if (b) ++iss_w1;
+    else ++iss_w0;
+  };
+  auto issue_u = [&](long long t) {
+    const unsigned nb = u_bytes(t);
+    if (nb) {
+      bulk_load(sm.U, u_old + t * L, nb, &sm.bar[2]);
+      ++iss_u;
+    }
+  };
   if (blockIdx.x < ntiles) {
-    fft_d_spectrum<float>(sm, a.d, a.d_scale, a.p, tw);      // sm.D, read per tile; ends with a barrier
+    if (tid == 0) {
+      issue_w(blockIdx.x, 0);       // the first tile's inputs arrive while d's spectrum is formed
+      issue_u(blockIdx.x);
+    }
+    const V twj = tw[j];
+    V z[8], pv[8];
+    // doubled spectrum of the lag-reversed, scaled d (point i = j + 256 r holds d entries 2i, 2i + 1)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int k0 = 2 * (j + 256 * r);
+      z[r].x = k0 < a.p ? (float)(a.d_scale * a.d[a.p - 1 - k0]) : 0.f;
+      z[r].y = k0 + 1 < a.p ? (float)(a.d_scale * a.d[a.p - 2 - k0]) : 0.f;
+    }
+    fft32_2048<false>(z, j, sm.A, sm.B, tw, [] {});
+    fft32_partner(z, pv, j);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      V xm;
+      sm.D[j + 256 * q] = fft32_split(z[q], pv[q], fft32_twf(twj, q), (q == 0 && j == 0) ? &xm : nullptr);
+      if (q == 0 && j == 0) sm.D[M] = xm;
+    }
+    __syncthreads();     // D complete; sm.A / sm.B free for the tiles
     V Sq[8], Sm = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) Sq[q] = make_float2(0.f, 0.f);
-    const float sc = 1.0f / (8.0f * M);
-    const float c = (float)coef;
+    double2* sacc = reinterpret_cast<double2*>(a.w.sacc32) + (size_t)blockIdx.x * (M + 1);
+    bool first_flush = true;
     int pending = 0;
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        double2& s = sm.S[j + 256 * q];
+        double2 s = first_flush ? make_double2(0.0, 0.0) : sacc[j + 256 * q];
         s.x += (double)Sq[q].x;
         s.y += (double)Sq[q].y;
+        sacc[j + 256 * q] = s;
         Sq[q] = make_float2(0.f, 0.f);
       }
       if (j == 0) {
-        sm.S[M].x += (double)Sm.x;
-        sm.S[M].y += (double)Sm.y;
+        double2 s = first_flush ? make_double2(0.0, 0.0) : sacc[M];
+        s.x += (double)Sm.x;
+        s.y += (double)Sm.y;
+        sacc[M] = s;
         Sm = make_float2(0.f, 0.f);
       }
+      first_flush = false;
       pending = 0;
     };
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const float sc = 1.0f / (8.0f * M);
+    const float c = (float)coef;
+    unsigned kw = 0, ku = 0;          // tiles consumed: spectrum buffer kw & 1 (phase kw >> 1), u_old phase ku
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++kw) {
+      const int b = kw & 1;
       const long long i0 = tile * L;
-      const int rows = (int)min((long long)L, a.m - i0);
-      const V* wt = wspec + (size_t)tile * (M + 1);
-      {
-        // ask L2 for the next tile's window spectrum and rows of u_old (one 128-byte line per thread) while this
-        // tile computes: their first use then waits on L2, not on HBM
-        const long long nt = tile + gridDim.x;
-        if (nt < ntiles) {
-          const char* pw = reinterpret_cast<const char*>(wspec + (size_t)nt * (M + 1));
-          const int wlines = (int)((sizeof(V) * (M + 1) + 127) / 128);
-          if (tid < wlines) asm volatile("prefetch.global.L2 [%0];" ::"l"(pw + 128 * tid));
-          if (u_old) {
-            const long long r0 = nt * L;
-            const int rn = (int)min((long long)L, a.m - r0);
-            const char* pu = reinterpret_cast<const char*>(u_old + r0);
-            const int ulines = (int)((sizeof(float) * rn + 127) / 128);
-            const int t2 = tid - wlines;
-            if (t2 >= 0 && t2 < ulines) asm volatile("prefetch.global.L2 [%0];" ::"l"(pu + 128 * t2));
-          }
-        }
-      }
-      // X d = IRFFT(W . conj(D)) on the tile's rows (W read again for the split: L2 holds it; fewer registers)
-      V z[8], pv[8];
+      const int rows = (int)lmin((long long)L, a.m - i0);
+      const long long nt = tile + gridDim.x;
+      if (!failed && !mbar_wait(&sm.bar[b], (kw >> 1) & 1u)) failed = true;
+      const V* wt = sm.W + b * WS;
+      // X d = IRFFT(W . conj(D)) on the tile's rows
 #pragma unroll
       for (int q = 0; q < 8; ++q) z[q] = cmulc(wt[j + 256 * q], sm.D[j + 256 * q]);
       fft32_partner(z, pv, j);
       if (j == 0) pv[0] = cmulc(wt[M], sm.D[M]);      // the partner of bin 0 is bin M
-      const V twj = tw[j];
 #pragma unroll
       for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
-      fft32_2048<true>(z, j, sm.A, sm.B, tw);
+      // past the first barrier every thread is done with the other spectrum buffer (the previous tile)
+      fft32_2048<true>(z, j, sm.A, sm.B, tw, [&] {
+        if (tid == 0 && nt < ntiles) issue_w(nt, b ^ 1);
+      });
       // rows 2i, 2i + 1 of u_old for the thread's points i = j + 256 r (tile offsets are even: L is)
+      const unsigned ub = u_bytes(tile);
+      const int rows_al = (int)(ub / sizeof(float));
+      if (ub) {
+        if (!failed && !mbar_wait(&sm.bar[2], ku & 1u)) failed = true;
+        ++ku;
+      }
       V uo[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int r0 = 2 * (j + 256 * r);
         uo[r] = make_float2(0.f, 0.f);
         if (u_old) {
-          if (r0 + 1 < rows) uo[r] = *reinterpret_cast<const V*>(u_old + i0 + r0);
-          else if (r0 < rows) uo[r].x = u_old[i0 + r0];
+          if (r0 + 1 < rows_al) {
+            uo[r] = *reinterpret_cast<const V*>(sm.U + r0);
+          } else {
+            if (r0 < rows) uo[r].x = r0 < rows_al ? sm.U[r0] : u_old[i0 + r0];
+            if (r0 + 1 < rows) uo[r].y = u_old[i0 + r0 + 1];
+          }
         }
       }
       // u = X d - c u_old on the tile's rows, zero elsewhere; u_new stored
@@ -810,12 +936,10 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
         z[r] = make_float2(u0, u1);
       }
       n2 += (double)nn;
-      if (!lags) {
-        __syncthreads();        // the next tile's first stage rewrites sm.A, read by this tile's last stage
-        continue;
-      }
-      // S += W . conj(U), U the doubled half spectrum of u
-      fft32_2048<false>(z, j, sm.B, sm.A, tw);
+      // S += W . conj(U), U the doubled half spectrum of u; past the first barrier u_old's buffer is free
+      fft32_2048<false>(z, j, sm.B, sm.A, tw, [&] {
+        if (tid == 0 && nt < ntiles) issue_u(nt);
+      });
       fft32_partner(z, pv, j);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -832,10 +956,39 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       }
       if (++pending == kFft32Flush) flush();
     }
-    flush();
+    {
+      if (pending) flush();
+      // tacc[k] = IRFFT(S)[k], k < nlag, from this thread's bins of the CTA's sum (S holds 4x the true spectrum:
+      // scale 1 / (8 M))
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double2 s = sacc[j + 256 * q];
+        z[q] = make_float2((float)s.x, (float)s.y);
+      }
+      fft32_partner(z, pv, j);
+      if (j == 0) {
+        const double2 s = sacc[M];
+        pv[0] = make_float2((float)s.x, (float)s.y);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
+      fft32_2048<true>(z, j, sm.A, sm.B, tw, [] {});
+      const double scd = 1.0 / (8.0 * M);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int k0 = 2 * (j + 256 * r);
+        if (k0 < nlag) sm.tacc[k0] = (double)z[r].x * scd;
+        if (k0 + 1 < nlag) sm.tacc[k0 + 1] = (double)z[r].y * scd;
+      }
+    }
   }
-  __syncthreads();
-  if (blockIdx.x < ntiles && lags) fft_finish_lags<float>(sm, nlag, tw);
+  if (tid == 0) {
+    // every copy this CTA issued has completed before it leaves (waits bounded like the others)
+    if (iss_w0 && !mbar_wait(&sm.bar[0], (iss_w0 - 1) & 1u)) failed = true;
+    if (iss_w1 && !mbar_wait(&sm.bar[1], (iss_w1 - 1) & 1u)) failed = true;
+    if (iss_u && !mbar_wait(&sm.bar[2], (iss_u - 1) & 1u)) failed = true;
+  }
+  if (failed && a.w.st) atomicExch(&a.w.st->dev_error, 1);
   __syncthreads();
   const double n2_cta = block_sum(n2, sm.scratch);
   for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
@@ -846,3 +999,5 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
   if (tid == 0 && a.worklog) a.worklog[a.work_slot] = 1 + tail;
   run_tail<float>(tail, a.w, a.gram, nlag, sm.tacc, n2_all, sm.scratch, a.out_t, a.out_n2);
 }
+
+static size_t fft32_pass_smem(int p_pad) { return Fft32Smem::bytes(p_pad); }

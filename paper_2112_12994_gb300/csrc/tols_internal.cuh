@@ -87,6 +87,7 @@ struct DevState {
   int fft;           // a batched pass with overlap-save FFT products ran for this series
   int no_precond;    // set by the host: plain LSQR (minimum-norm repeat of a rank-deficient problem)
   int f32_iter;      // inner iterations run with float products (a mixed solve that needed correction sweeps)
+  int dev_error;     // a kernel's bounded wait on its own copies gave up (the host reports TOLS_ERR_DEVICE_TIMEOUT)
 };
 
 // Device pointers of one solve's workspace.
@@ -116,6 +117,7 @@ struct Work {
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
   void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
   void* wspec64;          // the same for the float64 FFT tiles
+  void* sacc32;           // (float FFT passes) per-CTA float64 sums of W . conj(U): [kMaxGrid][N/2 + 1] double2
   void* dspec64;          // (batched float64 FFT series) doubled spectrum of the lag-reversed d, N/2 + 1 entries
   unsigned int* f32_active;  // (batches, nullable) count of the batch's series in a float correction sweep
 };
@@ -190,6 +192,7 @@ size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
 const void* fft_kernel_ptr(int is_double);
 int fft_size(int is_double);              // N of the real FFT per tile (float 4096, double 2048)
 size_t fft_spectra_bytes(int is_double, long long m, int p_pad);
+size_t fft32_sum_bytes();                 // the float FFT pass's per-CTA float64 sum buffer (Work::sacc32)
 cudaError_t launch_spectra(int is_double, const void* y, long long n, long long m, int p_pad, void* out,
                            const void* tw, int grid, cudaStream_t s);
 int pass_tile_rows(int is_double);

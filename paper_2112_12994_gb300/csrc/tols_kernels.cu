@@ -889,12 +889,14 @@ cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
   int g = (int)lmin((long long)grid, ntiles);
   if (g < 1) g = 1;
   if constexpr (sizeof(T) == 4) {
-    // float product passes take the register-blocked kernel (it moves u two rows at a time: 8-byte aligned u)
-    const bool aligned = ((reinterpret_cast<uintptr_t>(a.u_old) | reinterpret_cast<uintptr_t>(a.u_new)) & 7) == 0;
-    if (a.fft && !a.gram && aligned) {
+    // float product passes take the register-blocked kernel, whose inputs arrive by bulk copies: 16-byte aligned
+    // u vectors and spectra, and its float64 sum buffer
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.u_old) | reinterpret_cast<uintptr_t>(a.u_new) |
+                           reinterpret_cast<uintptr_t>(a.w.wspec32)) & 15) == 0;
+    if (a.fft && !a.gram && a.nlag > 0 && aligned && a.w.sacc32 && a.w.wspec32) {
       e = smem_opt_in((const void*)fft32_pass_kernel, 200 * 1024);
       if (e != cudaSuccess) return e;
-      fft32_pass_kernel<<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
+      fft32_pass_kernel<<<g, kThreads, fft32_pass_smem(a.p_pad), s>>>(a);
       return cudaGetLastError();
     }
   }
@@ -907,19 +909,21 @@ template cudaError_t launch_pass<float>(const PassArgs<float>&, int, cudaStream_
 template cudaError_t launch_pass<double>(const PassArgs<double>&, int, cudaStream_t);
 
 size_t pass_smem_bytes(int is_double, int p_pad, int fft) {
-  if (fft) return is_double ? fft_pass_smem<double>(p_pad) : fft_pass_smem<float>(p_pad);
+  if (fft) return is_double ? fft_pass_smem<double>(p_pad) : fft32_pass_smem(p_pad);
   return is_double ? pass_smem<double>(p_pad) : pass_smem<float>(p_pad);
 }
+// the kernel whose occupancy sizes the grid of FFT passes (float: the register-blocked kernel)
 const void* fft_kernel_ptr(int is_double) {
-  return is_double ? (const void*)fft_pass_kernel<double> : (const void*)fft_pass_kernel<float>;
+  return is_double ? (const void*)fft_pass_kernel<double> : (const void*)fft32_pass_kernel;
 }
+size_t fft32_sum_bytes() { return sizeof(double2) * (size_t)kMaxGrid * (FftCfg<float>::N / 2 + 1); }
 int fft_size(int is_double) { return is_double ? FftCfg<double>::N : FftCfg<float>::N; }
 
 template <typename T>
 static size_t spectra_bytes(long long m, int p_pad) {
   constexpr int N = FftCfg<T>::N;
   const long long L = N - p_pad;
-  return sizeof(typename FftCfg<T>::V) * (size_t)((m + L - 1) / L) * (N / 2 + 1);
+  return sizeof(typename FftCfg<T>::V) * (size_t)((m + L - 1) / L) * FftCfg<T>::WS;
 }
 size_t fft_spectra_bytes(int is_double, long long m, int p_pad) {
   return is_double ? spectra_bytes<double>(m, p_pad) : spectra_bytes<float>(m, p_pad);

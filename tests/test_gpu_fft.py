@@ -43,7 +43,10 @@ CASES = [(1, 9 * 2048 + 77), (17, 3 * 4096 + 5), (100, 5 * 4096 + 333), (257, 20
 
 @pytest.mark.parametrize("p,n", CASES)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fft_gk_pass(torch, tols, fctx, p, n, prec):
+@pytest.mark.parametrize("offset", [0, 1])
+def test_fft_gk_pass(torch, tols, fctx, p, n, prec, offset):
+    """offset 1: u_old and u_new are views one element into larger buffers (not 16-byte aligned), which the
+    float pass serves with its shared-memory kernel instead of the bulk-copy one."""
     rng = np.random.default_rng(p * 13 + n)
     y = ar_series(n, 3, config_id=51, series_index=p).y
     m = n - p
@@ -61,8 +64,8 @@ def test_fft_gk_pass(torch, tols, fctx, p, n, prec):
     ref_u = X @ vr - cr * uor
     d_y = torch.tensor(y, dtype=dt, device="cuda")
     d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
-    d_uo = torch.tensor(u_old, dtype=dt, device="cuda")
-    d_un = torch.empty(m, dtype=dt, device="cuda")
+    d_uo = torch.tensor(np.concatenate([np.zeros(offset), u_old]), dtype=dt, device="cuda")[offset:]
+    d_un = torch.empty(m + offset, dtype=dt, device="cuda")[offset:]
     d_t = torch.empty(p, dtype=torch.float64, device="cuda")
     n2 = tols.toeplitz_ols_gk_pass(fctx, P, d_y, n, p, d_v, d_uo, c, d_un, d_t)
     u = d_un.cpu().numpy().astype(np.float64)

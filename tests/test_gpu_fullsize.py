@@ -109,3 +109,64 @@ def test_bench_workload_lsar(tols, series):
     phi2 = oracle.compressed_ols(y[:m + 2], 2, rows[1], pi2[rows[1]], c)
     assert np.linalg.norm(phi_all[1, :2] - phi2) <= 1e-9 * np.linalg.norm(phi2)
     assert np.max(np.abs(tau - tau_exact)) <= 8.0 / math.sqrt(c)
+
+
+@pytest.mark.parametrize("p,n", [(100, (1 << 25) + 3), (500, (1 << 24) + 3)])
+def test_float_fft_pass_at_bench_lengths(tols, p, n):
+    """The float overlap-save pass (register-blocked; window spectra and u_old rows arrive by bulk copies) over
+    millions of rows: every CTA runs many tiles (at p = 100 more than one float flush of its spectral sums), and the
+    last tile's rows are not a multiple of four (its last rows are read directly, not copied). Dense u: sampled
+    rows of u_new against explicit dot products of rows of X, and every lag of X^T u normwise. Sparse u (v = 0,
+    c = -1, so u_new = u_old exactly): X^T u against the explicit sum over the nonzero rows, which no tile can drop
+    unnoticed."""
+    import torch
+    N, U32 = 4096, 2.0 ** -24
+    y = ar_series(n, 3, config_id=54, series_index=p).y
+    m = n - p
+    yr = y.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(p)
+    d_y = torch.tensor(y, dtype=torch.float32, device="cuda")
+    d_t = torch.empty(p, dtype=torch.float64, device="cuda")
+    L = N - ((p + 15) // 16) * 16
+    tiles = math.ceil(m / L)
+    assert (m - (tiles - 1) * L) % 4 != 0          # the ragged-tail case this test is about
+    k = 8 * U32 * math.log2(N)
+    win = math.sqrt(N) * np.max(np.abs(yr))
+    with tols.Context(precision=tols.TOLS_MIXED, product=tols.TOLS_PRODUCT_FFT) as ctx:
+        # dense
+        v = rng.standard_normal(p)
+        vr = v.astype(np.float32).astype(np.float64)
+        u_old = rng.standard_normal(m).astype(np.float32)
+        c = 0.375
+        d_v = torch.tensor(v, dtype=torch.float64, device="cuda")
+        d_uo = torch.tensor(u_old, device="cuda")
+        d_un = torch.empty(m, dtype=torch.float32, device="cuda")
+        n2 = tols.toeplitz_ols_gk_pass(ctx, tols.TOLS_MIXED, d_y, n, p, d_v, d_uo, c, d_un, d_t)
+        u = d_un.cpu().numpy().astype(np.float64)
+        t = d_t.cpu().numpy()
+        rows = np.unique(np.concatenate([[0, 1, L - 1, L, m - 4, m - 3, m - 2, m - 1], rng.integers(0, m, 256)]))
+        for i in rows:
+            ref = yr[p + i - np.arange(p) - 1] @ vr - c * float(u_old[i])
+            assert abs(u[i] - ref) <= k * win * np.linalg.norm(vr) + 2 * U32 * abs(c * u_old[i]), i
+        ynorm = np.linalg.norm(yr)
+        ref_t = np.array([np.dot(u, yr[p - 1 - j: p - 1 - j + m]) for j in range(p)])
+        assert np.max(np.abs(t - ref_t)) <= 16 * U32 * math.log2(N) * math.sqrt(2.0) * np.linalg.norm(u) * ynorm
+        assert n2 == pytest.approx(float(u @ u), rel=1e-5)
+        # sparse: the first and last rows of tiles spread over the CTAs, the ragged tail, random rows
+        nz = np.unique(np.concatenate([
+            [0, m - 3, m - 2, m - 1],
+            np.arange(0, tiles, 97) * L, np.minimum(np.arange(1, tiles, 89) * L - 1, m - 1),
+            rng.integers(0, m, 64)]))
+        us = np.zeros(m, dtype=np.float32)
+        us[nz] = rng.standard_normal(nz.size).astype(np.float32)
+        d_uo = torch.tensor(us, device="cuda")
+        d_v.zero_()
+        tols.toeplitz_ols_gk_pass(ctx, tols.TOLS_MIXED, d_y, n, p, d_v, d_uo, -1.0, d_un, d_t)
+        assert np.array_equal(d_un.cpu().numpy(), us)
+        t = d_t.cpu().numpy()
+    usd = us[nz].astype(np.float64)
+    ref_t = np.array([usd @ yr[p - 1 - j + nz] for j in range(p)])
+    touched = np.unique(nz // L).size
+    bound = k * win * math.sqrt(touched) * np.linalg.norm(usd) + 4 * U32 * np.array(
+        [np.abs(usd) @ np.abs(yr[p - 1 - j + nz]) for j in range(p)])
+    assert np.all(np.abs(t - ref_t) <= bound), np.max(np.abs(t - ref_t) / bound)

@@ -76,6 +76,8 @@ def parse():
                     help="batched / served fits checked against the oracle (the parity gate) per run")
     ap.add_argument("--lsar-only", action="store_true",
                     help="time only Algorithm LSAR on the AR(100) series (--lsar-lags, --lsar-c)")
+    ap.add_argument("--batch-precision", choices=["fp64", "mixed"], default="fp64",
+                    help="batch-only: precision of the batched solve")
     ap.add_argument("--batch-only", action="store_true",
                     help="one float64 batched solve of the batch workload (--batch-series), host-timed")
     ap.add_argument("--pacf-lags", type=int, default=120,
@@ -495,6 +497,7 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
                 "value_gated_est": value * passed / max(len(sample), 1),
                 "float_sweep_series": int(sum(1 for i in infos if i["precision_used"] == tols.TOLS_MIXED)),
                 "sampled_qr_series": int(sum(1 for i in infos if i["precond_used"] == 2)),
+                "plan": batch_plan_mix(tols, ps, infos),
                 "mean_iters": float(np.mean([i["iters"] for i in infos])),
                 "max_iters": int(max(i["iters"] for i in infos)),
                 "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches),
@@ -503,6 +506,18 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
                                  "kind": "oracle", "sample": f"{len(sample)} evenly spaced series of the batch"}})
     del d_ys, d_phi
     return out
+
+
+def batch_plan_mix(tols, ps, infos):
+    """Products the batch planner chose (timed per order class pad16(p + 1)): series counts and, per class, the
+    product its series took."""
+    cls = {}
+    for p, i in zip(ps, infos):
+        c = ((p + 1 + 15) // 16) * 16
+        cls.setdefault(c, set()).add("fft" if i["product_used"] == tols.TOLS_PRODUCT_FFT else "direct")
+    return {"fft_series": int(sum(1 for i in infos if i["product_used"] == tols.TOLS_PRODUCT_FFT)),
+            "direct_series": int(sum(1 for i in infos if i["product_used"] == tols.TOLS_PRODUCT_DIRECT)),
+            "by_pad16_p_plus_1": {str(c): "/".join(sorted(v)) for c, v in sorted(cls.items())}}
 
 
 def run_serving(tols, serve_in, args):
@@ -655,7 +670,7 @@ def run_srht(tols, torch, y, p, args):
 
 
 def run_batch_only(args):
-    """One float64 batched solve of the batch workload (after one warm-up solve), timed on the host."""
+    """One batched solve of the batch workload (after one warm-up solve) in --batch-precision, timed on the host."""
     import numpy as np
     import torch
 
@@ -667,7 +682,8 @@ def run_batch_only(args):
     dev = torch.device("cuda", 0)
     d_ys = [torch.tensor(y, dtype=torch.float64, device=dev) for y in ys]
     d_phi = torch.empty(sum(ps), dtype=torch.float64, device=dev)
-    with tols.Context(precision=tols.TOLS_FP64) as ctx:
+    prec = tols.TOLS_MIXED if args.batch_precision == "mixed" else tols.TOLS_FP64
+    with tols.Context(precision=prec) as ctx:
         tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -675,7 +691,7 @@ def run_batch_only(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     it = np.array([i["iters"] for i in infos])
-    print(json.dumps({"batch_only": True, "series": len(ys), "sum_n": int(sum(y.size for y in ys)), "seconds": dt,
+    print(json.dumps({"batch_only": True, "precision": args.batch_precision, "series": len(ys), "sum_n": int(sum(y.size for y in ys)), "seconds": dt,
                       "solves_per_s": len(ys) / dt, "mean_iters": float(it.mean()), "max_iters": int(it.max()),
                       "sampled_qr": int(sum(1 for i in infos if i["precond_used"] == 2))}), flush=True)
 
@@ -849,12 +865,11 @@ def run_ours(args, wl):
     return finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, rank, ranks)
 
 
-def fft_pass_flops(kind, m, p, gram=False):
-    """Counted flops of one overlap-save float64 pass (N = 2,048, tiles of N - pad16(p + 1) rows): a product pass
-    runs one inverse and one forward real transform per tile (2 x 2.5 N log2 N); a Gram pass one forward transform
-    plus pad16(p + 1) (p + 1) multiply-adds of edge corrections per tile when that is at most 24,576, else two
-    forward transforms (window and row block)."""
-    N = 2048
+def fft_pass_flops(kind, m, p, gram=False, N=2048):
+    """Counted flops of one overlap-save float64 pass (N = 2,048 or 4,096, tiles of N - pad16(p + 1) rows): a
+    product pass runs one inverse and one forward real transform per tile (2 x 2.5 N log2 N); a Gram pass one
+    forward transform plus pad16(p + 1) (p + 1) multiply-adds of edge corrections per tile when that is at most
+    24,576, else two forward transforms (window and row block)."""
     pg = ((p + 1 + 15) // 16) * 16
     tiles = math.ceil(m / (N - pg))
     t = 2.5 * N * math.log2(N)
@@ -880,24 +895,25 @@ def finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, 
     dom = max((k for k in r64["prof"] if r64["prof"][k][0] > 0 and k.startswith("pass_")),
               key=lambda k: r64["prof"][k][1])
     avg_ms, cnt = per_launch(r64["prof"], dom)
-    fft_used = r64["infos"][-1]["product_used"] == tols.TOLS_PRODUCT_FFT
+    fft_used = r64["infos"][-1]["product_used"] != tols.TOLS_PRODUCT_DIRECT
+    nfft = int(r64["infos"][-1]["nfft"]) or 2048
     gram = dom.endswith("gram")
     if fft_used:
-        flops = fft_pass_flops("fft", m, p, gram)
-        kname = f"fft_pass_kernel<double> ({dom})"
+        flops = fft_pass_flops("fft", m, p, gram, nfft)
+        kname = f"fft_pass_kernel<double, {nfft}> ({dom})"
     else:
         flops = (2.0 if gram else 4.0) * m * (p + 1 if gram else p)
         kname = f"pass_kernel<double> ({dom})"
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
-    traffic = TRAFFIC_PER_ROW.get((kname.split(" ")[0], p, gram))
+    traffic = TRAFFIC_PER_ROW.get((nfft if fft_used else 0, p, gram))
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
                 "traffic": traffic * n if traffic else None,
-                "traffic_source": (f"ncu dram__bytes_read+write of {kname.split(' ')[0]} at p = {p}, smaller n, "
+                "traffic_source": (f"ncu dram__bytes_read+write of {kname.rsplit(' (', 1)[0]} at p = {p}, smaller n, "
                                    f"{traffic:.2f} B per row of y scaled to n") if traffic else None,
                 "flop_per_launch": flops, "avg_launch_ms": avg_ms, "launches": cnt,
-                "product": "fft" if fft_used else "direct"}
+                "product": f"fft, N = {nfft}" if fft_used else "direct"}
 
     def line_of(r):
         i = r["infos"]
@@ -962,7 +978,9 @@ def finish_ours(args, wl, tols, s, results, e2e_ms, matvec, sweep, subl, world, 
 
 
 # DRAM bytes per row of y of the dominant kernel, from ncu (see profiles/): (kernel, p, gram pass) -> bytes / row
-TRAFFIC_PER_ROW = {("fft_pass_kernel<double>", 500, False): 25.15}
+# DRAM bytes per row of y (ncu dram__bytes_read + write of one launch / m) of the float64 product pass, keyed by
+# (FFT length N, p, Gram pass); measured at a smaller n, traffic grows in proportion to the rows
+TRAFFIC_PER_ROW = {(2048, 500, False): 25.15}
 
 
 def main():

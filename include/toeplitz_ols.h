@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
   TOLS_PRODUCT_AUTO = 0,      /* pick per (n, p, precision)                                               */
   TOLS_PRODUCT_DIRECT = 1,    /* sliding-window dot products                                              */
-  TOLS_PRODUCT_FFT = 2        /* overlap-save FFT blocks                                                  */
+  TOLS_PRODUCT_FFT = 2,       /* overlap-save FFT blocks of the default length (float 4,096; float64 2,048)  */
+  TOLS_PRODUCT_FFT4096 = 3    /* overlap-save FFT blocks of length 4,096 in both precisions               */
 } tols_product;
 
 typedef struct {
@@ -77,6 +78,10 @@ typedef struct {
   int precond;            /* tols_precond                                                                   */
   int product;            /* tols_product                                                                   */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = a stream owned by the context                   */
+  int wait_polls;         /* poll limit of a kernel's wait on its own bulk copies (the float FFT pass); 0 = the
+                             default, about two seconds; -1 = no polling, every such wait gives up at once (to
+                             test the path). A wait that gives up ends the call with TOLS_ERR_DEVICE_TIMEOUT; the
+                             kernel still lets its copies land before it exits, and the context stays usable   */
 } tols_config;
 
 /* Per-solve report. ne_ratio and rnorm always come from an explicit float64 pass over the data. */
@@ -94,6 +99,8 @@ typedef struct {
   double anorm_2;         /* estimate of ||X||_2 (power iteration on X^T X, a lower bound)                 */
   double anorm_f;         /* ||X||_F                                                                        */
   double cond_est;        /* max R_jj / min R_jj of the Cholesky factor (a rough lower bound of kappa(X))   */
+  long long nfft;         /* FFT length N of the overlap-save product passes (tiles of N - pad16(p + 1) rows);
+                             0 with direct products                                                           */
 } tols_info;
 
 typedef struct tols_ctx tols_ctx;

@@ -38,6 +38,7 @@ TOLS_PRECOND_SAMPLED_QR = 2
 TOLS_PRODUCT_AUTO = 0
 TOLS_PRODUCT_DIRECT = 1
 TOLS_PRODUCT_FFT = 2
+TOLS_PRODUCT_FFT4096 = 3
 TOLS_PROFILE_CLASSES = 13
 PROFILE_CLASS_NAMES = ["pass_f32_store", "pass_f32_lsqr", "pass_f32_necorr", "pass_f32_check", "pass_f32_gram",
                        "pass_f64_store", "pass_f64_lsqr", "pass_f64_necorr", "pass_f64_check", "pass_f64_gram",
@@ -47,14 +48,15 @@ PROFILE_CLASS_NAMES = ["pass_f32_store", "pass_f32_lsqr", "pass_f32_necorr", "pa
 class tols_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("device", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t),
                 ("max_iter", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("precond", ctypes.c_int),
-                ("product", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("product", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("wait_polls", ctypes.c_int)]
 
 
 class tols_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("precision_used", ctypes.c_int), ("precond_used", ctypes.c_int), ("product_used", ctypes.c_int),
                 ("ne_ratio", ctypes.c_double), ("rnorm", ctypes.c_double), ("bnorm", ctypes.c_double),
-                ("anorm_2", ctypes.c_double), ("anorm_f", ctypes.c_double), ("cond_est", ctypes.c_double)]
+                ("anorm_2", ctypes.c_double), ("anorm_f", ctypes.c_double), ("cond_est", ctypes.c_double),
+                ("nfft", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -183,12 +185,13 @@ class Context:
     """Owns a tols_ctx handle (toeplitz_ols_create / toeplitz_ols_destroy)."""
 
     def __init__(self, precision=TOLS_FP64, device=0, mem_cap_bytes=0, max_iter=0, max_sweeps=0,
-                 precond=TOLS_PRECOND_GRAM_CHOL, product=TOLS_PRODUCT_AUTO, cuda_stream=None):
+                 precond=TOLS_PRECOND_GRAM_CHOL, product=TOLS_PRODUCT_AUTO, cuda_stream=None, wait_polls=0):
         cfg = tols_config()
         lib.toeplitz_ols_config_default(ctypes.byref(cfg))
         cfg.precision, cfg.device, cfg.mem_cap_bytes = precision, device, mem_cap_bytes
         cfg.max_iter, cfg.max_sweeps, cfg.precond, cfg.product = max_iter, max_sweeps, precond, product
         cfg.cuda_stream = cuda_stream
+        cfg.wait_polls = wait_polls
         h = ctypes.c_void_p()
         rc = lib.toeplitz_ols_create(ctypes.byref(h), ctypes.byref(cfg))
         if rc != TOLS_OK:

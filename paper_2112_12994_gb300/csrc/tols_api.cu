@@ -19,6 +19,7 @@
 #include <chrono>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -51,7 +52,8 @@ struct tols_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t used = 0;
-  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, spec32, spec64, sacc32, b_spec, lsar, pcl;
+  DevBuf y64, y32, u0, u1, part, vecs, mats, state, scratch, rbuf, tune, tune_y, spec32, spec64, sacc32, b_spec, lsar,
+      pcl;
   // batched solves: pooled per-series buffers
   DevBuf b_y64, b_y32, b_u0, b_u1, b_part, b_cnt, b_vecs, b_phi, b_mats, b_state, b_series, b_tiles;
   double* h_stage = nullptr;    // pinned staging of host series for one H2D copy
@@ -62,12 +64,13 @@ struct tols_ctx {
   std::string err;
   std::map<int, StreamSeries> streams;
   int next_handle = 1;
-  int grid[4] = {0, 0, 0, 0};         // pass grid (float, double; direct, FFT)
-  size_t grid_pad[4] = {0, 0, 0, 0};  // p_pad the grid was computed for
-  void* tw32 = nullptr;               // FFT twiddle tables (float2[4096], double2[2048])
+  int grid[6] = {};                   // pass grid (float, double; direct, FFT of the default N, FFT of N = 4,096)
+  size_t grid_pad[6] = {};            // p_pad the grid was computed for
+  void* tw32 = nullptr;               // FFT twiddle tables (float2[4096], double2[2048], double2[4096])
   void* tw64 = nullptr;
-  std::map<int, int> fft_choice;      // autotuner: key (is_double, p_pad) -> 1 FFT, 0 direct
-  int last_fft = 0;                   // product of the last solve's iteration passes
+  void* tw64x = nullptr;
+  std::map<int, int> fft_choice;      // autotuner: key (is_double, p_pad, gram) -> FFT length N, or 0 (direct)
+  int last_fft = 0;                   // FFT length of the last solve's iteration passes (0: direct)
   // instrumentation (toeplitz_ols_profile)
   bool prof = false;
   long long launch_total = 0;
@@ -165,6 +168,7 @@ int take_event(tols_ctx* ctx, cudaEvent_t* e) {
 template <typename T>
 int run_pass(tols_ctx* ctx, PassArgs<T> a, int grid) {
   ctx->launch_total++;
+  a.wait_polls = ctx->cfg.wait_polls;
   if (!ctx->prof) {
     CK(launch_pass<T>(a, grid, ctx->stream));
     return TOLS_OK;
@@ -211,11 +215,13 @@ int run_small(tols_ctx* ctx, int kind, F launch) {
     if (rc_) return rc_;                \
   } while (0)
 
+// fft: 0 (direct products) or the FFT length N (1: the precision's default N).
 int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
-  const int slot = is_double + 2 * fft;
+  if (fft == 1) fft = fft_size(is_double);
+  const int slot = is_double + 2 * (fft == 0 ? 0 : fft == fft_size(is_double) ? 1 : 2);
   if (ctx->grid[slot] == 0 || ctx->grid_pad[slot] != (size_t)p_pad) {
     int nb = 0;
-    const void* fn = fft ? fft_kernel_ptr(is_double) : pass_kernel_ptr(is_double);
+    const void* fn = fft ? fft_kernel_ptr(is_double, fft) : pass_kernel_ptr(is_double);
     const size_t smem = pass_smem_bytes(is_double, p_pad, fft);
     smem_opt_in(fn, 200 * 1024);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
@@ -231,9 +237,12 @@ int pass_grid_for(tols_ctx* ctx, int is_double, int p_pad, int fft = 0) {
 
 // Doubled window spectra of series y (tiles of N - p_pad rows) in the context's buffer for that precision, which
 // every FFT pass reads. form: transform them here (spectrum_kernel); else only make room (a Gram pass fills it).
-int fft_spectra(tols_ctx* ctx, Work& w, int is_double, const void* y, long long n, long long m, int p_pad, bool form) {
+// nfft: the FFT length N (0 or 1: the precision's default).
+int fft_spectra(tols_ctx* ctx, Work& w, int is_double, const void* y, long long n, long long m, int p_pad, bool form,
+                int nfft = 0) {
+  if (nfft <= 1) nfft = fft_size(is_double);
   DevBuf& b = is_double ? ctx->spec64 : ctx->spec32;
-  RUN(ensure(ctx, b, fft_spectra_bytes(is_double, m, p_pad)));
+  RUN(ensure(ctx, b, fft_spectra_bytes(is_double, m, p_pad, nfft)));
   if (is_double) {
     w.wspec64 = b.p;
   } else {
@@ -243,29 +252,37 @@ int fft_spectra(tols_ctx* ctx, Work& w, int is_double, const void* y, long long 
   }
   if (!form) return TOLS_OK;
   return run_small(ctx, 12, [&] {
-    return launch_spectra(is_double, y, n, m, p_pad, b.p, is_double ? w.tw64 : w.tw32,
-                          pass_grid_for(ctx, is_double, p_pad, 1), ctx->stream);
+    return launch_spectra(is_double, y, n, m, p_pad, b.p, is_double ? (nfft == 4096 ? w.tw64x : w.tw64) : w.tw32,
+                          pass_grid_for(ctx, is_double, p_pad, nfft), ctx->stream, nfft);
   });
 }
 
 // Product kernel for a pass over series y (T = float or double): the sliding-window direct products or the
-// overlap-save FFT. DIRECT / FFT force one; AUTO times both once per (precision, p_pad) on the series at hand
-// when it is long enough for the choice to matter (cached in the context), else picks by p.
+// overlap-save FFT, and its length N. DIRECT / FFT / FFT4096 force one; AUTO times the direct and the FFT pass of
+// the default N once per (precision, p_pad) on the series at hand when it is long enough for the choice to matter
+// (cached in the context), else picks by p. Float64 transforms of N = 4,096 serve the orders the default N = 2,048
+// cannot (p_pad >= 1,024) and TOLS_PRODUCT_FFT4096; below that they were not faster on GB300 (one CTA per SM
+// instead of two: 7.73 against 7.72 ms at p = 500, n = 2^26, and slower at smaller p) and their rounding error
+// is larger (u log2 N sqrt(N) per window), which shows at the float64 floor of ill-conditioned series. Returns 0
+// (direct) or N.
 template <typename T>
 int choose_fft(tols_ctx* ctx, const Work& w, const T* y, long long n, int p, int p_pad, int nlag, int gram) {
   const int is_double = sizeof(T) == 8;
-  if (p_pad >= fft_size(is_double) / 2) return 0;       // too few rows per FFT tile
+  const int n_def = fft_size(is_double);
+  const bool def_ok = p_pad < n_def / 2;                   // enough rows per FFT tile
+  const bool long_ok = is_double && p_pad < 4096 / 2;
   if (ctx->cfg.product == TOLS_PRODUCT_DIRECT) return 0;
-  if (ctx->cfg.product == TOLS_PRODUCT_FFT) return 1;
+  if (ctx->cfg.product == TOLS_PRODUCT_FFT4096 && long_ok) return 4096;
+  if (ctx->cfg.product == TOLS_PRODUCT_FFT || ctx->cfg.product == TOLS_PRODUCT_FFT4096)
+    return def_ok ? n_def : long_ok ? 4096 : 0;
+  if (!def_ok) return long_ok ? 4096 : 0;                   // only the long transforms fit these orders
   const long long m = n - p;
   const int key = is_double * 100000 + p_pad * 2 + gram;
   auto it = ctx->fft_choice.find(key);
   if (it != ctx->fft_choice.end()) return it->second;
-  const int guess = p_pad >= (is_double ? 32 : 64);
+  const int guess = p_pad >= (is_double ? 32 : 64) ? n_def : 0;
   if (m < (1 << 20) || ensure(ctx, ctx->tune, sizeof(double) * (4 * (size_t)p_pad + 64)) != TOLS_OK) return guess;
   double* sc = (double*)ctx->tune.p;
-  Work wf = w;                    // the FFT pass reads (or, for the Gram, writes) the window spectra
-  if (fft_spectra(ctx, wf, is_double, y, n, m, p_pad, !gram) != TOLS_OK) return guess;
   PassArgs<T> a;
   memset(&a, 0, sizeof a);
   a.y = y;
@@ -278,29 +295,37 @@ int choose_fft(tols_ctx* ctx, const Work& w, const T* y, long long n, int p, int
   a.d = sc + 2 * p_pad;           // contents do not matter for timing
   a.d_scale = 1.0;
   a.tail = TAIL_STORE;
-  a.w = w;
   a.out_t = sc;
   a.out_n2 = sc + p_pad + 8;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best[2] = {0.f, 0.f};
-  for (int f = 0; f < 2; ++f) {
-    a.fft = f;
-    a.w = f ? wf : w;
-    const int grid = pass_grid_for(ctx, is_double, p_pad, f);
+  const int cand[2] = {0, n_def};
+  float best_ms = 0.f;
+  int choice = guess;
+  for (int c = 0; c < 2; ++c) {
+    if (cand[c] < 0) continue;
+    Work wf = w;                  // an FFT pass reads (or, for the Gram, writes) the window spectra of its N
+    if (cand[c] && fft_spectra(ctx, wf, is_double, y, n, m, p_pad, !gram, cand[c]) != TOLS_OK) continue;
+    a.fft = cand[c];
+    a.w = wf;
+    const int grid = pass_grid_for(ctx, is_double, p_pad, cand[c]);
     launch_pass<T>(a, grid, ctx->stream);                 // warm-up
     cudaEventRecord(e0, ctx->stream);
     launch_pass<T>(a, grid, ctx->stream);
     launch_pass<T>(a, grid, ctx->stream);
     cudaEventRecord(e1, ctx->stream);
     cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&best[f], e0, e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaGetLastError() != cudaSuccess) continue;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      choice = cand[c];
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (cudaGetLastError() != cudaSuccess) return guess;
-  const int choice = best[1] < best[0] ? 1 : 0;
   ctx->fft_choice[key] = choice;
   return choice;
 }
@@ -370,6 +395,7 @@ int prepare_work(tols_ctx* ctx, const double* y64, long long n, int p, bool mixe
   w.st = (DevState*)ctx->state.p;
   w.tw32 = ctx->tw32;
   w.tw64 = ctx->tw64;
+  w.tw64x = ctx->tw64x;
   return TOLS_OK;
 }
 
@@ -578,6 +604,7 @@ void fill_info(tols_info* info, const DevState& s, int prec) {
   info->precision_used = prec;
   info->precond_used = s.precond;
   info->product_used = s.fft ? TOLS_PRODUCT_FFT : TOLS_PRODUCT_DIRECT;  // single series: set after the call
+  info->nfft = s.fft ? kBatchFftN : 0;
   info->ne_ratio = s.ne_ratio;
   info->rnorm = s.rnorm;
   info->bnorm = s.bnorm;
@@ -621,7 +648,7 @@ int solve_core(tols_ctx* ctx, const double* d_y, long long n, int p, double tol,
   const int pp = pad_p(p);
   const int pg = pad_p(p + 1);
   const int fft64 = choose_fft<double>(ctx, w, w.y64, n, p, pp, p, 0);
-  if (fft64) RUN(fft_spectra(ctx, w, 1, w.y64, n, n - p, pg, false));
+  if (fft64) RUN(fft_spectra(ctx, w, 1, w.y64, n, n - p, pg, false, fft64));
   if ((rc = run_setup(ctx, w, mixed, no_precond, fft64))) return rc;
   if (phi0) {
     CK(cudaMemcpyAsync(w.phi, phi0, sizeof(double) * p, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -745,7 +772,10 @@ int solve_device_impl(tols_ctx* ctx, const double* d_y, long long n, int p, doub
   if (rnorm) *rnorm = s.rnorm;
   // a mixed request is reported as mixed only when float products did part of the work
   fill_info(info, s, mixed && s.f32_iter > 0 ? TOLS_MIXED : TOLS_FP64);
-  if (info && ctx->last_fft) info->product_used = TOLS_PRODUCT_FFT;
+  if (info) {
+    info->nfft = ctx->last_fft;
+    if (ctx->last_fft) info->product_used = ctx->last_fft == 4096 ? TOLS_PRODUCT_FFT4096 : TOLS_PRODUCT_FFT;
+  }
   return s.status;
 }
 
@@ -811,8 +841,91 @@ long long batch_units(long long m, int p, bool fx) {
   return std::max(d, (m + kTileF - 1) / kTileF);
 }
 
-void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status, bool mixed,
-                bool allow_fft = true) {
+// Batched products (a9): whether a series of order p runs its batched float64 passes on the overlap-save FFT
+// products (N = 2,048, tiles of N - pad_p(p + 1) rows) or on the direct ones. DIRECT forces the direct products;
+// FFT / FFT4096 take the FFT from pad_p(p + 1) = 32 up. AUTO measures, once per process, device and class
+// pad_p(p + 1): one direct and one FFT pass (best of three launches each) over a synthetic series of
+// kBatchTuneRows rows of that order, and takes the FFT only where it is at least 5 % faster. The choice is kept
+// for every context of the process, so a series' products, and so its result, do not depend on the context (or
+// server) that solved it. The float correction sweeps of mixed series use the direct float products.
+constexpr long long kBatchTuneRows = 1 << 18;
+std::mutex g_batch_tune_mu;
+std::map<long long, int> g_batch_tune;   // key device * 4096 + pad_p(p + 1) -> 1 FFT, 0 direct
+
+int batch_fft_choice(tols_ctx* ctx, int p) {
+  const int pp = pad_p(p + 1);
+  if (ctx->cfg.product == TOLS_PRODUCT_DIRECT || pp >= kBatchFftN / 2) return 0;
+  if (ctx->cfg.product != TOLS_PRODUCT_AUTO) return batch_fft_series(p) ? 1 : 0;
+  std::lock_guard<std::mutex> lock(g_batch_tune_mu);
+  const long long key = (long long)ctx->device * 4096 + pp;
+  auto it = g_batch_tune.find(key);
+  if (it != g_batch_tune.end()) return it->second;
+  const int guess = batch_fft_series(p) ? 1 : 0;
+  // synthetic series of order pt = pp - 1 (a fixed pseudo-random sequence: timing does not depend on values)
+  const int pt = pp - 1;
+  const long long n = kBatchTuneRows + pt;
+  // its own buffer for the series: a caller may hold a staged series in ctx->y64 (the PACF batch)
+  if (ensure(ctx, ctx->tune_y, sizeof(double) * (size_t)n) != TOLS_OK ||
+      ensure(ctx, ctx->tune, sizeof(double) * (4 * (size_t)pp + 64)) != TOLS_OK)
+    return guess;
+  std::vector<double> hy((size_t)n);
+  unsigned long long x = 0x9e3779b97f4a7c15ull;
+  for (auto& v : hy) {
+    x = x * 6364136223846793005ull + 1442695040888963407ull;
+    v = (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  const double* d_y = (const double*)ctx->tune_y.p;
+  if (cudaMemcpyAsync((void*)d_y, hy.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream) !=
+      cudaSuccess)
+    return guess;
+  Work w;
+  if (prepare_work(ctx, d_y, n, pt, false, true, w) != TOLS_OK) return guess;
+  double* sc = (double*)ctx->tune.p;
+  PassArgs<double> a = base_args<double>(w, d_y, n, pt, pp);
+  a.d = sc + 2 * pp;
+  a.u_old = (const double*)w.U[0];
+  a.u_new = (double*)w.U[1];
+  a.coef_host = 0.5;
+  a.tail = TAIL_STORE;
+  a.out_t = sc;
+  a.out_n2 = sc + pp + 8;
+  cudaMemsetAsync(w.U[0], 0, sizeof(double) * (size_t)kBatchTuneRows, ctx->stream);
+  cudaMemsetAsync(sc, 0, sizeof(double) * (4 * (size_t)pp + 64), ctx->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best[2] = {0.f, 0.f};
+  bool ok = true;
+  for (int f = 0; f < 2 && ok; ++f) {
+    Work wf = w;
+    if (f && fft_spectra(ctx, wf, 1, d_y, n, kBatchTuneRows, pp, true, kBatchFftN) != TOLS_OK) {
+      ok = false;
+      break;
+    }
+    a.fft = f ? kBatchFftN : 0;
+    a.w = wf;
+    const int grid = pass_grid_for(ctx, 1, pp, a.fft);
+    launch_pass<double>(a, grid, ctx->stream);           // warm-up
+    for (int r = 0; r < 3; ++r) {
+      cudaEventRecord(e0, ctx->stream);
+      launch_pass<double>(a, grid, ctx->stream);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r == 0 || ms < best[f]) best[f] = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || cudaGetLastError() != cudaSuccess) return guess;
+  const int choice = best[1] < 0.95f * best[0] ? 1 : 0;
+  g_batch_tune[key] = choice;
+  return choice;
+}
+
+void plan_batch(tols_ctx* ctx, BatchPlan& B, int count, const long long* n, const int* p, std::vector<int>& status,
+                bool mixed) {
   for (int k = 0; k < count; ++k) {
     if (p[k] < 1 || p[k] > TOLS_MAX_P || n[k] <= p[k]) { status[k] = TOLS_ERR_ARG; continue; }
     const long long nn = n[k], mm = nn - p[k];
@@ -825,7 +938,7 @@ void plan_batch(BatchPlan& B, int count, const long long* n, const int* p, std::
     B.y_elems += align_up((size_t)nn, 64);
     B.off_u.push_back((long long)B.u_elems);
     B.u_elems += align_up((size_t)mm, 64);
-    const bool fx = allow_fft && batch_fft_series(p[k]);
+    const bool fx = batch_fft_choice(ctx, p[k]) != 0;
     const long long ntd = fx ? 0 : (mm + kTileD - 1) / kTileD, ntf = (mm + kTileF - 1) / kTileF;
     const long long ntx = fx ? batch_fft_units(mm, p[k]) : 0;
     const long long nun = batch_units(mm, p[k], fx);
@@ -947,6 +1060,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     w.st = (DevState*)ctx->b_state.p + k;
     w.f32_active = mixed ? d_done + 1 : nullptr;   // the batch's count of series in a float correction sweep
     w.tw64 = ctx->tw64;
+    w.tw64x = ctx->tw64x;
     w.tw32 = ctx->tw32;
     if (B.fft[k]) {
       double* sp = (double*)ctx->b_spec.p + B.off_spec[k];
@@ -1087,7 +1201,7 @@ BatchPlan sub_plan(tols_ctx* ctx, const BatchPlan& B, const std::vector<int>& wh
     p.push_back(B.p[k]);
   }
   std::vector<int> st(which.size(), TOLS_OK);
-  plan_batch(S, (int)which.size(), n.data(), p.data(), st, false, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
+  plan_batch(ctx, S, (int)which.size(), n.data(), p.data(), st, false);
   for (int k : which)
     S.y_dev.push_back(B.y_dev.empty() ? (const double*)ctx->b_y64.p + B.off_y[k] : B.y_dev[k]);
   return S;
@@ -1206,10 +1320,10 @@ class ArenaAlloc {
 };
 
 // Bytes of one series' arena slice; with base != nullptr also lays the slice out into w.
-size_t series_slice(char* base, long long n, int p, bool mixed, Work* w) {
+// fx: the request's float64 passes take the batched FFT products (batch_fft_choice).
+size_t series_slice(char* base, long long n, int p, bool mixed, bool fx, Work* w) {
   const long long m = n - p;
   const size_t pp1 = (size_t)pad_p(p + 1);
-  const bool fx = batch_fft_series(p);
   const long long ntd = batch_units(m, p, fx), ngr = (ntd + kGroup - 1) / kGroup;
   const size_t es = sizeof(double);   // float64 even for mixed requests (float64 iterations when float cannot refine)
   size_t off = 0;
@@ -1350,6 +1464,7 @@ int upload_table(tols_server* srv, const std::vector<int>& list, BatchArgs& a, i
     memset(&hs[k], 0, sizeof(BatchSeries));
     hs[k].w = w;
     hs[k].w.tw64 = ctx->tw64;
+    hs[k].w.tw64x = ctx->tw64x;
     hs[k].w.tw32 = ctx->tw32;
     hs[k].tile0_f = tf;
     hs[k].tile0_d = td;
@@ -1390,13 +1505,14 @@ int server_admit(tols_server* srv, std::vector<int>& fresh) {
   tols_ctx* ctx = srv->ctx;
   while (!srv->queue.empty() && (int)srv->active.size() < srv->max_active) {
     SrvRequest& r = srv->queue.front();
-    const size_t bytes = series_slice(nullptr, r.n, r.p, r.mixed, nullptr);
+    const bool fx = batch_fft_choice(ctx, r.p) != 0;
+    const size_t bytes = series_slice(nullptr, r.n, r.p, r.mixed, fx, nullptr);
     size_t off = 0;
     if (!srv->alloc.alloc(bytes, &off)) break;  // FIFO: the head waits until memory frees up
     SrvActive a;
     a.off = off;
     a.bytes = bytes;
-    series_slice(srv->arena + off, r.n, r.p, r.mixed, &a.w);
+    series_slice(srv->arena + off, r.n, r.p, r.mixed, fx, &a.w);
     DevState st = initial_state(ctx->cfg, r.p, r.tol, r.mixed);
     st.no_precond = r.no_precond ? 1 : 0;
     CK(cudaMemcpyAsync((void*)a.w.y64, r.y.data(), sizeof(double) * (size_t)r.n, cudaMemcpyHostToDevice,
@@ -1583,6 +1699,7 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
   if (c.precision != TOLS_FP64 && c.precision != TOLS_MIXED) return TOLS_ERR_ARG;
   if (c.precond != TOLS_PRECOND_NONE && c.precond != TOLS_PRECOND_GRAM_CHOL && c.precond != TOLS_PRECOND_SAMPLED_QR)
     return TOLS_ERR_ARG;
+  if (c.product < TOLS_PRODUCT_AUTO || c.product > TOLS_PRODUCT_FFT4096 || c.wait_polls < -1) return TOLS_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= c.device || c.device < 0) {
     cudaGetLastError();
@@ -1614,7 +1731,7 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
   }
   {
     // FFT twiddles exp(-2 pi i t / N) in float64 on the host (libm), rounded to float for the float table
-    std::vector<double2> t64(2048);
+    std::vector<double2> t64(2048), t64x(4096);
     std::vector<float2> t32(4096);
     for (int t = 0; t < 2048; ++t) {
       const double a = -2.0 * M_PI * (double)t / 2048.0;
@@ -1623,10 +1740,13 @@ int toeplitz_ols_create(tols_ctx** out, const tols_config* cfg) {
     for (int t = 0; t < 4096; ++t) {
       const double a = -2.0 * M_PI * (double)t / 4096.0;
       t32[t] = make_float2((float)cos(a), (float)sin(a));
+      t64x[t] = make_double2(cos(a), sin(a));
     }
     if (cudaMalloc(&ctx->tw64, sizeof(double2) * 2048) != cudaSuccess ||
+        cudaMalloc(&ctx->tw64x, sizeof(double2) * 4096) != cudaSuccess ||
         cudaMalloc(&ctx->tw32, sizeof(float2) * 4096) != cudaSuccess ||
         cudaMemcpy(ctx->tw64, t64.data(), sizeof(double2) * 2048, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->tw64x, t64x.data(), sizeof(double2) * 4096, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->tw32, t32.data(), sizeof(float2) * 4096, cudaMemcpyHostToDevice) != cudaSuccess) {
       if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
       delete ctx;
@@ -1652,13 +1772,14 @@ int toeplitz_ols_destroy(tols_ctx* ctx) {
                     &ctx->mats,   &ctx->state, &ctx->scratch, &ctx->rbuf,  &ctx->b_y64,   &ctx->b_y32,
                     &ctx->b_u0,   &ctx->b_u1,  &ctx->b_part, &ctx->b_cnt,  &ctx->b_vecs,  &ctx->b_phi,
                     &ctx->b_mats, &ctx->b_state, &ctx->b_series, &ctx->b_tiles, &ctx->tune, &ctx->spec32,
-                    &ctx->spec64, &ctx->sacc32, &ctx->b_spec, &ctx->lsar, &ctx->pcl};
+                    &ctx->spec64, &ctx->sacc32, &ctx->b_spec, &ctx->lsar, &ctx->pcl, &ctx->tune_y};
   for (DevBuf* b : bufs) release(ctx, *b);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   if (ctx->h_state) cudaFreeHost(ctx->h_state);
   if (ctx->h_worklog) cudaFreeHost(ctx->h_worklog);
   if (ctx->tw32) cudaFree(ctx->tw32);
   if (ctx->tw64) cudaFree(ctx->tw64);
+  if (ctx->tw64x) cudaFree(ctx->tw64x);
   if (ctx->d_worklog) cudaFree(ctx->d_worklog);
   for (auto& q : ctx->pending) { cudaEventDestroy(q.e0); cudaEventDestroy(q.e1); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
@@ -1697,7 +1818,7 @@ int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y,
   if (tol <= 0) tol = 1e-12;
   std::vector<int> status(count, TOLS_OK);
   BatchPlan B;
-  plan_batch(B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
+  plan_batch(ctx, B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED);
   for (int k : B.idx)
     if (!y[k] || !phi[k]) return fail(ctx, TOLS_ERR_ARG, "null series or phi pointer");
   int rc;
@@ -1759,7 +1880,7 @@ int toeplitz_ols_pacf(tols_ctx* ctx, const double* y, long long n, int h_max, do
   std::vector<int> status((size_t)h_max, TOLS_OK);
   const bool mixed = ctx->cfg.precision == TOLS_MIXED;
   BatchPlan B;
-  plan_batch(B, h_max, nn.data(), pp.data(), status, mixed, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
+  plan_batch(ctx, B, h_max, nn.data(), pp.data(), status, mixed);
   for (size_t j = 0; j < B.idx.size(); ++j) B.y_dev.push_back((const double*)ctx->y64.p);
   std::vector<DevState> states;
   std::vector<int> prec_used;
@@ -2115,7 +2236,7 @@ int toeplitz_ols_solve_batched_device(tols_ctx* ctx, int count, const double* co
   if (tol <= 0) tol = 1e-12;
   std::vector<int> status(count, TOLS_OK);
   BatchPlan B;
-  plan_batch(B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED, ctx->cfg.product != TOLS_PRODUCT_DIRECT);
+  plan_batch(ctx, B, count, n, p, status, ctx->cfg.precision == TOLS_MIXED);
   for (int k : B.idx) {
     if (!d_y[k]) return fail(ctx, TOLS_ERR_ARG, "null device series pointer");
     B.y_dev.push_back(d_y[k]);
@@ -2216,7 +2337,7 @@ int toeplitz_ols_gk_pass(tols_ctx* ctx, int precision, const void* d_y, long lon
     a.out_n2 = d_n2;
     a.fft = choose_fft<double>(ctx, w, (const double*)d_y, n, p, pp, p, 0);
     if (a.fft) {
-      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true));
+      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true, a.fft));
       a.w.wspec64 = w.wspec64;
     }
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
@@ -2281,7 +2402,7 @@ int toeplitz_ols_gram(tols_ctx* ctx, int precision, const double* d_y, long long
     a.out_n2 = w.bnorm2;
     a.fft = choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
     if (a.fft) {
-      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pg, false));
+      RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pg, false, a.fft));
       a.w.wspec64 = w.wspec64;
     }
     RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
@@ -2311,7 +2432,7 @@ int toeplitz_ols_preconditioner(tols_ctx* ctx, int precision, const double* d_y,
   CK(cudaMemcpyAsync(w.st, ctx->h_state, sizeof(DevState), cudaMemcpyHostToDevice, ctx->stream));
   const int pg = pad_p(p + 1);
   const int fft = choose_fft<double>(ctx, w, d_y, n, p, pg, p + 1, 1);
-  if (fft) RUN(fft_spectra(ctx, w, 1, nullptr, n, n - p, pg, false));
+  if (fft) RUN(fft_spectra(ctx, w, 1, nullptr, n, n - p, pg, false, fft));
   RUN(run_setup(ctx, w, mixed, false, fft, kind));
   CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -2366,7 +2487,7 @@ int toeplitz_ols_residual(tols_ctx* ctx, const double* d_y, long long n, int p, 
   a.out_n2 = d_n2;
   a.fft = choose_fft<double>(ctx, w, d_y, n, p, pp, p, 0);
   if (a.fft) {
-    RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true));
+    RUN(fft_spectra(ctx, w, 1, d_y, n, n - p, pp, true, a.fft));
     a.w.wspec64 = w.wspec64;
   }
   RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pp, a.fft)));
@@ -2491,7 +2612,9 @@ int toeplitz_ols_server_destroy(tols_server* srv) {
 int toeplitz_ols_server_submit(tols_server* srv, long long id, const double* y, long long n, int p, double tol) {
   if (!srv || !y || p < 1 || p > TOLS_MAX_P || n <= p) return TOLS_ERR_ARG;
   // a mixed request may be re-run in float64, which needs the larger footprint
-  if (align_up(series_slice(nullptr, n, p, false, nullptr), 256) > srv->arena_cap) return TOLS_ERR_OOM;
+  if (align_up(series_slice(nullptr, n, p, false, batch_fft_choice(srv->ctx, p) != 0, nullptr), 256) >
+      srv->arena_cap)
+    return TOLS_ERR_OOM;
   SrvRequest r;
   r.id = id;
   r.n = n;

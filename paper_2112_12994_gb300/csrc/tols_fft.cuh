@@ -58,6 +58,10 @@ __device__ __forceinline__ V cmulc(V a, V b) {
   r.y = a.y * b.x - a.x * b.y;
   return r;
 }
+// float2 sums and differences as packed two-lane instructions (sm_100 and later: one issue slot instead of two;
+// per component the same rounding as a scalar add). a - b is fma(b, -1, a), exact before its one rounding.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 template <typename V>
 __device__ __forceinline__ V cconj(V a) { a.y = -a.y; return a; }
 template <typename V, typename S>
@@ -183,10 +187,12 @@ __device__ __forceinline__ void merge2(V vf, V vmf, V twf, V& zf, V& zmf) {
   zmf.y = -(ay - cbx);
 }
 
-template <typename T>
+template <typename T, int N = FftCfg<T>::N>
 struct FftCfg2 {
-  static constexpr int M = FftCfg<T>::N / 2;
+  static constexpr int M = N / 2;
   static constexpr int PADDED = M + M / 8 + 8;   // entries of a padded work array (index pix(f), f <= M)
+  // entries per tile of the window-spectrum array: bins 0 .. M, float tiles padded to a 16-byte multiple
+  static constexpr int WS = sizeof(T) == 4 ? M + 2 : M + 1;
 };
 
 __host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -200,11 +206,11 @@ struct GramCfg {
 
 // Shared memory of the FFT kernels: work arrays A, B (padded), the doubled spectrum D of the lag-reversed d,
 // the CTA's accumulated spectrum S (float64), the Gram pass's window segments ext[2 p_pad], tacc, scratch.
-template <typename T>
+template <typename T, int N = FftCfg<T>::N>
 struct FftSmem {
   using V = typename FftCfg<T>::V;
-  static constexpr int M = FftCfg<T>::N / 2;
-  static constexpr int PADDED = FftCfg2<T>::PADDED;
+  static constexpr int M = N / 2;
+  static constexpr int PADDED = FftCfg2<T, N>::PADDED;
   V *A, *B, *D;
   double2* S;
   T* ext;
@@ -228,11 +234,11 @@ struct FftSmem {
 };
 
 // Window y[i0 .. i0+N) (zero past n), packed in pairs, into sm.A; then its complex transform (result in sm.A).
-template <typename T>
-__device__ void fft_window(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long i0,
+template <typename T, int N = FftCfg<T>::N>
+__device__ void fft_window(FftSmem<T, N>& sm, const T* __restrict__ y, long long n, long long i0,
                            const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
+  constexpr int M = N / 2;
   for (int j = threadIdx.x; j < M; j += kThreads) {
     const long long g0 = i0 + 2 * j;
     V v;
@@ -245,10 +251,10 @@ __device__ void fft_window(FftSmem<T>& sm, const T* __restrict__ y, long long n,
 }
 
 // Doubled spectrum of the lag-reversed, scaled d, into sm.D.
-template <typename T>
-__device__ void fft_d_spectrum(FftSmem<T>& sm, const double* d, double d_scale, int p, const typename FftCfg<T>::V* tw) {
+template <typename T, int N = FftCfg<T>::N>
+__device__ void fft_d_spectrum(FftSmem<T, N>& sm, const double* d, double d_scale, int p, const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
+  constexpr int M = N / 2;
   for (int j = threadIdx.x; j < M; j += kThreads) {
     const int k0 = 2 * j, k1 = 2 * j + 1;
     V v;
@@ -276,12 +282,12 @@ __device__ __forceinline__ void acc_add(double2& s, V v) {
 // One tile of L rows starting at i0 of a product pass: u = X d - c u_old on the tile's rows (stored when u_new
 // is given), and W . conj(U) added into the CTA's spectrum sm.S. wt: the tile's doubled window spectrum
 // (M + 1 entries, global). Returns this thread's part of ||u||^2.
-template <typename T>
-__device__ double fft_tile(FftSmem<T>& sm, long long m, int L, const T* u_old, T* u_new, double coef, long long i0,
+template <typename T, int N = FftCfg<T>::N>
+__device__ double fft_tile(FftSmem<T, N>& sm, long long m, int L, const T* u_old, T* u_new, double coef, long long i0,
                            const typename FftCfg<T>::V* tw, const typename FftCfg<T>::V* __restrict__ wt,
                            bool lags) {
   using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
+  constexpr int M = N / 2;
   const T sc = (T)(1.0 / (8.0 * M));
   const int rows = (int)min((long long)L, m - i0);
   // X d = IRFFT(W . conj(D)) on rows [0, L)
@@ -334,12 +340,12 @@ __device__ double fft_tile(FftSmem<T>& sm, long long m, int L, const T* u_old, T
 //         last p_pad samples: sum_{j < p_pad} ext[j] ext[j + k], ext = (window tail, window head); the last
 //         tile also drops its pairs that start at rows >= m.
 //   else: S += W . conj(B), B the spectrum of the tile's row block (zero beyond its rows).
-template <typename T>
-__device__ void fft_gram_tile(FftSmem<T>& sm, const T* __restrict__ y, long long n, long long m, int L, int p_pad,
+template <typename T, int N = FftCfg<T>::N>
+__device__ void fft_gram_tile(FftSmem<T, N>& sm, const T* __restrict__ y, long long n, long long m, int L, int p_pad,
                               int nlag, long long i0, const typename FftCfg<T>::V* tw,
                               typename FftCfg<T>::V* __restrict__ wt, bool corr) {
   using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
+  constexpr int M = N / 2;
   const int rows = (int)min((long long)L, m - i0);
   if (corr) {
     for (int j = threadIdx.x; j < 2 * p_pad; j += kThreads) {
@@ -347,7 +353,7 @@ __device__ void fft_gram_tile(FftSmem<T>& sm, const T* __restrict__ y, long long
       sm.ext[j] = g < n ? y[g] : (T)0;
     }
   }
-  fft_window<T>(sm, y, n, i0, tw);
+  fft_window<T, N>(sm, y, n, i0, tw);
   for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
     V xf, xm;
     split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
@@ -389,10 +395,10 @@ __device__ void fft_gram_tile(FftSmem<T>& sm, const T* __restrict__ y, long long
 }
 
 // End of a CTA's tiles: tacc[k] += IRFFT(S)[k], k < nlag (S holds 4x the true spectrum: scale 1 / (8 M)).
-template <typename T>
-__device__ void fft_finish_lags(FftSmem<T>& sm, int nlag, const typename FftCfg<T>::V* tw) {
+template <typename T, int N = FftCfg<T>::N>
+__device__ void fft_finish_lags(FftSmem<T, N>& sm, int nlag, const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
-  constexpr int M = FftCfg<T>::N / 2;
+  constexpr int M = N / 2;
   for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
     V vf, vm, zf, zm;
     vf.x = (T)sm.S[f].x;
@@ -412,11 +418,19 @@ __device__ void fft_finish_lags(FftSmem<T>& sm, int nlag, const typename FftCfg<
   }
 }
 
-template <typename T>
+// Twiddle table of the N-point transforms: exp(-2 pi i t / N), t < N (float N = 4,096; float64 N = 2,048 or 4,096).
+template <typename T, int N>
+__device__ __forceinline__ const typename FftCfg<T>::V* fft_twiddles(const Work& w) {
+  using V = typename FftCfg<T>::V;
+  if (sizeof(T) == 4) return reinterpret_cast<const V*>(w.tw32);
+  return reinterpret_cast<const V*>(N == 4096 ? w.tw64x : w.tw64);
+}
+
+template <typename T, int N = FftCfg<T>::N>
 __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   using V = typename FftCfg<T>::V;
-  constexpr int N = FftCfg<T>::N;
   constexpr int M = N / 2;
+  constexpr int WS = FftCfg2<T, N>::WS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
   int tail = a.tail;
@@ -430,24 +444,24 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   }
   const int p_pad = a.p_pad, nlag = a.nlag;
   const int L = N - p_pad;
-  const V* tw = reinterpret_cast<const V*>(sizeof(T) == 8 ? a.w.tw64 : a.w.tw32);
+  const V* tw = fft_twiddles<T, N>(a.w);
   V* wspec = reinterpret_cast<V*>(sizeof(T) == 8 ? a.w.wspec64 : a.w.wspec32);
-  FftSmem<T> sm(smem_raw, p_pad);
+  FftSmem<T, N> sm(smem_raw, p_pad);
   const int tid = threadIdx.x;
   for (int k = tid; k < p_pad + 16; k += kThreads) sm.tacc[k] = 0.0;
   for (int f = tid; f <= M; f += kThreads) sm.S[f] = make_double2(0.0, 0.0);
   const long long ntiles = (a.m + L - 1) / L;
   const bool corr = a.gram && (long long)p_pad * nlag <= GramCfg<T>::kDirectMax;
-  if (!a.gram && blockIdx.x < ntiles) fft_d_spectrum<T>(sm, a.d, a.d_scale, a.p, tw);
+  if (!a.gram && blockIdx.x < ntiles) fft_d_spectrum<T, N>(sm, a.d, a.d_scale, a.p, tw);
   double n2 = 0.0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    V* wt = wspec + (size_t)tile * FftCfg<T>::WS;
-    if (a.gram) fft_gram_tile<T>(sm, a.y, a.n, a.m, L, p_pad, nlag, tile * L, tw, wt, corr);
-    else n2 += fft_tile<T>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt, nlag > 0);
+    V* wt = wspec + (size_t)tile * WS;
+    if (a.gram) fft_gram_tile<T, N>(sm, a.y, a.n, a.m, L, p_pad, nlag, tile * L, tw, wt, corr);
+    else n2 += fft_tile<T, N>(sm, a.m, L, u_old, u_new, coef, tile * L, tw, wt, nlag > 0);
   }
   __syncthreads();
-  if (blockIdx.x < ntiles && nlag > 0) fft_finish_lags<T>(sm, nlag, tw);
+  if (blockIdx.x < ntiles && nlag > 0) fft_finish_lags<T, N>(sm, nlag, tw);
   __syncthreads();
   const double n2_cta = block_sum(n2, sm.scratch);
   for (int k = tid; k < nlag; k += kThreads) a.w.part_t[(size_t)blockIdx.x * p_pad + k] = sm.tacc[k];
@@ -459,26 +473,26 @@ __global__ void __launch_bounds__(kThreads, 3) fft_pass_kernel(PassArgs<T> a) {
   run_tail<T>(tail, a.w, a.gram, nlag, sm.tacc, n2_all, sm.scratch, a.out_t, a.out_n2);
 }
 
-template <typename T>
+template <typename T, int N = FftCfg<T>::N>
 static size_t fft_pass_smem(int p_pad) {
-  return FftSmem<T>::bytes(p_pad);
+  return FftSmem<T, N>::bytes(p_pad);
 }
 
 // Doubled window spectra of every tile of a series (tiles of L = N - p_pad rows), for passes whose Gram pass did
 // not form them (another precision's Gram pass, or a single product pass): y does not change between passes.
-template <typename T>
+template <typename T, int N = FftCfg<T>::N>
 __global__ void __launch_bounds__(kThreads) spectrum_kernel(const T* __restrict__ y, long long n, long long m, int L,
                                                            typename FftCfg<T>::V* __restrict__ out,
                                                            const typename FftCfg<T>::V* tw) {
   using V = typename FftCfg<T>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int M = FftCfg<T>::N / 2;
-  FftSmem<T> sm(smem_raw, 0);
+  constexpr int M = N / 2;
+  FftSmem<T, N> sm(smem_raw, 0);
   const long long ntiles = (m + L - 1) / L;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
-    fft_window<T>(sm, y, n, tile * L, tw);
-    V* wt = out + (size_t)tile * FftCfg<T>::WS;
+    fft_window<T, N>(sm, y, n, tile * L, tw);
+    V* wt = out + (size_t)tile * FftCfg2<T, N>::WS;
     for (int f = threadIdx.x; f <= M / 2; f += kThreads) {
       V xf, xm;
       split2<V, T>(sm.A[pix(f)], sm.A[pix((M - f) & (M - 1))], tw[f], xf, xm);
@@ -593,6 +607,15 @@ __global__ void __launch_bounds__(kThreads) batch_dspec_kernel(const BatchSeries
 // global memory (each thread owns its bins: no atomics); the CTA transforms its sum back once, at its end.
 constexpr int kFft32Flush = 16;
 
+// t * exp(-+2 pi i r / 8) (INV: +) for r = 1, 2, 3, without products by 0 or 1 (h = 1/sqrt(2)).
+template <bool INV, int r>
+__device__ __forceinline__ float2 mul_e8(float2 t) {
+  const float h = 0.70710678118654752f;
+  if (r == 1) return INV ? make_float2(h * (t.x - t.y), h * (t.x + t.y)) : make_float2(h * (t.x + t.y), h * (t.y - t.x));
+  if (r == 2) return INV ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+  return INV ? make_float2(-h * (t.x + t.y), h * (t.x - t.y)) : make_float2(h * (t.y - t.x), -h * (t.x + t.y));
+}
+
 __device__ __forceinline__ int fft32_j(int tid) {
   const int w = tid >> 5, l = tid & 31;
   const int a = 16 * w + (l & 15);
@@ -669,15 +692,13 @@ __device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float
     b[r] = bufA[pix(j + 256 + 512 * r)];
   }
   // twiddles of butterfly j + 256: those of j times exp(-+2 pi i r / 8)
-  const float h = 0.70710678118654752f;
 #pragma unroll
   for (int r = 1; r < 4; ++r) {
     float2 ta = tw[2 * r * j];
     if (INV) ta.y = -ta.y;
-    const float2 e8 = r == 1 ? make_float2(h, INV ? h : -h) : r == 2 ? make_float2(0.f, INV ? 1.f : -1.f)
-                                                                     : make_float2(-h, INV ? h : -h);
+    const float2 tb = r == 1 ? mul_e8<INV, 1>(ta) : r == 2 ? mul_e8<INV, 2>(ta) : mul_e8<INV, 3>(ta);
     a[r] = cmul(a[r], ta);
-    b[r] = cmul(b[r], cmul(ta, e8));
+    b[r] = cmul(b[r], tb);
   }
   dft_small<float2, float, 4>(a, INV);
   dft_small<float2, float, 4>(b, INV);
@@ -688,13 +709,18 @@ __device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float
   }
 }
 
-// w^f for f = j + 256 q (N = 4,096): w^j exp(-i pi q / 8), one table entry and a product with a constant.
+// w^f for f = j + 256 q (N = 4,096): w^j exp(-i pi q / 8), one table entry and a product with a constant (for
+// even q a multiple of exp(-i pi / 4): no products by 0 or 1).
 __device__ __forceinline__ float2 fft32_twf(float2 base, int q) {
-  const float cq[8] = {1.0f, 0.92387953251128676f, 0.70710678118654752f, 0.38268343236508977f,
-                       0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128676f};
-  const float sq[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128676f,
-                       1.0f, 0.92387953251128676f, 0.70710678118654752f, 0.38268343236508977f};
-  return q == 0 ? base : cmul(base, make_float2(cq[q], -sq[q]));
+  if (q == 0) return base;
+  if (q == 2) return mul_e8<false, 1>(base);
+  if (q == 4) return mul_e8<false, 2>(base);
+  if (q == 6) return mul_e8<false, 3>(base);
+  const float c = q == 1 ? 0.92387953251128676f : q == 3 ? 0.38268343236508977f : q == 5 ? -0.38268343236508977f
+                                                                                            : -0.92387953251128676f;
+  const float sn = q == 1 ? 0.38268343236508977f : q == 3 ? 0.92387953251128676f : q == 5 ? 0.92387953251128676f
+                                                                                           : 0.38268343236508977f;
+  return cmul(base, make_float2(c, -sn));
 }
 
 // 2Z[f] of the packed input of an inverse transform from the doubled half spectrum V at bins f and M - f (merge2).
@@ -730,12 +756,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
-// Wait for the phase of parity `parity` of bar to complete, polling at most kMbarPolls times (each poll suspends
-// for up to about a microsecond); false if it gave up.
+// Wait for the phase of parity `parity` of bar to complete, polling at most `polls` times (each poll suspends for
+// up to about a microsecond); false if it gave up.
 constexpr int kMbarPolls = 1 << 21;
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int polls = kMbarPolls) {
   const unsigned a = smem_addr(bar);
-  for (int i = 0; i < kMbarPolls; ++i) {
+  for (int i = 0; i < polls; ++i) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, 1000;\n\tselp.u32 %0, 1, 0, q;\n\t}"
@@ -810,7 +836,11 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
   __syncthreads();
   const long long ntiles = (a.m + L - 1) / L;
   double n2 = 0.0;
-  bool failed = false;              // a wait gave up (this thread)
+  // a wait that gives up marks the thread failed: it waits no more, and thread 0 issues no further copy (a buffer
+  // whose copy may still be landing is never the target of another), so the rest of the launch runs on stale data
+  // and ends; the host reads the flag and reports TOLS_ERR_DEVICE_TIMEOUT
+  const int polls = a.wait_polls > 0 ? a.wait_polls : a.wait_polls < 0 ? 0 : kMbarPolls;
+  bool failed = false;
   unsigned iss_w0 = 0u, iss_w1 = 0u, iss_u = 0u;   // thread 0: copies issued on bar[0], bar[1], bar[2]
   // u_old rows of a tile that arrive by the bulk copy (a multiple of 4 rows; the rest are read directly)
   auto u_bytes = [&](long long t) -> unsigned {
@@ -853,7 +883,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       if (q == 0 && j == 0) sm.D[M] = xm;
     }
     __syncthreads();     // D complete; sm.A / sm.B free for the tiles
-    V Sq[8], Sm = make_float2(0.f, 0.f);
+    V Sq[8], Sm = make_float2(0.f, 0.f), nnq = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 8; ++q) Sq[q] = make_float2(0.f, 0.f);
     double2* sacc = reinterpret_cast<double2*>(a.w.sacc32) + (size_t)blockIdx.x * (M + 1);
@@ -875,6 +905,8 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
         sacc[M] = s;
         Sm = make_float2(0.f, 0.f);
       }
+      n2 += (double)nnq.x + (double)nnq.y;
+      nnq = make_float2(0.f, 0.f);
       first_flush = false;
       pending = 0;
     };
@@ -886,7 +918,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       const long long i0 = tile * L;
       const int rows = (int)lmin((long long)L, a.m - i0);
       const long long nt = tile + gridDim.x;
-      if (!failed && !mbar_wait(&sm.bar[b], (kw >> 1) & 1u)) failed = true;
+      if (!failed && !mbar_wait(&sm.bar[b], (kw >> 1) & 1u, polls)) failed = true;
       const V* wt = sm.W + b * WS;
       // X d = IRFFT(W . conj(D)) on the tile's rows
 #pragma unroll
@@ -897,13 +929,13 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
       // past the first barrier every thread is done with the other spectrum buffer (the previous tile)
       fft32_2048<true>(z, j, sm.A, sm.B, tw, [&] {
-        if (tid == 0 && nt < ntiles) issue_w(nt, b ^ 1);
+        if (tid == 0 && !failed && nt < ntiles) issue_w(nt, b ^ 1);
       });
       // rows 2i, 2i + 1 of u_old for the thread's points i = j + 256 r (tile offsets are even: L is)
       const unsigned ub = u_bytes(tile);
       const int rows_al = (int)(ub / sizeof(float));
       if (ub) {
-        if (!failed && !mbar_wait(&sm.bar[2], ku & 1u)) failed = true;
+        if (!failed && !mbar_wait(&sm.bar[2], ku & 1u, polls)) failed = true;
         ++ku;
       }
       V uo[8];
@@ -920,34 +952,33 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
           }
         }
       }
-      // u = X d - c u_old on the tile's rows, zero elsewhere; u_new stored
-      float nn = 0.f;
+      // u = X d - c u_old on the tile's rows, zero elsewhere; u_new stored; ||u||^2 summed in float over the
+      // flush window, per lane pair
+      const float2 sc2 = make_float2(sc, sc), mc2 = make_float2(-c, -c);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int r0 = 2 * (j + 256 * r);
-        float u0 = 0.f, u1 = 0.f;
-        if (r0 < rows) u0 = u_old ? fmaf(-c, uo[r].x, z[r].x * sc) : z[r].x * sc;
-        if (r0 + 1 < rows) u1 = u_old ? fmaf(-c, uo[r].y, z[r].y * sc) : z[r].y * sc;
+        float2 u = __fmul2_rn(z[r], sc2);
+        if (u_old) u = __ffma2_rn(uo[r], mc2, u);
+        if (r0 >= rows) u.x = 0.f;
+        if (r0 + 1 >= rows) u.y = 0.f;
         if (u_new) {
-          if (r0 + 1 < rows) *reinterpret_cast<V*>(u_new + i0 + r0) = make_float2(u0, u1);
-          else if (r0 < rows) u_new[i0 + r0] = u0;
+          if (r0 + 1 < rows) *reinterpret_cast<V*>(u_new + i0 + r0) = u;
+          else if (r0 < rows) u_new[i0 + r0] = u.x;
         }
-        nn = fmaf(u0, u0, fmaf(u1, u1, nn));
-        z[r] = make_float2(u0, u1);
+        nnq = __ffma2_rn(u, u, nnq);
+        z[r] = u;
       }
-      n2 += (double)nn;
       // S += W . conj(U), U the doubled half spectrum of u; past the first barrier u_old's buffer is free
       fft32_2048<false>(z, j, sm.B, sm.A, tw, [&] {
-        if (tid == 0 && nt < ntiles) issue_u(nt);
+        if (tid == 0 && !failed && nt < ntiles) issue_u(nt);
       });
       fft32_partner(z, pv, j);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         V xm;
         const V x = fft32_split(z[q], pv[q], fft32_twf(twj, q), (q == 0 && j == 0) ? &xm : nullptr);
-        const V t = cmulc(wt[j + 256 * q], x);
-        Sq[q].x += t.x;
-        Sq[q].y += t.y;
+        Sq[q] = __fadd2_rn(Sq[q], cmulc(wt[j + 256 * q], x));
         if (q == 0 && j == 0) {
           const V tm = cmulc(wt[M], xm);
           Sm.x += tm.x;
@@ -983,7 +1014,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
     }
   }
   if (tid == 0) {
-    // every copy this CTA issued has completed before it leaves (waits bounded like the others)
+    // every copy this CTA issued has completed before it leaves (waits bounded, at the full limit)
     if (iss_w0 && !mbar_wait(&sm.bar[0], (iss_w0 - 1) & 1u)) failed = true;
     if (iss_w1 && !mbar_wait(&sm.bar[1], (iss_w1 - 1) & 1u)) failed = true;
     if (iss_u && !mbar_wait(&sm.bar[2], (iss_u - 1) & 1u)) failed = true;

@@ -115,6 +115,7 @@ struct Work {
   DevState* st;
   const void* tw32;       // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (float2)
   const void* tw64;       // FFT twiddles exp(-2 pi i t / 2048), t < 2048 (double2)
+  const void* tw64x;      // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (double2): float64 passes with N = 4,096
   void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
   void* wspec64;          // the same for the float64 FFT tiles
   void* sacc32;           // (float FFT passes) per-CTA float64 sums of W . conj(U): [kMaxGrid][N/2 + 1] double2
@@ -143,7 +144,10 @@ struct PassArgs {
   int check_done;         // 1: return at once when w.st->done is set
   int* worklog;           // nullable: the tail writes 1 + tail + 5 * (T == double) into worklog[work_slot]
   int work_slot;
-  int fft;                // 1: overlap-save FFT products (fft_pass_kernel) instead of the direct ones
+  int fft;                // 0: direct products; N: overlap-save FFT products of length N (float 4,096; float64
+                          // 2,048 or 4,096)
+  int wait_polls;         // poll limit of the kernel's waits on its own bulk copies (0: the default, about 2 s;
+                          // negative: none, every such wait gives up at once)
 };
 
 // One series of a batch (device array). Its Work points at the series' own slices of the batch buffers; its
@@ -188,13 +192,13 @@ __host__ __device__ constexpr size_t batch_fft_spectra_doubles(long long m, int 
 
 // Launch helpers (tols_kernels.cu).
 cudaError_t smem_opt_in(const void* fn, int bytes);   // per-device dynamic shared-memory opt-in, set once
-size_t pass_smem_bytes(int is_double, int p_pad, int fft = 0);
-const void* fft_kernel_ptr(int is_double);
-int fft_size(int is_double);              // N of the real FFT per tile (float 4096, double 2048)
-size_t fft_spectra_bytes(int is_double, long long m, int p_pad);
+size_t pass_smem_bytes(int is_double, int p_pad, int nfft = 0);   // nfft: 0 (direct products) or the FFT length
+const void* fft_kernel_ptr(int is_double, int nfft);
+int fft_size(int is_double);              // default N of the real FFT per tile (float 4096, double 2048)
+size_t fft_spectra_bytes(int is_double, long long m, int p_pad, int nfft);
 size_t fft32_sum_bytes();                 // the float FFT pass's per-CTA float64 sum buffer (Work::sacc32)
 cudaError_t launch_spectra(int is_double, const void* y, long long n, long long m, int p_pad, void* out,
-                           const void* tw, int grid, cudaStream_t s);
+                           const void* tw, int grid, cudaStream_t s, int nfft);
 int pass_tile_rows(int is_double);
 const void* pass_kernel_ptr(int is_double);
 template <typename T>

@@ -880,27 +880,42 @@ static size_t pass_smem(int p_pad) {
   return b;
 }
 
+// FFT length of a pass: PassArgs::fft is 0 (direct products) or N (1 also means the precision's default N).
+template <typename T>
+static int pass_nfft(const PassArgs<T>& a) { return a.fft == 0 ? 0 : a.fft == 1 ? FftCfg<T>::N : a.fft; }
+
 template <typename T>
 cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
-  cudaError_t e = smem_opt_in(a.fft ? (const void*)fft_pass_kernel<T> : (const void*)pass_kernel<T>, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  const long long rows_per_tile = a.fft ? (long long)(FftCfg<T>::N - a.p_pad) : (long long)TileCfg<T>::TILE;
+  const int nfft = pass_nfft(a);
+  if (nfft && nfft != FftCfg<T>::N && !(sizeof(T) == 8 && nfft == 4096)) return cudaErrorInvalidValue;
+  const long long rows_per_tile = nfft ? (long long)(nfft - a.p_pad) : (long long)TileCfg<T>::TILE;
+  if (rows_per_tile < 1) return cudaErrorInvalidValue;
   const long long ntiles = (a.m + rows_per_tile - 1) / rows_per_tile;
   int g = (int)lmin((long long)grid, ntiles);
   if (g < 1) g = 1;
+  cudaError_t e;
   if constexpr (sizeof(T) == 4) {
     // float product passes take the register-blocked kernel, whose inputs arrive by bulk copies: 16-byte aligned
     // u vectors and spectra, and its float64 sum buffer
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.u_old) | reinterpret_cast<uintptr_t>(a.u_new) |
                            reinterpret_cast<uintptr_t>(a.w.wspec32)) & 15) == 0;
-    if (a.fft && !a.gram && a.nlag > 0 && aligned && a.w.sacc32 && a.w.wspec32) {
+    if (nfft && !a.gram && a.nlag > 0 && aligned && a.w.sacc32 && a.w.wspec32) {
       e = smem_opt_in((const void*)fft32_pass_kernel, 200 * 1024);
       if (e != cudaSuccess) return e;
       fft32_pass_kernel<<<g, kThreads, fft32_pass_smem(a.p_pad), s>>>(a);
       return cudaGetLastError();
     }
+  } else {
+    if (nfft == 4096) {
+      e = smem_opt_in((const void*)fft_pass_kernel<double, 4096>, 200 * 1024);
+      if (e != cudaSuccess) return e;
+      fft_pass_kernel<double, 4096><<<g, kThreads, fft_pass_smem<double, 4096>(a.p_pad), s>>>(a);
+      return cudaGetLastError();
+    }
   }
-  if (a.fft) fft_pass_kernel<T><<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
+  e = smem_opt_in(nfft ? (const void*)fft_pass_kernel<T> : (const void*)pass_kernel<T>, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  if (nfft) fft_pass_kernel<T><<<g, kThreads, fft_pass_smem<T>(a.p_pad), s>>>(a);
   else pass_kernel<T><<<g, kThreads, pass_smem<T>(a.p_pad), s>>>(a);
   return cudaGetLastError();
 }
@@ -908,44 +923,49 @@ cudaError_t launch_pass(const PassArgs<T>& a, int grid, cudaStream_t s) {
 template cudaError_t launch_pass<float>(const PassArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_pass<double>(const PassArgs<double>&, int, cudaStream_t);
 
-size_t pass_smem_bytes(int is_double, int p_pad, int fft) {
-  if (fft) return is_double ? fft_pass_smem<double>(p_pad) : fft32_pass_smem(p_pad);
+size_t pass_smem_bytes(int is_double, int p_pad, int nfft) {
+  if (nfft) {
+    if (!is_double) return fft32_pass_smem(p_pad);
+    return nfft == 4096 ? fft_pass_smem<double, 4096>(p_pad) : fft_pass_smem<double>(p_pad);
+  }
   return is_double ? pass_smem<double>(p_pad) : pass_smem<float>(p_pad);
 }
-// the kernel whose occupancy sizes the grid of FFT passes (float: the register-blocked kernel)
-const void* fft_kernel_ptr(int is_double) {
-  return is_double ? (const void*)fft_pass_kernel<double> : (const void*)fft32_pass_kernel;
+// the kernel whose occupancy sizes the grid of FFT passes of length nfft (float: the register-blocked kernel)
+const void* fft_kernel_ptr(int is_double, int nfft) {
+  if (!is_double) return (const void*)fft32_pass_kernel;
+  return nfft == 4096 ? (const void*)fft_pass_kernel<double, 4096> : (const void*)fft_pass_kernel<double>;
 }
 size_t fft32_sum_bytes() { return sizeof(double2) * (size_t)kMaxGrid * (FftCfg<float>::N / 2 + 1); }
 int fft_size(int is_double) { return is_double ? FftCfg<double>::N : FftCfg<float>::N; }
 
-template <typename T>
+template <typename T, int N>
 static size_t spectra_bytes(long long m, int p_pad) {
-  constexpr int N = FftCfg<T>::N;
   const long long L = N - p_pad;
-  return sizeof(typename FftCfg<T>::V) * (size_t)((m + L - 1) / L) * FftCfg<T>::WS;
+  return sizeof(typename FftCfg<T>::V) * (size_t)((m + L - 1) / L) * FftCfg2<T, N>::WS;
 }
-size_t fft_spectra_bytes(int is_double, long long m, int p_pad) {
-  return is_double ? spectra_bytes<double>(m, p_pad) : spectra_bytes<float>(m, p_pad);
+size_t fft_spectra_bytes(int is_double, long long m, int p_pad, int nfft) {
+  if (!is_double) return spectra_bytes<float, 4096>(m, p_pad);
+  return nfft == 4096 ? spectra_bytes<double, 4096>(m, p_pad) : spectra_bytes<double, 2048>(m, p_pad);
 }
 
-template <typename T>
+template <typename T, int N>
 static cudaError_t launch_spectra_t(const T* y, long long n, long long m, int p_pad, void* out, const void* tw,
                                     int grid, cudaStream_t s) {
   using V = typename FftCfg<T>::V;
-  const size_t smem = round16(sizeof(V) * 2 * (size_t)FftCfg2<T>::PADDED);   // the work arrays A, B only
-  cudaError_t e = smem_opt_in((const void*)spectrum_kernel<T>, 200 * 1024);
+  const size_t smem = round16(sizeof(V) * 2 * (size_t)FftCfg2<T, N>::PADDED);   // the work arrays A, B only
+  cudaError_t e = smem_opt_in((const void*)spectrum_kernel<T, N>, 200 * 1024);
   if (e != cudaSuccess) return e;
-  const int L = FftCfg<T>::N - p_pad;
+  const int L = N - p_pad;
   const long long ntiles = (m + L - 1) / L;
   const int g = (int)lmin((long long)grid, ntiles);
-  spectrum_kernel<T><<<g < 1 ? 1 : g, kThreads, smem, s>>>(y, n, m, L, (V*)out, (const V*)tw);
+  spectrum_kernel<T, N><<<g < 1 ? 1 : g, kThreads, smem, s>>>(y, n, m, L, (V*)out, (const V*)tw);
   return cudaGetLastError();
 }
 cudaError_t launch_spectra(int is_double, const void* y, long long n, long long m, int p_pad, void* out,
-                           const void* tw, int grid, cudaStream_t s) {
-  return is_double ? launch_spectra_t<double>((const double*)y, n, m, p_pad, out, tw, grid, s)
-                   : launch_spectra_t<float>((const float*)y, n, m, p_pad, out, tw, grid, s);
+                           const void* tw, int grid, cudaStream_t s, int nfft) {
+  if (!is_double) return launch_spectra_t<float, 4096>((const float*)y, n, m, p_pad, out, tw, grid, s);
+  return nfft == 4096 ? launch_spectra_t<double, 4096>((const double*)y, n, m, p_pad, out, tw, grid, s)
+                      : launch_spectra_t<double, 2048>((const double*)y, n, m, p_pad, out, tw, grid, s);
 }
 int pass_tile_rows(int is_double) { return is_double ? TileCfg<double>::TILE : TileCfg<float>::TILE; }
 const void* pass_kernel_ptr(int is_double) {

@@ -119,11 +119,32 @@ def test_batched_device_equals_host_batched(tols, ctx):
         off += p
 
 
-def test_batch_products_by_order(tols, ctx, prec):
-    # series with pad16(p + 1) >= 32 take the overlap-save float64 FFT products and the others the direct ones, in
-    # both precisions (a mixed series runs its Gram pass and checks in float64 too)
-    ys, ps = _batch(12, 43, 5_000, 40_000, 2, 60)
-    phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(ctx, ys, ps, 1e-12)
-    for p, info in zip(ps, infos):
-        want = tols.TOLS_PRODUCT_FFT if ((p + 1 + 15) // 16) * 16 >= 32 else tols.TOLS_PRODUCT_DIRECT
-        assert info["product_used"] == want, (p, info)
+@pytest.mark.parametrize("product", ["auto", "fft", "direct"])
+def test_batch_products_by_order(tols, prec, product):
+    """Products per batched series: DIRECT forces the direct products; FFT takes the overlap-save float64 FFT
+    products (N = 2,048) from pad16(p + 1) = 32 up; AUTO the choice timed per order class, which every context of
+    the process shares (a second context plans alike). Whichever the choice, every series matches the oracle (a
+    mixed series runs its Gram pass and checks in float64 too)."""
+    ys, ps = _batch(12, 43, 5_000, 40_000, 2, 200)
+    P = tols.TOLS_FP64 if prec == "fp64" else tols.TOLS_MIXED
+    prod = {"auto": tols.TOLS_PRODUCT_AUTO, "fft": tols.TOLS_PRODUCT_FFT, "direct": tols.TOLS_PRODUCT_DIRECT}[product]
+    with tols.Context(precision=P, product=prod) as c:
+        phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(c, ys, ps, 1e-12)
+    with tols.Context(precision=P, product=prod) as c:
+        _, _, infos2, _ = tols.toeplitz_ols_solve_batched(c, ys, ps, 1e-12)
+    tol = 1e-8 if prec == "fp64" else 1e-6
+    for k, (y, p, info) in enumerate(zip(ys, ps, infos)):
+        pp = ((p + 1 + 15) // 16) * 16
+        if product == "direct":
+            assert info["product_used"] == tols.TOLS_PRODUCT_DIRECT, (p, info)
+        elif product == "fft":
+            want = tols.TOLS_PRODUCT_FFT if pp >= 32 else tols.TOLS_PRODUCT_DIRECT
+            assert info["product_used"] == want, (p, info)
+        else:
+            assert info["product_used"] in (tols.TOLS_PRODUCT_FFT, tols.TOLS_PRODUCT_DIRECT), (p, info)
+            assert infos2[k]["product_used"] == info["product_used"], (p, info, infos2[k])
+        assert info["nfft"] == (2048 if info["product_used"] == tols.TOLS_PRODUCT_FFT else 0), info
+        sol = oracle.ols_qr(y, p)
+        if sol.forward_error_bound() <= tol / 10:
+            assert coef_rel_err(phis[k], sol.phi) <= tol, (p, info)
+        assert rn[k] == pytest.approx(sol.rnorm, rel=1e-11)

@@ -1004,7 +1004,8 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   if ((rc = ensure(ctx, ctx->b_mats, B.mat_bytes))) return rc;
   if ((rc = ensure(ctx, ctx->b_state, sizeof(DevState) * cnt))) return rc;
   if ((rc = ensure(ctx, ctx->b_series, sizeof(BatchSeries) * cnt))) return rc;
-  if ((rc = ensure(ctx, ctx->b_tiles, sizeof(int) * (size_t)(B.tiles_f + B.tiles_d + B.tiles_x)))) return rc;
+  const size_t tiles_bytes = align_up(sizeof(int) * (size_t)(B.tiles_f + B.tiles_d + B.tiles_x), 16);
+  if ((rc = ensure(ctx, ctx->b_tiles, tiles_bytes + 4 * sizeof(long long)))) return rc;
   if (B.spec_doubles && (rc = ensure(ctx, ctx->b_spec, sizeof(double) * B.spec_doubles))) return rc;
   (void)fresh_cnt;
   // counters (and the done counter after them) start at zero; every pass leaves the counters at zero
@@ -1096,6 +1097,9 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   CK(cudaMemcpyAsync(ctx->b_series.p, hs.data(), sizeof(BatchSeries) * cnt, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_state.p, states.data(), sizeof(DevState) * cnt, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
+  long long* d_live = (long long*)((char*)ctx->b_tiles.p + tiles_bytes);
+  long long h_live[3] = {B.tiles_f, B.tiles_d, B.tiles_x};
+  CK(cudaMemcpyAsync(d_live, h_live, sizeof h_live, cudaMemcpyHostToDevice, ctx->stream));
   BatchArgs a;
   memset(&a, 0, sizeof a);
   a.series = d_series;
@@ -1106,6 +1110,7 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   a.tiles_d = B.tiles_d;
   a.tiles_x = B.tiles_x;
   a.done_count = d_done;
+  a.live = d_live;
   const int gf = batch_grid(ctx, 0, B.p_pad_max), gd = batch_grid(ctx, 1, B.p_pad_max);
 
   // setup: float copy, Gram lag sums, preconditioner, LSQR start
@@ -1160,6 +1165,40 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     }
   }
   unsigned int* h_done = (unsigned int*)ctx->h_worklog;  // pinned, reused as landing slots: done, in float sweeps
+  // Compaction of the tile lists to the series not yet done: the per-series tile ranges stay contiguous and in
+  // order (a series' partial-sum slots are indexed by its local tile or unit number, tile - tile0), only each
+  // series' first index (tile0_*) moves. The kernels read the list lengths from d_live at run time, so the
+  // captured graphs stay valid.
+  long long listed = cnt;
+  auto compact_lists = [&]() -> int {
+    CK(cudaMemcpyAsync(states.data(), ctx->b_state.p, sizeof(DevState) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    long long nf = 0, nd = 0, nx = 0, na = 0;
+    for (int k = 0; k < cnt; ++k) {
+      const DevState& st = states[k];
+      if (st.done || st.phase == PH_DONE) continue;
+      ++na;
+      hs[k].tile0_f = nf;
+      hs[k].tile0_d = nd;
+      hs[k].tile0_x = nx;
+      for (long long t = 0; t < B.ntf[k]; ++t) tiles[(size_t)(nf + t)] = k;
+      for (long long t = 0; t < B.ntd[k]; ++t) tiles[(size_t)(B.tiles_f + nd + t)] = k;
+      for (long long t = 0; t < B.ntx[k]; ++t) tiles[(size_t)(B.tiles_f + B.tiles_d + nx + t)] = k;
+      nf += B.ntf[k];
+      nd += B.ntd[k];
+      nx += B.ntx[k];
+    }
+    CK(cudaMemcpyAsync(ctx->b_series.p, hs.data(), sizeof(BatchSeries) * cnt, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->b_tiles.p, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    h_live[0] = nf;
+    h_live[1] = nd;
+    h_live[2] = nx;
+    CK(cudaMemcpyAsync(d_live, h_live, sizeof h_live, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    listed = na;
+    return TOLS_OK;
+  };
   int max_iter_all = 0;
   for (int k = 0; k < cnt; ++k) max_iter_all = std::max(max_iter_all, states[k].max_iter);
   const long long max_rounds = ((long long)(max_iter_all + 4) * (max_sweeps + 2) * 2) / burst + 16;
@@ -1180,6 +1219,10 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     if (h_done[0] >= (unsigned)cnt) break;
     if (round > max_rounds) { out = fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "batched solve did not finish"); break; }
     with_float = mixed && h_done[1] > 0;
+    // once half of the series still listed are done, the lists keep only the unfinished ones: a pass launch over
+    // the full lists would spend its time skipping finished series' tiles
+    const long long active = (long long)cnt - h_done[0];
+    if (active * 2 <= listed && (out = compact_lists()) != TOLS_OK) break;
   }
   for (auto x : exec)
     if (x) cudaGraphExecDestroy(x);

@@ -516,7 +516,8 @@ __global__ void __launch_bounds__(kThreads, 3) batch_fft_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_last;
   const int tid = threadIdx.x;
-  for (long long g = blockIdx.x; g < a.tiles_x; g += gridDim.x) {
+  const long long tiles_x = a.live ? a.live[2] : a.tiles_x;
+  for (long long g = blockIdx.x; g < tiles_x; g += gridDim.x) {
     const int sidx = a.tile_series_x[g];
     const BatchSeries& S = a.series[sidx];
     const Work& w = S.w;

@@ -168,6 +168,9 @@ struct BatchArgs {
   long long tiles_x;            // units in that list
   int gram;                     // 1: Gram lag-sum pass (TAIL_GRAM) instead of a solver pass
   unsigned int* done_count;     // incremented once per series that reaches PH_DONE
+  const long long* live;        // (nullable) device counts {tiles_f, tiles_d, tiles_x} of the lists as they are now:
+                                // the host compacts the lists to the unfinished series between graph replays, so
+                                // a kernel reads its count at run time (tiles_f, tiles_d, tiles_x size the grid)
 };
 
 // Batched series with p_pad(p + 1) in [32, 1024) take the overlap-save float64 FFT products (N = 2,048, tiles of

@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, TileCfg<T>::MINB) batch_pass_kernel(
   __shared__ int s_last;
   __shared__ int s_skip;
   const int is_double = sizeof(T) == 8;
-  const long long total = is_double ? a.tiles_d : a.tiles_f;
+  const long long total = a.live ? a.live[is_double ? 1 : 0] : (is_double ? a.tiles_d : a.tiles_f);
   const int* tile_series = is_double ? a.tile_series_d : a.tile_series_f;
   const int tid = threadIdx.x;
   for (long long g = blockIdx.x; g < total; g += gridDim.x) {

@@ -4,11 +4,14 @@
 // machine. The host launches pass kernels; the last CTA of each pass performs the scalar step and writes
 // the next phase into DevState, so the host only polls a status word every few launches:
 //
-//   FP64  : Gram pass -> Cholesky preconditioner -> LSQR passes (float64) -> float64 check pass
-//           [-> LSQR on the residual -> check ...]
-//   MIXED : Gram pass (float products) -> Cholesky -> LSQR passes (float products, float64 scalars)
-//           -> float64 check pass -> correction solve (float products) -> float64 check pass -> ...
-//           Falls back to FP64 when the refinement stops contracting (kappa(X)^2 too large for float).
+//   FP64  : Gram pass (float64 products) -> preconditioner (Cholesky factor of the Gram matrix, or the R of sampled
+//           rows when that factor is not trusted) -> trusted factor: semi-normal-equation start
+//           phi0 = R^-1 R^-T X^T b; else LSQR passes from zero -> float64 check pass
+//           [-> LSQR on the stored residual -> check ...] until the ratio meets tol or a check stops improving
+//   MIXED : the same route; after a check that misses tol, while the factor is trusted and kappa(X) u32 <= 1e-2,
+//           the correction sweep uses float products (Golub-Kahan Bidiag 2 on the normal-equation correction,
+//           float64 scalars) -> float64 check pass -> ...; float64 LSQR sweeps otherwise, and a warm-started
+//           float64 repeat when the float sweeps stop contracting.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>

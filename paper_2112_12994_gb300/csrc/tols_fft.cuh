@@ -640,24 +640,34 @@ __device__ __forceinline__ void fft32_partner(const float2* v, float2* pv, int j
   }
 }
 
+// Per-thread base twiddles of the register-blocked transform (forward sign; the inverse conjugates them): the
+// second stage's w = exp(-2 pi i (j mod 8) / 64), the third's exp(-2 pi i (j mod 64) / 512) and the last stage's
+// exp(-2 pi i j / 2048). They depend on j only, so a thread reads them once per launch and forms every other
+// twiddle of its butterflies from them by products (each within a few ulp).
+struct Fft32Tw {
+  float2 s2, s3, s4;
+};
+__device__ __forceinline__ Fft32Tw fft32_base_twiddles(const float2* tw, int j) {
+  Fft32Tw t;
+  t.s2 = tw[64 * (j & 7)];
+  t.s3 = tw[8 * (j & 63)];
+  t.s4 = tw[2 * j];
+  return t;
+}
+
 // One Stockham radix-8 stage between shared buffers for the thread's butterfly j (stride 256): in[j + 256 r],
-// twiddles tw[ts r k] (k = j mod Ls), out[g Ln + k + Ls q].
-template <bool INV, int Ls, int TS>
-__device__ __forceinline__ void fft32_stage8(float2* z, int j, const float2* in, float2* out, const float2* tw) {
+// twiddles w^r (w the stage's base twiddle), out[g Ln + k + Ls q] with k = j mod Ls.
+template <bool INV, int Ls>
+__device__ __forceinline__ void fft32_stage8(float2* z, int j, const float2* in, float2* out, float2 w) {
   constexpr int Ln = Ls * 8;
   const int k = j & (Ls - 1), g = j / Ls;
 #pragma unroll
   for (int r = 0; r < 8; ++r) z[r] = in[pix(j + 256 * r)];
-  // twiddles w^r, r = 1..7, from three table entries (w, w^2, w^4) and four products: each is within a few ulp
   float2 t[8];
-  t[1] = tw[TS * k];
-  t[2] = tw[2 * TS * k];
-  t[4] = tw[4 * TS * k];
-  if (INV) {
-    t[1].y = -t[1].y;
-    t[2].y = -t[2].y;
-    t[4].y = -t[4].y;
-  }
+  t[1] = w;
+  if (INV) t[1].y = -t[1].y;
+  t[2] = cmul(t[1], t[1]);
+  t[4] = cmul(t[2], t[2]);
   t[3] = cmul(t[1], t[2]);
   t[5] = cmul(t[4], t[1]);
   t[6] = cmul(t[4], t[2]);
@@ -675,16 +685,16 @@ __device__ __forceinline__ void fft32_stage8(float2* z, int j, const float2* in,
 // after_first_sync() runs in every thread right after the first barrier (every thread has then left the code
 // before this call).
 template <bool INV, typename F>
-__device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float2* bufB, const float2* tw,
+__device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float2* bufB, const Fft32Tw& tw,
                                            F&& after_first_sync) {
   dft_small<float2, float, 8>(z, INV);
 #pragma unroll
   for (int q = 0; q < 8; ++q) bufA[pix(8 * j + q)] = z[q];
   __syncthreads();
   after_first_sync();
-  fft32_stage8<INV, 8, 64>(z, j, bufA, bufB, tw);
+  fft32_stage8<INV, 8>(z, j, bufA, bufB, tw.s2);
   __syncthreads();
-  fft32_stage8<INV, 64, 8>(z, j, bufB, bufA, tw);
+  fft32_stage8<INV, 64>(z, j, bufB, bufA, tw.s3);
   __syncthreads();
   float2 a[4], b[4];
 #pragma unroll
@@ -692,13 +702,16 @@ __device__ __forceinline__ void fft32_2048(float2* z, int j, float2* bufA, float
     a[r] = bufA[pix(j + 512 * r)];
     b[r] = bufA[pix(j + 256 + 512 * r)];
   }
-  // twiddles of butterfly j + 256: those of j times exp(-+2 pi i r / 8)
+  // twiddles w^r of butterfly j (w = exp(-+2 pi i j / 2048)); those of j + 256 times exp(-+2 pi i r / 8)
+  float2 ta[4];
+  ta[1] = tw.s4;
+  if (INV) ta[1].y = -ta[1].y;
+  ta[2] = cmul(ta[1], ta[1]);
+  ta[3] = cmul(ta[1], ta[2]);
 #pragma unroll
   for (int r = 1; r < 4; ++r) {
-    float2 ta = tw[2 * r * j];
-    if (INV) ta.y = -ta.y;
-    const float2 tb = r == 1 ? mul_e8<INV, 1>(ta) : r == 2 ? mul_e8<INV, 2>(ta) : mul_e8<INV, 3>(ta);
-    a[r] = cmul(a[r], ta);
+    const float2 tb = r == 1 ? mul_e8<INV, 1>(ta[r]) : r == 2 ? mul_e8<INV, 2>(ta[r]) : mul_e8<INV, 3>(ta[r]);
+    a[r] = cmul(a[r], ta[r]);
     b[r] = cmul(b[r], tb);
   }
   dft_small<float2, float, 4>(a, INV);
@@ -867,6 +880,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       issue_u(blockIdx.x);
     }
     const V twj = tw[j];
+    const Fft32Tw twb = fft32_base_twiddles(tw, j);
     V z[8], pv[8];
     // doubled spectrum of the lag-reversed, scaled d (point i = j + 256 r holds d entries 2i, 2i + 1)
 #pragma unroll
@@ -875,7 +889,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       z[r].x = k0 < a.p ? (float)(a.d_scale * a.d[a.p - 1 - k0]) : 0.f;
       z[r].y = k0 + 1 < a.p ? (float)(a.d_scale * a.d[a.p - 2 - k0]) : 0.f;
     }
-    fft32_2048<false>(z, j, sm.A, sm.B, tw, [] {});
+    fft32_2048<false>(z, j, sm.A, sm.B, twb, [] {});
     fft32_partner(z, pv, j);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -929,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
 #pragma unroll
       for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
       // past the first barrier every thread is done with the other spectrum buffer (the previous tile)
-      fft32_2048<true>(z, j, sm.A, sm.B, tw, [&] {
+      fft32_2048<true>(z, j, sm.A, sm.B, twb, [&] {
         if (tid == 0 && !failed && nt < ntiles) issue_w(nt, b ^ 1);
       });
       // rows 2i, 2i + 1 of u_old for the thread's points i = j + 256 r (tile offsets are even: L is)
@@ -971,7 +985,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
         z[r] = u;
       }
       // S += W . conj(U), U the doubled half spectrum of u; past the first barrier u_old's buffer is free
-      fft32_2048<false>(z, j, sm.B, sm.A, tw, [&] {
+      fft32_2048<false>(z, j, sm.B, sm.A, twb, [&] {
         if (tid == 0 && !failed && nt < ntiles) issue_u(nt);
       });
       fft32_partner(z, pv, j);
@@ -1004,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));
-      fft32_2048<true>(z, j, sm.A, sm.B, tw, [] {});
+      fft32_2048<true>(z, j, sm.A, sm.B, twb, [] {});
       const double scd = 1.0 / (8.0 * M);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {

@@ -594,7 +594,20 @@ int run_setup(tols_ctx* ctx, Work& w, bool mixed, bool no_precond, int fft = 0, 
   a.fft = fft;
   RUN(run_pass<double>(ctx, a, pass_grid_for(ctx, 1, pg, a.fft)));
   const int want = no_precond ? 0 : want_override >= 0 ? want_override : ctx->cfg.precond;
-  if (w.p >= kPclMinP) return precond_large(ctx, w, want, mixed);
+  if (w.p >= kPclMinP) {
+    // Orders whose Gram factor fits the one-CTA kernel's shared memory try that kernel first: one launch serves
+    // the common case of a trusted factor, where the tiled multi-CTA steps spend their time in launches and in
+    // host reads of the factorisation's report (AR(100), n = 2^22: 1.34 ms per solve with the tiled steps).
+    // An untrusted factor goes on to the multi-CTA path: more sampled rows, and a regularised QR.
+    if (want == TOLS_PRECOND_GRAM_CHOL && w.p <= kPrecondSmemP) {
+      RUN(run_small(ctx, 10, [&] { return launch_precond(w, 3, ctx->stream); }));
+      int trusted = 0;
+      CK(cudaMemcpyAsync(&trusted, &w.st->trusted, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (trusted) return TOLS_OK;
+    }
+    return precond_large(ctx, w, want, mixed);
+  }
   RUN(run_small(ctx, 10, [&] { return launch_precond(w, want, ctx->stream); }));
   return TOLS_OK;
 }
@@ -848,10 +861,11 @@ long long batch_units(long long m, int p, bool fx) {
 // products (N = 2,048, tiles of N - pad_p(p + 1) rows) or on the direct ones. DIRECT forces the direct products;
 // FFT / FFT4096 take the FFT from pad_p(p + 1) = 32 up. AUTO measures, once per process, device and class
 // pad_p(p + 1): one direct and one FFT pass (best of three launches each) over a synthetic series of
-// kBatchTuneRows rows of that order, and takes the FFT only where it is at least 5 % faster. The choice is kept
+// kBatchTuneRows rows of that order (enough tiles for several waves of CTAs, so that the passes run at their
+// steady rate), and takes the FFT only where it is at least 5 % faster. The choice is kept
 // for every context of the process, so a series' products, and so its result, do not depend on the context (or
 // server) that solved it. The float correction sweeps of mixed series use the direct float products.
-constexpr long long kBatchTuneRows = 1 << 18;
+constexpr long long kBatchTuneRows = 1 << 21;
 std::mutex g_batch_tune_mu;
 std::map<long long, int> g_batch_tune;   // key device * 4096 + pad_p(p + 1) -> 1 FFT, 0 direct
 
@@ -1309,6 +1323,7 @@ int batch_solve_all(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::ve
     DevState s2 = *ctx->h_state;
     s2.total_iter += s.total_iter;
     s2.sweeps += s.sweeps;
+    s2.fft = ctx->last_fft ? 1 : 0;     // the products of the single-series repeat (N = 2,048 at these orders)
     states[k] = s2;
     CK(cudaMemcpy(phi_host.data() + B.off_phi[k], d_phi, sizeof(double) * B.p[k], cudaMemcpyDeviceToHost));
     prec_used[k] = TOLS_FP64;

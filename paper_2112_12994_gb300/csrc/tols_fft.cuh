@@ -603,9 +603,11 @@ __global__ void __launch_bounds__(kThreads) batch_dspec_kernel(const BatchSeries
 // A tile's inputs from HBM — its window spectrum (16,400 bytes) and its rows of u_old — arrive by bulk copies
 // (cp.async.bulk, completion counted on an mbarrier) issued one tile ahead by thread 0: the spectrum into one of two
 // shared buffers while the previous tile still reads the other, u_old into one buffer as soon as the previous
-// tile's rows have been read. No thread waits on a global load of the main loop. The CTA's spectral sum
-// W . conj(U) is kept per thread in float over at most kFft32Flush tiles and then added to the CTA's float64 sum in
-// global memory (each thread owns its bins: no atomics); the CTA transforms its sum back once, at its end.
+// tile's rows have been read. No thread waits on a global load of the main loop. Twiddles: each thread reads the
+// base twiddle of each of its stages once per launch and forms the rest by products. The CTA's spectral sum
+// W . conj(U) is kept per thread in float over at most kFft32Flush tiles and then added to the CTA's running sum, a
+// float pair per bin in global memory (each thread owns its bins: no atomics); the CTA transforms its sum back once,
+// at its end.
 constexpr int kFft32Flush = 16;
 
 // t * exp(-+2 pi i r / 8) (INV: +) for r = 1, 2, 3, without products by 0 or 1 (h = 1/sqrt(2)).
@@ -899,28 +901,39 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
     }
     __syncthreads();     // D complete; sm.A / sm.B free for the tiles
     V Sq[8], Sm = make_float2(0.f, 0.f), nnq = make_float2(0.f, 0.f);
+    float n2h = 0.f, n2l = 0.f;    // this thread's ||u||^2, a float pair (TwoSum per flush)
 #pragma unroll
     for (int q = 0; q < 8; ++q) Sq[q] = make_float2(0.f, 0.f);
-    double2* sacc = reinterpret_cast<double2*>(a.w.sacc32) + (size_t)blockIdx.x * (M + 1);
+    // the CTA's running sum per bin as an unevaluated float pair {re, im, re lo, im lo}: each flush adds by Knuth's
+    // TwoSum, so the pair keeps about twice float's precision with float instructions only (a float64 add here
+    // costs a warp 64 issue cycles of GB300's FP64 pipe)
+    float4* sacc = reinterpret_cast<float4*>(a.w.sacc32) + (size_t)blockIdx.x * (M + 1);
     bool first_flush = true;
     int pending = 0;
+    auto two_sum_add = [](float4& s, float2 x) {
+      const float hx = s.x + x.x, bx = hx - s.x, ex = (s.x - (hx - bx)) + (x.x - bx);
+      const float hy = s.y + x.y, by = hy - s.y, ey = (s.y - (hy - by)) + (x.y - by);
+      s = make_float4(hx, hy, s.z + ex, s.w + ey);
+    };
     auto flush = [&]() {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        double2 s = first_flush ? make_double2(0.0, 0.0) : sacc[j + 256 * q];
-        s.x += (double)Sq[q].x;
-        s.y += (double)Sq[q].y;
+        float4 s = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : sacc[j + 256 * q];
+        two_sum_add(s, Sq[q]);
         sacc[j + 256 * q] = s;
         Sq[q] = make_float2(0.f, 0.f);
       }
       if (j == 0) {
-        double2 s = first_flush ? make_double2(0.0, 0.0) : sacc[M];
-        s.x += (double)Sm.x;
-        s.y += (double)Sm.y;
+        float4 s = first_flush ? make_float4(0.f, 0.f, 0.f, 0.f) : sacc[M];
+        two_sum_add(s, Sm);
         sacc[M] = s;
         Sm = make_float2(0.f, 0.f);
       }
-      n2 += (double)nnq.x + (double)nnq.y;
+      {
+        const float x = nnq.x + nnq.y, h = n2h + x, bb = h - n2h;
+        n2l += (n2h - (h - bb)) + (x - bb);
+        n2h = h;
+      }
       nnq = make_float2(0.f, 0.f);
       first_flush = false;
       pending = 0;
@@ -1004,17 +1017,18 @@ __global__ void __launch_bounds__(kThreads, 2) fft32_pass_kernel(PassArgs<float>
     }
     {
       if (pending) flush();
+      n2 = (double)n2h + (double)n2l;
       // tacc[k] = IRFFT(S)[k], k < nlag, from this thread's bins of the CTA's sum (S holds 4x the true spectrum:
       // scale 1 / (8 M))
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const double2 s = sacc[j + 256 * q];
-        z[q] = make_float2((float)s.x, (float)s.y);
+        const float4 s = sacc[j + 256 * q];
+        z[q] = make_float2(s.x + s.z, s.y + s.w);
       }
       fft32_partner(z, pv, j);
       if (j == 0) {
-        const double2 s = sacc[M];
-        pv[0] = make_float2((float)s.x, (float)s.y);
+        const float4 s = sacc[M];
+        pv[0] = make_float2(s.x + s.z, s.y + s.w);
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) z[q] = fft32_merge(z[q], pv[q], fft32_twf(twj, q));

@@ -39,6 +39,11 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
 // Round p up to the lag-chunk granularity used by the direct kernels.
 __host__ __device__ constexpr int pad_p(int p) { return (p + 15) & ~15; }
 
+// One-CTA preconditioner (precond_kernel): it factors in shared memory up to this order, leaving G in global memory
+// untouched. Its want_precond: 0 none, 1 the Gram factor (the sampled-row QR when that is not trusted), 2 the
+// sampled-row QR, 3 the Gram factor only (no QR; the caller reads DevState::trusted).
+constexpr int kPrecondSmemP = 112;
+
 // Sampled-row QR preconditioner: orders it serves and rows sampled per coefficient; its scratch (doubles).
 constexpr int kQrMaxP = 256;
 constexpr int kQrRowsPerP = 8;
@@ -118,7 +123,7 @@ struct Work {
   const void* tw64x;      // FFT twiddles exp(-2 pi i t / 4096), t < 4096 (double2): float64 passes with N = 4,096
   void* wspec32;          // doubled window spectra of the float FFT tiles ([tiles][N/2 + 1]; FFT passes only)
   void* wspec64;          // the same for the float64 FFT tiles
-  void* sacc32;           // (float FFT passes) per-CTA float64 sums of W . conj(U): [kMaxGrid][N/2 + 1] double2
+  void* sacc32;           // (float FFT passes) per-CTA sums of W . conj(U) as float pairs: [kMaxGrid][N/2 + 1] float4
   void* dspec64;          // (batched float64 FFT series) doubled spectrum of the lag-reversed d, N/2 + 1 entries
   unsigned int* f32_active;  // (batches, nullable) count of the batch's series in a float correction sweep
 };

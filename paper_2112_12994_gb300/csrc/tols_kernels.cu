@@ -935,7 +935,7 @@ const void* fft_kernel_ptr(int is_double, int nfft) {
   if (!is_double) return (const void*)fft32_pass_kernel;
   return nfft == 4096 ? (const void*)fft_pass_kernel<double, 4096> : (const void*)fft_pass_kernel<double>;
 }
-size_t fft32_sum_bytes() { return sizeof(double2) * (size_t)kMaxGrid * (FftCfg<float>::N / 2 + 1); }
+size_t fft32_sum_bytes() { return sizeof(float4) * (size_t)kMaxGrid * (FftCfg<float>::N / 2 + 1); }
 int fft_size(int is_double) { return is_double ? FftCfg<double>::N : FftCfg<float>::N; }
 
 template <typename T, int N>
@@ -1012,9 +1012,9 @@ const void* batch_kernel_ptr(int is_double) {
 // M = R^{-1} and M^T (float64 and float copies). One CTA; G is symmetric on entry.
 __device__ __forceinline__ double* scratch_vec(const Work& w) { return w.t; }  // w.t, w.g: 2 p_pad doubles
 
-// G and R^{-1} are worked on in shared memory when both fit (p <= kPrecondSmemP): the factorisation and the back
-// substitutions are chains of dependent read-modify-writes, which would wait on L2 round trips in global memory.
-constexpr int kPrecondSmemP = 112;
+// G and R^{-1} are worked on in shared memory when both fit (p <= kPrecondSmemP, tols_internal.cuh): the
+// factorisation and the back substitutions are chains of dependent read-modify-writes, which would wait on L2
+// round trips in global memory.
 
 // s / d by multiplication with magic = ceil(2^32 / d) = (2^32 - 1) / d + 1 (division by an invariant integer,
 // Granlund & Montgomery 1994): exact while s d < 2^32, integer instructions only (the general division
@@ -1468,7 +1468,7 @@ __device__ void precond_body(const Work& w, int want_precond, double* smem) {
   // preconditioner. R from QR carries errors of order kappa u, not kappa^2 u, so LSQR on X R^{-1} converges in
   // a few tens of iterations up to kappa(X) ~ 1/u. The Gram factor stays if the sample is rank deficient.
   bool qr_used = false;
-  if (want_precond && !st->no_precond && (want_precond == 2 || !trusted) && w.qr &&
+  if (want_precond && !st->no_precond && (want_precond == 2 || (!trusted && want_precond != 3)) && w.qr &&
       p <= kQrMaxP && w.m >= (long long)kQrRowsPerP * p) {
     if (sampled_qr(w, G, qw, qpart, scratch)) {
       cond = invert_and_estimate();

@@ -461,7 +461,6 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
                        "unfiltered seeds"}
     with tols.Context(precision=prec, device=dev.index, cuda_stream=stream.cuda_stream) as ctx:
         tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)       # warm-up
-        tols.toeplitz_ols_profile(ctx, True)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -470,8 +469,12 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
         torch.cuda.synchronize()
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
+        # one more solve, untimed, with the library's per-launch events (passes launched one by one, not from
+        # the graphs): launches per batch and the device time per kernel class
+        tols.toeplitz_ols_profile(ctx, True)
+        tols.toeplitz_ols_solve_batched_device(ctx, d_ys, ps, d_phi, BATCH_TOL)
         launches, _ = tols.toeplitz_ols_profile_read(ctx, -1)
-        f32 = tols.toeplitz_ols_profile_read(ctx, 2)
+        prof = {k: v for k, v in profile_dict(tols, ctx).items() if v[0]}
         tols.toeplitz_ols_profile(ctx, False)
         t1 = time.perf_counter()
         tols.toeplitz_ols_solve_batched(ctx, ys, ps, BATCH_TOL)                      # end to end from host memory
@@ -500,8 +503,8 @@ def run_batched(tols, torch, dev, stream, batch_in, args, barrier, max_over_rank
                 "plan": batch_plan_mix(tols, ps, infos),
                 "mean_iters": float(np.mean([i["iters"] for i in infos])),
                 "max_iters": int(max(i["iters"] for i in infos)),
-                "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches),
-                "f32_necorr_pass_launches": f32[0], "f32_necorr_pass_ms": f32[1],
+                "e2e_solves_per_s": len(ys) / e2e_dt, "gpu_launches": int(launches) * steps,
+                "kernel_ms_per_batch": {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items()},
                 "cpu_baseline": {"value": len(sample) / t_or, "unit": "solves/s", "cores": cpu_cores(),
                                  "kind": "oracle", "sample": f"{len(sample)} evenly spaced series of the batch"}})
     del d_ys, d_phi

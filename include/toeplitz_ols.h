@@ -363,9 +363,12 @@ int toeplitz_ols_srht(tols_ctx* ctx, const double* d_y, long long n, int p, int 
  *   0..4  float32 pass kernel with tail STORE, LSQR, NECORR, CHECK, GRAM
  *   5..9  float64 pass kernel with tail STORE, LSQR, NECORR, CHECK, GRAM
  *   10    preconditioner (Cholesky + inverse), 11 float32 conversion, 12 other small kernels
+ *   13..16 batched solves: float64 FFT pass, float64 direct pass, float32 direct pass, d spectra (every launch,
+ *         whether or not it found work; while profiling, batches launch their passes one by one instead of
+ *         replaying CUDA graphs)
  *   -1    every kernel launch the context made since profiling was enabled (launches only; ms = 0),
  *         counted whether or not timing is on, including launches that found no work. */
-#define TOLS_PROFILE_CLASSES 13
+#define TOLS_PROFILE_CLASSES 17
 int toeplitz_ols_profile(tols_ctx* ctx, int enable);
 int toeplitz_ols_profile_read(tols_ctx* ctx, int kind, long long* launches, double* total_ms);
 

@@ -39,10 +39,11 @@ TOLS_PRODUCT_AUTO = 0
 TOLS_PRODUCT_DIRECT = 1
 TOLS_PRODUCT_FFT = 2
 TOLS_PRODUCT_FFT4096 = 3
-TOLS_PROFILE_CLASSES = 13
+TOLS_PROFILE_CLASSES = 17
 PROFILE_CLASS_NAMES = ["pass_f32_store", "pass_f32_lsqr", "pass_f32_necorr", "pass_f32_check", "pass_f32_gram",
                        "pass_f64_store", "pass_f64_lsqr", "pass_f64_necorr", "pass_f64_check", "pass_f64_gram",
-                       "precond", "convert_f32", "small"]
+                       "precond", "convert_f32", "small",
+                       "batch_f64_fft", "batch_f64_direct", "batch_f32_direct", "batch_dspec"]
 
 
 class tols_config(ctypes.Structure):

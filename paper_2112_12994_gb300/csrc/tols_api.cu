@@ -1143,9 +1143,8 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   // series of a mixed batch run a float correction sweep, the float pass joins them
   const int per_pass = (B.tiles_x ? 2 : 0) + (B.tiles_d ? 1 : 0);
   // the Gram pass (float64 products for every series); the FFT series' one also forms their window spectra
-  ctx->launch_total += (B.tiles_x ? 1 : 0) + (B.tiles_d ? 1 : 0);
-  if (B.tiles_x) CK(launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream));
-  if (B.tiles_d) CK(launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream));
+  if (B.tiles_x) RUN(run_small(ctx, 13, [&] { return launch_batch_fft(ag, gx, B.p_pad_max_x, ctx->stream); }));
+  if (B.tiles_d) RUN(run_small(ctx, 14, [&] { return launch_batch_pass<double>(ag, gd, B.p_pad_max, ctx->stream); }));
   const int want = no_precond ? 0 : ctx->cfg.precond;
   RUN(run_small(ctx, 10, [&] { return launch_precond_batch(d_series, cnt, want, ctx->stream, B.p_pad_max); }));
   RUN(run_small(ctx, 12, [&] { return launch_init_lsqr_batch(d_series, cnt, d_done, ctx->stream); }));
@@ -1153,14 +1152,16 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
   // iterations: a burst of batched passes captured once into a CUDA graph, replayed until all series are done
   const int burst = 4;
   auto enqueue_burst = [&](bool with_float) -> int {
+    // run_small counts each launch, and times it when profiling (which replaces the graphs by direct launches)
     for (int k = 0; k < burst; ++k) {
-      ctx->launch_total += per_pass + (with_float ? 1 : 0);
-      if (with_float) CK(launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream));
+      if (with_float)
+        RUN(run_small(ctx, 15, [&] { return launch_batch_pass<float>(a, gf, B.p_pad_max, ctx->stream); }));
       if (B.tiles_x) {
-        CK(launch_batch_dspec(d_series, cnt, ctx->stream));
-        CK(launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream));
+        RUN(run_small(ctx, 16, [&] { return launch_batch_dspec(d_series, cnt, ctx->stream); }));
+        RUN(run_small(ctx, 13, [&] { return launch_batch_fft(a, gx, B.p_pad_max_x, ctx->stream); }));
       }
-      if (B.tiles_d) CK(launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream));
+      if (B.tiles_d)
+        RUN(run_small(ctx, 14, [&] { return launch_batch_pass<double>(a, gd, B.p_pad_max, ctx->stream); }));
     }
     return TOLS_OK;
   };

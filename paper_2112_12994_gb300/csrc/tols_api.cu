@@ -1233,13 +1233,15 @@ int batch_core(tols_ctx* ctx, BatchPlan& B, double tol, bool mixed, std::vector<
     cudaError_t e = cudaMemcpyAsync(h_done, d_done, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) { out = fail(ctx, TOLS_ERR_CUDA, "batched poll", e); break; }
+    // read the landing slots before flush_profile, which reuses the same pinned buffer for the work log
+    const unsigned done_now = h_done[0], float_now = h_done[1];
     if ((out = flush_profile(ctx))) break;
-    if (h_done[0] >= (unsigned)cnt) break;
+    if (done_now >= (unsigned)cnt) break;
     if (round > max_rounds) { out = fail(ctx, TOLS_ERR_DEVICE_TIMEOUT, "batched solve did not finish"); break; }
-    with_float = mixed && h_done[1] > 0;
+    with_float = mixed && float_now > 0;
     // once half of the series still listed are done, the lists keep only the unfinished ones: a pass launch over
     // the full lists would spend its time skipping finished series' tiles
-    const long long active = (long long)cnt - h_done[0];
+    const long long active = (long long)cnt - done_now;
     if (active * 2 <= listed && (out = compact_lists()) != TOLS_OK) break;
   }
   for (auto x : exec)

@@ -148,3 +148,27 @@ def test_batch_products_by_order(tols, prec, product):
         if sol.forward_error_bound() <= tol / 10:
             assert coef_rel_err(phis[k], sol.phi) <= tol, (p, info)
         assert rn[k] == pytest.approx(sol.rnorm, rel=1e-11)
+
+
+def test_profiled_batch_matches_graph_replays(tols, prec):
+    """With the library's per-launch events on, a batch launches its passes one by one instead of replaying its
+    CUDA graphs: the results are bitwise those of the graph replays, and the batched kernel classes record the
+    launches (float64 FFT and direct passes for a batch with orders on both sides of the FFT threshold)."""
+    ys, ps = _batch(10, 44, 5_000, 60_000, 2, 120)
+    P = tols.TOLS_FP64 if prec == "fp64" else tols.TOLS_MIXED
+    with tols.Context(precision=P) as c:
+        phis, rn, infos, rc = tols.toeplitz_ols_solve_batched(c, ys, ps, 1e-12)
+        tols.toeplitz_ols_profile(c, True)
+        phis2, rn2, infos2, rc2 = tols.toeplitz_ols_solve_batched(c, ys, ps, 1e-12)
+        names = tols.PROFILE_CLASS_NAMES
+        counts = {names[k]: tols.toeplitz_ols_profile_read(c, k) for k in range(tols.TOLS_PROFILE_CLASSES)}
+        tols.toeplitz_ols_profile(c, False)
+    assert rc == rc2
+    for a, b in zip(phis, phis2):
+        assert np.array_equal(a, b)
+    used = {i["product_used"] for i in infos}
+    if tols.TOLS_PRODUCT_FFT in used:
+        assert counts["batch_f64_fft"][0] > 0 and counts["batch_f64_fft"][1] > 0
+    if tols.TOLS_PRODUCT_DIRECT in used:
+        assert counts["batch_f64_direct"][0] > 0
+    assert counts["precond"][0] > 0

@@ -100,3 +100,39 @@ def test_binding_checks_sketch_buffers(lib):
     with pytest.raises(t.TolsError, match="d_rh_unif"):
         t.toeplitz_ols_rh_lsar(None, y, 3000, 4, 100, 4, keep, torch.zeros(4 * (100 + 749), dtype=torch.float64),
                                torch.zeros(100, dtype=torch.float64), torch.zeros(400, dtype=torch.float64))
+
+
+def _header_structs():
+    """Field names and C types of the header's `typedef struct { ... } name;` blocks, comments stripped."""
+    import re
+    text = open(os.path.join(ROOT, "include", "toeplitz_ols.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"^(long long|\w+)\s*(\*?)\s*(.+)$", decl)     # one type, one or more names
+            for nm in m.group(3).split(","):
+                fields.append((nm.strip(), (m.group(1) + m.group(2)).replace(" ", "")))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_mirror_the_header():
+    """Every struct the C ABI passes by pointer has its ctypes mirror in the binding with the same fields in the
+    same order and of the same size, so the two sides agree on the layout."""
+    import ctypes
+    import paper_2112_12994_gb300 as t
+    sizes = {"int": 4, "double": 8, "longlong": 8, "size_t": 8, "void*": 8}
+    for name, fields in _header_structs().items():
+        mirror = getattr(t, name)
+        assert [f for f, _ in mirror._fields_] == [f for f, _ in fields], name
+        for (f, ctype), (_, py) in zip(fields, mirror._fields_):
+            want = sizes.get(ctype, None)
+            got = ctypes.sizeof(py)
+            if want is None:            # a nested struct: compare with its own mirror
+                want = ctypes.sizeof(getattr(t, ctype))
+            assert got == want, (name, f, ctype, got)

@@ -140,9 +140,12 @@ int toeplitz_ols_solve_device(tols_ctx* ctx, const double* d_y, long long n, int
 
 /* Solve count independent problems (host series y[k][0..n[k]-1], orders p[k]) in one batched launch
  * sequence (each problem is eq. (xphi) for its own series, Section 3). Every pass kernel covers all
- * series at once; series with pad16(p[k] + 1) >= 32 take the overlap-save float64 FFT products, the others the
- * direct products, unless the context's product setting says otherwise (TOLS_PRODUCT_DIRECT forces the direct
- * products); the float correction sweeps of a mixed batch use the direct float products. A series' result does not depend on the rest of the batch.
+ * series at once. Products per series: under TOLS_PRODUCT_AUTO the overlap-save float64 FFT (N = 2,048) or the
+ * direct products, chosen per order class pad16(p[k] + 1) by a timing made once per process and device and shared
+ * by every context of the process; TOLS_PRODUCT_FFT (or FFT4096) takes the FFT from pad16(p[k] + 1) = 32 up,
+ * TOLS_PRODUCT_DIRECT the direct products. The float correction sweeps of a mixed batch use the direct float
+ * products. A series' result does not depend on the rest of the batch, nor on the context that solved it.
+ * info[k].product_used and nfft report the products a series took.
  * phi[k] (host, p[k] doubles), rnorm (host, count, nullable), info (host, count, nullable).
  * Returns the worst status over the batch; info[k].status holds each series' own code. */
 int toeplitz_ols_solve_batched(tols_ctx* ctx, int count, const double* const* y, const long long* n,
